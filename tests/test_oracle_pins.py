@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: a direct DFT, properties
+of the log-Gabor transfer function, a closed form for gratings, the 90-degree rotation
+invariant of the MIM, the paper's worked histogram example, hand-built FAST patterns and
+brute-force search.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------------- FFT
+def direct_dft2(x):
+    h, w = x.shape
+    out = np.zeros((h, w), dtype=np.complex128)
+    for v in range(h):
+        for u in range(w):
+            acc = 0j
+            for y in range(h):
+                for xx in range(w):
+                    acc += x[y, xx] * np.exp(-2j * math.pi * (u * xx / w + v * y / h))
+            out[v, u] = acc
+    return out
+
+
+@pytest.mark.parametrize("n", [16, 15])
+def test_fft_matches_direct_dft(n):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((n, n))
+    ref = direct_dft2(x)
+    got = np.fft.fft2(x)
+    assert np.max(np.abs(got - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_responses_use_fft_convolution_definition():
+    # EO = ifft2(fft2(I) G) is the circular convolution of I with the filter's kernel;
+    # check one response against a direct circular convolution on a 12x10 image.
+    rng = np.random.default_rng(2)
+    img = rng.random((12, 10))
+    eo = O.responses(img)
+    g = O.log_gabor_bank(12, 10)[1, 2]
+    kern = np.fft.ifft2(g)                       # spatial kernel of the filter
+    conv = np.zeros((12, 10), dtype=np.complex128)
+    for y in range(12):
+        for x in range(10):
+            for yy in range(12):
+                for xx in range(10):
+                    conv[y, x] += img[yy, xx] * kern[(y - yy) % 12, (x - xx) % 10]
+    assert np.max(np.abs(eo[1, 2] - conv)) < 1e-12
+
+
+# --------------------------------------------------------------------- filters
+def test_frequency_grid_convention():
+    r, th = O.frequency_grid(8, 10)
+    assert r[0, 0] == 1.0
+    assert math.isclose(r[0, 1], 0.1) and math.isclose(r[1, 0], 0.125)
+    assert math.isclose(r[0, 5], 0.5)            # Nyquist column of an even width
+    assert th[0, 1] == 0.0                       # +u axis is theta = 0
+    assert math.isclose(th[7, 0], math.pi / 2)   # negative row frequency is theta = +90 deg
+    assert math.isclose(th[1, 0], -math.pi / 2)
+
+
+def test_radial_peak_bandwidth_and_lowpass():
+    p = O.DEFAULT
+    for s in range(p.n_scales):
+        f = O.center_frequency(s, p)
+        assert math.isclose(f, 1.0 / (3.0 * 1.6 ** s))
+        lp = O.lowpass(np.array(f), p)
+        # unit peak (before the low-pass) exactly at the centre frequency
+        assert math.isclose(float(O.radial(np.array(f), s, p)), float(lp), rel_tol=1e-14)
+        # the Gaussian on a log axis falls to exp(-1/2) one log-sigma away on both sides
+        for fac in (p.sigma_onf, 1.0 / p.sigma_onf):
+            rr = np.array(f * fac)
+            val = float(O.radial(rr, s, p)) / float(O.lowpass(rr, p))
+            assert math.isclose(val, math.exp(-0.5), rel_tol=1e-12)
+        # and is symmetric on the log axis
+        a = float(O.radial(np.array(f * 1.3), s, p) / O.lowpass(np.array(f * 1.3), p))
+        b = float(O.radial(np.array(f / 1.3), s, p) / O.lowpass(np.array(f / 1.3), p))
+        assert math.isclose(a, b, rel_tol=1e-12)
+    # Butterworth: 1/2 at the cutoff, 1/3 where (r/c)^(2n) = 2
+    assert math.isclose(float(O.lowpass(np.array(0.45))), 0.5)
+    assert math.isclose(float(O.lowpass(np.array(0.45 * 2 ** (1 / 30)))), 1 / 3, rel_tol=1e-12)
+    # DC is removed
+    r, _ = O.frequency_grid(6, 6)
+    assert O.radial(r, 0)[0, 0] == 0.0
+
+
+def test_angular_window_values_partition_and_one_sidedness():
+    no = 6
+    d = math.pi / no
+    for o in range(no):
+        t0 = o * d
+        vals = O.angular(np.array([t0, t0 + d / 2, t0 - d, t0 + d, t0 + 2 * d, t0 - 2 * d,
+                                   t0 + math.pi, t0 + 2.5 * d]), o)
+        np.testing.assert_allclose(vals, [1.0, (1 + math.cos(math.pi / 4)) / 2, 0.5, 0.5,
+                                          0.0, 0.0, 0.0, 0.0], atol=1e-15)
+    th = np.linspace(-math.pi, math.pi, 2001)
+    total = sum(O.angular(th, o) for o in range(no))
+    inner = (th >= math.pi / 6) & (th <= 2 * math.pi / 3)
+    np.testing.assert_allclose(total[inner], 2.0, atol=1e-12)
+    for o in range(no):
+        prod = O.angular(th, o) * O.angular(th + math.pi, o)
+        assert np.max(prod) == 0.0
+
+
+# -------------------------------------------------------- grating closed form
+@pytest.mark.parametrize("k1,k2", [(5, 0), (3, 4), (-6, 7), (0, 9), (11, -2)])
+def test_grating_amplitude_and_mim_closed_form(k1, k2):
+    h, w = 64, 48
+    y, x = np.mgrid[0:h, 0:w]
+    img = np.cos(2 * math.pi * (k1 * x / w + k2 * y / h))
+    eo = O.responses(img)
+    u, v = k1 / w, k2 / h
+    r = math.hypot(u, v)
+    th_pos = math.atan2(-v, u)
+    th_neg = math.atan2(v, -u)
+    expect = np.zeros((4, 6))
+    for s in range(4):
+        for o in range(6):
+            gp = float(O.radial(np.array(r), s)) * float(O.angular(np.array(th_pos), o))
+            gn = float(O.radial(np.array(r), s)) * float(O.angular(np.array(th_neg), o))
+            assert gp * gn == 0.0  # one-sided: at most one of the two deltas passes
+            expect[s, o] = (gp + gn) / 2.0
+    np.testing.assert_allclose(np.abs(eo), np.broadcast_to(expect[:, :, None, None], eo.shape),
+                               atol=1e-12)
+    a = O.amplitude_sums(eo)
+    mim, _ = O.max_index_map(a)
+    tot = expect.sum(axis=0)
+    best = np.flatnonzero(tot >= tot.max() * (1 - 1e-9))   # exact ties: any of the tied set
+    assert np.all(np.isin(mim, best))
+    if len(best) == 1:
+        assert np.all(mim == best[0])
+
+
+def test_grating_phase_congruency_closed_form():
+    # A pure grating gives every scale the same phase: E_s = a_s cos(phi), O_s = a_s sin(phi),
+    # so Er = A^2/(A+eps), the median of |EO_0| is a_0 itself, width = (A/a_max - 1)/3.
+    h, w = 40, 40
+    y, x = np.mgrid[0:h, 0:w]
+    img = np.cos(2 * math.pi * (4 * x / w + 3 * y / h))
+    p = O.DEFAULT
+    eo = O.responses(img, p)
+    pc, t = O.phase_congruency(eo, p)
+    amp = np.abs(eo)[:, :, 0, 0]                 # a_s per (s, o), constant over pixels
+    for o in range(6):
+        a_s = amp[:, o]
+        big_a = a_s.sum()
+        tau = a_s[0] / math.sqrt(math.log(4))
+        tot = tau * (1 - 1.6 ** -4) / (1 - 1 / 1.6)
+        t_exp = tot * (math.sqrt(math.pi / 2) + math.sqrt((4 - math.pi) / 2))
+        assert math.isclose(t[o], t_exp, rel_tol=1e-9, abs_tol=1e-15)
+        if big_a < 1e-9:
+            assert np.all(pc[o] == 0)
+            continue
+        width = (big_a / (a_s.max() + p.eps) - 1) / 3
+        wgt = 1 / (1 + math.exp((0.5 - width) * 3))
+        energy = big_a * big_a / (big_a + p.eps)
+        expect = wgt * max(energy - t_exp, 0.0) / big_a
+        np.testing.assert_allclose(pc[o], expect, rtol=1e-7, atol=1e-12)
+
+
+# -------------------------------------------------- rotation invariant (§III, Fig. 3)
+def test_mim_shifts_by_half_the_orientations_under_rot90():
+    # Odd size: the DFT grid is symmetric under a quarter turn, so the invariant is exact.
+    rng = np.random.default_rng(3)
+    from synth import scene
+    img = scene(63, 63, np.random.Generator(np.random.PCG64(7)), n_blobs=12, n_segments=6)
+    img = img + 0.02 * rng.standard_normal(img.shape)
+    a = O.amplitude_sums(O.responses(img))
+    ar = O.amplitude_sums(O.responses(np.rot90(img)))
+    mim, margin = O.max_index_map(a)
+    mim_r, _ = O.max_index_map(ar)
+    ok = np.rot90(margin) >= 1e-5
+    assert ok.mean() > 0.99
+    expect = (np.rot90(mim).astype(int) + 3) % 6
+    assert np.array_equal(mim_r[ok], expect[ok])
+    # amplitudes themselves rotate with the orientation shift
+    for o in range(6):
+        np.testing.assert_allclose(ar[(o + 3) % 6], np.rot90(a[o]), atol=1e-10)
+
+
+def test_recoded_histogram_invariant_under_rot90():
+    from synth import scene
+    img = scene(105, 105, np.random.Generator(np.random.PCG64(11)), n_blobs=25, n_segments=12)
+    mim, _ = O.max_index_map(O.amplitude_sums(O.responses(img)))
+    mim_r, margin_r = O.max_index_map(O.amplitude_sums(O.responses(np.rot90(img))))
+    # patch around the centre; in the rotated frame take the rotated window explicitly
+    c = 52
+    # the same pixels seen from both frames: rotate the whole map, then cut the window
+    win = np.rot90(mim)[c - 20:c + 20, c - 20:c + 20]
+    win_r = mim_r[c - 20:c + 20, c - 20:c + 20]
+    hist = np.bincount(win.ravel(), minlength=6)
+    hist_r = np.bincount(win_r.ravel(), minlength=6)
+    s, _, _ = O.dominant_indices(hist)
+    s_r, _, _ = O.dominant_indices(hist_r)
+    assert (s_r - s) % 6 == 3
+    # recoded patches agree pixel by pixel after the spatial quarter turn (Fig. 3(h))
+    rec = O.recode(win, s)
+    rec_r = O.recode(win_r, s_r)
+    ok = margin_r[c - 20:c + 20, c - 20:c + 20] >= 1e-5
+    assert np.array_equal(rec[ok], rec_r[ok])
+    hn = np.bincount(rec.ravel(), minlength=6)
+    hn_r = np.bincount(rec_r.ravel(), minlength=6)
+    assert np.array_equal(hn, hn_r)
+
+
+# ------------------------------------------------- dominant index (§III, Eq. 1-2)
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out[key] = [int(v) for v in vals]
+    return out
+
+
+def test_worked_example_histogram_shift_and_recode():
+    g = _golden("worked_example_histogram.txt")
+    h1 = np.array(g["hist_mim1"])
+    # moving the initial layer by one shifts every bin down by one (MIM 2 -> 1)
+    mim1 = np.repeat(np.arange(6), h1)
+    mim2 = O.recode(mim1, 1)
+    assert np.array_equal(np.bincount(mim2, minlength=6), g["hist_mim2"])
+    s, s2, has2 = O.dominant_indices(h1)
+    assert s + 1 == g["dominant_1based"][0]
+    assert has2 == bool(g["has_secondary"][0])
+    rec = np.bincount(O.recode(mim1, s), minlength=6)
+    assert np.array_equal(rec, g["recoded"])
+    # the recoded histogram does not depend on the initial layer
+    for shift in range(6):
+        m = O.recode(mim1, shift)
+        sm, _, _ = O.dominant_indices(np.bincount(m, minlength=6))
+        assert np.array_equal(np.bincount(O.recode(m, sm), minlength=6), g["recoded"])
+
+
+def test_recode_is_eq2_one_based():
+    # Eq. 2 in the paper's 1-based indices, evaluated literally for every (MIM, s)
+    for s1 in range(1, 7):
+        for m1 in range(1, 7):
+            lit = m1 - s1 + 1 if m1 >= s1 else m1 + 6 - s1 + 1
+            assert int(O.recode(m1 - 1, s1 - 1)) + 1 == lit
+
+
+def test_secondary_ratio_boundary():
+    assert O.dominant_indices([100, 80, 0, 0, 0, 0])[2]           # exactly 80 %
+    assert not O.dominant_indices([100, 79, 0, 0, 0, 0])[2]
+    assert O.dominant_indices([5, 4, 0, 0, 0, 0])[2]
+    s, s2, has2 = O.dominant_indices([7, 9, 9, 1, 0, 0])          # tie: lowest index wins
+    assert (s, s2, has2) == (1, 2, True)
+
+
+def test_descriptor_counts_and_permutation():
+    rng = np.random.default_rng(5)
+    mim = rng.integers(0, 6, size=(200, 200)).astype(np.uint8)
+    xy = np.array([[60, 70], [100, 120], [48, 48], [151, 151]])
+    desc, dkp, ddom, info = O.describe(mim, xy)
+    for i in range(len(desc)):
+        x, y = xy[dkp[i]]
+        patch = mim[y - 48:y + 48, x - 48:x + 48].astype(int)
+        rec = O.recode(patch, ddom[i])
+        for ci in range(6):
+            for cj in range(6):
+                cell = rec[ci * 16:(ci + 1) * 16, cj * 16:(cj + 1) * 16]
+                np.testing.assert_array_equal(desc[i, (ci * 6 + cj) * 6:(ci * 6 + cj + 1) * 6],
+                                              np.bincount(cell.ravel(), minlength=6))
+        assert desc[i].sum() == 96 * 96
+        assert desc[i].reshape(36, 6).sum(axis=1).tolist() == [256] * 36
+
+
+# ------------------------------------------------------------------------- FAST
+def brute_fast(mn, t, arc=9):
+    h, w = mn.shape
+    corner = np.zeros((h, w), bool)
+    score = np.zeros((h, w))
+    for y in range(3, h - 3):
+        for x in range(3, w - 3):
+            p = mn[y, x]
+            vals = [mn[y + dy, x + dx] for dx, dy in O.CIRCLE]
+            for sign in (1, -1):
+                ok = [sign * (q - p) > t for q in vals]
+                if any(all(ok[(st + j) % 16] for j in range(arc)) for st in range(16)):
+                    corner[y, x] = True
+            if corner[y, x]:
+                vb = sum(q - p - t for q in vals if q > p + t)
+                vd = sum(p - q - t for q in vals if q < p - t)
+                score[y, x] = max(vb, vd)
+    return corner, score
+
+
+def test_fast_hand_built_patterns():
+    p = O.Params(patch=6, cells=6)        # 3-pixel border: the whole interior is a candidate
+    img = np.zeros((15, 15))
+    img[7, 7] = 1.0                        # isolated bright pixel: all 16 circle pixels darker
+    c, v, _ = O.fast_corners(img, p)
+    assert c[7, 7] and math.isclose(v[7, 7], 16 * (1.0 - 0.001))
+    img = np.zeros((15, 15))
+    img[:, 7] = 1.0                        # thin line: at most 2 contiguous darker pixels
+    c, _, _ = O.fast_corners(img, p)
+    assert not c[7, 7]
+    img = np.zeros((15, 15))
+    img[7:, 7:] = 1.0                      # block corner: dark pixel just outside it is a corner
+    c, _, _ = O.fast_corners(img, p)
+    assert c[7, 7] or c[6, 6]
+
+
+def test_fast_matches_brute_force():
+    rng = np.random.default_rng(9)
+    mn = rng.random((20, 22)) * 0.02
+    p = O.Params(patch=6, cells=6, fast_threshold=0.002)
+    c, v, _ = O.fast_corners(mn, p)
+    cb, vb = brute_fast(mn, 0.002)
+    assert np.array_equal(c, cb)
+    np.testing.assert_allclose(v, vb, atol=1e-15)
+
+
+def test_nms_and_topk_brute_force():
+    rng = np.random.default_rng(10)
+    corner = rng.random((12, 13)) < 0.5
+    score = np.round(rng.random((12, 13)) * 4) / 4 * corner      # many exact ties
+    keep, _ = O.nms3x3(corner, score)
+    h, w = corner.shape
+    for y in range(h):
+        for x in range(w):
+            exp = corner[y, x]
+            for dy, dx in itertools.product((-1, 0, 1), repeat=2):
+                yy, xx = y + dy, x + dx
+                if (dy or dx) and 0 <= yy < h and 0 <= xx < w and corner[yy, xx]:
+                    if not ((score[y, x], -(y * w + x)) > (score[yy, xx], -(yy * w + xx))):
+                        exp = False
+            assert keep[y, x] == exp
+    xy, v, _ = O.top_k(keep, score, 5)
+    allk = sorted([(-score[y, x], y * w + x) for y, x in zip(*np.nonzero(keep))])[:5]
+    assert [(-vv, yy * w + xx) for (xx, yy), vv in zip(xy, v)] == allk
+
+
+# -------------------------------------------------------------------------- NN
+def test_match_brute_force():
+    rng = np.random.default_rng(12)
+    a = rng.integers(0, 20, size=(30, 216))
+    b = rng.integers(0, 20, size=(40, 216))
+    b[7] = a[3]                     # an exact match
+    b[9] = b[7]                     # and its duplicate: lowest index must win
+    nn, d1, d2, near = O.match(a, b)
+    for i in range(30):
+        ds = []
+        for j in range(40):
+            ai, bj = a[i].astype(float), b[j].astype(float)
+            ds.append(np.sum((ai / np.linalg.norm(ai) - bj / np.linalg.norm(bj)) ** 2))
+        j = int(np.argmin(ds))
+        srt = sorted(ds)
+        if srt[1] - srt[0] > 1e-9:
+            assert nn[i] == j
+        assert math.isclose(d1[i], srt[0], abs_tol=1e-12)
+        assert math.isclose(d2[i], srt[1], abs_tol=1e-12)
+    assert nn[3] == 7 and near[3]
+
+
+def test_median_even_count():
+    assert O.median_even_mean([4.0, 1.0, 3.0, 2.0]) == 2.5
+    x = np.random.default_rng(4).random(1001)
+    assert O.median_even_mean(x) == sorted(x)[500]
+
+
+def test_moments_of_single_orientation():
+    # PC only in orientation o: M = PC^2 (edge), m ~ 0 (no corner)
+    pc = np.zeros((6, 1, 1))
+    for o in range(6):
+        pc[:] = 0
+        pc[o] = 0.7
+        mx, mn = O.moments(pc)
+        # (Sxx + Syy) = PC^2 / 3, den = PC^2/3 + eps  ->  M = PC^2/3 + eps/2, m = -eps/2
+        assert math.isclose(mx.item(), 0.49 / 3 + 0.5e-4, rel_tol=1e-12)
+        assert math.isclose(mn.item(), -0.5e-4, rel_tol=1e-9)
+    # isotropic PC: equal in all orientations gives den = eps (Sxy = 0, Sxx = Syy)
+    pc[:] = 0.5
+    mx, mn = O.moments(pc)
+    assert math.isclose(mx.item(), mn.item() + 1e-4, rel_tol=1e-9)
