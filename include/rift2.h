@@ -1,0 +1,244 @@
+/*
+ * rift2.h — C ABI of the GB300 (sm_103a) RIFT2 feature pipeline.
+ *
+ * RIFT2 (Li, Shi, Hu, Zhang, "RIFT2: Speeding-up RIFT with A New Rotation-Invariance
+ * Technique") matches multimodal images in three stages (§II, Fig. 1): keypoint
+ * detection on the phase-congruency maximum-moment map (§II-A), description by
+ * 6x6-cell histograms of the maximum index map (MIM, §II-B) normalised by the dominant
+ * index (§III, Eq. 1 and Eq. 2), and brute-force nearest-feature matching (§IV).
+ * This library runs those stages as hand-written CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - All data pointers are DEVICE pointers on the context's device unless stated.
+ *    The caller owns every image, feature and match buffer; the context owns its plans,
+ *    twiddle tables and workspace.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Every call only enqueues work on that stream and returns; results are ready once
+ *    the stream has reached that point.  Calls on one context must not run concurrently
+ *    from several host threads, and work on one context is serialised on the streams it
+ *    is given (the workspace is shared).
+ *  - Return codes: RIFT2_OK (0) or a negative RIFT2_E_*.  Argument errors are detected
+ *    on the host before anything is enqueued.  Errors found on the device (a bounded
+ *    wait that ran out) are latched in a device status word that rift2_sync() returns.
+ *  - Indices are 0-based.  The paper's 1-based orientation / bin index is value + 1.
+ */
+#ifndef RIFT2_H_
+#define RIFT2_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIFT2_VERSION_MAJOR 0
+#define RIFT2_VERSION_MINOR 1
+
+/* The kernels are compiled for the paper's bank and descriptor geometry:
+ * Ns = 4 scales, No = 6 orientations (§II), patch 96 (Table 1), 6x6 cells (§II-B). */
+#define RIFT2_NS 4
+#define RIFT2_NO 6
+#define RIFT2_PATCH 96
+#define RIFT2_CELLS 6
+#define RIFT2_DESC_DIM (RIFT2_CELLS * RIFT2_CELLS * RIFT2_NO) /* 216 */
+#define RIFT2_MAX_BATCH 32      /* images (or pairs) per internal launch group */
+
+enum {
+  RIFT2_OK = 0,
+  RIFT2_E_INVAL = -1,     /* bad argument (NULL pointer, size, parameter out of range) */
+  RIFT2_E_NOMEM = -2,     /* workspace would exceed the HBM budget or cudaMalloc failed */
+  RIFT2_E_CAPACITY = -3,  /* a caller buffer is smaller than the worst case it may hold */
+  RIFT2_E_CUDA = -4,      /* a CUDA runtime call failed (launch, copy, sync) */
+  RIFT2_E_TIMEOUT = -5,   /* a bounded device wait gave up (reported by rift2_sync) */
+  RIFT2_E_UNIMPL = -6     /* valid request outside what the kernels are built for */
+};
+
+/* Flags (rift2_params.flags). */
+#define RIFT2_FLAG_PLAIN_MATCH 0x1   /* CUDA-core matcher instead of the tcgen05 one */
+#define RIFT2_FLAG_NO_GROUPING 0x2   /* one image / pair per launch (plain form) */
+
+/*
+ * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
+ * patch 96, FAST threshold 0.001, dominant ratio 0.8), §II-B (6x6 grid, No bins) and
+ * the log-Gabor bank of §II (Ns = 4, No = 6, minimum wavelength 3, multiplier 1.6);
+ * the paper is silent on the remaining values, which follow the Kovesi phase-congruency
+ * model RIFT builds on: sigma_onf 0.75, k 1, g 3, cutoff 0.5, eps 1e-4, low-pass cutoff
+ * 0.45 of order 15.  n_scales, n_orient, patch and cells must equal the RIFT2_* values
+ * above; anything else returns RIFT2_E_UNIMPL.
+ */
+typedef struct rift2_params {
+  int   n_scales;        /* Ns */
+  int   n_orient;        /* No */
+  float min_wavelength;  /* wavelength of the finest scale, px */
+  float mult;            /* wavelength ratio between scales */
+  float sigma_onf;       /* radial bandwidth: sigma of the log-Gaussian / centre freq */
+  float k;               /* noise threshold = mean + k sigma of the noise energy */
+  float g;               /* sharpness of the frequency-spread weight */
+  float cutoff;          /* frequency-spread cutoff of the weight */
+  float eps;             /* small constant guarding divisions */
+  float lp_cutoff;       /* low-pass cutoff, cycles/px */
+  int   lp_order;        /* low-pass order n: 1 / (1 + (r/c)^(2n)) */
+  float fast_threshold;  /* FAST threshold on the min-max normalised moment map */
+  int   fast_arc;        /* contiguous circle pixels required (9 of 16) */
+  int   max_keypoints;   /* strongest keypoints kept per image */
+  int   patch;           /* descriptor patch side, px */
+  int   cells;           /* cells per patch side */
+  float second_ratio;    /* second dominant bin kept if >= ratio * peak (integer test) */
+  int   flags;           /* RIFT2_FLAG_* */
+} rift2_params;
+
+typedef struct rift2_ctx rift2_ctx;
+
+/* One grey image: float32 in [0, 1], row-major, `pitch` elements between rows. */
+typedef struct rift2_image {
+  const float* data;
+  int height, width;
+  long long pitch;
+} rift2_image;
+
+/*
+ * Optional per-image intermediate maps (any member may be NULL; all float32 unless
+ * stated).  Used to check each stage against the oracle.
+ *   amp    [No][H][W]  A_o = sum_s |EO_s,o|                                (§II-B)
+ *   er     [No][H][W]  phase-congruency energy before the noise threshold
+ *   q      [No][H][W]  frequency-spread weight / A_o
+ *   an0    [No][H][W]  |EO_0,o|, the smallest-scale amplitude (noise estimate)
+ *   pc     [No][H][W]  PC_o                                                 (§II-A)
+ *   moment [H][W]      maximum moment M (edge map FAST runs on)             (§II-A)
+ *   mim    [H][W]      uint8 maximum index map, values 0..No-1              (§II-B)
+ *   noise_t [No]       noise thresholds T_o
+ */
+typedef struct rift2_debug_maps {
+  float* amp;
+  float* er;
+  float* q;
+  float* an0;
+  float* pc;
+  float* moment;
+  unsigned char* mim;
+  float* noise_t;
+} rift2_debug_maps;
+
+/*
+ * Features of one image (outputs of rift2_extract; inputs of rift2_match).
+ *   kp_xy     int32 [cap_kp][2]      keypoint (x, y), strongest first
+ *   kp_score  float [cap_kp]         FAST score
+ *   desc      uint16 [cap_desc][216] descriptor counts, cell-major (6x6 row-major), bin
+ *                                    minor, bins recoded by the dominant index (Eq. 2)
+ *   desc_norm float [cap_desc]       L2 norm of the count vector (descriptor = desc/norm)
+ *   desc_kp   int32 [cap_desc]       keypoint each descriptor belongs to
+ *   desc_dom  uint8 [cap_desc]       dominant index used to recode it (0..No-1)
+ *   counts    int32 [2]              written on the device: n_kp, n_desc
+ * cap_kp >= max_keypoints and cap_desc >= 2 * max_keypoints are required (each keypoint
+ * yields one or two descriptors, §III), otherwise RIFT2_E_CAPACITY.
+ */
+typedef struct rift2_features {
+  int cap_kp, cap_desc;
+  int* kp_xy;
+  float* kp_score;
+  unsigned short* desc;
+  float* desc_norm;
+  int* desc_kp;
+  unsigned char* desc_dom;
+  int* counts;
+  rift2_debug_maps* debug;   /* HOST pointer to a struct of device pointers, or NULL */
+} rift2_features;
+
+/*
+ * Putative correspondences of one pair (§IV: nearest feature distance, no ratio test,
+ * no RANSAC).  Row i is descriptor i of image A:
+ *   q_desc = i, nn_desc = nearest descriptor of B, kp_a / kp_b their keypoints,
+ *   d1 / d2 = smallest and second-smallest ||a/|a| - b/|b|||^2 (d2 = +inf if B has one
+ *   descriptor), near_tie = 1 if (d2 - d1) < 1e-5 * max(d1, 1e-12).
+ *   count = number of rows (= n_desc of A), written on the device.
+ * cap >= 2 * max_keypoints is required.
+ */
+typedef struct rift2_matches {
+  int cap;
+  int* q_desc;
+  int* nn_desc;
+  int* kp_a;
+  int* kp_b;
+  float* d1;
+  float* d2;
+  unsigned char* near_tie;
+  int* count;
+} rift2_matches;
+
+/* Fills *p with the defaults listed above. */
+void rift2_default_params(rift2_params* p);
+
+/* Human-readable name of a status code (static storage). */
+const char* rift2_status_str(int status);
+
+/*
+ * Creates a context on CUDA device `device`.  `params` may be NULL (defaults); it is
+ * copied.  `hbm_budget_bytes` caps the workspace the context may allocate (0 = 16 GiB);
+ * the workspace grows on demand up to it and is freed by rift2_destroy.
+ * Errors: RIFT2_E_INVAL (bad params / out == NULL), RIFT2_E_UNIMPL (geometry other
+ * than Ns=4, No=6, patch 96, 6x6 cells), RIFT2_E_CUDA (device cannot be used).
+ */
+int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes,
+                 rift2_ctx** out);
+
+/*
+ * Extracts keypoints and descriptors of `n_images` images (§II-A, §II-B, §III):
+ * log-Gabor bank in the frequency domain -> MIM and phase congruency -> maximum
+ * moment -> FAST + NMS + top-K -> dominant-index-recoded 6x6xNo descriptors.
+ * imgs[i] (host array of n_images structs; data on the device) -> out[i] (host array).
+ * Each side must be >= 16 with prime factors in {2, 3, 5, 7}; images smaller than
+ * patch + 6 on a side produce zero keypoints.  Images of equal size are grouped into
+ * shared launches unless RIFT2_FLAG_NO_GROUPING is set.
+ * Errors: RIFT2_E_INVAL, RIFT2_E_UNIMPL (size), RIFT2_E_CAPACITY, RIFT2_E_NOMEM,
+ * RIFT2_E_CUDA.
+ */
+int rift2_extract(rift2_ctx* ctx, int n_images, const rift2_image* imgs,
+                  rift2_features* out, void* stream);
+
+/*
+ * Brute-force nearest-neighbour matching of `n_pairs` feature pairs, A -> B (§IV).
+ * a[i], b[i], out[i] are host arrays of structs whose buffers are on the device; the
+ * descriptor counts are read on the device (counts[1]).  Lowest B index wins exact ties.
+ * Errors: RIFT2_E_INVAL, RIFT2_E_CAPACITY, RIFT2_E_NOMEM, RIFT2_E_CUDA.
+ */
+int rift2_match(rift2_ctx* ctx, int n_pairs, const rift2_features* a,
+                const rift2_features* b, rift2_matches* out, void* stream);
+
+/* Waits for `stream`, then returns and clears the device status word (RIFT2_OK or
+ * RIFT2_E_TIMEOUT), or RIFT2_E_CUDA if the stream reported an error. */
+int rift2_sync(rift2_ctx* ctx, void* stream);
+
+/* Frees the context and its workspace (waits for the device first). */
+int rift2_destroy(rift2_ctx* ctx);
+
+/* ------------------------------------------------------------------------------
+ * Stage entry points.  Each runs one stage of the pipeline on caller-supplied inputs
+ * so that the stage can be checked against the oracle in isolation (an oracle near-tie
+ * upstream then cannot cascade).  Same conventions as above.
+ * ---------------------------------------------------------------------------- */
+
+/* Forward 2-D DFT (no scaling) of n real images img [n][H][W] -> out [n][H][W] complex
+ * (interleaved re, im float32): the first step of the frequency-domain log-Gabor
+ * filtering of §II-B. */
+int rift2_fft2(rift2_ctx* ctx, int n, const float* img, int height, int width,
+               float* out, void* stream);
+
+/* Keypoints from given maximum-moment maps moment [n][H][W] (§II-A, Table 1): min-max
+ * normalisation, FAST, 3x3 NMS, top max_keypoints.  Writes kp_xy, kp_score and
+ * counts[0] of out[i]; counts[1] is set to 0. */
+int rift2_detect(rift2_ctx* ctx, int n, const float* moment, int height, int width,
+                 rift2_features* out, void* stream);
+
+/* Descriptors (§II-B, §III, Eq. 1-2) of given keypoints on given MIMs mim [n][H][W]
+ * (uint8, 0..No-1).  feats[i].kp_xy and feats[i].counts[0] are inputs (every keypoint
+ * must satisfy 48 <= x < W-48, 48 <= y < H-48); desc, desc_norm, desc_kp, desc_dom and
+ * counts[1] are written. */
+int rift2_describe(rift2_ctx* ctx, int n, const unsigned char* mim, int height, int width,
+                   rift2_features* feats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIFT2_H_ */

@@ -1,0 +1,296 @@
+"""Python binding of the RIFT2 GB300 library (librift2.so, C ABI in include/rift2.h).
+
+Argument marshalling only: every step of the pipeline runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  If the library has not been built the import
+of `lib()` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librift2.so")
+
+OK, E_INVAL, E_NOMEM, E_CAPACITY, E_CUDA, E_TIMEOUT, E_UNIMPL = 0, -1, -2, -3, -4, -5, -6
+FLAG_PLAIN_MATCH = 0x1
+FLAG_NO_GROUPING = 0x2
+NS, NO, PATCH, CELLS = 4, 6, 96, 6
+DESC_DIM = CELLS * CELLS * NO
+
+# Every symbol include/rift2.h declares.
+EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_extract",
+           "rift2_match", "rift2_sync", "rift2_destroy", "rift2_fft2", "rift2_detect",
+           "rift2_describe")
+
+
+class Params(C.Structure):
+    _fields_ = [("n_scales", C.c_int), ("n_orient", C.c_int), ("min_wavelength", C.c_float),
+                ("mult", C.c_float), ("sigma_onf", C.c_float), ("k", C.c_float),
+                ("g", C.c_float), ("cutoff", C.c_float), ("eps", C.c_float),
+                ("lp_cutoff", C.c_float), ("lp_order", C.c_int), ("fast_threshold", C.c_float),
+                ("fast_arc", C.c_int), ("max_keypoints", C.c_int), ("patch", C.c_int),
+                ("cells", C.c_int), ("second_ratio", C.c_float), ("flags", C.c_int)]
+
+
+class Image(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("height", C.c_int), ("width", C.c_int),
+                ("pitch", C.c_longlong)]
+
+
+class DebugMaps(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("amp", "er", "q", "an0", "pc", "moment", "mim",
+                                          "noise_t")]
+
+
+class FeaturesC(C.Structure):
+    _fields_ = [("cap_kp", C.c_int), ("cap_desc", C.c_int), ("kp_xy", C.c_void_p),
+                ("kp_score", C.c_void_p), ("desc", C.c_void_p), ("desc_norm", C.c_void_p),
+                ("desc_kp", C.c_void_p), ("desc_dom", C.c_void_p), ("counts", C.c_void_p),
+                ("debug", C.POINTER(DebugMaps))]
+
+
+class MatchesC(C.Structure):
+    _fields_ = [("cap", C.c_int), ("q_desc", C.c_void_p), ("nn_desc", C.c_void_p),
+                ("kp_a", C.c_void_p), ("kp_b", C.c_void_p), ("d1", C.c_void_p),
+                ("d2", C.c_void_p), ("near_tie", C.c_void_p), ("count", C.c_void_p)]
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded library; raises if it is missing (build it with __graft_entry__.build())."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"RIFT2 CUDA library not built: {LIB_PATH} is missing")
+        L = C.CDLL(LIB_PATH)
+        L.rift2_status_str.restype = C.c_char_p
+        L.rift2_status_str.argtypes = [C.c_int]
+        L.rift2_default_params.argtypes = [C.POINTER(Params)]
+        L.rift2_create.argtypes = [C.POINTER(Params), C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]
+        L.rift2_extract.argtypes = [C.c_void_p, C.c_int, C.POINTER(Image), C.POINTER(FeaturesC),
+                                    C.c_void_p]
+        L.rift2_match.argtypes = [C.c_void_p, C.c_int, C.POINTER(FeaturesC),
+                                  C.POINTER(FeaturesC), C.POINTER(MatchesC), C.c_void_p]
+        L.rift2_sync.argtypes = [C.c_void_p, C.c_void_p]
+        L.rift2_destroy.argtypes = [C.c_void_p]
+        L.rift2_fft2.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                 C.c_void_p]
+        L.rift2_detect.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                   C.POINTER(FeaturesC), C.c_void_p]
+        L.rift2_describe.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                     C.POINTER(FeaturesC), C.c_void_p]
+        _LIB = L
+    return _LIB
+
+
+class Rift2Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {lib().rift2_status_str(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise Rift2Error(code, what)
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    lib().rift2_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Features:
+    """Device buffers of one image's features (see rift2_features in include/rift2.h)."""
+    kp_xy: torch.Tensor      # int32 [cap_kp][2]
+    kp_score: torch.Tensor   # float32 [cap_kp]
+    desc: torch.Tensor       # uint16 as int16 storage [cap_desc][216]
+    desc_norm: torch.Tensor  # float32 [cap_desc]
+    desc_kp: torch.Tensor    # int32 [cap_desc]
+    desc_dom: torch.Tensor   # uint8 [cap_desc]
+    counts: torch.Tensor     # int32 [2]: n_kp, n_desc
+    debug: dict | None = None
+
+    @staticmethod
+    def alloc(max_kp: int, device, debug_shape=None):
+        dev = torch.device(device)
+        f = Features(
+            kp_xy=torch.zeros((max_kp, 2), dtype=torch.int32, device=dev),
+            kp_score=torch.zeros(max_kp, dtype=torch.float32, device=dev),
+            desc=torch.zeros((2 * max_kp, DESC_DIM), dtype=torch.int16, device=dev),
+            desc_norm=torch.zeros(2 * max_kp, dtype=torch.float32, device=dev),
+            desc_kp=torch.zeros(2 * max_kp, dtype=torch.int32, device=dev),
+            desc_dom=torch.zeros(2 * max_kp, dtype=torch.uint8, device=dev),
+            counts=torch.zeros(2, dtype=torch.int32, device=dev))
+        if debug_shape is not None:
+            h, w = debug_shape
+            f.debug = {n: torch.zeros((NO, h, w), dtype=torch.float32, device=dev)
+                       for n in ("amp", "er", "q", "an0", "pc")}
+            f.debug["moment"] = torch.zeros((h, w), dtype=torch.float32, device=dev)
+            f.debug["mim"] = torch.zeros((h, w), dtype=torch.uint8, device=dev)
+            f.debug["noise_t"] = torch.zeros(NO, dtype=torch.float32, device=dev)
+        return f
+
+    def to_c(self):
+        c = FeaturesC(self.kp_xy.shape[0], self.desc.shape[0], _ptr(self.kp_xy).value,
+                      _ptr(self.kp_score).value, _ptr(self.desc).value,
+                      _ptr(self.desc_norm).value, _ptr(self.desc_kp).value,
+                      _ptr(self.desc_dom).value, _ptr(self.counts).value, None)
+        keep = None
+        if self.debug is not None:
+            keep = DebugMaps(*[self.debug[n].data_ptr() if n in self.debug else None
+                               for n, _ in DebugMaps._fields_])
+            c.debug = C.pointer(keep)
+        return c, keep
+
+    def host(self):
+        """Trimmed CPU copies (synchronising): dict of numpy arrays."""
+        n_kp, n_desc = [int(v) for v in self.counts.cpu()]
+        return dict(xy=self.kp_xy[:n_kp].cpu().numpy(), score=self.kp_score[:n_kp].cpu().numpy(),
+                    desc=self.desc[:n_desc].cpu().numpy().view("uint16"),
+                    desc_norm=self.desc_norm[:n_desc].cpu().numpy(),
+                    desc_kp=self.desc_kp[:n_desc].cpu().numpy(),
+                    desc_dom=self.desc_dom[:n_desc].cpu().numpy())
+
+
+@dataclass
+class Matches:
+    q_desc: torch.Tensor
+    nn_desc: torch.Tensor
+    kp_a: torch.Tensor
+    kp_b: torch.Tensor
+    d1: torch.Tensor
+    d2: torch.Tensor
+    near_tie: torch.Tensor
+    count: torch.Tensor
+
+    @staticmethod
+    def alloc(cap: int, device):
+        dev = torch.device(device)
+        z = lambda dt: torch.zeros(cap, dtype=dt, device=dev)  # noqa: E731
+        return Matches(z(torch.int32), z(torch.int32), z(torch.int32), z(torch.int32),
+                       z(torch.float32), z(torch.float32), z(torch.uint8),
+                       torch.zeros(1, dtype=torch.int32, device=dev))
+
+    def to_c(self):
+        return MatchesC(self.q_desc.shape[0], *[t.data_ptr() for t in (
+            self.q_desc, self.nn_desc, self.kp_a, self.kp_b, self.d1, self.d2, self.near_tie,
+            self.count)])
+
+    def host(self):
+        n = int(self.count.cpu()[0])
+        return {k: getattr(self, k)[:n].cpu().numpy() for k in
+                ("q_desc", "nn_desc", "kp_a", "kp_b", "d1", "d2", "near_tie")}
+
+
+class Context:
+    """One rift2_ctx on one CUDA device."""
+
+    def __init__(self, params: Params | None = None, device: int = 0, hbm_budget: int = 0):
+        self.params = params if params is not None else default_params()
+        self.device = device
+        h = C.c_void_p()
+        _check(lib().rift2_create(C.byref(self.params), device, hbm_budget, C.byref(h)),
+               "rift2_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rift2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def max_kp(self) -> int:
+        return int(self.params.max_keypoints)
+
+    def alloc_features(self, debug_shape=None) -> Features:
+        return Features.alloc(self.max_kp, f"cuda:{self.device}", debug_shape)
+
+    def alloc_matches(self) -> Matches:
+        return Matches.alloc(2 * self.max_kp, f"cuda:{self.device}")
+
+    def extract(self, images, feats=None, stream=None, debug=False):
+        """images: list of float32 CUDA tensors [H][W] (rows may be strided)."""
+        n = len(images)
+        if feats is None:
+            feats = [self.alloc_features(tuple(im.shape) if debug else None) for im in images]
+        arr = (Image * n)()
+        for i, im in enumerate(images):
+            if im.dtype != torch.float32 or im.dim() != 2 or im.stride(1) != 1:
+                raise ValueError("images must be 2-D float32 with unit column stride")
+            arr[i] = Image(im.data_ptr(), im.shape[0], im.shape[1], im.stride(0))
+        fc = (FeaturesC * n)()
+        keep = []
+        for i, f in enumerate(feats):
+            fc[i], k = f.to_c()
+            keep.append(k)
+        _check(lib().rift2_extract(self._h, n, arr, fc, _stream(stream)), "rift2_extract")
+        return feats
+
+    def match(self, fa, fb, out=None, stream=None):
+        n = len(fa)
+        if out is None:
+            out = [self.alloc_matches() for _ in range(n)]
+        ca, cb, cm = (FeaturesC * n)(), (FeaturesC * n)(), (MatchesC * n)()
+        for i in range(n):
+            ca[i], _ = fa[i].to_c()
+            cb[i], _ = fb[i].to_c()
+            cm[i] = out[i].to_c()
+        _check(lib().rift2_match(self._h, n, ca, cb, cm, _stream(stream)), "rift2_match")
+        return out
+
+    def sync(self, stream=None):
+        _check(lib().rift2_sync(self._h, _stream(stream)), "rift2_sync")
+
+    # ---- stage entry points
+    def fft2(self, img, stream=None):
+        """img: float32 CUDA [n][H][W] contiguous -> complex64 [n][H][W]."""
+        n, h, w = img.shape
+        out = torch.empty((n, h, w), dtype=torch.complex64, device=img.device)
+        _check(lib().rift2_fft2(self._h, n, _ptr(img), h, w, _ptr(out), _stream(stream)),
+               "rift2_fft2")
+        return out
+
+    def detect(self, moment, feats=None, stream=None):
+        n, h, w = moment.shape
+        if feats is None:
+            feats = [self.alloc_features() for _ in range(n)]
+        fc = (FeaturesC * n)()
+        for i, f in enumerate(feats):
+            fc[i], _ = f.to_c()
+        _check(lib().rift2_detect(self._h, n, _ptr(moment), h, w, fc, _stream(stream)),
+               "rift2_detect")
+        return feats
+
+    def describe(self, mim, feats, stream=None):
+        n, h, w = mim.shape
+        fc = (FeaturesC * n)()
+        for i, f in enumerate(feats):
+            fc[i], _ = f.to_c()
+        _check(lib().rift2_describe(self._h, n, _ptr(mim), h, w, fc, _stream(stream)),
+               "rift2_describe")
+        return feats

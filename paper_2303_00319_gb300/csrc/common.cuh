@@ -1,0 +1,70 @@
+// Shared device-side definitions of the RIFT2 kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rift2.h"
+
+namespace rift2 {
+
+constexpr int NS = RIFT2_NS;
+constexpr int NO = RIFT2_NO;
+constexpr int PATCH = RIFT2_PATCH;
+constexpr int HALF_PATCH = RIFT2_PATCH / 2;
+constexpr int CELLS = RIFT2_CELLS;
+constexpr int CELL = RIFT2_PATCH / RIFT2_CELLS;  // 16
+constexpr int DESC_DIM = RIFT2_DESC_DIM;         // 216
+constexpr int MAXB = RIFT2_MAX_BATCH;
+
+// Device status word values (latched by bounded waits).
+constexpr int ST_TIMEOUT = 1;
+
+// Scalar parameters the kernels read, derived on the host in double precision and
+// rounded once to float.
+struct KParams {
+  float log_fs[NS];      // ln(centre frequency of scale s)
+  float inv_2ls2;        // 1 / (2 ln^2 sigma_onf)
+  float inv_lp_c2;       // 1 / lp_cutoff^2
+  int lp_order;
+  float cos_o[NO], sin_o[NO];   // orientation angle o*pi/No
+  float eps, g, cutoff, inv_ns1;
+  float noise_c;         // T_o = median * noise_c (tau, scale sum and Rayleigh stats)
+  float fast_t;
+  int fast_arc;
+  int max_kp;
+  int ratio_pm;          // dominant ratio in per mille (integer comparison)
+};
+
+// Per-launch-group pointers to the caller's buffers (passed by value).
+struct FeatPtrs {
+  int* kp_xy[MAXB];
+  float* kp_score[MAXB];
+  unsigned short* desc[MAXB];
+  float* desc_norm[MAXB];
+  int* desc_kp[MAXB];
+  unsigned char* desc_dom[MAXB];
+  int* counts[MAXB];
+};
+
+struct ImgPtrs {
+  const float* img[MAXB];
+  long long pitch[MAXB];
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// DFT bin k of an n-point transform in cycles per sample (numpy fftfreq order).
+__device__ __forceinline__ float fftfreq(int k, int n) {
+  int kk = (k < (n + 1) / 2) ? k : k - n;
+  return (float)kk / (float)n;
+}
+
+}  // namespace rift2

@@ -1,0 +1,212 @@
+// Keypoint detection on the maximum-moment map (§II-A: FAST "detects edge features on
+// the maximum moment map"; Table 1: FAST threshold 0.001, at most 5000 keypoints).
+//
+//   fast_nms  : min-max normalisation of M, FAST segment test (>= arc contiguous pixels of
+//               the radius-3 Bresenham circle all brighter than p + t or all darker than
+//               p - t), sum-of-differences score V, 3x3 non-maximum suppression on
+//               (V, -raster index); survivors are appended as 64-bit keys
+//               (~bits(V) << 32 | raster index), whose ascending order is (V desc, index asc).
+//   topk_sort : one CTA per image keeps the max_keypoints smallest keys: radix refinement
+//               on 8-bit digits until the boundary bucket fits in shared memory, then a
+//               bitonic sort.  The result order is deterministic.
+#include "kernels.h"
+
+namespace rift2 {
+
+constexpr int FT = 32;          // output tile side
+constexpr int FH = 4;           // halo: 3 for the circle + 1 for the NMS
+constexpr int FS = FT + 2 * FH; // 40
+constexpr int VS = FT + 2;      // score map side (1-pixel halo)
+
+__constant__ int c_circle_dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
+__constant__ int c_circle_dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
+
+__device__ __forceinline__ bool has_arc(unsigned m16, int arc) {
+  unsigned r = m16 | (m16 << 16);   // cyclic: any run of length <= 16 appears linearly
+  unsigned acc = r;
+  for (int k = 1; k < arc; ++k) acc &= (r >> k);
+  return acc != 0;
+}
+
+__global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment, int H, int W,
+                                                KParams kp, DetectWs ws) {
+  __shared__ float mn[FS][FS];
+  __shared__ float vs[VS][VS];
+  const int img = blockIdx.z;
+  const int tx0 = blockIdx.x * FT, ty0 = blockIdx.y * FT;
+  const int ylo = HALF_PATCH, yhi = H - HALF_PATCH, xlo = HALF_PATCH, xhi = W - HALF_PATCH;
+  // tiles with no candidate pixel in or next to them do nothing
+  if (tx0 - 1 >= xhi || tx0 + FT + 1 <= xlo || ty0 - 1 >= yhi || ty0 + FT + 1 <= ylo) return;
+  const float lo = __uint_as_float(ws.minmax[2 * img]);
+  const float hi = __uint_as_float(ws.minmax[2 * img + 1]);
+  if (!(hi > lo)) return;   // constant map: no keypoints
+  const float range = hi - lo;
+  const float* M = moment + (size_t)img * H * W;
+  for (int i = threadIdx.x; i < FS * FS; i += blockDim.x) {
+    int y = ty0 - FH + i / FS, x = tx0 - FH + i % FS;
+    float v = 0.f;
+    if (y >= 0 && y < H && x >= 0 && x < W) v = (__ldg(M + (size_t)y * W + x) - lo) / range;
+    mn[i / FS][i % FS] = v;
+  }
+  __syncthreads();
+  const float t = kp.fast_t;
+  for (int i = threadIdx.x; i < VS * VS; i += blockDim.x) {
+    int ly = i / VS, lx = i % VS;
+    int y = ty0 - 1 + ly, x = tx0 - 1 + lx;
+    float score = 0.f;
+    if (y >= ylo && y < yhi && x >= xlo && x < xhi) {
+      int sy = ly + FH - 1, sx = lx + FH - 1;
+      float p = mn[sy][sx];
+      unsigned bright = 0, dark = 0;
+      float vb = 0.f, vd = 0.f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        float q = mn[sy + c_circle_dy[k]][sx + c_circle_dx[k]];
+        if (q > p + t) { bright |= 1u << k; vb += q - p - t; }
+        if (q < p - t) { dark |= 1u << k; vd += p - q - t; }
+      }
+      if (has_arc(bright, kp.fast_arc) || has_arc(dark, kp.fast_arc)) score = fmaxf(vb, vd);
+    }
+    vs[ly][lx] = score;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < FT * FT; i += blockDim.x) {
+    int ly = i / FT + 1, lx = i % FT + 1;
+    float v = vs[ly][lx];
+    bool keep = v > 0.f;
+    if (keep) {
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (dy == 0 && dx == 0) continue;
+          float qv = vs[ly + dy][lx + dx];
+          if (qv > 0.f) {
+            bool q_before = dy < 0 || (dy == 0 && dx < 0);
+            bool wins = q_before ? (v > qv) : (v >= qv);
+            keep = keep && wins;
+          }
+        }
+    }
+    unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    if (ballot) {
+      int lane = threadIdx.x & 31;
+      int leader = __ffs(ballot) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(ws.cand_count + img, (unsigned)__popc(ballot));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (keep) {
+        unsigned pos = base + __popc(ballot & ((1u << lane) - 1));
+        int y = ty0 + ly - 1, x = tx0 + lx - 1;
+        unsigned long long key = ((unsigned long long)(~__float_as_uint(v)) << 32) |
+                                 (unsigned)(y * W + x);
+        if (pos < (unsigned)ws.cap_cand) ws.cand[(size_t)img * ws.cap_cand + pos] = key;
+      }
+    }
+  }
+}
+
+constexpr int SORT_CAP = 16384;
+
+__device__ void bitonic_sort(unsigned long long* s, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = s[i], b = s[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws, FeatPtrs fp) {
+  extern __shared__ unsigned long long keys[];
+  __shared__ unsigned hist[256];
+  __shared__ unsigned s_sel[4];
+  const int img = blockIdx.x;
+  const unsigned long long* cand = ws.cand + (size_t)img * ws.cap_cand;
+  unsigned n = ws.cand_count[img];
+  if (n > (unsigned)ws.cap_cand) n = ws.cap_cand;
+  const unsigned K = kp.max_kp;
+  int pbits = 0;
+  unsigned long long prefix = 0;
+  unsigned nsel = n;   // keys to gather: those whose top pbits bits are <= prefix
+  if (n > SORT_CAP) {
+    unsigned below = 0, rank = K - 1;
+    while (true) {
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+      __syncthreads();
+      for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        unsigned long long k = cand[i];
+        if (pbits == 0 || (k >> (64 - pbits)) == prefix)
+          atomicAdd(&hist[(unsigned)(k >> (56 - pbits)) & 0xFFu], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned cum = 0;
+        int d = 0;
+        for (; d < 255; ++d) {
+          if (rank < cum + hist[d]) break;
+          cum += hist[d];
+        }
+        s_sel[0] = d;
+        s_sel[1] = cum;
+        s_sel[2] = hist[d];
+      }
+      __syncthreads();
+      unsigned d = s_sel[0], cum = s_sel[1], hd = s_sel[2];
+      below += cum;
+      rank -= cum;
+      prefix = (prefix << 8) | d;
+      pbits += 8;
+      __syncthreads();
+      if (below + hd <= SORT_CAP || pbits >= 64) { nsel = below + hd; break; }
+    }
+  }
+  int nsort = 1;
+  while (nsort < (int)nsel) nsort <<= 1;
+  if (nsort < 2) nsort = 2;
+  if (threadIdx.x == 0) s_sel[3] = 0;
+  for (int i = threadIdx.x; i < nsort; i += blockDim.x) keys[i] = ~0ull;
+  __syncthreads();
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    unsigned long long k = cand[i];
+    if (pbits == 0 || (k >> (64 - pbits)) <= prefix) {
+      unsigned pos = atomicAdd(&s_sel[3], 1u);
+      if (pos < (unsigned)nsort) keys[pos] = k;
+    }
+  }
+  __syncthreads();
+  bitonic_sort(keys, nsort);
+  unsigned nout = n < K ? n : K;
+  int* xy = fp.kp_xy[img];
+  float* sc = fp.kp_score[img];
+  for (unsigned r = threadIdx.x; r < nout; r += blockDim.x) {
+    unsigned long long k = keys[r];
+    unsigned idx = (unsigned)k;
+    xy[2 * r] = (int)(idx % (unsigned)W);
+    xy[2 * r + 1] = (int)(idx / (unsigned)W);
+    sc[r] = __uint_as_float(~(unsigned)(k >> 32));
+  }
+  if (threadIdx.x == 0) {
+    fp.counts[img][0] = (int)nout;
+    fp.counts[img][1] = 0;
+  }
+}
+
+cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
+                          DetectWs ws, const FeatPtrs& fp, cudaStream_t st) {
+  dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, nimg);
+  fast_nms<<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
+  size_t sm = SORT_CAP * sizeof(unsigned long long);
+  cudaFuncSetAttribute(topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  topk_sort<<<nimg, 1024, sm, st>>>(W, kp, ws, fp);
+  return cudaGetLastError();
+}
+
+}  // namespace rift2

@@ -1,0 +1,269 @@
+// Log-Gabor filter bank in the frequency domain (§II-B: "response components of the
+// Log-Gabor filter"; the bank itself is the RIFT / phase-congruency one, §II-A).
+//
+//   fwd_rows / fwd_cols : F = FFT2(I), full complex spectrum [H][W]
+//   lg_cols_inverse     : for each (s, o): column inverse DFT of F * G_so, G evaluated in
+//                         registers from its closed form -> scratch [s][o][H][W]
+//   lg_rows_reduce      : row inverse DFT of the four scales of each orientation, fused
+//                         with the per-pixel reductions (amplitude sum A_o, MIM argmax,
+//                         phase-congruency energy Er_o, spread weight / A_o, |EO_0,o|).
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace rift2 {
+
+// ------------------------------------------------------------------ twiddle tables
+// tw[e] = exp(-2 pi i e / n), computed in double precision (the only FP64 step).
+__global__ void twiddle_gen(float2* tw, int n) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)n, &s, &c);
+  tw[e] = make_float2((float)c, (float)s);
+}
+
+// ------------------------------------------------------------------ forward 2-D DFT
+// Rows of real images: tile of `tr` rows, complex FFT with zero imaginary part.
+__global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restrict__ dense,
+                                                float2* __restrict__ spec, int H, int W, int tr,
+                                                FftPlan pw) {
+  extern __shared__ float2 sm[];
+  const int img = blockIdx.y;
+  const int r0 = blockIdx.x * tr;
+  const int nel = tr * W;
+  float2* a = sm;
+  float2* b = sm + nel;
+  const float* src = dense ? dense + (size_t)img * H * W : ip.img[img];
+  const long long pitch = dense ? W : ip.pitch[img];
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    int r = r0 + i / W, x = i % W;
+    float v = (r < H) ? __ldg(src + (size_t)r * pitch + x) : 0.f;
+    a[i] = make_float2(v, 0.f);
+  }
+  __syncthreads();
+  float2* res = fft_smem<false, false>(a, b, pw, tr, W, 1);
+  float2* dst = spec + (size_t)img * H * W;
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    int r = r0 + i / W;
+    if (r < H) dst[(size_t)r * W + (i % W)] = res[i];
+  }
+}
+
+// Columns, in place on spec [H][W]: tile of `tc` columns.
+__global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H, int W, int tc,
+                                                FftPlan ph) {
+  extern __shared__ float2 sm[];
+  const int img = blockIdx.y;
+  const int c0 = blockIdx.x * tc;
+  const int nel = H * tc;
+  float2* a = sm;
+  float2* b = sm + nel;
+  float2* base = spec + (size_t)img * H * W;
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    int v = i / tc, c = i % tc;
+    a[i] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2* res = fft_smem<false, true>(a, b, ph, tc, 1, tc);
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    int v = i / tc, c = i % tc;
+    if (c0 + c < W) base[(size_t)v * W + c0 + c] = res[i];
+  }
+}
+
+// ------------------------------------------------------------- log-Gabor transfer
+// Radial part of scale s at squared radius r2 (cycles/px)^2:
+//   exp(-(ln r - ln f_s)^2 / (2 ln^2 sigma_onf)) / (1 + (r^2 / c^2)^n), zero at DC.
+__device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams& kp) {
+  if (r2 <= 0.f) return 0.f;
+  float lr = 0.5f * logf(r2);
+  float d = lr - log_fs;
+  float x = r2 * kp.inv_lp_c2;   // (r/c)^2
+  float p = 1.f, base = x;
+  for (int e = kp.lp_order; e > 0; e >>= 1) {   // (r/c)^(2n) by squaring
+    if (e & 1) p *= base;
+    base *= base;
+  }
+  return expf(-d * d * kp.inv_2ls2) / (1.f + p);
+}
+
+// Angular raised-cosine window of orientation (cos_o, sin_o) at frequency (u, v):
+// with c = cos(theta - theta_o), theta = atan2(-v, u), the window (1 + cos(3 dtheta))/2
+// for |dtheta| < pi/3 equals (1 + c)(2c - 1)^2 / 2 (triple-angle identity), 0 beyond.
+__device__ __forceinline__ float lg_angular(float u, float v, float rinv, float co, float so) {
+  float c = (u * co - v * so) * rinv;
+  if (!(c > 0.5f)) return 0.f;
+  float t = 2.f * c - 1.f;
+  return 0.5f * (1.f + c) * t * t;
+}
+
+// Column pass of the inverse for the six orientations of scale blockIdx.y.
+// smem: base (F * R_s), a, b each [H][tc].
+__global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict__ spec,
+                                                       float2* __restrict__ scratch, int H, int W,
+                                                       int tc, FftPlan ph, KParams kp) {
+  extern __shared__ float2 sm[];
+  const int s = blockIdx.y;
+  const int img = blockIdx.z;
+  const int c0 = blockIdx.x * tc;
+  const int nel = H * tc;
+  float2* base = sm;
+  float2* a = sm + nel;
+  float2* b = sm + 2 * nel;
+  const float2* F = spec + (size_t)img * H * W;
+  const float log_fs = kp.log_fs[s];
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    int v = i / tc, c = i % tc, u = c0 + c;
+    float2 f = make_float2(0.f, 0.f);
+    if (u < W) {
+      float fu = fftfreq(u, W), fv = fftfreq(v, H);
+      float rs = lg_radial(fu * fu + fv * fv, log_fs, kp);
+      float2 x = __ldg(F + (size_t)v * W + u);
+      f = make_float2(x.x * rs, x.y * rs);
+    }
+    base[i] = f;
+  }
+  for (int o = 0; o < NO; ++o) {
+    __syncthreads();
+    const float co = kp.cos_o[o], so = kp.sin_o[o];
+    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+      int v = i / tc, c = i % tc, u = c0 + c;
+      float fu = fftfreq(u, W), fv = fftfreq(v, H);
+      float r2 = fu * fu + fv * fv;
+      float g = (r2 > 0.f && u < W) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
+      float2 x = base[i];
+      a[i] = make_float2(x.x * g, x.y * g);
+    }
+    __syncthreads();
+    float2* res = fft_smem<true, true>(a, b, ph, tc, 1, tc);
+    float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * H * W;
+    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+      int v = i / tc, c = i % tc;
+      if (c0 + c < W) dst[(size_t)v * W + c0 + c] = res[i];
+    }
+    // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
+  }
+}
+
+// Row pass of the inverse with the fused per-pixel reductions.  One row per CTA;
+// for each orientation the four scales are transformed together.
+constexpr int RR_MAXPIX = 8;   // pixels per thread: W <= 8 * blockDim.x
+
+__global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__ scratch, int H,
+                                                      int W, FftPlan pw, KParams kp,
+                                                      float* __restrict__ er_out,
+                                                      float* __restrict__ q_out,
+                                                      float* __restrict__ an0_out,
+                                                      float* __restrict__ amp_out,
+                                                      unsigned char* __restrict__ mim_out,
+                                                      int mim_pitch) {
+  extern __shared__ float2 sm[];
+  const int row = blockIdx.x;
+  const int img = blockIdx.y;
+  const int nel = NS * W;
+  float2* a = sm;
+  float2* b = sm + nel;
+  const size_t P = (size_t)H * W;
+  const float scale = 1.f / ((float)H * (float)W);
+  float best[RR_MAXPIX];
+  int besto[RR_MAXPIX];
+#pragma unroll
+  for (int k = 0; k < RR_MAXPIX; ++k) { best[k] = -1.f; besto[k] = 0; }
+
+  for (int o = 0; o < NO; ++o) {
+    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+      int s = i / W, x = i - s * W;
+      a[i] = __ldg(scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W + x);
+    }
+    __syncthreads();
+    float2* res = fft_smem<true, false>(a, b, pw, NS, W, 1);
+#pragma unroll
+    for (int k = 0; k < RR_MAXPIX; ++k) {
+      int x = threadIdx.x + k * blockDim.x;
+      if (x >= W) break;
+      float e[NS], od[NS];
+      float sum_e = 0.f, sum_o = 0.f, sum_an = 0.f, max_an = 0.f, an0 = 0.f;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        float2 z = res[s * W + x];
+        e[s] = z.x * scale;
+        od[s] = z.y * scale;
+        float an = sqrtf(e[s] * e[s] + od[s] * od[s]);
+        if (s == 0) an0 = an;
+        sum_e += e[s];
+        sum_o += od[s];
+        sum_an += an;
+        max_an = fmaxf(max_an, an);
+      }
+      float xe = sqrtf(sum_e * sum_e + sum_o * sum_o) + kp.eps;
+      float me = sum_e / xe, mo = sum_o / xe;
+      float energy = 0.f;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        energy += e[s] * me + od[s] * mo - fabsf(e[s] * mo - od[s] * me);
+      float width = (sum_an / (max_an + kp.eps) - 1.f) * kp.inv_ns1;
+      float wgt = 1.f / (1.f + expf((kp.cutoff - width) * kp.g));
+      float q = (sum_an > 0.f) ? wgt / sum_an : 0.f;
+      size_t off = ((size_t)img * NO + o) * P + (size_t)row * W + x;
+      er_out[off] = energy;
+      q_out[off] = q;
+      an0_out[off] = an0;
+      if (amp_out) amp_out[off] = sum_an;
+      if (sum_an > best[k]) { best[k] = sum_an; besto[k] = o; }   // lowest o on ties
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < RR_MAXPIX; ++k) {
+    int x = threadIdx.x + k * blockDim.x;
+    if (x >= W) break;
+    mim_out[(size_t)img * H * mim_pitch + (size_t)row * mim_pitch + x] = (unsigned char)besto[k];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+void launch_twiddles(float2* tw, int n, cudaStream_t st) {
+  twiddle_gen<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
+}
+
+static int rows_tile(int W) { return W >= 4096 ? 1 : 4096 / W; }
+static int cols_tile(int H) {
+  int tc = 8192 / H;
+  if (tc > 16) tc = 16;
+  if (tc < 1) tc = 1;
+  return tc;
+}
+
+cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
+                                int H, int W, const FftPlan& ph, const FftPlan& pw,
+                                cudaStream_t st) {
+  int tr = rows_tile(W);
+  size_t smr = 2 * (size_t)tr * W * sizeof(float2);
+  cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  ImgPtrs none{};
+  fwd_rows<<<dim3((H + tr - 1) / tr, nimg), 512, smr, st>>>(ip ? *ip : none, dense, spec, H, W,
+                                                           tr, pw);
+  int tc = cols_tile(H);
+  size_t smc = 2 * (size_t)tc * H * sizeof(float2);
+  cudaFuncSetAttribute(fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  fwd_cols<<<dim3((W + tc - 1) / tc, nimg), 512, smc, st>>>(spec, H, W, tc, ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filterbank(const float2* spec, float2* scratch, int nimg, int H, int W,
+                              const FftPlan& ph, const FftPlan& pw, const KParams& kp,
+                              float* er, float* q, float* an0, float* amp, unsigned char* mim,
+                              int mim_pitch, cudaStream_t st) {
+  int tc = cols_tile(H);
+  size_t sm2 = 3 * (size_t)tc * H * sizeof(float2);
+  cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  lg_cols_inverse<<<dim3((W + tc - 1) / tc, NS, nimg), 512, sm2, st>>>(spec, scratch, H, W, tc,
+                                                                       ph, kp);
+  size_t sm3 = 2 * (size_t)NS * W * sizeof(float2);
+  cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+  lg_rows_reduce<<<dim3(H, nimg), 512, sm3, st>>>(scratch, H, W, pw, kp, er, q, an0, amp, mim,
+                                                  mim_pitch);
+  return cudaGetLastError();
+}
+
+}  // namespace rift2

@@ -1,0 +1,187 @@
+// Noise threshold and phase congruency (§II-A: "one-dimensional phase congruency for
+// each orientation of the log-Gabor convolutions", "analyzes the change of moment with
+// orientations").  The noise model follows the phase-congruency model RIFT builds on:
+// T_o is a fixed multiple of the median smallest-scale amplitude.
+//
+//   median_hist / median_select : exact median of |EO_0,o| over the whole image by a
+//     three-round radix select on the float bit patterns (12 + 12 + 8 bits).  The
+//     amplitudes are non-negative, so their bit patterns order like the values.  For an
+//     even pixel count the two middle values are selected and averaged.
+//   pc_moment : PC_o = q_o max(Er_o - T_o, 0), covariance moments over the orientations,
+//     maximum moment M, and the image-wide min / max of M for the FAST normalisation.
+#include "kernels.h"
+
+namespace rift2 {
+
+constexpr int MED_BINS = 4096;
+
+__device__ __forceinline__ void med_digit(unsigned bits, int round, unsigned& pre, unsigned& dig) {
+  if (round == 0) { pre = 0; dig = bits >> 20; }
+  else if (round == 1) { pre = bits >> 20; dig = (bits >> 8) & 0xFFFu; }
+  else { pre = bits >> 8; dig = bits & 0xFFu; }
+}
+
+__global__ void __launch_bounds__(256) median_hist(const float* __restrict__ an0, long long P,
+                                                   int round, MedianWs ws) {
+  __shared__ unsigned h[2][MED_BINS];
+  const int o = blockIdx.y, img = blockIdx.z;
+  for (int i = threadIdx.x; i < 2 * MED_BINS; i += blockDim.x) (&h[0][0])[i] = 0;
+  const unsigned* st = ws.state + ((size_t)img * NO + o) * 4;
+  const unsigned pre0 = st[0], pre1 = st[2];
+  __syncthreads();
+  const float* src = an0 + ((size_t)img * NO + o) * P;
+  const long long chunk = (P + gridDim.x - 1) / gridDim.x;
+  const long long beg = blockIdx.x * chunk;
+  const long long end = min(P, beg + chunk);
+  for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    unsigned bits = __float_as_uint(__ldg(src + i));
+    unsigned pre, dig;
+    med_digit(bits, round, pre, dig);
+    if (round == 0) {
+      atomicAdd(&h[0][dig], 1u);
+    } else {
+      if (pre == pre0) atomicAdd(&h[0][dig], 1u);
+      if (pre == pre1) atomicAdd(&h[1][dig], 1u);
+    }
+  }
+  __syncthreads();
+  unsigned* gh = ws.hist + ((size_t)img * NO + o) * 2 * MED_BINS;
+  for (int i = threadIdx.x; i < 2 * MED_BINS; i += blockDim.x) {
+    unsigned c = (&h[0][0])[i];
+    if (c) atomicAdd(gh + i, c);
+  }
+}
+
+// One warp per target rank (warp 0: lower middle, warp 1: upper middle).
+__global__ void __launch_bounds__(64) median_select(long long P, int round, float noise_c,
+                                                    MedianWs ws) {
+  const int o = blockIdx.x, img = blockIdx.y;
+  const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned* gh = ws.hist + ((size_t)img * NO + o) * 2 * MED_BINS;
+  unsigned* st = ws.state + ((size_t)img * NO + o) * 4;
+  const int nbins = (round == 2) ? 256 : MED_BINS;
+  const int shift = (round == 2) ? 8 : 12;
+  const unsigned* hist = gh + ((round == 0) ? 0 : t) * MED_BINS;
+  unsigned prefix, rank;
+  if (round == 0) {
+    prefix = 0;
+    rank = (unsigned)(t == 0 ? (P - 1) / 2 : P / 2);
+  } else {
+    prefix = st[2 * t];
+    rank = st[2 * t + 1];
+  }
+  const int per = nbins / 32;
+  unsigned lsum = 0;
+  for (int i = 0; i < per; ++i) lsum += hist[lane * per + i];
+  unsigned incl = lsum;
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  unsigned excl = incl - lsum;
+  unsigned hit = __ballot_sync(0xffffffffu, excl <= rank && rank < incl);
+  int src = hit ? __ffs(hit) - 1 : 31;
+  unsigned dig = 0, newrank = 0;
+  if (lane == src) {
+    unsigned acc = excl;
+    int i = 0;
+    for (; i < per - 1; ++i) {
+      unsigned c = hist[lane * per + i];
+      if (rank < acc + c) break;
+      acc += c;
+    }
+    dig = lane * per + i;
+    newrank = rank - acc;
+  }
+  dig = __shfl_sync(0xffffffffu, dig, src);
+  newrank = __shfl_sync(0xffffffffu, newrank, src);
+  __syncthreads();   // every warp has read the histogram
+  if (lane == 0) {
+    st[2 * t] = (prefix << shift) | dig;
+    st[2 * t + 1] = newrank;
+  }
+  for (int i = threadIdx.x; i < 2 * MED_BINS; i += blockDim.x) gh[i] = 0;   // ready for next round
+  if (round == 2) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float v0 = __uint_as_float(st[0]), v1 = __uint_as_float(st[2]);
+      ws.noise_t[img * NO + o] = 0.5f * (v0 + v1) * noise_c;
+    }
+  }
+}
+
+cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, const KParams& kp,
+                                   MedianWs ws, cudaStream_t st) {
+  int chunks = (int)((P + 16383) / 16384);
+  if (chunks > 64) chunks = 64;
+  if (chunks < 1) chunks = 1;
+  for (int r = 0; r < 3; ++r) {
+    median_hist<<<dim3(chunks, NO, nimg), 256, 0, st>>>(an0, P, r, ws);
+    median_select<<<dim3(NO, nimg), 64, 0, st>>>(P, r, kp.noise_c, ws);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ PC and moments
+__global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
+                                                 const float* __restrict__ q,
+                                                 const float* __restrict__ noise_t, long long P,
+                                                 KParams kp, float* __restrict__ moment,
+                                                 unsigned* __restrict__ minmax,
+                                                 float* __restrict__ pc_out) {
+  const int img = blockIdx.y;
+  float tn[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) tn[o] = __ldg(noise_t + img * NO + o);
+  float lo = 3.0e38f, hi = 0.f;
+  const float inv_half = 2.f / NO, four_over = 4.f / NO;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    float sxx = 0.f, syy = 0.f, sxy = 0.f;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      size_t off = ((size_t)img * NO + o) * P + i;
+      float pc = __ldg(q + off) * fmaxf(__ldg(er + off) - tn[o], 0.f);
+      if (pc_out) pc_out[off] = pc;
+      float a = pc * kp.cos_o[o], b = pc * kp.sin_o[o];
+      sxx += a * a;
+      syy += b * b;
+      sxy += a * b;
+    }
+    sxx *= inv_half;
+    syy *= inv_half;
+    sxy *= four_over;
+    float d = sxx - syy;
+    float den = sqrtf(sxy * sxy + d * d) + kp.eps;
+    float m = 0.5f * (sxx + syy + den);
+    moment[(size_t)img * P + i] = m;
+    lo = fminf(lo, m);
+    hi = fmaxf(hi, m);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+  }
+  __shared__ float slo[8], shi[8];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { slo[w] = lo; shi[w] = hi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { lo = fminf(lo, slo[k]); hi = fmaxf(hi, shi[k]); }
+    // M > 0, so the bit patterns order like the values
+    atomicMin(minmax + 2 * img, __float_as_uint(lo));
+    atomicMax(minmax + 2 * img + 1, __float_as_uint(hi));
+  }
+}
+
+cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t, int nimg,
+                             long long P, const KParams& kp, float* moment, unsigned* minmax,
+                             float* pc_out, cudaStream_t st) {
+  long long blocks = (P + 255) / 256;
+  if (blocks > 1216) blocks = 1216;   // 8 per SM on 152 SMs; grid-stride beyond
+  pc_moment<<<dim3((unsigned)blocks, nimg), 256, 0, st>>>(er, q, noise_t, P, kp, moment, minmax,
+                                                          pc_out);
+  return cudaGetLastError();
+}
+
+}  // namespace rift2

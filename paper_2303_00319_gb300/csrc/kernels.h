@@ -1,0 +1,74 @@
+// Host-side launchers of the RIFT2 kernels (one translation unit per stage group).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace rift2 {
+
+// k_filterbank.cu
+void launch_twiddles(float2* tw, int n, cudaStream_t st);
+cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
+                                int H, int W, const FftPlan& ph, const FftPlan& pw,
+                                cudaStream_t st);
+cudaError_t launch_filterbank(const float2* spec, float2* scratch, int nimg, int H, int W,
+                              const FftPlan& ph, const FftPlan& pw, const KParams& kp,
+                              float* er, float* q, float* an0, float* amp, unsigned char* mim,
+                              int mim_pitch, cudaStream_t st);
+
+// k_pc.cu — exact median of |EO_0,o| (radix select), noise thresholds, PC, moments.
+struct MedianWs {
+  unsigned* hist;    // [nimg][NO][2][4096]
+  unsigned* state;   // [nimg][NO][2][2]  (prefix, rank)
+  float* noise_t;    // [nimg][NO]
+};
+cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, const KParams& kp,
+                                   MedianWs ws, cudaStream_t st);
+cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t, int nimg,
+                             long long P, const KParams& kp, float* moment, unsigned* minmax,
+                             float* pc_out, cudaStream_t st);
+
+// k_detect.cu — FAST + NMS on the normalised moment map, then top-K.
+struct DetectWs {
+  const unsigned* minmax;       // [nimg][2] float bits of min / max of M
+  unsigned long long* cand;     // [nimg][cap_cand]
+  unsigned* cand_count;         // [nimg]
+  int cap_cand;
+};
+cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
+                          DetectWs ws, const FeatPtrs& fp, cudaStream_t st);
+
+// k_describe.cu — MIM patch histograms, dominant index, recoded descriptors.
+struct DescribeWs {
+  unsigned short* raw;   // [nimg][max_kp][216]
+  unsigned* info;        // [nimg][max_kp]
+  int* off;              // [nimg][max_kp]
+  int* status;           // device status word
+};
+cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
+                            const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
+                            cudaStream_t st);
+
+// k_match.cu — brute-force nearest neighbour.
+struct MatchPtrs {
+  const unsigned short* desc_a[MAXB];
+  const unsigned short* desc_b[MAXB];
+  const int* counts_a[MAXB];
+  const int* counts_b[MAXB];
+  const int* desc_kp_a[MAXB];
+  const int* desc_kp_b[MAXB];
+  int* q_desc[MAXB];
+  int* nn_desc[MAXB];
+  int* kp_a[MAXB];
+  int* kp_b[MAXB];
+  float* d1[MAXB];
+  float* d2[MAXB];
+  unsigned char* near_tie[MAXB];
+  int* count[MAXB];
+};
+cudaError_t launch_match_simt(const MatchPtrs& mp, int npairs, int max_desc, cudaStream_t st);
+
+}  // namespace rift2

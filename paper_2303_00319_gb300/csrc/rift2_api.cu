@@ -1,0 +1,594 @@
+// C ABI of the RIFT2 pipeline (include/rift2.h): context, FFT plans, workspace arena and
+// the launch sequences of rift2_extract / rift2_match and the stage entry points.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace rift2;
+
+struct rift2_ctx {
+  int device = 0;
+  rift2_params p{};
+  KParams kp{};
+  size_t budget = 0;
+  void* ws = nullptr;
+  size_t ws_size = 0;
+  int* status = nullptr;
+  std::map<int, FftPlan> plans;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define RIFT2_CU(call)                                                     \
+  do {                                                                     \
+    cudaError_t e__ = (call);                                              \
+    if (e__ != cudaSuccess) {                                              \
+      fprintf(stderr, "rift2: %s failed: %s\n", #call, cudaGetErrorString(e__)); \
+      return RIFT2_E_CUDA;                                                 \
+    }                                                                      \
+  } while (0)
+
+bool factor_plan(int n, FftPlan& pl) {
+  pl.n = n;
+  pl.nst = 0;
+  int m = n, a = 0;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  std::vector<int> rs;
+  int q = a / 3, r = a % 3;
+  if (r == 1 && q >= 1) { q -= 1; rs.push_back(4); rs.push_back(4); }
+  else if (r == 1) rs.push_back(2);
+  else if (r == 2) rs.push_back(4);
+  for (int i = 0; i < q; ++i) rs.insert(rs.begin(), 8);
+  for (int f : {3, 5, 7})
+    while (m % f == 0) { m /= f; rs.push_back(f); }
+  if (m != 1 || (int)rs.size() > FFT_MAX_STAGES) return false;
+  pl.nst = (int)rs.size();
+  for (int i = 0; i < pl.nst; ++i) pl.radix[i] = rs[i];
+  return true;
+}
+
+int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
+  auto it = c->plans.find(n);
+  if (it != c->plans.end()) { *out = it->second; return RIFT2_OK; }
+  FftPlan pl{};
+  if (!factor_plan(n, pl)) return RIFT2_E_UNIMPL;
+  float2* tw = nullptr;
+  RIFT2_CU(cudaMalloc(&tw, sizeof(float2) * n));
+  launch_twiddles(tw, n, st);
+  RIFT2_CU(cudaGetLastError());
+  RIFT2_CU(cudaStreamSynchronize(st));
+  pl.tw = tw;
+  c->plans[n] = pl;
+  *out = pl;
+  return RIFT2_OK;
+}
+
+int ensure_ws(rift2_ctx* c, size_t need) {
+  if (need <= c->ws_size) return RIFT2_OK;
+  if (need > c->budget) return RIFT2_E_NOMEM;
+  if (c->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_size = 0;
+  }
+  size_t sz = align_up(need, 1 << 20);
+  if (sz > c->budget) sz = need;
+  if (cudaMalloc(&c->ws, sz) != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return RIFT2_E_NOMEM;
+  }
+  c->ws_size = sz;
+  return RIFT2_OK;
+}
+
+void derive_kparams(const rift2_params& p, KParams& k) {
+  for (int s = 0; s < NS; ++s)
+    k.log_fs[s] = (float)(-std::log((double)p.min_wavelength) - s * std::log((double)p.mult));
+  double ls = std::log((double)p.sigma_onf);
+  k.inv_2ls2 = (float)(1.0 / (2.0 * ls * ls));
+  k.inv_lp_c2 = (float)(1.0 / ((double)p.lp_cutoff * p.lp_cutoff));
+  k.lp_order = p.lp_order;
+  for (int o = 0; o < NO; ++o) {
+    double a = o * M_PI / NO;
+    k.cos_o[o] = (float)std::cos(a);
+    k.sin_o[o] = (float)std::sin(a);
+  }
+  k.eps = p.eps;
+  k.g = p.g;
+  k.cutoff = p.cutoff;
+  k.inv_ns1 = (float)(1.0 / (p.n_scales - 1));
+  double inv_mult = 1.0 / p.mult;
+  double scale_sum = (1.0 - std::pow(inv_mult, p.n_scales)) / (1.0 - inv_mult);
+  k.noise_c = (float)(scale_sum / std::sqrt(std::log(4.0)) *
+                      (std::sqrt(M_PI / 2.0) + p.k * std::sqrt((4.0 - M_PI) / 2.0)));
+  k.fast_t = p.fast_threshold;
+  k.fast_arc = p.fast_arc;
+  k.max_kp = p.max_keypoints;
+  k.ratio_pm = (int)std::lround(p.second_ratio * 1000.0);
+}
+
+int check_size(int H, int W) {
+  if (H < 16 || W < 16) return RIFT2_E_INVAL;
+  FftPlan t{};
+  if (!factor_plan(H, t) || !factor_plan(W, t)) return RIFT2_E_UNIMPL;
+  if ((size_t)2 * NS * W * sizeof(float2) > 227 * 1024) return RIFT2_E_UNIMPL;   // row pass
+  if (W > 4096 || H > 8192) return RIFT2_E_UNIMPL;
+  return RIFT2_OK;
+}
+
+// ------------------------------------------------------------------ workspace layout
+struct Layout {
+  size_t spec, scratch, er, q, an0, amp, pc, moment, mim, mhist, mstate, noise, minmax, ccount,
+      cand, raw, info, off, total;
+  int mim_pitch, cap_cand;
+};
+
+Layout extract_layout(int g, int H, int W, int max_kp, bool debug) {
+  Layout L{};
+  const size_t P = (size_t)H * W;
+  L.mim_pitch = (int)align_up((size_t)(W > 112 ? W : 112), 16);
+  L.cap_cand = ((H + 1) / 2) * ((W + 1) / 2);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+  L.spec = take((size_t)g * P * sizeof(float2));
+  L.scratch = take((size_t)g * NS * NO * P * sizeof(float2));
+  L.er = take((size_t)g * NO * P * 4);
+  L.q = take((size_t)g * NO * P * 4);
+  L.an0 = take((size_t)g * NO * P * 4);
+  L.amp = debug ? take((size_t)g * NO * P * 4) : (size_t)-1;
+  L.pc = debug ? take((size_t)g * NO * P * 4) : (size_t)-1;
+  L.moment = take((size_t)g * P * 4);
+  L.mim = take((size_t)g * H * L.mim_pitch);
+  L.mhist = take((size_t)g * NO * 2 * 4096 * 4);
+  L.mstate = take((size_t)g * NO * 4 * 4);
+  L.noise = take((size_t)g * NO * 4);
+  L.minmax = take((size_t)g * 2 * 4);
+  L.ccount = take((size_t)g * 4);
+  L.cand = take((size_t)g * L.cap_cand * 8);
+  L.raw = take((size_t)g * max_kp * DESC_DIM * 2);
+  L.info = take((size_t)g * max_kp * 4);
+  L.off = take((size_t)g * max_kp * 4);
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+__global__ void init_group(unsigned* minmax, unsigned* ccount, int g) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < g) {
+    minmax[2 * i] = 0xFFFFFFFFu;
+    minmax[2 * i + 1] = 0u;
+    ccount[i] = 0u;
+  }
+}
+
+__global__ void minmax_kernel(const float* __restrict__ m, long long P, unsigned* minmax) {
+  const int img = blockIdx.y;
+  float lo = 3.0e38f, hi = -3.0e38f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v = m[(size_t)img * P + i];
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // callers of the stage entry pass non-negative moment maps (M >= eps / 2 > 0)
+    atomicMin(minmax + 2 * img, __float_as_uint(fmaxf(lo, 0.f)));
+    atomicMax(minmax + 2 * img + 1, __float_as_uint(fmaxf(hi, 0.f)));
+  }
+}
+
+int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int g, int H, int pitch) {
+  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)H, (cuuint64_t)g};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * H};
+  cuuint32_t box[3] = {RIFT2_PATCH + 16, RIFT2_PATCH, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, mim, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fprintf(stderr, "rift2: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
+    return RIFT2_E_CUDA;
+  }
+  return RIFT2_OK;
+}
+
+int check_features(const rift2_ctx* c, const rift2_features& f, bool need_desc) {
+  if (!f.kp_xy || !f.kp_score || !f.counts) return RIFT2_E_INVAL;
+  if (f.cap_kp < c->p.max_keypoints) return RIFT2_E_CAPACITY;
+  if (need_desc) {
+    if (!f.desc || !f.desc_norm || !f.desc_kp || !f.desc_dom) return RIFT2_E_INVAL;
+    if (f.cap_desc < 2 * c->p.max_keypoints) return RIFT2_E_CAPACITY;
+  }
+  return RIFT2_OK;
+}
+
+FeatPtrs feat_ptrs(const rift2_features* f, int n) {
+  FeatPtrs fp{};
+  for (int i = 0; i < n; ++i) {
+    fp.kp_xy[i] = f[i].kp_xy;
+    fp.kp_score[i] = f[i].kp_score;
+    fp.desc[i] = f[i].desc;
+    fp.desc_norm[i] = f[i].desc_norm;
+    fp.desc_kp[i] = f[i].desc_kp;
+    fp.desc_dom[i] = f[i].desc_dom;
+    fp.counts[i] = f[i].counts;
+  }
+  return fp;
+}
+
+int copy_debug(const rift2_features* f, int n, void* ws, const Layout& L, int H, int W,
+               cudaStream_t st) {
+  const size_t P = (size_t)H * W;
+  for (int i = 0; i < n; ++i) {
+    const rift2_debug_maps* d = f[i].debug;
+    if (!d) continue;
+    auto cp = [&](void* dst, size_t off, size_t bytes_per_img) -> cudaError_t {
+      if (!dst || off == (size_t)-1) return cudaSuccess;
+      return cudaMemcpyAsync(dst, static_cast<char*>(ws) + off + i * bytes_per_img, bytes_per_img,
+                             cudaMemcpyDeviceToDevice, st);
+    };
+    RIFT2_CU(cp(d->amp, L.amp, NO * P * 4));
+    RIFT2_CU(cp(d->er, L.er, NO * P * 4));
+    RIFT2_CU(cp(d->q, L.q, NO * P * 4));
+    RIFT2_CU(cp(d->an0, L.an0, NO * P * 4));
+    RIFT2_CU(cp(d->pc, L.pc, NO * P * 4));
+    RIFT2_CU(cp(d->moment, L.moment, P * 4));
+    RIFT2_CU(cp(d->noise_t, L.noise, NO * 4));
+    if (d->mim)
+      RIFT2_CU(cudaMemcpy2DAsync(d->mim, W, static_cast<char*>(ws) + L.mim + (size_t)i * H * L.mim_pitch,
+                                 L.mim_pitch, W, H, cudaMemcpyDeviceToDevice, st));
+  }
+  return RIFT2_OK;
+}
+
+bool wants_debug(const rift2_features* f, int n) {
+  for (int i = 0; i < n; ++i)
+    if (f[i].debug) return true;
+  return false;
+}
+
+// One launch group: g images of the same size.
+int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* out,
+                  cudaStream_t st) {
+  const int H = imgs[0].height, W = imgs[0].width;
+  const long long P = (long long)H * W;
+  FftPlan ph{}, pw{};
+  int rc = get_plan(c, H, st, &ph);
+  if (rc) return rc;
+  rc = get_plan(c, W, st, &pw);
+  if (rc) return rc;
+  const bool dbg = wants_debug(out, g);
+  Layout L = extract_layout(g, H, W, c->p.max_keypoints, dbg);
+  rc = ensure_ws(c, L.total);
+  if (rc) return rc;
+  void* ws = c->ws;
+  ImgPtrs ip{};
+  for (int i = 0; i < g; ++i) {
+    ip.img[i] = imgs[i].data;
+    ip.pitch[i] = imgs[i].pitch;
+  }
+  FeatPtrs fp = feat_ptrs(out, g);
+  unsigned* minmax = at<unsigned>(ws, L.minmax);
+  unsigned* ccount = at<unsigned>(ws, L.ccount);
+  init_group<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
+  RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * 2 * 4096 * 4, st));
+  float2* spec = at<float2>(ws, L.spec);
+  RIFT2_CU(launch_fft2_forward(&ip, nullptr, spec, g, H, W, ph, pw, st));
+  float* er = at<float>(ws, L.er);
+  float* q = at<float>(ws, L.q);
+  float* an0 = at<float>(ws, L.an0);
+  unsigned char* mim = at<unsigned char>(ws, L.mim);
+  RIFT2_CU(launch_filterbank(spec, at<float2>(ws, L.scratch), g, H, W, ph, pw, c->kp, er, q, an0,
+                             at<float>(ws, L.amp), mim, L.mim_pitch, st));
+  MedianWs mw{at<unsigned>(ws, L.mhist), at<unsigned>(ws, L.mstate), at<float>(ws, L.noise)};
+  RIFT2_CU(launch_noise_threshold(an0, g, P, c->kp, mw, st));
+  float* moment = at<float>(ws, L.moment);
+  RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, g, P, c->kp, moment, minmax, at<float>(ws, L.pc),
+                            st));
+  DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand};
+  RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
+  if (H >= RIFT2_PATCH && W >= RIFT2_PATCH) {
+    CUtensorMap tm;
+    rc = make_mim_map(c, &tm, mim, g, H, L.mim_pitch);
+    if (rc) return rc;
+    DescribeWs dsw{at<unsigned short>(ws, L.raw), at<unsigned>(ws, L.info), at<int>(ws, L.off),
+                   c->status};
+    RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
+  }
+  return copy_debug(out, g, ws, L, H, W, st);
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void rift2_default_params(rift2_params* p) {
+  if (!p) return;
+  p->n_scales = 4;
+  p->n_orient = 6;
+  p->min_wavelength = 3.0f;
+  p->mult = 1.6f;
+  p->sigma_onf = 0.75f;
+  p->k = 1.0f;
+  p->g = 3.0f;
+  p->cutoff = 0.5f;
+  p->eps = 1e-4f;
+  p->lp_cutoff = 0.45f;
+  p->lp_order = 15;
+  p->fast_threshold = 0.001f;
+  p->fast_arc = 9;
+  p->max_keypoints = 5000;
+  p->patch = 96;
+  p->cells = 6;
+  p->second_ratio = 0.8f;
+  p->flags = 0;
+}
+
+const char* rift2_status_str(int s) {
+  switch (s) {
+    case RIFT2_OK: return "ok";
+    case RIFT2_E_INVAL: return "invalid argument";
+    case RIFT2_E_NOMEM: return "workspace exceeds the HBM budget or allocation failed";
+    case RIFT2_E_CAPACITY: return "output buffer capacity too small";
+    case RIFT2_E_CUDA: return "CUDA error";
+    case RIFT2_E_TIMEOUT: return "bounded device wait timed out";
+    case RIFT2_E_UNIMPL: return "not implemented for this size or geometry";
+    default: return "unknown status";
+  }
+}
+
+int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes, rift2_ctx** out) {
+  if (!out) return RIFT2_E_INVAL;
+  *out = nullptr;
+  rift2_params p;
+  rift2_default_params(&p);
+  if (params) p = *params;
+  if (p.n_scales != NS || p.n_orient != NO || p.patch != PATCH || p.cells != CELLS)
+    return RIFT2_E_UNIMPL;
+  if (!(p.min_wavelength > 0) || !(p.mult > 1) || !(p.sigma_onf > 0 && p.sigma_onf < 1) ||
+      !(p.lp_cutoff > 0) || p.lp_order < 1 || p.fast_arc < 1 || p.fast_arc > 16 ||
+      p.max_keypoints < 1 || p.max_keypoints > 16384 || !(p.fast_threshold >= 0) ||
+      !(p.second_ratio >= 0) || !(p.eps > 0))
+    return RIFT2_E_INVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return RIFT2_E_CUDA;
+  }
+  DeviceGuard dg(device);
+  rift2_ctx* c = new rift2_ctx();
+  c->device = device;
+  c->p = p;
+  derive_kparams(p, c->kp);
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)16 << 30);
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &qr) != cudaSuccess ||
+      qr != cudaDriverEntryPointSuccess || !fn) {
+    delete c;
+    return RIFT2_E_CUDA;
+  }
+  c->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+    delete c;
+    return RIFT2_E_CUDA;
+  }
+  *out = c;
+  return RIFT2_OK;
+}
+
+int rift2_destroy(rift2_ctx* c) {
+  if (!c) return RIFT2_E_INVAL;
+  DeviceGuard dg(c->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : c->plans) cudaFree(const_cast<float2*>(kv.second.tw));
+  if (c->ws) cudaFree(c->ws);
+  if (c->status) cudaFree(c->status);
+  delete c;
+  return RIFT2_OK;
+}
+
+int rift2_sync(rift2_ctx* c, void* stream) {
+  if (!c) return RIFT2_E_INVAL;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RIFT2_E_CUDA;
+  if (h) {
+    cudaMemsetAsync(c->status, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+    return RIFT2_E_TIMEOUT;
+  }
+  return RIFT2_OK;
+}
+
+int rift2_extract(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* out, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!imgs || !out))) return RIFT2_E_INVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!imgs[i].data || imgs[i].pitch < imgs[i].width) return RIFT2_E_INVAL;
+    int rc = check_size(imgs[i].height, imgs[i].width);
+    if (rc) return rc;
+    rc = check_features(c, out[i], true);
+    if (rc) return rc;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool group = !(c->p.flags & RIFT2_FLAG_NO_GROUPING);
+  int i = 0;
+  while (i < n) {
+    int j = i + 1;
+    while (group && j < n && j - i < MAXB && imgs[j].height == imgs[i].height &&
+           imgs[j].width == imgs[i].width)
+      ++j;
+    // shrink the group until its workspace fits the budget
+    int g = j - i;
+    while (g > 1 && extract_layout(g, imgs[i].height, imgs[i].width, c->p.max_keypoints,
+                                   wants_debug(out + i, g)).total > c->budget)
+      g = (g + 1) / 2;
+    int rc = extract_group(c, g, imgs + i, out + i, st);
+    if (rc) return rc;
+    i += g;
+  }
+  return RIFT2_OK;
+}
+
+int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_features* b,
+                rift2_matches* out, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!a || !b || !out))) return RIFT2_E_INVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!a[i].desc || !b[i].desc || !a[i].counts || !b[i].counts || !a[i].desc_kp ||
+        !b[i].desc_kp)
+      return RIFT2_E_INVAL;
+    const rift2_matches& m = out[i];
+    if (!m.q_desc || !m.nn_desc || !m.kp_a || !m.kp_b || !m.d1 || !m.d2 || !m.near_tie ||
+        !m.count)
+      return RIFT2_E_INVAL;
+    if (m.cap < 2 * c->p.max_keypoints) return RIFT2_E_CAPACITY;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int step = (c->p.flags & RIFT2_FLAG_NO_GROUPING) ? 1 : MAXB;
+  for (int i0 = 0; i0 < n; i0 += step) {
+    int g = n - i0 < step ? n - i0 : step;
+    MatchPtrs mp{};
+    for (int k = 0; k < g; ++k) {
+      const rift2_features& fa = a[i0 + k];
+      const rift2_features& fb = b[i0 + k];
+      const rift2_matches& m = out[i0 + k];
+      mp.desc_a[k] = fa.desc;
+      mp.desc_b[k] = fb.desc;
+      mp.counts_a[k] = fa.counts;
+      mp.counts_b[k] = fb.counts;
+      mp.desc_kp_a[k] = fa.desc_kp;
+      mp.desc_kp_b[k] = fb.desc_kp;
+      mp.q_desc[k] = m.q_desc;
+      mp.nn_desc[k] = m.nn_desc;
+      mp.kp_a[k] = m.kp_a;
+      mp.kp_b[k] = m.kp_b;
+      mp.d1[k] = m.d1;
+      mp.d2[k] = m.d2;
+      mp.near_tie[k] = m.near_tie;
+      mp.count[k] = m.count;
+    }
+    RIFT2_CU(launch_match_simt(mp, g, 2 * c->p.max_keypoints, st));
+  }
+  return RIFT2_OK;
+}
+
+int rift2_fft2(rift2_ctx* c, int n, const float* img, int H, int W, float* out, void* stream) {
+  if (!c || n < 1 || !img || !out) return RIFT2_E_INVAL;
+  int rc = check_size(H, W);
+  if (rc) return rc;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FftPlan ph{}, pw{};
+  rc = get_plan(c, H, st, &ph);
+  if (rc) return rc;
+  rc = get_plan(c, W, st, &pw);
+  if (rc) return rc;
+  for (int i0 = 0; i0 < n; i0 += 65535) {
+    int g = n - i0 < 65535 ? n - i0 : 65535;
+    RIFT2_CU(launch_fft2_forward(nullptr, img + (size_t)i0 * H * W,
+                                 reinterpret_cast<float2*>(out) + (size_t)i0 * H * W, g, H, W, ph,
+                                 pw, st));
+  }
+  return RIFT2_OK;
+}
+
+int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_features* out,
+                 void* stream) {
+  if (!c || n < 1 || !moment || !out || H < 16 || W < 16) return RIFT2_E_INVAL;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_features(c, out[i], false);
+    if (rc) return rc;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long P = (long long)H * W;
+  for (int i0 = 0; i0 < n; i0 += MAXB) {
+    int g = n - i0 < MAXB ? n - i0 : MAXB;
+    Layout L = extract_layout(g, H, W, c->p.max_keypoints, false);
+    int rc = ensure_ws(c, L.total);
+    if (rc) return rc;
+    unsigned* minmax = at<unsigned>(c->ws, L.minmax);
+    unsigned* ccount = at<unsigned>(c->ws, L.ccount);
+    init_group<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
+    const float* m = moment + (size_t)i0 * P;
+    minmax_kernel<<<dim3(256, g), 256, 0, st>>>(m, P, minmax);
+    FeatPtrs fp = feat_ptrs(out + i0, g);
+    DetectWs dw{minmax, at<unsigned long long>(c->ws, L.cand), ccount, L.cap_cand};
+    RIFT2_CU(launch_detect(m, g, H, W, c->kp, dw, fp, st));
+  }
+  return RIFT2_OK;
+}
+
+int rift2_describe(rift2_ctx* c, int n, const unsigned char* mim, int H, int W,
+                   rift2_features* feats, void* stream) {
+  if (!c || n < 1 || !mim || !feats || H < RIFT2_PATCH || W < RIFT2_PATCH) return RIFT2_E_INVAL;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_features(c, feats[i], true);
+    if (rc) return rc;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i0 = 0; i0 < n; i0 += MAXB) {
+    int g = n - i0 < MAXB ? n - i0 : MAXB;
+    Layout L = extract_layout(g, H, W, c->p.max_keypoints, false);
+    int rc = ensure_ws(c, L.total);
+    if (rc) return rc;
+    unsigned char* wm = at<unsigned char>(c->ws, L.mim);
+    RIFT2_CU(cudaMemcpy2DAsync(wm, L.mim_pitch, mim + (size_t)i0 * H * W, W, W, (size_t)g * H,
+                               cudaMemcpyDeviceToDevice, st));
+    CUtensorMap tm;
+    rc = make_mim_map(c, &tm, wm, g, H, L.mim_pitch);
+    if (rc) return rc;
+    FeatPtrs fp = feat_ptrs(feats + i0, g);
+    DescribeWs dsw{at<unsigned short>(c->ws, L.raw), at<unsigned>(c->ws, L.info),
+                   at<int>(c->ws, L.off), c->status};
+    RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
+  }
+  return RIFT2_OK;
+}
+
+}  // extern "C"
