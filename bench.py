@@ -1,0 +1,352 @@
+"""Benchmark of the RIFT2 hot path on GB300: pairs/s at 1024x1024.
+
+One step = extract(A) + extract(B) + match(A -> B) for every pair of one batch of
+synthetic 1024^2 pairs (400 blobs, 200 segments, random rotation, intensity remap and
+gamma speckle; at most 5000 keypoints per image).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--pairs B] [--impl ours|reference]
+
+Multi-GPU: independent replicas (the pairs shard with no exchange step); launched with
+torch.distributed.run, one rank per GPU, timing = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s at 1024x1024 (extract A + extract B + NN match A->B)"
+H = W = 1024
+MAX_KP = 5000
+ROTATE = 4   # input batches rotated between steps
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- roofline model
+# Algorithmic bytes per pixel of one image for each stage (minimal traffic of the
+# two-pass schedule): the column pass reads the spectrum once (8 B) and writes 24
+# complex responses (192 B); the row pass reads them (192 B) and writes Er, q, |EO_0|
+# for 6 orientations (72 B) and the MIM (1 B).
+STAGE_BYTES_PER_PX = {"fft_fwd": 16.0, "lg_cols": 200.0, "lg_rows": 265.0, "noise": 24.0,
+                      "moment": 52.0, "detect": 4.0}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_pair_seconds(size: int, max_kp: int, seed: int) -> float:
+    import oracle
+    import synth
+    pr = synth.make_pair(size, size, seed, angle_deg=None)
+    p = oracle.Params(max_keypoints=max_kp)
+    t0 = time.perf_counter()
+    fa = oracle.extract(pr.a.astype(np.float64), p)
+    fb = oracle.extract(pr.b.astype(np.float64), p)
+    oracle.match(fa.desc, fb.desc)
+    return time.perf_counter() - t0
+
+
+def reference_sample_size(steps: int, warmup: int) -> int:
+    # ~25 s per 1024^2 pair on one host: keep the whole run near two minutes
+    for s in (1024, 768, 512, 384, 256):
+        if (steps + warmup) * 25.0 * (s / 1024.0) ** 2 <= 150.0:
+            return s
+    return 256
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    s = reference_sample_size(args.steps, args.warmup)
+    frac = (s / 1024.0) ** 2
+    kp = max(100, int(round(MAX_KP * frac)))
+    for i in range(args.warmup):
+        oracle_pair_seconds(s, kp, 20231001 + i)
+    times = [oracle_pair_seconds(s, kp, 20232001 + i) for i in range(args.steps)]
+    t = sum(times) / len(times)
+    value = frac / t
+    sample = (f"each step: one {s}x{s} pair (2 FP64 oracle extracts with <= {kp} keypoints + "
+              f"brute-force match), credited as {frac:.4f} of a 1024^2 pair (pixel ratio)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1024x1024 synthetic multimodal pairs", "pairs_per_step": frac,
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2303_00319_gb300 as pkg
+    import synth
+    from paper_2303_00319_gb300 import _build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    _build.build()
+    B = args.pairs
+    flags = pkg.FLAG_PLAIN_MATCH
+    ctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=flags), device=local,
+                      hbm_budget=96 << 30)
+
+    # inputs: ROTATE batches of B pairs, distinct per rank; pinned host copies for e2e
+    host = []
+    for r in range(ROTATE):
+        batch = []
+        for b in range(B):
+            pr = synth.make_pair(H, W, synth.pair_seed(1, 100000 * rank + r * B + b),
+                                 angle_deg=None, n_blobs=400, n_segments=200)
+            batch += [pr.a, pr.b]
+        host.append(torch.from_numpy(np.stack(batch)).pin_memory())
+    devb = [h.to(dev) for h in host]
+    feats = [ctx.alloc_features() for _ in range(2 * B)]
+    matches = [ctx.alloc_matches() for _ in range(B)]
+    stream = torch.cuda.current_stream()
+
+    def step(imgs):
+        ctx.extract([imgs[i] for i in range(2 * B)], feats, stream=stream)
+        ctx.match(feats[0::2], feats[1::2], matches, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        step(devb[i % ROTATE])
+    ctx.sync()
+    ctx.profile_read()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.set_profiling(True)
+    launches0 = ctx.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        step(devb[i % ROTATE])
+        evs[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = ctx.launch_count() - launches0
+    ctx.set_profiling(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof = ctx.profile_read()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    out_h = [torch.empty(2 * MAX_KP * 2 + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
+    barrier()
+    for i in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        imgs = host[i % ROTATE].to(dev, non_blocking=True)
+        step(imgs)
+        for b in range(B):
+            m = matches[b]
+            out_h[b][:2 * MAX_KP].copy_(m.nn_desc, non_blocking=True)
+            out_h[b][2 * MAX_KP:4 * MAX_KP].copy_(m.d1.view(torch.int32), non_blocking=True)
+            out_h[b][4 * MAX_KP:].copy_(m.count, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_total = torch.tensor([sum(e2e_ms)], device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_total, op=dist.ReduceOp.MAX)
+    e2e_value = world * B * args.steps / (float(e2e_total.item()) / 1000.0)
+    h2d = int(host[0].numel() * 4)
+    d2h = int(B * (2 * MAX_KP * 2 + 1) * 4)
+
+    # plain form: one pair per call, no grouping, CUDA-core matcher
+    plain = None
+    if not args.no_plain:
+        pctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP,
+                                              flags=pkg.FLAG_PLAIN_MATCH | pkg.FLAG_NO_GROUPING),
+                           device=local, hbm_budget=16 << 30)
+        pf = [pctx.alloc_features() for _ in range(2)]
+        pm = [pctx.alloc_matches()]
+        lat = []
+        for i in range(2 + min(args.steps, 8)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            imgs = devb[i % ROTATE]
+            e0.record(stream)
+            pctx.extract([imgs[0], imgs[1]], pf, stream=stream)
+            pctx.match([pf[0]], [pf[1]], pm, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 2:
+                lat.append(e0.elapsed_time(e1))
+        lat.sort()
+        plain = {"value": 1000.0 / statistics.mean(lat), "unit": "pairs/s",
+                 "latency_ms_p50": lat[len(lat) // 2],
+                 "latency_ms_p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                 "form": "one pair per call, no launch grouping, CUDA-core matcher"}
+        pctx.close()
+
+    # roofline of the dominant HBM-bound stage
+    peak, peak_kind = load_peaks()
+    dom = max((k for k in STAGE_BYTES_PER_PX if prof[k][1] > 0), key=lambda k: prof[k][0])
+    ms_dom, n_dom = prof[dom]
+    imgs_per_launch = 2 * B
+    bytes_per_launch = STAGE_BYTES_PER_PX[dom] * H * W * imgs_per_launch
+    achieved = bytes_per_launch / (ms_dom / n_dom / 1000.0) / 1e9
+    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tcpu = oracle_pair_seconds(H, MAX_KP, synth.pair_seed(1, 0))
+        cpu = {"value": 1.0 / tcpu, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one 1024x1024 pair (2 FP64 oracle extracts + brute-force match); "
+                         "numpy FFT runs on one core, the matching matmul on the BLAS threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "1024x1024 synthetic multimodal pairs (400 blobs, 200 segments, "
+                                   "random rotation, 1-v^0.6 remap, gamma speckle), <=5000 kp",
+                       "pairs_per_step": B, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs rotate over {ROTATE} batches ({ROTATE * 2 * B * 4} MB) and "
+                             "each step streams ~0.3 GB of workspace per image, > L2"},
+            "mpix_per_s": value * 2 * H * W / 1e6,
+            "plain_form": plain,
+            "stage_ms_per_step": stage_ms,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--pairs", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -213,6 +213,35 @@ int rift2_sync(rift2_ctx* ctx, void* stream);
 int rift2_destroy(rift2_ctx* ctx);
 
 /* ------------------------------------------------------------------------------
+ * Tracing.  With profiling on, the context brackets every stage of every launch group
+ * with CUDA events on the call's stream (a few microseconds of overhead per stage);
+ * rift2_profile_read waits for those events and reports the accumulated device time.
+ * The launch counter counts every kernel the library enqueues, profiling on or off.
+ * ---------------------------------------------------------------------------- */
+enum {
+  RIFT2_STAGE_FFT_FWD = 0,   /* forward 2-D DFT of the images                       */
+  RIFT2_STAGE_LG_COLS = 1,   /* column pass of the 24 filtered inverse DFTs          */
+  RIFT2_STAGE_LG_ROWS = 2,   /* row pass + amplitude / MIM / PC-energy reductions    */
+  RIFT2_STAGE_NOISE = 3,     /* exact median of |EO_0,o| and noise thresholds        */
+  RIFT2_STAGE_MOMENT = 4,    /* phase congruency and maximum moment                  */
+  RIFT2_STAGE_DETECT = 5,    /* FAST + NMS + top-K                                   */
+  RIFT2_STAGE_DESCRIBE = 6,  /* patch histograms, dominant index, descriptors        */
+  RIFT2_STAGE_MATCH = 7,     /* nearest-neighbour matching                           */
+  RIFT2_N_STAGES = 8
+};
+
+/* Turns per-stage event timing on (1) or off (0). */
+int rift2_set_profiling(rift2_ctx* ctx, int enable);
+
+/* Waits for the recorded events and writes, for each stage s < n, the device time
+ * accumulated since the last reset (ms[s]) and the number of timed launches of that
+ * stage (count[s]); either array may be NULL.  Then clears the accumulators. */
+int rift2_profile_read(rift2_ctx* ctx, int n, double* ms, long long* count);
+
+/* Kernels enqueued by this context since it was created. */
+long long rift2_launch_count(const rift2_ctx* ctx);
+
+/* ------------------------------------------------------------------------------
  * Stage entry points.  Each runs one stage of the pipeline on caller-supplied inputs
  * so that the stage can be checked against the oracle in isolation (an oracle near-tie
  * upstream then cannot cascade).  Same conventions as above.

@@ -23,8 +23,10 @@ DESC_DIM = CELLS * CELLS * NO
 
 # Every symbol include/rift2.h declares.
 EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_extract",
-           "rift2_match", "rift2_sync", "rift2_destroy", "rift2_fft2", "rift2_detect",
+           "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
+           "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
            "rift2_describe")
+STAGES = ("fft_fwd", "lg_cols", "lg_rows", "noise", "moment", "detect", "describe", "match")
 
 
 class Params(C.Structure):
@@ -79,6 +81,11 @@ def lib():
                                   C.POINTER(FeaturesC), C.POINTER(MatchesC), C.c_void_p]
         L.rift2_sync.argtypes = [C.c_void_p, C.c_void_p]
         L.rift2_destroy.argtypes = [C.c_void_p]
+        L.rift2_set_profiling.argtypes = [C.c_void_p, C.c_int]
+        L.rift2_profile_read.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_longlong)]
+        L.rift2_launch_count.argtypes = [C.c_void_p]
+        L.rift2_launch_count.restype = C.c_longlong
         L.rift2_fft2.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                  C.c_void_p]
         L.rift2_detect.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
@@ -265,6 +272,21 @@ class Context:
 
     def sync(self, stream=None):
         _check(lib().rift2_sync(self._h, _stream(stream)), "rift2_sync")
+
+    # ---- tracing
+    def set_profiling(self, on: bool):
+        _check(lib().rift2_set_profiling(self._h, int(bool(on))), "rift2_set_profiling")
+
+    def profile_read(self) -> dict:
+        """{stage: (ms, launches)} accumulated since the last read (waits for the events)."""
+        n = len(STAGES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_longlong * n)()
+        _check(lib().rift2_profile_read(self._h, n, ms, cnt), "rift2_profile_read")
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def launch_count(self) -> int:
+        return int(lib().rift2_launch_count(self._h))
 
     # ---- stage entry points
     def fft2(self, img, stream=None):

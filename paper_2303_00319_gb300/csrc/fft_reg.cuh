@@ -1,0 +1,163 @@
+// Register-tiled Stockham FFT for power-of-two lengths: a group of T threads owns one
+// N-point transform, each thread holding E = N / T elements in registers.  Each pass of
+// radix R runs E / R radix-R butterflies per thread entirely in registers; passes talk
+// through one padded shared-memory buffer per transform, so an N = 1024 transform is two
+// radix-32 passes with a single exchange and only warp-level synchronisation.
+//
+// Pass with radix R after NS = product of the earlier radices, butterfly j (k = j mod NS):
+//     v_r = x[j + r N/R] * W_{NS R}^{k r},  v = DFT_R(v),  y[(j - k) R + k + r NS] = v_r.
+#pragma once
+
+#include "fft.cuh"
+
+namespace rift2 {
+
+// cos / sin (2 pi m / 32), m = 0..31: the roots of unity the in-register DFTs use.
+__device__ constexpr float kCos32[32] = {
+    1.000000000e+00f,  9.807852804e-01f,  9.238795325e-01f,  8.314696123e-01f,
+    7.071067812e-01f,  5.555702330e-01f,  3.826834324e-01f,  1.950903220e-01f,
+    0.0f,              -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
+    -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f,
+    -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f,
+    -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f,
+    0.0f,              1.950903220e-01f,  3.826834324e-01f,  5.555702330e-01f,
+    7.071067812e-01f,  8.314696123e-01f,  9.238795325e-01f,  9.807852804e-01f};
+__device__ constexpr float kSin32[32] = {
+    0.0f,              1.950903220e-01f,  3.826834324e-01f,  5.555702330e-01f,
+    7.071067812e-01f,  8.314696123e-01f,  9.238795325e-01f,  9.807852804e-01f,
+    1.000000000e+00f,  9.807852804e-01f,  9.238795325e-01f,  8.314696123e-01f,
+    7.071067812e-01f,  5.555702330e-01f,  3.826834324e-01f,  1.950903220e-01f,
+    0.0f,              -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
+    -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f,
+    -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f,
+    -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f};
+
+// exp(-+ 2 pi i m / R) for R | 32 (forward sign; INV conjugates).  m is a compile-time
+// constant after unrolling, so the table reads fold into immediates.
+template <int R, bool INV>
+__device__ __forceinline__ float2 wr(int m) {
+  const int e = (m * (32 / R)) & 31;
+  return make_float2(kCos32[e], INV ? kSin32[e] : -kSin32[e]);
+}
+
+// In-register DFT of length R in natural order (R = 1, 2, 4, 8, 16, 32).  R = 16, 32 are
+// split as R1 x 4: R1-point DFTs over n1 of x[4 n1 + n2], internal twiddles W_R^{n2 k1},
+// then 4-point DFTs over n2, with output k1 + R1 k2.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2* v) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v);
+  } else if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else {
+    constexpr int R2 = 4, R1 = R / 4;
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      float2 t[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
+      dft_reg<R1, INV>(t);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1)
+        v[R2 * k1 + n2] = (n2 * k1 == 0) ? t[k1] : cmul(t[k1], wr<R, INV>(n2 * k1));
+    }
+    float2 out[R];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      float2 t[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) t[n2] = v[R2 * k1 + n2];
+      dft4<INV>(t);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) out[k1 + R1 * k2] = t[k2];
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = out[i];
+  }
+}
+
+// Padded index into a transform's exchange buffer: one spare slot per 32 elements keeps
+// the strided butterfly stores free of bank conflicts.
+__device__ __forceinline__ int xpad(int i) { return i + (i >> 5); }
+template <int N>
+struct XBuf {
+  static constexpr int SIZE = N + N / 32 + 2;   // +2: staggers consecutive buffers' banks
+};
+
+// One pass.  Inputs come from `ld(index)` (FIRST) or the exchange buffer; outputs go to
+// `st(index, value)` (LAST) or the exchange buffer.  `sync()` synchronises the group.
+template <int N, int T, int R, int NS, bool INV, bool FIRST, bool LAST, class Ld, class St,
+          class Sync>
+__device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __restrict__ tw,
+                                         Ld& ld, St& st, Sync& sync) {
+  constexpr int E = N / T, B = E / R, M = N / R;
+  static_assert(E % R == 0, "radix must divide the elements per thread");
+  float2 v[B][R];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const int j = t + T * i;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i][r] = FIRST ? ld(j + r * M) : xb[xpad(j + r * M)];
+  }
+  if (!FIRST) sync();   // every read of xb is done before this pass overwrites it
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const int j = t + T * i;
+    const int k = j % NS;
+    if constexpr (NS > 1) {
+      constexpr int TSTEP = N / (NS * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle<INV>(tw, k * r * TSTEP));
+    }
+    dft_reg<R, INV>(v[i]);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (LAST) st(base + r * NS, v[i][r]);
+      else xb[xpad(base + r * NS)] = v[i][r];
+    }
+  }
+  if (!LAST) sync();
+}
+
+// Full transform as up to three passes of radices R0, R1, R2 (1 = unused).
+template <int N, int T, int R0, int R1, int R2, bool INV, class Ld, class St, class Sync>
+__device__ __forceinline__ void group_fft(float2* xb, int t, const float2* __restrict__ tw, Ld& ld,
+                                          St& st, Sync& sync) {
+  static_assert(R0 * R1 * R2 == N, "radices must multiply to N");
+  if constexpr (R1 == 1) {
+    reg_pass<N, T, R0, 1, INV, true, true>(xb, t, tw, ld, st, sync);
+  } else if constexpr (R2 == 1) {
+    reg_pass<N, T, R0, 1, INV, true, false>(xb, t, tw, ld, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, true>(xb, t, tw, ld, st, sync);
+  } else {
+    reg_pass<N, T, R0, 1, INV, true, false>(xb, t, tw, ld, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, false>(xb, t, tw, ld, st, sync);
+    reg_pass<N, T, R2, R0 * R1, INV, false, true>(xb, t, tw, ld, st, sync);
+  }
+}
+
+// Register-path shapes: transform length -> threads per transform and pass radices.
+template <int N>
+struct RegShape;
+template <>
+struct RegShape<256> {
+  static constexpr int T = 16, R0 = 16, R1 = 16, R2 = 1;
+};
+template <>
+struct RegShape<512> {
+  static constexpr int T = 16, R0 = 32, R1 = 16, R2 = 1;
+};
+template <>
+struct RegShape<1024> {
+  static constexpr int T = 32, R0 = 32, R1 = 32, R2 = 1;
+};
+template <>
+struct RegShape<2048> {
+  static constexpr int T = 64, R0 = 32, R1 = 8, R2 = 8;
+};
+
+}  // namespace rift2

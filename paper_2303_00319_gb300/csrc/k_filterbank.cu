@@ -8,6 +8,7 @@
 //                         with the per-pixel reductions (amplitude sum A_o, MIM argmax,
 //                         phase-congruency energy Er_o, spread weight / A_o, |EO_0,o|).
 #include "fft.cuh"
+#include "fft_reg.cuh"
 #include "kernels.h"
 
 namespace rift2 {
@@ -23,11 +24,34 @@ __global__ void twiddle_gen(float2* tw, int n) {
 }
 
 // ------------------------------------------------------------------ forward 2-D DFT
+// The large DC term dominates the rounding error of an FP32 FFT.  Each 1-D transform
+// therefore runs on its input minus the input's mean and gets its bin 0 back as the
+// input sum afterwards: DFT(x) = DFT(x - m) + m N delta_0 exactly, so the result is the
+// same transform with an error set by the non-DC content only.
+__device__ __forceinline__ void seg_means(const float2* a, int nseg, int len, int es, int ss,
+                                          float2* mean) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int g = warp; g < nseg; g += nw) {
+    float sx = 0.f, sy = 0.f;
+    for (int i = lane; i < len; i += 32) {
+      float2 v = a[g * ss + i * es];
+      sx += v.x;
+      sy += v.y;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, d);
+      sy += __shfl_xor_sync(0xffffffffu, sy, d);
+    }
+    if (lane == 0) mean[g] = make_float2(sx / len, sy / len);
+  }
+}
+
 // Rows of real images: tile of `tr` rows, complex FFT with zero imaginary part.
 __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restrict__ dense,
                                                 float2* __restrict__ spec, int H, int W, int tr,
                                                 FftPlan pw) {
   extern __shared__ float2 sm[];
+  __shared__ float2 mean[256];
   const int img = blockIdx.y;
   const int r0 = blockIdx.x * tr;
   const int nel = tr * W;
@@ -41,11 +65,17 @@ __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restr
     a[i] = make_float2(v, 0.f);
   }
   __syncthreads();
+  seg_means(a, tr, W, 1, W, mean);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) a[i].x -= mean[i / W].x;
+  __syncthreads();
   float2* res = fft_smem<false, false>(a, b, pw, tr, W, 1);
   float2* dst = spec + (size_t)img * H * W;
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    int r = r0 + i / W;
-    if (r < H) dst[(size_t)r * W + (i % W)] = res[i];
+    int r = r0 + i / W, x = i % W;
+    float2 v = res[i];
+    if (x == 0) v.x += mean[i / W].x * W;
+    if (r < H) dst[(size_t)r * W + x] = v;
   }
 }
 
@@ -53,6 +83,7 @@ __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restr
 __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H, int W, int tc,
                                                 FftPlan ph) {
   extern __shared__ float2 sm[];
+  __shared__ float2 mean[64];
   const int img = blockIdx.y;
   const int c0 = blockIdx.x * tc;
   const int nel = H * tc;
@@ -64,10 +95,23 @@ __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H
     a[i] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
+  seg_means(a, tc, H, tc, 1, mean);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    float2 m = mean[i % tc];
+    a[i].x -= m.x;
+    a[i].y -= m.y;
+  }
+  __syncthreads();
   float2* res = fft_smem<false, true>(a, b, ph, tc, 1, tc);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     int v = i / tc, c = i % tc;
-    if (c0 + c < W) base[(size_t)v * W + c0 + c] = res[i];
+    float2 r = res[i];
+    if (v == 0) {
+      r.x += mean[c].x * H;
+      r.y += mean[c].y * H;
+    }
+    if (c0 + c < W) base[(size_t)v * W + c0 + c] = r;
   }
 }
 
@@ -221,12 +265,192 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
   }
 }
 
+// ------------------------------------------------------- register-tiled fast path
+// Column pass for power-of-two H: one group of T threads per column, COLS columns per
+// CTA.  F * R_s is staged once per CTA (coalesced rows of COLS columns); each orientation
+// multiplies the angular window in the first FFT pass, and the results are written back
+// through the exchange buffers as coalesced row segments.
+constexpr int REG_THREADS = 256;
+
+template <int H>
+__global__ void __launch_bounds__(REG_THREADS) lg_cols_reg(const float2* __restrict__ spec,
+                                                           float2* __restrict__ scratch, int W,
+                                                           const float2* __restrict__ twh,
+                                                           KParams kp) {
+  using S = RegShape<H>;
+  constexpr int T = S::T;
+  constexpr int COLS = REG_THREADS / T;
+  constexpr int XS = XBuf<H>::SIZE;
+  extern __shared__ float2 sm[];
+  float2* base = sm;               // [COLS][XS]
+  float2* xbuf = sm + COLS * XS;   // [COLS][XS]
+  const int s = blockIdx.y, img = blockIdx.z;
+  const int c0 = blockIdx.x * COLS;
+  const int tid = threadIdx.x;
+  const float2* F = spec + (size_t)img * H * W;
+  const float log_fs = kp.log_fs[s];
+  for (int i = tid; i < H * COLS; i += REG_THREADS) {
+    const int v = i / COLS, c = i % COLS, u = c0 + c;
+    float2 f = make_float2(0.f, 0.f);
+    if (u < W) {
+      const float fu = fftfreq(u, W), fv = fftfreq(v, H);
+      const float rs = lg_radial(fu * fu + fv * fv, log_fs, kp);
+      const float2 x = __ldg(F + (size_t)v * W + u);
+      f = make_float2(x.x * rs, x.y * rs);
+    }
+    base[c * XS + xpad(v)] = f;
+  }
+  __syncthreads();
+  const int col = tid / T, t = tid % T;
+  const int u = c0 + col;
+  const float fu = fftfreq(u, W);
+  float2* xb = xbuf + col * XS;
+  const float2* bc = base + col * XS;
+  auto sync = [] {
+    if constexpr (T <= 32) __syncwarp();
+    else __syncthreads();
+  };
+  for (int o = 0; o < NO; ++o) {
+    const float co = kp.cos_o[o], so = kp.sin_o[o];
+    auto ld = [&](int v) -> float2 {
+      const float fv = fftfreq(v, H);
+      const float r2 = fu * fu + fv * fv;
+      const float g = (r2 > 0.f && u < W) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
+      const float2 x = bc[xpad(v)];
+      return make_float2(x.x * g, x.y * g);
+    };
+    auto st = [&](int v, float2 val) { xb[xpad(v)] = val; };
+    group_fft<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, ld, st, sync);
+    __syncthreads();
+    float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W;
+    for (int i = tid; i < H * COLS; i += REG_THREADS) {
+      const int v = i / COLS, c = i % COLS;
+      if (c0 + c < W) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
+    }
+    __syncthreads();
+  }
+}
+
+// Row pass for power-of-two W: one group per (row, scale) transform, ROWS rows per CTA;
+// after each orientation's four scales are in shared memory every thread reduces its
+// pixels (same formulas as lg_rows_reduce).
+template <int WN>
+__global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restrict__ scratch, int H,
+                                                           const float2* __restrict__ tww,
+                                                           KParams kp, float* __restrict__ er_out,
+                                                           float* __restrict__ q_out,
+                                                           float* __restrict__ an0_out,
+                                                           float* __restrict__ amp_out,
+                                                           unsigned char* __restrict__ mim_out,
+                                                           int mim_pitch) {
+  using S = RegShape<WN>;
+  constexpr int T = S::T;
+  constexpr int GROUPS = REG_THREADS / T;
+  constexpr int ROWS = GROUPS / NS;
+  constexpr int XS = XBuf<WN>::SIZE;
+  constexpr int PIX = ROWS * WN / REG_THREADS;
+  static_assert(ROWS >= 1 && PIX >= 1, "row tile");
+  extern __shared__ float2 sm[];   // [GROUPS][XS], group g = (row g / NS, scale g % NS)
+  const int img = blockIdx.y;
+  const int row0 = blockIdx.x * ROWS;
+  const int tid = threadIdx.x;
+  const int grp = tid / T, t = tid % T;
+  const int rr = grp / NS, sc = grp % NS;
+  const int row = row0 + rr;
+  float2* xb = sm + grp * XS;
+  const size_t P = (size_t)H * WN;
+  const float scale = 1.f / ((float)H * (float)WN);
+  float best[PIX];
+  int besto[PIX];
+#pragma unroll
+  for (int k = 0; k < PIX; ++k) { best[k] = -1.f; besto[k] = 0; }
+  auto sync = [] {
+    if constexpr (T <= 32) __syncwarp();
+    else __syncthreads();
+  };
+  for (int o = 0; o < NO; ++o) {
+    const float2* src = scratch + (((size_t)img * NS + sc) * NO + o) * P + (size_t)row * WN;
+    auto ld = [&](int x) -> float2 { return row < H ? __ldg(src + x) : make_float2(0.f, 0.f); };
+    auto st = [&](int x, float2 val) { xb[xpad(x)] = val; };
+    group_fft<WN, T, S::R0, S::R1, S::R2, true>(xb, t, tww, ld, st, sync);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+      const int pix = tid + REG_THREADS * k;
+      const int r2 = pix / WN, x = pix % WN;
+      if (row0 + r2 >= H) continue;
+      float e[NS], od[NS];
+      float sum_e = 0.f, sum_o = 0.f, sum_an = 0.f, max_an = 0.f, an0 = 0.f;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const float2 z = sm[(r2 * NS + s) * XS + xpad(x)];
+        e[s] = z.x * scale;
+        od[s] = z.y * scale;
+        const float an = sqrtf(e[s] * e[s] + od[s] * od[s]);
+        if (s == 0) an0 = an;
+        sum_e += e[s];
+        sum_o += od[s];
+        sum_an += an;
+        max_an = fmaxf(max_an, an);
+      }
+      const float xe = sqrtf(sum_e * sum_e + sum_o * sum_o) + kp.eps;
+      const float me = sum_e / xe, mo = sum_o / xe;
+      float energy = 0.f;
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        energy += e[s] * me + od[s] * mo - fabsf(e[s] * mo - od[s] * me);
+      const float width = (sum_an / (max_an + kp.eps) - 1.f) * kp.inv_ns1;
+      const float wgt = 1.f / (1.f + expf((kp.cutoff - width) * kp.g));
+      const float q = (sum_an > 0.f) ? wgt / sum_an : 0.f;
+      const size_t off = ((size_t)img * NO + o) * P + (size_t)(row0 + r2) * WN + x;
+      er_out[off] = energy;
+      q_out[off] = q;
+      an0_out[off] = an0;
+      if (amp_out) amp_out[off] = sum_an;
+      if (sum_an > best[k]) { best[k] = sum_an; besto[k] = o; }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < PIX; ++k) {
+    const int pix = tid + REG_THREADS * k;
+    const int r2 = pix / WN, x = pix % WN;
+    if (row0 + r2 < H)
+      mim_out[(size_t)img * H * mim_pitch + (size_t)(row0 + r2) * mim_pitch + x] =
+          (unsigned char)besto[k];
+  }
+}
+
+template <int H>
+static cudaError_t cols_reg(const float2* spec, float2* scratch, int nimg, int W,
+                            const FftPlan& ph, const KParams& kp, cudaStream_t st) {
+  constexpr int COLS = REG_THREADS / RegShape<H>::T;
+  const size_t sm = 2 * (size_t)COLS * XBuf<H>::SIZE * sizeof(float2);
+  cudaFuncSetAttribute(lg_cols_reg<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  lg_cols_reg<H><<<dim3((W + COLS - 1) / COLS, NS, nimg), REG_THREADS, sm, st>>>(spec, scratch, W,
+                                                                                ph.tw, kp);
+  return cudaGetLastError();
+}
+
+template <int WN>
+static cudaError_t rows_reg(const float2* scratch, int nimg, int H, const FftPlan& pw,
+                            const KParams& kp, float* er, float* q, float* an0, float* amp,
+                            unsigned char* mim, int mim_pitch, cudaStream_t st) {
+  constexpr int GROUPS = REG_THREADS / RegShape<WN>::T;
+  constexpr int ROWS = GROUPS / NS;
+  const size_t sm = (size_t)GROUPS * XBuf<WN>::SIZE * sizeof(float2);
+  cudaFuncSetAttribute(lg_rows_reg<WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  lg_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_THREADS, sm, st>>>(
+      scratch, H, pw.tw, kp, er, q, an0, amp, mim, mim_pitch);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 void launch_twiddles(float2* tw, int n, cudaStream_t st) {
   twiddle_gen<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
 }
 
-static int rows_tile(int W) { return W >= 4096 ? 1 : 4096 / W; }
+static int rows_tile(int W) { return W >= 4096 ? 1 : (4096 / W > 256 ? 256 : 4096 / W); }
 static int cols_tile(int H) {
   int tc = 8192 / H;
   if (tc > 16) tc = 16;
@@ -250,15 +474,33 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
   return cudaGetLastError();
 }
 
-cudaError_t launch_filterbank(const float2* spec, float2* scratch, int nimg, int H, int W,
-                              const FftPlan& ph, const FftPlan& pw, const KParams& kp,
-                              float* er, float* q, float* an0, float* amp, unsigned char* mim,
-                              int mim_pitch, cudaStream_t st) {
+cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
+                           const FftPlan& ph, const KParams& kp, cudaStream_t st) {
+  switch (H) {
+    case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, st);
+    case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, st);
+    case 1024: return cols_reg<1024>(spec, scratch, nimg, W, ph, kp, st);
+    case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, st);
+    default: break;
+  }
   int tc = cols_tile(H);
   size_t sm2 = 3 * (size_t)tc * H * sizeof(float2);
   cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   lg_cols_inverse<<<dim3((W + tc - 1) / tc, NS, nimg), 512, sm2, st>>>(spec, scratch, H, W, tc,
                                                                        ph, kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
+                           const KParams& kp, float* er, float* q, float* an0, float* amp,
+                           unsigned char* mim, int mim_pitch, cudaStream_t st) {
+  switch (W) {
+    case 256: return rows_reg<256>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
+    case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
+    case 1024: return rows_reg<1024>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
+    case 2048: return rows_reg<2048>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
+    default: break;
+  }
   size_t sm3 = 2 * (size_t)NS * W * sizeof(float2);
   cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
   lg_rows_reduce<<<dim3(H, nimg), 512, sm3, st>>>(scratch, H, W, pw, kp, er, q, an0, amp, mim,

@@ -14,10 +14,11 @@ void launch_twiddles(float2* tw, int n, cudaStream_t st);
 cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
                                 int H, int W, const FftPlan& ph, const FftPlan& pw,
                                 cudaStream_t st);
-cudaError_t launch_filterbank(const float2* spec, float2* scratch, int nimg, int H, int W,
-                              const FftPlan& ph, const FftPlan& pw, const KParams& kp,
-                              float* er, float* q, float* an0, float* amp, unsigned char* mim,
-                              int mim_pitch, cudaStream_t st);
+cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
+                           const FftPlan& ph, const KParams& kp, cudaStream_t st);
+cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
+                           const KParams& kp, float* er, float* q, float* an0, float* amp,
+                           unsigned char* mim, int mim_pitch, cudaStream_t st);
 
 // k_pc.cu — exact median of |EO_0,o| (radix select), noise thresholds, PC, moments.
 struct MedianWs {

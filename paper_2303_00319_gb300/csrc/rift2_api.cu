@@ -24,6 +24,14 @@ struct rift2_ctx {
   int* status = nullptr;
   std::map<int, FftPlan> plans;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  // tracing
+  long long launches = 0;
+  bool prof = false;
+  struct Mark { int stage; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> free_events;
+  double acc_ms[RIFT2_N_STAGES] = {};
+  long long acc_n[RIFT2_N_STAGES] = {};
 };
 
 namespace {
@@ -80,6 +88,7 @@ int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
   float2* tw = nullptr;
   RIFT2_CU(cudaMalloc(&tw, sizeof(float2) * n));
   launch_twiddles(tw, n, st);
+  c->launches += 1;
   RIFT2_CU(cudaGetLastError());
   RIFT2_CU(cudaStreamSynchronize(st));
   pl.tw = tw;
@@ -142,6 +151,43 @@ int check_size(int H, int W) {
   if (W > 4096 || H > 8192) return RIFT2_E_UNIMPL;
   return RIFT2_OK;
 }
+
+// ------------------------------------------------------------------ tracing
+// Kernels enqueued by each launcher (kept next to the launch sequences they count).
+constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_LG_ROWS = 1, K_NOISE = 6, K_MOMENT = 1,
+              K_DETECT = 2, K_DESCRIBE = 3, K_MATCH = 1, K_INIT = 1;
+
+cudaEvent_t take_event(rift2_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct StageScope {
+  rift2_ctx* c;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageScope(rift2_ctx* c_, int stage_, cudaStream_t st_, int kernels) : c(c_), stage(stage_), st(st_) {
+    c->launches += kernels;
+    if (c->prof) {
+      a = take_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~StageScope() {
+    if (c->prof && a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, st);
+      c->marks.push_back({stage, a, b});
+    }
+  }
+};
 
 // ------------------------------------------------------------------ workspace layout
 struct Layout {
@@ -306,29 +352,51 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   FeatPtrs fp = feat_ptrs(out, g);
   unsigned* minmax = at<unsigned>(ws, L.minmax);
   unsigned* ccount = at<unsigned>(ws, L.ccount);
+  c->launches += K_INIT;
   init_group<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
   RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * 2 * 4096 * 4, st));
   float2* spec = at<float2>(ws, L.spec);
-  RIFT2_CU(launch_fft2_forward(&ip, nullptr, spec, g, H, W, ph, pw, st));
+  {
+    StageScope sc(c, RIFT2_STAGE_FFT_FWD, st, K_FFT_FWD);
+    RIFT2_CU(launch_fft2_forward(&ip, nullptr, spec, g, H, W, ph, pw, st));
+  }
   float* er = at<float>(ws, L.er);
   float* q = at<float>(ws, L.q);
   float* an0 = at<float>(ws, L.an0);
   unsigned char* mim = at<unsigned char>(ws, L.mim);
-  RIFT2_CU(launch_filterbank(spec, at<float2>(ws, L.scratch), g, H, W, ph, pw, c->kp, er, q, an0,
-                             at<float>(ws, L.amp), mim, L.mim_pitch, st));
+  float2* scratch = at<float2>(ws, L.scratch);
+  {
+    StageScope sc(c, RIFT2_STAGE_LG_COLS, st, K_LG_COLS);
+    RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, st));
+  }
+  {
+    StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, K_LG_ROWS);
+    RIFT2_CU(launch_lg_rows(scratch, g, H, W, pw, c->kp, er, q, an0, at<float>(ws, L.amp), mim,
+                            L.mim_pitch, st));
+  }
   MedianWs mw{at<unsigned>(ws, L.mhist), at<unsigned>(ws, L.mstate), at<float>(ws, L.noise)};
-  RIFT2_CU(launch_noise_threshold(an0, g, P, c->kp, mw, st));
+  {
+    StageScope sc(c, RIFT2_STAGE_NOISE, st, K_NOISE);
+    RIFT2_CU(launch_noise_threshold(an0, g, P, c->kp, mw, st));
+  }
   float* moment = at<float>(ws, L.moment);
-  RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, g, P, c->kp, moment, minmax, at<float>(ws, L.pc),
-                            st));
+  {
+    StageScope sc(c, RIFT2_STAGE_MOMENT, st, K_MOMENT);
+    RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, g, P, c->kp, moment, minmax, at<float>(ws, L.pc),
+                              st));
+  }
   DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand};
-  RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
+  {
+    StageScope sc(c, RIFT2_STAGE_DETECT, st, K_DETECT);
+    RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
+  }
   if (H >= RIFT2_PATCH && W >= RIFT2_PATCH) {
     CUtensorMap tm;
     rc = make_mim_map(c, &tm, mim, g, H, L.mim_pitch);
     if (rc) return rc;
     DescribeWs dsw{at<unsigned short>(ws, L.raw), at<unsigned>(ws, L.info), at<int>(ws, L.off),
                    c->status};
+    StageScope sc(c, RIFT2_STAGE_DESCRIBE, st, K_DESCRIBE);
     RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
   }
   return copy_debug(out, g, ws, L, H, W, st);
@@ -421,11 +489,42 @@ int rift2_destroy(rift2_ctx* c) {
   DeviceGuard dg(c->device);
   cudaDeviceSynchronize();
   for (auto& kv : c->plans) cudaFree(const_cast<float2*>(kv.second.tw));
+  for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+  for (auto e : c->free_events) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
   if (c->status) cudaFree(c->status);
   delete c;
   return RIFT2_OK;
 }
+
+int rift2_set_profiling(rift2_ctx* c, int enable) {
+  if (!c) return RIFT2_E_INVAL;
+  c->prof = enable != 0;
+  return RIFT2_OK;
+}
+
+int rift2_profile_read(rift2_ctx* c, int n, double* ms, long long* count) {
+  if (!c || n < 0) return RIFT2_E_INVAL;
+  DeviceGuard dg(c->device);
+  for (auto& m : c->marks) {
+    if (cudaEventSynchronize(m.b) != cudaSuccess) return RIFT2_E_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) != cudaSuccess) return RIFT2_E_CUDA;
+    c->acc_ms[m.stage] += t;
+    c->acc_n[m.stage] += 1;
+    c->free_events.push_back(m.a);
+    c->free_events.push_back(m.b);
+  }
+  c->marks.clear();
+  for (int s = 0; s < n && s < RIFT2_N_STAGES; ++s) {
+    if (ms) ms[s] = c->acc_ms[s];
+    if (count) count[s] = c->acc_n[s];
+  }
+  for (int s = 0; s < RIFT2_N_STAGES; ++s) { c->acc_ms[s] = 0; c->acc_n[s] = 0; }
+  return RIFT2_OK;
+}
+
+long long rift2_launch_count(const rift2_ctx* c) { return c ? c->launches : -1; }
 
 int rift2_sync(rift2_ctx* c, void* stream) {
   if (!c) return RIFT2_E_INVAL;
@@ -511,6 +610,7 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
       mp.near_tie[k] = m.near_tie;
       mp.count[k] = m.count;
     }
+    StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH);
     RIFT2_CU(launch_match_simt(mp, g, 2 * c->p.max_keypoints, st));
   }
   return RIFT2_OK;
@@ -529,6 +629,7 @@ int rift2_fft2(rift2_ctx* c, int n, const float* img, int H, int W, float* out, 
   if (rc) return rc;
   for (int i0 = 0; i0 < n; i0 += 65535) {
     int g = n - i0 < 65535 ? n - i0 : 65535;
+    c->launches += K_FFT_FWD;
     RIFT2_CU(launch_fft2_forward(nullptr, img + (size_t)i0 * H * W,
                                  reinterpret_cast<float2*>(out) + (size_t)i0 * H * W, g, H, W, ph,
                                  pw, st));
@@ -553,6 +654,7 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
     if (rc) return rc;
     unsigned* minmax = at<unsigned>(c->ws, L.minmax);
     unsigned* ccount = at<unsigned>(c->ws, L.ccount);
+    c->launches += K_INIT + 1 + K_DETECT;
     init_group<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
     const float* m = moment + (size_t)i0 * P;
     minmax_kernel<<<dim3(256, g), 256, 0, st>>>(m, P, minmax);
@@ -584,6 +686,7 @@ int rift2_describe(rift2_ctx* c, int n, const unsigned char* mim, int H, int W,
     rc = make_mim_map(c, &tm, wm, g, H, L.mim_pitch);
     if (rc) return rc;
     FeatPtrs fp = feat_ptrs(feats + i0, g);
+    c->launches += K_DESCRIBE;
     DescribeWs dsw{at<unsigned short>(c->ws, L.raw), at<unsigned>(c->ws, L.info),
                    at<int>(c->ws, L.off), c->status};
     RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));

@@ -1,0 +1,289 @@
+"""GPU parity: every stage of the CUDA path through the C ABI against the FP64 oracle.
+
+Stage tests feed the oracle's upstream outputs to the GPU stage, so a near tie upstream
+cannot cascade.  End-to-end tests compare the whole path on the seeded pairs.
+
+Tolerances (float maps): the CUDA path computes the filter bank in FP32; its FFT has an
+error of ~1e-7 of the spectrum's scale, so element-wise errors are measured against
+max(|oracle|, floor * max|oracle|).  Integer outputs (MIM, keypoints, dominant indices,
+descriptor counts, NN indices) must be identical except at oracle-certified near ties
+(relative top-two margin below 1e-5).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from parity_util import compare_keypoints, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2303_00319_gb300 as p
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return p
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def small(pkg, dev):
+    """256^2 pair (30 degrees), <= 500 keypoints: oracle with all maps + GPU with debug maps."""
+    pr = synth.config_pair(0)
+    p = O.Params(max_keypoints=500)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=500), device=0)
+    oa = O.extract(pr.a.astype(np.float64), p, keep_maps=True)
+    ob = O.extract(pr.b.astype(np.float64), p, keep_maps=True)
+    fa, fb = ctx.extract([torch.from_numpy(pr.a).to(dev), torch.from_numpy(pr.b).to(dev)],
+                         debug=True)
+    m = ctx.match([fa], [fb])[0]
+    ctx.sync()
+    return dict(pr=pr, p=p, ctx=ctx, oa=oa, ob=ob, fa=fa, fb=fb, m=m)
+
+
+# --------------------------------------------------------------------------- FFT
+@pytest.mark.parametrize("h,w", [(16, 16), (256, 256), (1024, 1024), (48, 80), (105, 63),
+                                 (384, 640), (224, 448)])
+def test_fft2_matches_numpy(pkg, dev, h, w):
+    ctx = pkg.Context(pkg.default_params(), device=0)
+    x = np.random.default_rng(h * 7 + w).random((2, h, w)).astype(np.float32)
+    got = ctx.fft2(torch.from_numpy(x).to(dev)).cpu().numpy()
+    exp = np.fft.fft2(x.astype(np.float64))
+    err = np.max(np.abs(got - exp)) / np.max(np.abs(exp))
+    assert err < 2e-6, err
+
+
+# ------------------------------------------------------------------------- maps
+def test_amplitude_sums(small):
+    d = small["fa"].debug
+    assert rel_err(d["amp"].cpu().numpy(), small["oa"].maps["A"], 1e-3) < 1e-4
+
+
+def test_mim_exact_except_near_ties(small):
+    for f, o in ((small["fa"], small["oa"]), (small["fb"], small["ob"])):
+        mim = f.debug["mim"].cpu().numpy()
+        mis = mim != o.maps["mim"]
+        assert np.all(o.maps["mim_margin"][mis] < TIE), int(mis.sum())
+
+
+def test_noise_threshold(small):
+    t = small["fa"].debug["noise_t"].cpu().numpy()
+    np.testing.assert_allclose(t, small["oa"].maps["T"], rtol=1e-5)
+
+
+def test_pc_terms_and_moment(small):
+    d = {k: v.cpu().numpy() for k, v in small["fa"].debug.items()}
+    m = small["oa"].maps
+    assert rel_err(d["an0"], m["An0"], 1e-2) < 1e-4
+    assert rel_err(d["q"], m["q"], 1e-3) < 1e-4
+    assert rel_err(d["er"], m["Er"], 5e-2) < 1e-4
+    assert rel_err(d["pc"], m["pc"], 1.0) < 1e-4      # PC in [0, 1]: against its scale
+    mo = m["M"]
+    # normalised units (what FAST compares): well inside the 1e-5 certification margin
+    assert np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min()) < 5e-6
+    assert rel_err(d["moment"], mo, 1e-2) < 1e-4
+
+
+# --------------------------------------------------------------------- stages
+def test_detect_stage_on_oracle_moment(pkg, dev, small):
+    p = small["p"]
+    for o in (small["oa"], small["ob"]):
+        m32 = o.maps["M"].astype(np.float32)
+        f, = small["ctx"].detect(torch.from_numpy(m32[None].copy()).to(dev))
+        g = f.host()
+        xy, v, unc, btie = O.detect(m32.astype(np.float64), p)
+        r = compare_keypoints(g["xy"], g["score"], xy, v, unc, btie)
+        assert not r["bad"] and r["inversions"] == 0, r
+        common = min(len(v), len(g["score"]))
+        np.testing.assert_allclose(g["score"][:common], v[:common], rtol=1e-5)
+
+
+def test_detect_stage_edge_cases(pkg, dev):
+    ctx = pkg.Context(pkg.default_params(max_keypoints=50), device=0)
+    # constant map: no keypoints
+    f, = ctx.detect(torch.full((1, 128, 160), 0.3, device=dev))
+    assert f.counts.cpu().tolist() == [0, 0]
+    # map too small for a patch: no keypoints
+    f, = ctx.detect(torch.rand((1, 90, 90), device=dev))
+    assert f.counts.cpu()[0] == 0
+    # more survivors than max_keypoints, with many exact ties (checkerboard + plateaus)
+    rng = np.random.default_rng(3)
+    m = (np.round(rng.random((200, 232)) * 8) / 8).astype(np.float32)
+    f, = ctx.detect(torch.from_numpy(m[None].copy()).to(dev))
+    g = f.host()
+    xy, v, unc, btie = O.detect(m.astype(np.float64), O.Params(max_keypoints=50))
+    assert len(g["xy"]) == len(xy) == 50
+    r = compare_keypoints(g["xy"], g["score"], xy, v, unc, btie)
+    assert not r["bad"], r
+
+
+def test_describe_stage_bit_exact(pkg, dev, small):
+    ctx = small["ctx"]
+    for o in (small["oa"], small["ob"]):
+        f = ctx.alloc_features()
+        n = len(o.xy)
+        f.kp_xy[:n] = torch.from_numpy(o.xy.astype(np.int32)).to(dev)
+        f.counts[0] = n
+        ctx.describe(torch.from_numpy(o.maps["mim"][None].copy()).to(dev), [f])
+        g = f.host()
+        assert np.array_equal(g["desc"].astype(np.int64), o.desc)
+        assert np.array_equal(g["desc_kp"], o.desc_kp)
+        assert np.array_equal(g["desc_dom"], o.desc_dom)
+        np.testing.assert_allclose(g["desc_norm"], np.sqrt((o.desc ** 2).sum(axis=1)), rtol=1e-7)
+
+
+def test_describe_stage_patch_edges_and_ragged(pkg, dev):
+    # keypoints at the extreme corners of the admissible region, odd width (x start not
+    # 16-aligned), random MIM
+    ctx = pkg.Context(pkg.default_params(max_keypoints=64), device=0)
+    h, w = 150, 203
+    mim = np.random.default_rng(8).integers(0, 6, size=(h, w)).astype(np.uint8)
+    pts = [(48, 48), (w - 49, 48), (48, h - 49), (w - 49, h - 49), (100, 75), (61, 99), (63, 50)]
+    xy = np.array(pts, dtype=np.int64)
+    f = ctx.alloc_features()
+    f.kp_xy[:len(xy)] = torch.from_numpy(xy.astype(np.int32)).to(dev)
+    f.counts[0] = len(xy)
+    ctx.describe(torch.from_numpy(mim[None].copy()).to(dev), [f])
+    g = f.host()
+    desc, dkp, ddom, _ = O.describe(mim, xy, O.Params(max_keypoints=64))
+    assert np.array_equal(g["desc"].astype(np.int64), desc)
+    assert np.array_equal(g["desc_kp"], dkp) and np.array_equal(g["desc_dom"], ddom)
+
+
+def _features_from(ctx, dev, desc, dkp):
+    f = ctx.alloc_features()
+    f.desc[:len(desc)] = torch.from_numpy(desc.astype(np.int16)).to(dev)
+    f.desc_kp[:len(desc)] = torch.from_numpy(dkp.astype(np.int32)).to(dev)
+    f.counts[1] = len(desc)
+    return f
+
+
+def test_match_stage_exact(pkg, dev, small):
+    ctx = small["ctx"]
+    oa, ob = small["oa"], small["ob"]
+    fa = _features_from(ctx, dev, oa.desc, oa.desc_kp)
+    fb = _features_from(ctx, dev, ob.desc, ob.desc_kp)
+    m = ctx.match([fa], [fb])[0].host()
+    nn, d1, d2, near = O.match(oa.desc, ob.desc)
+    assert len(m["nn_desc"]) == len(nn)
+    assert np.all((m["nn_desc"] == nn) | near)
+    assert np.array_equal(m["kp_b"][~near], ob.desc_kp[nn][~near])
+    np.testing.assert_allclose(m["d1"], d1, rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(m["d2"], d2, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(m["near_tie"].astype(bool), near)
+
+
+def test_match_stage_duplicates_and_single(pkg, dev):
+    ctx = pkg.Context(pkg.default_params(max_keypoints=100), device=0)
+    rng = np.random.default_rng(4)
+    a = rng.integers(0, 40, size=(70, 216))
+    b = rng.integers(0, 40, size=(130, 216))
+    b[5] = a[0]
+    b[77] = a[0]          # exact duplicate: the lower index must win
+    fa = _features_from(ctx, dev, a, np.arange(70))
+    fb = _features_from(ctx, dev, b, np.arange(130))
+    m = ctx.match([fa], [fb])[0].host()
+    nn, d1, d2, near = O.match(a, b)
+    assert m["nn_desc"][0] == 5 and nn[0] == 5
+    assert np.all((m["nn_desc"] == nn) | near)
+    # one descriptor in B: d2 = inf
+    fb1 = _features_from(ctx, dev, b[:1], np.arange(1))
+    m1 = ctx.match([fa], [fb1])[0].host()
+    assert np.all(m1["nn_desc"] == 0) and np.all(np.isinf(m1["d2"]))
+    # empty A
+    fa0 = _features_from(ctx, dev, a[:0], np.arange(0))
+    m0 = ctx.match([fa0], [fb])[0]
+    assert int(m0.count.cpu()[0]) == 0
+
+
+# -------------------------------------------------------------------- end to end
+def _e2e_check(f, o, ctx_p):
+    g = f.host()
+    r = compare_keypoints(g["xy"], g["score"], o.xy, o.score, o.maps["kp_uncertain"],
+                          o.maps["kp_boundary_tie"])
+    assert not r["bad"] and r["inversions"] == 0, r
+    return g, r
+
+
+def test_end_to_end_small_pair(small):
+    ga, ra = _e2e_check(small["fa"], small["oa"], small["p"])
+    gb, rb = _e2e_check(small["fb"], small["ob"], small["p"])
+    if ra["flips"] == 0 and rb["flips"] == 0:
+        # same keypoints: descriptors differ only where an uncertain MIM pixel is in a patch
+        for g, o, f in ((ga, small["oa"], small["fa"]), (gb, small["ob"], small["fb"])):
+            mim_gpu = f.debug["mim"].cpu().numpy()
+            if np.array_equal(mim_gpu, o.maps["mim"]):
+                assert np.array_equal(g["desc"].astype(np.int64), o.desc)
+        m = small["m"].host()
+        nn, d1, d2, near = O.match(small["oa"].desc, small["ob"].desc)
+        if np.array_equal(ga["desc"].astype(np.int64), small["oa"].desc) and \
+                np.array_equal(gb["desc"].astype(np.int64), small["ob"].desc):
+            assert np.all((m["nn_desc"] == nn) | near)
+
+
+@pytest.mark.slow
+def test_end_to_end_1024(pkg, dev):
+    """Full-size workload (1024^2, <= 5000 keypoints) in the benchmark's launch grouping:
+    both images of a pair in one extract call; the oracle runs on image A."""
+    pr = synth.config_pair(1)
+    ctx = pkg.Context(pkg.default_params(), device=0)
+    fa, fb = ctx.extract([torch.from_numpy(pr.a).to(dev), torch.from_numpy(pr.b).to(dev)],
+                         debug=True)
+    m = ctx.match([fa], [fb])[0]
+    ctx.sync()
+    oa = O.extract(pr.a.astype(np.float64), O.Params(), keep_maps=True)
+    d = {k: v.cpu().numpy() for k, v in fa.debug.items()}
+    mis = d["mim"] != oa.maps["mim"]
+    assert np.all(oa.maps["mim_margin"][mis] < TIE)
+    assert rel_err(d["amp"], oa.maps["A"], 1e-3) < 1e-4
+    np.testing.assert_allclose(d["noise_t"], oa.maps["T"], rtol=1e-5)
+    mo = oa.maps["M"]
+    assert np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min()) < 5e-6
+    ga, r = _e2e_check(fa, oa, None)
+    assert len(ga["xy"]) == 5000
+    # descriptors of keypoints common to both lists: equal where the patch has no MIM near tie
+    gi = {tuple(p): i for i, p in enumerate(ga["xy"].tolist())}
+    checked = 0
+    for k, (x, y) in enumerate(oa.xy.tolist()):
+        if (x, y) not in gi or checked >= 300:
+            continue
+        patch_mis = mis[y - 48:y + 48, x - 48:x + 48].any()
+        if patch_mis:
+            continue
+        jo = np.flatnonzero(oa.desc_kp == k)
+        jg = np.flatnonzero(ga["desc_kp"] == gi[(x, y)])
+        assert np.array_equal(ga["desc"][jg].astype(np.int64), oa.desc[jo])
+        checked += 1
+    assert checked >= 100
+    mh = m.host()
+    assert len(mh["nn_desc"]) == len(ga["desc"])
+    assert np.all((mh["nn_desc"] >= 0) & (mh["nn_desc"] < int(fb.counts.cpu()[1])))
+
+
+def test_edge_images(pkg, dev):
+    ctx = pkg.Context(pkg.default_params(max_keypoints=100), device=0)
+    # constant image: every amplitude is zero, no keypoints, no descriptors
+    z = torch.full((128, 128), 0.5, device=dev)
+    # smaller than a patch: no keypoints; ragged mixed-radix sizes
+    s = torch.rand((64, 80), device=dev)
+    r = torch.from_numpy(synth.make_pair(120, 210, 5, 10.0, 8, 4).a).to(dev)
+    f = ctx.extract([z, s, r])
+    ctx.sync()
+    assert f[0].counts.cpu().tolist() == [0, 0]
+    assert f[1].counts.cpu().tolist() == [0, 0]
+    o = O.extract(r.cpu().numpy().astype(np.float64), O.Params(max_keypoints=100), keep_maps=True)
+    g, _ = _e2e_check(f[2], o, None)
+    # unsupported size (prime factor 11) is refused, not computed wrongly
+    with pytest.raises(pkg.Rift2Error):
+        ctx.extract([torch.rand((121, 128), device=dev)])
