@@ -55,7 +55,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -174,8 +174,7 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     _build.build()
     B = args.pairs
-    flags = pkg.FLAG_PLAIN_MATCH
-    ctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=flags), device=local,
+    ctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP), device=local,
                       hbm_budget=96 << 30)
 
     # inputs: ROTATE batches of B pairs, distinct per rank; pinned host copies for e2e
@@ -335,7 +334,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--pairs", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))

@@ -141,6 +141,30 @@ __device__ __forceinline__ float lg_angular(float u, float v, float rinv, float 
   return 0.5f * (1.f + c) * t * t;
 }
 
+// Columns u whose angular window is zero on every row: S_o(u, v) = 0 for all v, so the
+// filtered spectrum column and its inverse transform are exactly zero.  The one-sided
+// wedge of each orientation misses about a third of all (o, u) columns.  Evaluated with
+// the very expression the column pass uses, so the table is exact for that pass.
+__global__ void angular_zero_cols(int H, int W, KParams kp, unsigned char* __restrict__ zc) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = blockIdx.y;
+  if (u >= W) return;
+  const float co = kp.cos_o[o], so = kp.sin_o[o];
+  const float fu = fftfreq(u, W);
+  bool zero = true;
+  for (int v = 0; v < H && zero; ++v) {
+    const float fv = fftfreq(v, H);
+    const float r2 = fu * fu + fv * fv;
+    const float g = (r2 > 0.f) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
+    zero = (g == 0.f);
+  }
+  zc[o * W + u] = zero ? 1 : 0;
+}
+
+void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaStream_t st) {
+  angular_zero_cols<<<dim3((W + 127) / 128, NO), 128, 0, st>>>(H, W, kp, zc);
+}
+
 // Column pass of the inverse for the six orientations of scale blockIdx.y.
 // smem: base (F * R_s), a, b each [H][tc].
 __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict__ spec,
@@ -200,7 +224,8 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
                                                       float* __restrict__ an0_out,
                                                       float* __restrict__ amp_out,
                                                       unsigned char* __restrict__ mim_out,
-                                                      int mim_pitch) {
+                                                      int mim_pitch,
+                                                      const unsigned char* __restrict__ zc) {
   extern __shared__ float2 sm[];
   const int row = blockIdx.x;
   const int img = blockIdx.y;
@@ -217,7 +242,8 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
   for (int o = 0; o < NO; ++o) {
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
       int s = i / W, x = i - s * W;
-      a[i] = __ldg(scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W + x);
+      a[i] = zc[o * W + x] ? make_float2(0.f, 0.f)
+                           : __ldg(scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W + x);
     }
     __syncthreads();
     float2* res = fft_smem<true, false>(a, b, pw, NS, W, 1);
@@ -276,7 +302,8 @@ template <int H>
 __global__ void __launch_bounds__(REG_THREADS) lg_cols_reg(const float2* __restrict__ spec,
                                                            float2* __restrict__ scratch, int W,
                                                            const float2* __restrict__ twh,
-                                                           KParams kp) {
+                                                           KParams kp,
+                                                           const unsigned char* __restrict__ zc) {
   using S = RegShape<H>;
   constexpr int T = S::T;
   constexpr int COLS = REG_THREADS / T;
@@ -312,20 +339,29 @@ __global__ void __launch_bounds__(REG_THREADS) lg_cols_reg(const float2* __restr
   };
   for (int o = 0; o < NO; ++o) {
     const float co = kp.cos_o[o], so = kp.sin_o[o];
-    auto ld = [&](int v) -> float2 {
-      const float fv = fftfreq(v, H);
-      const float r2 = fu * fu + fv * fv;
-      const float g = (r2 > 0.f && u < W) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
-      const float2 x = bc[xpad(v)];
-      return make_float2(x.x * g, x.y * g);
-    };
-    auto st = [&](int v, float2 val) { xb[xpad(v)] = val; };
-    group_fft<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, ld, st, sync);
+    // a column whose window is zero everywhere transforms to zero: skip it, and leave it
+    // unwritten (the row pass reads the same table and substitutes zeros).  The skip is
+    // taken per synchronisation domain of the FFT: a warp, or the CTA when T > 32.
+    const bool zcol = (u >= W) || zc[o * W + u];
+    bool skip;
+    if constexpr (T <= 32) skip = __all_sync(0xffffffffu, zcol);
+    else skip = __syncthreads_and(zcol);
+    if (!skip) {
+      auto ld = [&](int v) -> float2 {
+        const float fv = fftfreq(v, H);
+        const float r2 = fu * fu + fv * fv;
+        const float g = (r2 > 0.f && u < W) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
+        const float2 x = bc[xpad(v)];
+        return make_float2(x.x * g, x.y * g);
+      };
+      auto st = [&](int v, float2 val) { xb[xpad(v)] = val; };
+      group_fft<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, ld, st, sync);
+    }
     __syncthreads();
     float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W;
     for (int i = tid; i < H * COLS; i += REG_THREADS) {
       const int v = i / COLS, c = i % COLS;
-      if (c0 + c < W) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
+      if (c0 + c < W && !zc[o * W + c0 + c]) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
     }
     __syncthreads();
   }
@@ -342,7 +378,8 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
                                                            float* __restrict__ an0_out,
                                                            float* __restrict__ amp_out,
                                                            unsigned char* __restrict__ mim_out,
-                                                           int mim_pitch) {
+                                                           int mim_pitch,
+                                                           const unsigned char* __restrict__ zc) {
   using S = RegShape<WN>;
   constexpr int T = S::T;
   constexpr int GROUPS = REG_THREADS / T;
@@ -351,6 +388,9 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
   constexpr int PIX = ROWS * WN / REG_THREADS;
   static_assert(ROWS >= 1 && PIX >= 1, "row tile");
   extern __shared__ float2 sm[];   // [GROUPS][XS], group g = (row g / NS, scale g % NS)
+  __shared__ unsigned char zcs[NO * WN];
+  for (int i = threadIdx.x; i < NO * WN; i += REG_THREADS) zcs[i] = zc[i];
+  __syncthreads();
   const int img = blockIdx.y;
   const int row0 = blockIdx.x * ROWS;
   const int tid = threadIdx.x;
@@ -370,7 +410,10 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
   };
   for (int o = 0; o < NO; ++o) {
     const float2* src = scratch + (((size_t)img * NS + sc) * NO + o) * P + (size_t)row * WN;
-    auto ld = [&](int x) -> float2 { return row < H ? __ldg(src + x) : make_float2(0.f, 0.f); };
+    const unsigned char* zco = zcs + o * WN;
+    auto ld = [&](int x) -> float2 {
+      return (row < H && !zco[x]) ? __ldg(src + x) : make_float2(0.f, 0.f);
+    };
     auto st = [&](int x, float2 val) { xb[xpad(x)] = val; };
     group_fft<WN, T, S::R0, S::R1, S::R2, true>(xb, t, tww, ld, st, sync);
     __syncthreads();
@@ -423,25 +466,27 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
 
 template <int H>
 static cudaError_t cols_reg(const float2* spec, float2* scratch, int nimg, int W,
-                            const FftPlan& ph, const KParams& kp, cudaStream_t st) {
+                            const FftPlan& ph, const KParams& kp, const unsigned char* zc,
+                            cudaStream_t st) {
   constexpr int COLS = REG_THREADS / RegShape<H>::T;
   const size_t sm = 2 * (size_t)COLS * XBuf<H>::SIZE * sizeof(float2);
   cudaFuncSetAttribute(lg_cols_reg<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   lg_cols_reg<H><<<dim3((W + COLS - 1) / COLS, NS, nimg), REG_THREADS, sm, st>>>(spec, scratch, W,
-                                                                                ph.tw, kp);
+                                                                                ph.tw, kp, zc);
   return cudaGetLastError();
 }
 
 template <int WN>
 static cudaError_t rows_reg(const float2* scratch, int nimg, int H, const FftPlan& pw,
                             const KParams& kp, float* er, float* q, float* an0, float* amp,
-                            unsigned char* mim, int mim_pitch, cudaStream_t st) {
+                            unsigned char* mim, int mim_pitch, const unsigned char* zc,
+                            cudaStream_t st) {
   constexpr int GROUPS = REG_THREADS / RegShape<WN>::T;
   constexpr int ROWS = GROUPS / NS;
   const size_t sm = (size_t)GROUPS * XBuf<WN>::SIZE * sizeof(float2);
   cudaFuncSetAttribute(lg_rows_reg<WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   lg_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_THREADS, sm, st>>>(
-      scratch, H, pw.tw, kp, er, q, an0, amp, mim, mim_pitch);
+      scratch, H, pw.tw, kp, er, q, an0, amp, mim, mim_pitch, zc);
   return cudaGetLastError();
 }
 
@@ -475,12 +520,13 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
 }
 
 cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
-                           const FftPlan& ph, const KParams& kp, cudaStream_t st) {
+                           const FftPlan& ph, const KParams& kp, const unsigned char* zc,
+                           cudaStream_t st) {
   switch (H) {
-    case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, st);
-    case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, st);
-    case 1024: return cols_reg<1024>(spec, scratch, nimg, W, ph, kp, st);
-    case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, st);
+    case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, zc, st);
+    case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
+    case 1024: return cols_reg<1024>(spec, scratch, nimg, W, ph, kp, zc, st);
+    case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, zc, st);
     default: break;
   }
   int tc = cols_tile(H);
@@ -493,18 +539,19 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H,
 
 cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
-                           unsigned char* mim, int mim_pitch, cudaStream_t st) {
+                           unsigned char* mim, int mim_pitch, const unsigned char* zc,
+                           cudaStream_t st) {
   switch (W) {
-    case 256: return rows_reg<256>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
-    case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
-    case 1024: return rows_reg<1024>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
-    case 2048: return rows_reg<2048>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, st);
+    case 256: return rows_reg<256>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
+    case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
+    case 1024: return rows_reg<1024>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
+    case 2048: return rows_reg<2048>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     default: break;
   }
   size_t sm3 = 2 * (size_t)NS * W * sizeof(float2);
   cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
   lg_rows_reduce<<<dim3(H, nimg), 512, sm3, st>>>(scratch, H, W, pw, kp, er, q, an0, amp, mim,
-                                                  mim_pitch);
+                                                  mim_pitch, zc);
   return cudaGetLastError();
 }
 

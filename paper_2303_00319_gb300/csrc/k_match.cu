@@ -11,34 +11,9 @@
 //   match_simt : CUDA-core form.  A CTA holds 64 queries and streams B in tiles of 64,
 //                each thread owning a 4x4 block of dot products and a running top-2.
 #include "kernels.h"
+#include "match_common.cuh"
 
 namespace rift2 {
-
-struct Cand {
-  float dot;
-  float n2;
-  int j;
-};
-
-__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
-  unsigned long long da = (unsigned long long)a.dot, db = (unsigned long long)b.dot;
-  unsigned long long lhs = da * da * (unsigned long long)b.n2;
-  unsigned long long rhs = db * db * (unsigned long long)a.n2;
-  return lhs > rhs || (lhs == rhs && a.j < b.j);
-}
-
-__device__ __forceinline__ void push2(Cand& c1, Cand& c2, const Cand& x) {
-  if (better(x, c1)) { c2 = c1; c1 = x; }
-  else if (better(x, c2)) { c2 = x; }
-}
-
-__device__ __forceinline__ float exact_dist(float n2a, const Cand& c) {
-  unsigned long long na = (unsigned long long)n2a, nb = (unsigned long long)c.n2;
-  unsigned long long dt = (unsigned long long)c.dot;
-  unsigned long long num = na * nb - dt * dt;        // >= 0 (Cauchy-Schwarz), exact
-  float nn = sqrtf((float)(na * nb));
-  return 2.f * (float)num / ((nn + c.dot) * nn);
-}
 
 constexpr int MT = 64;   // queries per CTA and candidates per tile
 

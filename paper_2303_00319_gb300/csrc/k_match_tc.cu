@@ -1,0 +1,498 @@
+// Brute-force nearest-neighbour matching on the tcgen05 tensor cores (§IV: nearest
+// feature distance over all descriptor pairs).  The only dense contraction of the path.
+//
+//   nn_prep   : descriptor counts -> BF16 rows padded to K = 256 (counts <= 256 are exact
+//               in BF16), exact squared norms, 1/|b| for the screening scores.
+//   nn_tc     : per CTA 128 queries x a range of 128-wide tiles of B.  One thread issues
+//               TMA loads (128-byte swizzle), one issues tcgen05.mma (BF16 x BF16 -> FP32
+//               in TMEM, M = 128, N = 128, 14 K-steps of 16 cover K = 216); four epilogue
+//               warps read the accumulators with tcgen05.ld (double-buffered in TMEM so
+//               the next tile's MMAs overlap) and keep each query's 8 best candidates by
+//               the FP32 score dot / |b|.  No score matrix ever reaches HBM.
+//   nn_rerank : one warp per query: exact integer dot products for its candidates, the
+//               exact comparison of match_common.cuh, distances and near-tie flags.
+// The products and sums of integer counts stay below 2^24, so the tensor-core dot
+// products are exact; the re-rank recomputes them anyway from the integer counts.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+#include "match_common.cuh"
+
+namespace rift2 {
+
+constexpr int TC_BM = 128, TC_BN = 64, TC_KP = 256, TC_KATOM = 64, TC_NATOM = 4;
+constexpr int TC_KSTEPS = 14;                             // 14 x 16 = 224 >= 216
+constexpr int TC_A_ATOM = TC_BM * 128;                    // 128 rows x 128 bytes = 16 KB
+constexpr int TC_B_ATOM = TC_BN * 128;                    // 64 rows x 128 bytes = 8 KB
+constexpr int TC_A_BYTES = TC_NATOM * TC_A_ATOM;          // 64 KB
+constexpr int TC_B_BYTES = TC_NATOM * TC_B_ATOM;          // 32 KB per stage
+constexpr int TC_STAGES = 4;                              // B tiles in flight
+constexpr int TC_ACC = 4;                                 // accumulators in TMEM
+constexpr int TC_TOPK = 8;
+constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;        // warp 0 TMA, warp 1 MMA, epilogue
+constexpr int TC_HALVES = TC_EPI_WARPS / 4;               // column slices per quadrant
+constexpr int TC_SLICE = TC_BN / TC_HALVES;               // 32 columns per epilogue warp
+constexpr int TC_TMEM_COLS = TC_ACC * TC_BN;              // 256
+constexpr long long TC_WAIT = 1ll << 26;                  // bounded mbarrier polls
+constexpr int TC_NBARS = 1 + 5 * TC_STAGES;
+constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 +
+                           TC_ACC * TC_BN * sizeof(float);
+static_assert(TC_STAGES == TC_ACC, "one barrier set per stage / accumulator index");
+static_assert(TC_NBARS * 8 + 8 <= 256, "barrier block");
+
+// --------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < TC_WAIT; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand stored with the 128-byte swizzle:
+// start address >> 4, leading offset unused (1), stride between 8-row groups 1024 B,
+// descriptor version 1, layout SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N and M.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+// One FP32 accumulator column of this thread's TMEM lane.
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+  uint32_t v;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  return v;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// --------------------------------------------------------------------------- prep
+// grid (rows / 8, 2 sides, pairs); warp per descriptor row.
+__global__ void __launch_bounds__(256) nn_prep(MatchPtrs mp, __nv_bfloat16* __restrict__ abf,
+                                               __nv_bfloat16* __restrict__ bbf,
+                                               float* __restrict__ rinv_b,
+                                               int* __restrict__ n2_a, int* __restrict__ n2_b,
+                                               int cap) {
+  const int pr = blockIdx.z, side = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  const int n = side ? mp.counts_b[pr][1] : mp.counts_a[pr][1];
+  if (row >= n) return;
+  const unsigned short* src = (side ? mp.desc_b[pr] : mp.desc_a[pr]) + (size_t)row * DESC_DIM;
+  __nv_bfloat16* dst = (side ? bbf : abf) + ((size_t)pr * cap + row) * TC_KP;
+  unsigned n2 = 0;
+  __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = lane * 8 + i;
+    const unsigned c = (k < DESC_DIM) ? src[k] : 0u;
+    n2 += c * c;
+    v[i] = __float2bfloat16_rn((float)c);   // counts <= 256: exact
+  }
+  *reinterpret_cast<uint4*>(dst + lane * 8) = *reinterpret_cast<const uint4*>(v);
+  for (int d = 16; d > 0; d >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, d);
+  if (lane == 0) {
+    if (side) {
+      n2_b[(size_t)pr * cap + row] = (int)n2;
+      rinv_b[(size_t)pr * cap + row] = 1.f / sqrtf((float)n2);
+    } else {
+      n2_a[(size_t)pr * cap + row] = (int)n2;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- GEMM
+struct TcArgs {
+  const int* counts_a[MAXB];
+  const int* counts_b[MAXB];
+  const float* rinv_b;   // [pairs][cap]
+  int* cand;             // [pairs][nsplit * TC_HALVES][cap][TOPK]
+  int cap, nsplit;
+  int* status;
+};
+
+__device__ __forceinline__ void topk_insert(float (&sc)[TC_TOPK], int (&id)[TC_TOPK], float s,
+                                            int j) {
+  sc[TC_TOPK - 1] = s;
+  id[TC_TOPK - 1] = j;
+#pragma unroll
+  for (int k = TC_TOPK - 1; k > 0; --k) {
+    if (sc[k] > sc[k - 1]) {
+      const float ts = sc[k]; sc[k] = sc[k - 1]; sc[k - 1] = ts;
+      const int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ CUtensorMap tmA,
+                                                       const __grid_constant__ CUtensorMap tmB,
+                                                       TcArgs args) {
+  extern __shared__ unsigned char tsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pr = blockIdx.z, split = blockIdx.y;
+  const int m0 = blockIdx.x * TC_BM;
+  const int nA = *args.counts_a[pr], nB = *args.counts_b[pr];
+  if (m0 >= nA) return;   // uniform: before any barrier, TMEM or TMA work
+  const int ntiles = (nB + TC_BN - 1) / TC_BN;
+  const int t0 = (int)((long long)split * ntiles / args.nsplit);
+  const int t1 = (int)((long long)(split + 1) * ntiles / args.nsplit);
+  const int nt = t1 - t0;
+
+  // 1024-byte aligned: A | B stages | barriers, TMEM slot, flag (256 B) | 1/|b| slots
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;
+  unsigned char* sB = base + TC_A_BYTES;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(sB + TC_STAGES * TC_B_BYTES);
+  const uint32_t full_a = su32(&bars[0]);
+  const uint32_t full_b0 = su32(&bars[1]);
+  const uint32_t empty_b0 = full_b0 + 8 * TC_STAGES;
+  const uint32_t tfull0 = empty_b0 + 8 * TC_STAGES;
+  const uint32_t tempty0 = tfull0 + 8 * TC_STAGES;
+  const uint32_t rfull0 = tempty0 + 8 * TC_STAGES;   // 1/|b| slice of a tile staged in smem
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(&bars[TC_NBARS]);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* rinv_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 256);
+
+  if (threadIdx.x == 0) {
+    mbar_init(full_a, 1);
+    for (int i = 0; i < TC_STAGES; ++i) {
+      mbar_init(full_b0 + 8 * i, 1);
+      mbar_init(empty_b0 + 8 * i, 1);
+      mbar_init(tfull0 + 8 * i, 1);
+      mbar_init(tempty0 + 8 * i, 32 * TC_EPI_WARPS);
+      mbar_init(rfull0 + 8 * i, TC_BN);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(args.status, ST_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ TMA producer
+      mbar_expect_tx(full_a, TC_A_BYTES);
+      for (int a = 0; a < TC_NATOM; ++a)
+        tma_load_3d(su32(sA + a * TC_A_ATOM), &tmA, a * TC_KATOM, m0, pr, full_a);
+      for (int i = 0; i < nt && !*abort_flag; ++i) {
+        const int st = i % TC_STAGES;
+        if (i >= TC_STAGES &&
+            !mbar_wait_bounded(empty_b0 + 8 * st, ((i / TC_STAGES) - 1) & 1)) { fail(); break; }
+        mbar_expect_tx(full_b0 + 8 * st, TC_B_BYTES);
+        for (int a = 0; a < TC_NATOM; ++a)
+          tma_load_3d(su32(sB + st * TC_B_BYTES + a * TC_B_ATOM), &tmB, a * TC_KATOM,
+                      (t0 + i) * TC_BN, pr, full_b0 + 8 * st);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = umma_idesc_bf16(TC_BM, TC_BN);
+      bool ok = mbar_wait_bounded(full_a, 0);
+      if (!ok) fail();
+      for (int i = 0; ok && i < nt && !*abort_flag; ++i) {
+        const int st = i % TC_STAGES, acc = i % TC_ACC;
+        if (!mbar_wait_bounded(full_b0 + 8 * st, (i / TC_STAGES) & 1)) { fail(); break; }
+        if (i >= TC_ACC && !mbar_wait_bounded(tempty0 + 8 * acc, ((i / TC_ACC) - 1) & 1)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
+        const uint32_t a0 = su32(sA), b0 = su32(sB + st * TC_B_BYTES);
+#pragma unroll
+        for (int ks = 0; ks < TC_KSTEPS; ++ks) {
+          const uint32_t ka = (uint32_t)((ks >> 2) * TC_A_ATOM + (ks & 3) * 32);
+          const uint32_t kb = (uint32_t)((ks >> 2) * TC_B_ATOM + (ks & 3) * 32);
+          umma_bf16(d, umma_desc_sw128(a0 + ka), umma_desc_sw128(b0 + kb), idesc, ks > 0);
+        }
+        umma_commit(empty_b0 + 8 * st);   // B stage free once these MMAs have read it
+        umma_commit(tfull0 + 8 * acc);    // accumulator ready for the epilogue
+      }
+    }
+  } else {
+    // ----------------------------------------------------------------- epilogue
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (the quadrant the hardware lets it access)
+    // and one slice of TC_SLICE columns of every accumulator tile.
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int etid = threadIdx.x - 64;
+    const int row = m0 + q * 32 + lane;
+    float sc[TC_TOPK];
+    int id[TC_TOPK];
+#pragma unroll
+    for (int k = 0; k < TC_TOPK; ++k) { sc[k] = -1.f; id[k] = -1; }
+    const float* rinv = args.rinv_b + (size_t)pr * args.cap;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    // 1/|b| of the next tile, prefetched one tile ahead into registers, staged in smem
+    float rnext = (nt > 0 && etid < TC_BN) ? __ldg(rinv + t0 * TC_BN + etid) : 0.f;
+    for (int i = 0; i < nt; ++i) {
+      const int acc = i % TC_ACC;
+      bool ok = true;
+      if (etid < TC_BN) {
+        // slot `acc` was last read for tile i - TC_ACC; every epilogue thread arrived on
+        // tempty[acc] for that tile once its reads were done
+        if (i >= TC_ACC) ok = mbar_wait_bounded(tempty0 + 8 * acc, ((i / TC_ACC) - 1) & 1);
+        rinv_s[acc * TC_BN + etid] = rnext;
+        mbar_arrive(rfull0 + 8 * acc);
+        if (i + 1 < nt) rnext = __ldg(rinv + (t0 + i + 1) * TC_BN + etid);
+      }
+      ok = ok && mbar_wait_bounded(rfull0 + 8 * acc, (i / TC_ACC) & 1);
+      // warp-uniform decision: tcgen05.ld below is a warp-collective instruction
+      const bool ready =
+          __all_sync(0xffffffffu, ok && mbar_wait_bounded(tfull0 + 8 * acc, (i / TC_ACC) & 1));
+      if (!ready) {
+        if (lane == 0) fail();
+        break;
+      }
+      tc_fence_after();
+      const int col0 = acc * TC_BN + half * TC_SLICE;
+      const int j0 = (t0 + i) * TC_BN + half * TC_SLICE;
+      const float* rs = rinv_s + col0;
+      uint32_t r[32];
+      tmem_ld32(lane_base + (uint32_t)col0, r);
+      // columns whose score beats this row's current 8th best (one compare per column)
+      const float thr = sc[TC_TOPK - 1];
+      unsigned m = 0;
+#pragma unroll
+      for (int e4 = 0; e4 < 8; ++e4) {
+        const float4 rb = *reinterpret_cast<const float4*>(rs + e4 * 4);
+        m |= (__uint_as_float(r[e4 * 4 + 0]) * rb.x > thr ? 1u : 0u) << (e4 * 4 + 0);
+        m |= (__uint_as_float(r[e4 * 4 + 1]) * rb.y > thr ? 1u : 0u) << (e4 * 4 + 1);
+        m |= (__uint_as_float(r[e4 * 4 + 2]) * rb.z > thr ? 1u : 0u) << (e4 * 4 + 2);
+        m |= (__uint_as_float(r[e4 * 4 + 3]) * rb.w > thr ? 1u : 0u) << (e4 * 4 + 3);
+      }
+      if (j0 + 32 > nB) m &= (j0 >= nB) ? 0u : ((1u << (nB - j0)) - 1u);
+      // visit the union of the lanes' columns: the re-read of one column is warp-collective
+      unsigned um = __reduce_or_sync(0xffffffffu, m);
+      while (um) {
+        const int e = __ffs(um) - 1;
+        um &= um - 1;
+        const float s = __uint_as_float(tmem_ld1(lane_base + (uint32_t)(col0 + e))) * rs[e];
+        if (((m >> e) & 1u) && s > sc[TC_TOPK - 1]) topk_insert(sc, id, s, j0 + e);
+      }
+      tc_fence_before();
+      mbar_arrive(tempty0 + 8 * acc);
+    }
+    if (row < nA) {
+      int* out = args.cand +
+                 (((size_t)pr * args.nsplit * TC_HALVES + split * TC_HALVES + half) * args.cap + row) *
+                     TC_TOPK;
+#pragma unroll
+      for (int k = 0; k < TC_TOPK; ++k) out[k] = id[k];
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    if (*abort_flag && nt > 0) {
+      // let the last committed MMAs land before the accumulator memory is released
+      mbar_wait_bounded(tfull0 + 8 * ((nt - 1) % TC_ACC), ((nt - 1) / TC_ACC) & 1);
+    }
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------ re-rank
+// One warp per query.  A descriptor row is 216 uint16 = 54 uint2 words; lane l holds words
+// l and l + 32.  Exact integer dot products for every candidate of every list.
+__device__ __forceinline__ unsigned dot4(uint2 a, uint2 b) {
+  return (a.x & 0xFFFFu) * (b.x & 0xFFFFu) + (a.x >> 16) * (b.x >> 16) +
+         (a.y & 0xFFFFu) * (b.y & 0xFFFFu) + (a.y >> 16) * (b.y >> 16);
+}
+
+__global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int* __restrict__ cand,
+                                                 const int* __restrict__ n2_a,
+                                                 const int* __restrict__ n2_b, int cap,
+                                                 int nsplit) {
+  constexpr int WORDS = DESC_DIM / 4;   // 54
+  const int pr = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * 8 + warp;
+  const int nA = mp.counts_a[pr][1], nB = mp.counts_b[pr][1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *mp.count[pr] = nA;
+  if (q >= nA) return;
+  const uint2* a = reinterpret_cast<const uint2*>(mp.desc_a[pr] + (size_t)q * DESC_DIM);
+  const uint2 z = make_uint2(0u, 0u);
+  const uint2 a0 = a[lane], a1 = (lane + 32 < WORDS) ? a[lane + 32] : z;
+  Cand c1{0.f, 1.f, 0x7fffffff}, c2 = c1;
+  const int nl = nsplit * TC_HALVES;
+  for (int sp = 0; sp < nl; ++sp) {
+    const int* cl = cand + (((size_t)pr * nl + sp) * cap + q) * TC_TOPK;
+    int js[TC_TOPK];
+    uint2 b0[TC_TOPK], b1[TC_TOPK];
+#pragma unroll
+    for (int k = 0; k < TC_TOPK; ++k) {
+      js[k] = cl[k];
+      const bool ok = js[k] >= 0 && js[k] < nB;
+      const uint2* b = reinterpret_cast<const uint2*>(mp.desc_b[pr] + (size_t)(ok ? js[k] : 0) * DESC_DIM);
+      b0[k] = ok ? b[lane] : z;
+      b1[k] = (ok && lane + 32 < WORDS) ? b[lane + 32] : z;
+      if (!ok) js[k] = -1;
+    }
+#pragma unroll
+    for (int k = 0; k < TC_TOPK; ++k) {
+      unsigned dot = dot4(a0, b0[k]) + dot4(a1, b1[k]);
+      for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);
+      if (js[k] >= 0) push2(c1, c2, Cand{(float)dot, (float)n2_b[(size_t)pr * cap + js[k]], js[k]});
+    }
+  }
+  if (lane == 0) {
+    const float na2 = (float)n2_a[(size_t)pr * cap + q];
+    const bool ok1 = c1.j != 0x7fffffff, ok2 = c2.j != 0x7fffffff;
+    const float d1 = ok1 ? exact_dist(na2, c1) : __int_as_float(0x7f800000);
+    const float d2 = ok2 ? exact_dist(na2, c2) : __int_as_float(0x7f800000);
+    mp.q_desc[pr][q] = q;
+    mp.nn_desc[pr][q] = ok1 ? c1.j : -1;
+    mp.kp_a[pr][q] = mp.desc_kp_a[pr][q];
+    mp.kp_b[pr][q] = ok1 ? mp.desc_kp_b[pr][c1.j] : -1;
+    mp.d1[pr][q] = d1;
+    mp.d2[pr][q] = d2;
+    mp.near_tie[pr][q] = (ok2 && (d2 - d1) < 1e-5f * fmaxf(d1, 1e-12f)) ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------- launcher
+size_t match_tc_ws_bytes(int npairs, int cap, int nsplit) {
+  size_t bf = (size_t)npairs * cap * TC_KP * 2;
+  size_t per = (size_t)npairs * cap * 4;
+  return 2 * bf + 3 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 4 + 4096;
+}
+
+int match_tc_nsplit(int npairs, int cap) {
+  const int mtiles = (cap + TC_BM - 1) / TC_BM;
+  int ns = (2 * 152 + npairs * mtiles - 1) / (npairs * mtiles);
+  return ns < 1 ? 1 : (ns > 4 ? 4 : ns);
+}
+
+cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
+                            const CUtensorMap* tmA, const CUtensorMap* tmB, int nsplit,
+                            int* status, cudaStream_t st) {
+  char* p = static_cast<char*>(ws);
+  __nv_bfloat16* abf = reinterpret_cast<__nv_bfloat16*>(p);
+  p += (size_t)npairs * cap * TC_KP * 2;
+  __nv_bfloat16* bbf = reinterpret_cast<__nv_bfloat16*>(p);
+  p += (size_t)npairs * cap * TC_KP * 2;
+  float* rinv = reinterpret_cast<float*>(p);
+  p += (size_t)npairs * cap * 4;
+  int* n2a = reinterpret_cast<int*>(p);
+  p += (size_t)npairs * cap * 4;
+  int* n2b = reinterpret_cast<int*>(p);
+  p += (size_t)npairs * cap * 4;
+  int* cand = reinterpret_cast<int*>(p);
+  nn_prep<<<dim3((cap + 7) / 8, 2, npairs), 256, 0, st>>>(mp, abf, bbf, rinv, n2a, n2b, cap);
+  TcArgs ta{};
+  for (int i = 0; i < npairs; ++i) {
+    ta.counts_a[i] = mp.counts_a[i] + 1;
+    ta.counts_b[i] = mp.counts_b[i] + 1;
+  }
+  ta.rinv_b = rinv;
+  ta.cand = cand;
+  ta.cap = cap;
+  ta.nsplit = nsplit;
+  ta.status = status;
+  const size_t sm = TC_SMEM;
+  cudaFuncSetAttribute(nn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  nn_tc<<<dim3((cap + TC_BM - 1) / TC_BM, nsplit, npairs), TC_THREADS, sm, st>>>(*tmA, *tmB, ta);
+  nn_rerank<<<dim3((cap + 7) / 8, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, cap, nsplit);
+  return cudaGetLastError();
+}
+
+// The BF16 operand arrays [pairs][cap][256] inside the workspace; the A map uses boxes of
+// 64 x TC_BM x 1 and the B map boxes of 64 x TC_BN x 1 (128-byte swizzle).
+int match_tc_box_rows(int operand) { return operand == 0 ? TC_BM : TC_BN; }
+void match_tc_operands(void* ws, int npairs, int cap, void** abf, void** bbf) {
+  char* p = static_cast<char*>(ws);
+  *abf = p;
+  *bbf = p + (size_t)npairs * cap * TC_KP * 2;
+}
+
+}  // namespace rift2

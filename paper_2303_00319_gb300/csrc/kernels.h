@@ -14,11 +14,15 @@ void launch_twiddles(float2* tw, int n, cudaStream_t st);
 cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
                                 int H, int W, const FftPlan& ph, const FftPlan& pw,
                                 cudaStream_t st);
+// zc [NO][W]: 1 where orientation o's angular window is zero on the whole column u.
+void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaStream_t st);
 cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
-                           const FftPlan& ph, const KParams& kp, cudaStream_t st);
+                           const FftPlan& ph, const KParams& kp, const unsigned char* zc,
+                           cudaStream_t st);
 cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
-                           unsigned char* mim, int mim_pitch, cudaStream_t st);
+                           unsigned char* mim, int mim_pitch, const unsigned char* zc,
+                           cudaStream_t st);
 
 // k_pc.cu — exact median of |EO_0,o| (radix select), noise thresholds, PC, moments.
 struct MedianWs {
@@ -71,5 +75,15 @@ struct MatchPtrs {
   int* count[MAXB];
 };
 cudaError_t launch_match_simt(const MatchPtrs& mp, int npairs, int max_desc, cudaStream_t st);
+
+// k_match_tc.cu — tcgen05 BF16 distance GEMM fused with top-8 selection, exact re-rank.
+// `cap` (descriptor rows per pair) must be a multiple of 128.
+size_t match_tc_ws_bytes(int npairs, int cap, int nsplit);
+int match_tc_nsplit(int npairs, int cap);
+void match_tc_operands(void* ws, int npairs, int cap, void** abf, void** bbf);
+int match_tc_box_rows(int operand);   // 0: A (queries), 1: B
+cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
+                            const CUtensorMap* tmA, const CUtensorMap* tmB, int nsplit,
+                            int* status, cudaStream_t st);
 
 }  // namespace rift2

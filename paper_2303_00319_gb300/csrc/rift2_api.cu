@@ -23,6 +23,7 @@ struct rift2_ctx {
   size_t ws_size = 0;
   int* status = nullptr;
   std::map<int, FftPlan> plans;
+  std::map<std::pair<int, int>, unsigned char*> zero_cols;   // (H, W) -> [NO][W]
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   // tracing
   long long launches = 0;
@@ -97,6 +98,21 @@ int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
   return RIFT2_OK;
 }
 
+int get_zero_cols(rift2_ctx* c, int H, int W, cudaStream_t st, unsigned char** out) {
+  auto key = std::make_pair(H, W);
+  auto it = c->zero_cols.find(key);
+  if (it != c->zero_cols.end()) { *out = it->second; return RIFT2_OK; }
+  unsigned char* zc = nullptr;
+  RIFT2_CU(cudaMalloc(&zc, (size_t)NO * W));
+  launch_zero_cols(H, W, c->kp, zc, st);
+  c->launches += 1;
+  RIFT2_CU(cudaGetLastError());
+  RIFT2_CU(cudaStreamSynchronize(st));
+  c->zero_cols[key] = zc;
+  *out = zc;
+  return RIFT2_OK;
+}
+
 int ensure_ws(rift2_ctx* c, size_t need) {
   if (need <= c->ws_size) return RIFT2_OK;
   if (need > c->budget) return RIFT2_E_NOMEM;
@@ -155,7 +171,7 @@ int check_size(int H, int W) {
 // ------------------------------------------------------------------ tracing
 // Kernels enqueued by each launcher (kept next to the launch sequences they count).
 constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_LG_ROWS = 1, K_NOISE = 6, K_MOMENT = 1,
-              K_DETECT = 2, K_DESCRIBE = 3, K_MATCH = 1, K_INIT = 1;
+              K_DETECT = 2, K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 3, K_INIT = 1;
 
 cudaEvent_t take_event(rift2_ctx* c) {
   if (!c->free_events.empty()) {
@@ -274,6 +290,22 @@ int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int g, int H
   return RIFT2_OK;
 }
 
+int make_operand_map(rift2_ctx* c, CUtensorMap* tm, void* base, int npairs, int cap,
+                     int box_rows) {
+  cuuint64_t dims[3] = {256, (cuuint64_t)cap, (cuuint64_t)npairs};
+  cuuint64_t strides[2] = {256 * 2, (cuuint64_t)cap * 256 * 2};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fprintf(stderr, "rift2: cuTensorMapEncodeTiled (operands) failed (%d)\n", (int)r);
+    return RIFT2_E_CUDA;
+  }
+  return RIFT2_OK;
+}
+
 int check_features(const rift2_ctx* c, const rift2_features& f, bool need_desc) {
   if (!f.kp_xy || !f.kp_score || !f.counts) return RIFT2_E_INVAL;
   if (f.cap_kp < c->p.max_keypoints) return RIFT2_E_CAPACITY;
@@ -339,6 +371,9 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   if (rc) return rc;
   rc = get_plan(c, W, st, &pw);
   if (rc) return rc;
+  unsigned char* zc = nullptr;
+  rc = get_zero_cols(c, H, W, st, &zc);
+  if (rc) return rc;
   const bool dbg = wants_debug(out, g);
   Layout L = extract_layout(g, H, W, c->p.max_keypoints, dbg);
   rc = ensure_ws(c, L.total);
@@ -367,12 +402,12 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   float2* scratch = at<float2>(ws, L.scratch);
   {
     StageScope sc(c, RIFT2_STAGE_LG_COLS, st, K_LG_COLS);
-    RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, st));
+    RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st));
   }
   {
     StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, K_LG_ROWS);
     RIFT2_CU(launch_lg_rows(scratch, g, H, W, pw, c->kp, er, q, an0, at<float>(ws, L.amp), mim,
-                            L.mim_pitch, st));
+                            L.mim_pitch, zc, st));
   }
   MedianWs mw{at<unsigned>(ws, L.mhist), at<unsigned>(ws, L.mstate), at<float>(ws, L.noise)};
   {
@@ -489,6 +524,7 @@ int rift2_destroy(rift2_ctx* c) {
   DeviceGuard dg(c->device);
   cudaDeviceSynchronize();
   for (auto& kv : c->plans) cudaFree(const_cast<float2*>(kv.second.tw));
+  for (auto& kv : c->zero_cols) cudaFree(kv.second);
   for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : c->free_events) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
@@ -610,8 +646,24 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
       mp.near_tie[k] = m.near_tie;
       mp.count[k] = m.count;
     }
-    StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH);
-    RIFT2_CU(launch_match_simt(mp, g, 2 * c->p.max_keypoints, st));
+    if (c->p.flags & RIFT2_FLAG_PLAIN_MATCH) {
+      StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH);
+      RIFT2_CU(launch_match_simt(mp, g, 2 * c->p.max_keypoints, st));
+    } else {
+      const int cap = (2 * c->p.max_keypoints + 127) / 128 * 128;
+      const int nsplit = match_tc_nsplit(g, cap);
+      int rc = ensure_ws(c, match_tc_ws_bytes(g, cap, nsplit));
+      if (rc) return rc;
+      void *abf, *bbf;
+      match_tc_operands(c->ws, g, cap, &abf, &bbf);
+      CUtensorMap ta, tb;
+      rc = make_operand_map(c, &ta, abf, g, cap, match_tc_box_rows(0));
+      if (rc) return rc;
+      rc = make_operand_map(c, &tb, bbf, g, cap, match_tc_box_rows(1));
+      if (rc) return rc;
+      StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH_TC);
+      RIFT2_CU(launch_match_tc(mp, g, cap, c->ws, &ta, &tb, nsplit, c->status, st));
+    }
   }
   return RIFT2_OK;
 }

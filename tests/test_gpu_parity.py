@@ -287,3 +287,60 @@ def test_edge_images(pkg, dev):
     # unsupported size (prime factor 11) is refused, not computed wrongly
     with pytest.raises(pkg.Rift2Error):
         ctx.extract([torch.rand((121, 128), device=dev)])
+
+
+@pytest.mark.parametrize("na,nb", [(3000, 4500), (129, 127), (1, 300), (640, 1)])
+def test_tensor_core_matcher_matches_oracle_and_cuda_core_form(pkg, dev, na, nb):
+    """tcgen05 path (default) against the oracle and the CUDA-core form, several tiles and
+    ragged edges; descriptors are random count vectors with cells summing to 256."""
+    rng = np.random.default_rng(na + 7 * nb)
+
+    def rand_desc(n):
+        d = np.zeros((n, 216), dtype=np.int64)
+        for c in range(36):
+            w = rng.dirichlet(np.full(6, 0.7), size=n)
+            d[:, c * 6:(c + 1) * 6] = rng.multinomial(256, [1 / 6] * 6, size=n) if False else \
+                np.array([rng.multinomial(256, wi) for wi in w])
+        return d
+    a, b = rand_desc(na), rand_desc(nb)
+    b[nb // 2] = a[0]
+    ctx_tc = pkg.Context(pkg.default_params(max_keypoints=2500), device=0)
+    ctx_pl = pkg.Context(pkg.default_params(max_keypoints=2500, flags=pkg.FLAG_PLAIN_MATCH),
+                         device=0)
+    out = []
+    for ctx in (ctx_tc, ctx_pl):
+        fa = _features_from(ctx, dev, a, np.arange(na))
+        fb = _features_from(ctx, dev, b, np.arange(nb))
+        m = ctx.match([fa], [fb])[0]
+        ctx.sync()
+        out.append(m.host())
+    nn, d1, d2, near = O.match(a, b)
+    for m in out:
+        assert len(m["nn_desc"]) == na
+        assert np.all((m["nn_desc"] == nn) | near)
+        np.testing.assert_allclose(m["d1"], d1, rtol=1e-5, atol=1e-9)
+        if nb > 1:
+            np.testing.assert_allclose(m["d2"], d2, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(out[0]["nn_desc"], out[1]["nn_desc"])
+
+
+def test_tensor_core_matcher_batch_of_pairs(pkg, dev):
+    """Several pairs of different sizes in one call share the launches."""
+    rng = np.random.default_rng(11)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=800), device=0)
+    sizes = [(900, 1500), (1, 1), (1600, 200), (0, 50)]
+    fas, fbs, exp = [], [], []
+    for na, nb in sizes:
+        a = rng.integers(0, 60, size=(na, 216))
+        b = rng.integers(0, 60, size=(nb, 216))
+        fas.append(_features_from(ctx, dev, a, np.arange(na)))
+        fbs.append(_features_from(ctx, dev, b, np.arange(nb)))
+        exp.append(O.match(a, b) if na else None)
+    ms = ctx.match(fas, fbs)
+    ctx.sync()
+    for m, e, (na, nb) in zip(ms, exp, sizes):
+        h = m.host()
+        assert len(h["nn_desc"]) == na
+        if na:
+            nn, d1, d2, near = e
+            assert np.all((h["nn_desc"] == nn) | near)
