@@ -20,26 +20,25 @@
 
 namespace rift2 {
 
-constexpr int TC_BM = 128, TC_BN = 64, TC_KP = 256, TC_KATOM = 64, TC_NATOM = 4;
+constexpr int TC_BM = 128, TC_BN = 128, TC_KP = 256, TC_KATOM = 64, TC_NATOM = 4;
 constexpr int TC_KSTEPS = 14;                             // 14 x 16 = 224 >= 216
 constexpr int TC_A_ATOM = TC_BM * 128;                    // 128 rows x 128 bytes = 16 KB
-constexpr int TC_B_ATOM = TC_BN * 128;                    // 64 rows x 128 bytes = 8 KB
+constexpr int TC_B_ATOM = TC_BN * 128;                    // 16 KB: one K-atom of a B tile
 constexpr int TC_A_BYTES = TC_NATOM * TC_A_ATOM;          // 64 KB
-constexpr int TC_B_BYTES = TC_NATOM * TC_B_ATOM;          // 32 KB per stage
-constexpr int TC_STAGES = 4;                              // B tiles in flight
-constexpr int TC_ACC = 4;                                 // accumulators in TMEM
+constexpr int TC_SLOTS = 8;                               // B K-atoms in flight (2 tiles)
+constexpr int TC_ACC = 2;                                 // accumulators in TMEM
 constexpr int TC_TOPK = 8;
 constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;        // warp 0 TMA, warp 1 MMA, epilogue
 constexpr int TC_HALVES = TC_EPI_WARPS / 4;               // column slices per quadrant
-constexpr int TC_SLICE = TC_BN / TC_HALVES;               // 32 columns per epilogue warp
+constexpr int TC_SLICE = TC_BN / TC_HALVES;               // 64 columns per epilogue warp
 constexpr int TC_TMEM_COLS = TC_ACC * TC_BN;              // 256
 constexpr long long TC_WAIT = 1ll << 26;                  // bounded mbarrier polls
-constexpr int TC_NBARS = 1 + 5 * TC_STAGES;
-constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_STAGES * TC_B_BYTES + 256 +
+constexpr int TC_NBARS = 1 + 2 * TC_SLOTS + 3 * TC_ACC;
+constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_SLOTS * TC_B_ATOM + 256 +
                            TC_ACC * TC_BN * sizeof(float);
-static_assert(TC_STAGES == TC_ACC, "one barrier set per stage / accumulator index");
 static_assert(TC_NBARS * 8 + 8 <= 256, "barrier block");
+static_assert(TC_SMEM <= 232448, "shared memory");
 
 // --------------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -105,14 +104,6 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                    bar)
                : "memory");
 }
-// One FP32 accumulator column of this thread's TMEM lane.
-__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
-  uint32_t v;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  return v;
-}
-
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -193,6 +184,20 @@ __device__ __forceinline__ void topk_insert(float (&sc)[TC_TOPK], int (&id)[TC_T
   }
 }
 
+// v[e] for a run-time e in 0..31 without indexing registers dynamically: a select tree.
+__device__ __forceinline__ float pick32(const float (&v)[32], int e) {
+  float a[16], b[8], c[4], d[2];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[k] = (e & 1) ? v[2 * k + 1] : v[2 * k];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) b[k] = (e & 2) ? a[2 * k + 1] : a[2 * k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k] = (e & 4) ? b[2 * k + 1] : b[2 * k];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) d[k] = (e & 8) ? c[2 * k + 1] : c[2 * k];
+  return (e & 16) ? d[1] : d[0];
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ CUtensorMap tmA,
                                                        const __grid_constant__ CUtensorMap tmB,
                                                        TcArgs args) {
@@ -207,28 +212,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
   const int t1 = (int)((long long)(split + 1) * ntiles / args.nsplit);
   const int nt = t1 - t0;
 
-  // 1024-byte aligned: A | B stages | barriers, TMEM slot, flag (256 B) | 1/|b| slots
+  // 1024-byte aligned: A | B K-atom slots | barriers, TMEM slot, flag (256 B) | 1/|b| slots
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tsm) + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;
   unsigned char* sB = base + TC_A_BYTES;
-  unsigned long long* bars =
-      reinterpret_cast<unsigned long long*>(sB + TC_STAGES * TC_B_BYTES);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sB + TC_SLOTS * TC_B_ATOM);
   const uint32_t full_a = su32(&bars[0]);
-  const uint32_t full_b0 = su32(&bars[1]);
-  const uint32_t empty_b0 = full_b0 + 8 * TC_STAGES;
-  const uint32_t tfull0 = empty_b0 + 8 * TC_STAGES;
-  const uint32_t tempty0 = tfull0 + 8 * TC_STAGES;
-  const uint32_t rfull0 = tempty0 + 8 * TC_STAGES;   // 1/|b| slice of a tile staged in smem
+  const uint32_t full0 = su32(&bars[1]);             // B slot filled
+  const uint32_t empty0 = full0 + 8 * TC_SLOTS;      // B slot read by its MMAs
+  const uint32_t tfull0 = empty0 + 8 * TC_SLOTS;     // accumulator ready
+  const uint32_t tempty0 = tfull0 + 8 * TC_ACC;      // accumulator drained
+  const uint32_t rfull0 = tempty0 + 8 * TC_ACC;      // 1/|b| slice staged
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(&bars[TC_NBARS]);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* rinv_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 256);
 
   if (threadIdx.x == 0) {
     mbar_init(full_a, 1);
-    for (int i = 0; i < TC_STAGES; ++i) {
-      mbar_init(full_b0 + 8 * i, 1);
-      mbar_init(empty_b0 + 8 * i, 1);
+    for (int i = 0; i < TC_SLOTS; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < TC_ACC; ++i) {
       mbar_init(tfull0 + 8 * i, 1);
       mbar_init(tempty0 + 8 * i, 32 * TC_EPI_WARPS);
       mbar_init(rfull0 + 8 * i, TC_BN);
@@ -259,14 +265,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
       mbar_expect_tx(full_a, TC_A_BYTES);
       for (int a = 0; a < TC_NATOM; ++a)
         tma_load_3d(su32(sA + a * TC_A_ATOM), &tmA, a * TC_KATOM, m0, pr, full_a);
-      for (int i = 0; i < nt && !*abort_flag; ++i) {
-        const int st = i % TC_STAGES;
-        if (i >= TC_STAGES &&
-            !mbar_wait_bounded(empty_b0 + 8 * st, ((i / TC_STAGES) - 1) & 1)) { fail(); break; }
-        mbar_expect_tx(full_b0 + 8 * st, TC_B_BYTES);
-        for (int a = 0; a < TC_NATOM; ++a)
-          tma_load_3d(su32(sB + st * TC_B_BYTES + a * TC_B_ATOM), &tmB, a * TC_KATOM,
-                      (t0 + i) * TC_BN, pr, full_b0 + 8 * st);
+      for (int u = 0; u < nt * TC_NATOM && !*abort_flag; ++u) {
+        const int slot = u % TC_SLOTS, a = u % TC_NATOM;
+        if (u >= TC_SLOTS && !mbar_wait_bounded(empty0 + 8 * slot, ((u / TC_SLOTS) - 1) & 1)) {
+          fail();
+          break;
+        }
+        mbar_expect_tx(full0 + 8 * slot, TC_B_ATOM);
+        tma_load_3d(su32(sB + slot * TC_B_ATOM), &tmB, a * TC_KATOM, (t0 + u / TC_NATOM) * TC_BN,
+                    pr, full0 + 8 * slot);
       }
     }
   } else if (warp == 1) {
@@ -275,24 +282,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
       constexpr uint32_t idesc = umma_idesc_bf16(TC_BM, TC_BN);
       bool ok = mbar_wait_bounded(full_a, 0);
       if (!ok) fail();
+      const uint32_t a0 = su32(sA), b0 = su32(sB);
       for (int i = 0; ok && i < nt && !*abort_flag; ++i) {
-        const int st = i % TC_STAGES, acc = i % TC_ACC;
-        if (!mbar_wait_bounded(full_b0 + 8 * st, (i / TC_STAGES) & 1)) { fail(); break; }
+        const int acc = i % TC_ACC;
         if (i >= TC_ACC && !mbar_wait_bounded(tempty0 + 8 * acc, ((i / TC_ACC) - 1) & 1)) {
           fail();
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
-        const uint32_t a0 = su32(sA), b0 = su32(sB + st * TC_B_BYTES);
-#pragma unroll
-        for (int ks = 0; ks < TC_KSTEPS; ++ks) {
-          const uint32_t ka = (uint32_t)((ks >> 2) * TC_A_ATOM + (ks & 3) * 32);
-          const uint32_t kb = (uint32_t)((ks >> 2) * TC_B_ATOM + (ks & 3) * 32);
-          umma_bf16(d, umma_desc_sw128(a0 + ka), umma_desc_sw128(b0 + kb), idesc, ks > 0);
+        for (int a = 0; a < TC_NATOM; ++a) {
+          const int u = i * TC_NATOM + a, slot = u % TC_SLOTS;
+          if (!mbar_wait_bounded(full0 + 8 * slot, (u / TC_SLOTS) & 1)) { ok = false; break; }
+          tc_fence_after();
+          const int ks_end = (a == TC_NATOM - 1) ? TC_KSTEPS - 4 * a : 4;
+          for (int kk = 0; kk < ks_end; ++kk) {
+            umma_bf16(d, umma_desc_sw128(a0 + a * TC_A_ATOM + kk * 32),
+                      umma_desc_sw128(b0 + slot * TC_B_ATOM + kk * 32), idesc, (a | kk) != 0);
+          }
+          umma_commit(empty0 + 8 * slot);   // slot free once these MMAs have read it
         }
-        umma_commit(empty_b0 + 8 * st);   // B stage free once these MMAs have read it
-        umma_commit(tfull0 + 8 * acc);    // accumulator ready for the epilogue
+        if (!ok) { fail(); break; }
+        umma_commit(tfull0 + 8 * acc);      // accumulator ready for the epilogue
       }
     }
   } else {
@@ -331,30 +342,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
         break;
       }
       tc_fence_after();
-      const int col0 = acc * TC_BN + half * TC_SLICE;
-      const int j0 = (t0 + i) * TC_BN + half * TC_SLICE;
-      const float* rs = rinv_s + col0;
-      uint32_t r[32];
-      tmem_ld32(lane_base + (uint32_t)col0, r);
-      // columns whose score beats this row's current 8th best (one compare per column)
-      const float thr = sc[TC_TOPK - 1];
-      unsigned m = 0;
+#pragma unroll 1
+      for (int c = 0; c < TC_SLICE / 32; ++c) {
+        const int col0 = acc * TC_BN + half * TC_SLICE + c * 32;
+        const int j0 = (t0 + i) * TC_BN + half * TC_SLICE + c * 32;
+        const float* rs = rinv_s + col0;
+        uint32_t r[32];
+        tmem_ld32(lane_base + (uint32_t)col0, r);
+        float sv[32];
+        const float thr = sc[TC_TOPK - 1];
+        unsigned m = 0;
 #pragma unroll
-      for (int e4 = 0; e4 < 8; ++e4) {
-        const float4 rb = *reinterpret_cast<const float4*>(rs + e4 * 4);
-        m |= (__uint_as_float(r[e4 * 4 + 0]) * rb.x > thr ? 1u : 0u) << (e4 * 4 + 0);
-        m |= (__uint_as_float(r[e4 * 4 + 1]) * rb.y > thr ? 1u : 0u) << (e4 * 4 + 1);
-        m |= (__uint_as_float(r[e4 * 4 + 2]) * rb.z > thr ? 1u : 0u) << (e4 * 4 + 2);
-        m |= (__uint_as_float(r[e4 * 4 + 3]) * rb.w > thr ? 1u : 0u) << (e4 * 4 + 3);
-      }
-      if (j0 + 32 > nB) m &= (j0 >= nB) ? 0u : ((1u << (nB - j0)) - 1u);
-      // visit the union of the lanes' columns: the re-read of one column is warp-collective
-      unsigned um = __reduce_or_sync(0xffffffffu, m);
-      while (um) {
-        const int e = __ffs(um) - 1;
-        um &= um - 1;
-        const float s = __uint_as_float(tmem_ld1(lane_base + (uint32_t)(col0 + e))) * rs[e];
-        if (((m >> e) & 1u) && s > sc[TC_TOPK - 1]) topk_insert(sc, id, s, j0 + e);
+        for (int e4 = 0; e4 < 8; ++e4) {
+          const float4 rb = *reinterpret_cast<const float4*>(rs + e4 * 4);
+          sv[e4 * 4 + 0] = __uint_as_float(r[e4 * 4 + 0]) * rb.x;
+          sv[e4 * 4 + 1] = __uint_as_float(r[e4 * 4 + 1]) * rb.y;
+          sv[e4 * 4 + 2] = __uint_as_float(r[e4 * 4 + 2]) * rb.z;
+          sv[e4 * 4 + 3] = __uint_as_float(r[e4 * 4 + 3]) * rb.w;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) m |= (sv[e4 * 4 + e] > thr ? 1u : 0u) << (e4 * 4 + e);
+        }
+        if (j0 + 32 > nB) m &= (j0 >= nB) ? 0u : ((1u << (nB - j0)) - 1u);
+        // each lane walks only its own columns above its threshold (rare after warm-up)
+        while (m) {
+          const int e = __ffs(m) - 1;
+          m &= m - 1;
+          const float s = pick32(sv, e);
+          if (s > sc[TC_TOPK - 1]) {
+            sc[TC_TOPK - 1] = s;
+            id[TC_TOPK - 1] = j0 + e;
+#pragma unroll
+            for (int k = TC_TOPK - 1; k > 0; --k) {
+              if (sc[k] > sc[k - 1]) {
+                const float ts = sc[k]; sc[k] = sc[k - 1]; sc[k - 1] = ts;
+                const int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
+              }
+            }
+          }
+        }
+        __syncwarp();
       }
       tc_fence_before();
       mbar_arrive(tempty0 + 8 * acc);
