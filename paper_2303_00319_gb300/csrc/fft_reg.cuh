@@ -140,6 +140,45 @@ __device__ __forceinline__ void group_fft(float2* xb, int t, const float2* __res
   }
 }
 
+// The same transform when the input already sits in the exchange buffer: every pass
+// (the first included) reads xb and synchronises before overwriting it.
+template <int N, int T, int R0, int R1, int R2, bool INV, class St, class Sync>
+__device__ __forceinline__ void group_fft_xb(float2* xb, int t, const float2* __restrict__ tw,
+                                             St& st, Sync& sync) {
+  static_assert(R0 * R1 * R2 == N, "radices must multiply to N");
+  auto none = [](int) { return make_float2(0.f, 0.f); };
+  if constexpr (R1 == 1) {
+    reg_pass<N, T, R0, 1, INV, false, true>(xb, t, tw, none, st, sync);
+  } else if constexpr (R2 == 1) {
+    reg_pass<N, T, R0, 1, INV, false, false>(xb, t, tw, none, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, true>(xb, t, tw, none, st, sync);
+  } else {
+    reg_pass<N, T, R0, 1, INV, false, false>(xb, t, tw, none, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, false>(xb, t, tw, none, st, sync);
+    reg_pass<N, T, R2, R0 * R1, INV, false, true>(xb, t, tw, none, st, sync);
+  }
+}
+
+// Column-pass shapes (more threads per transform, fewer registers per thread).
+template <int N>
+struct ColShape;
+template <>
+struct ColShape<256> {
+  static constexpr int T = 16, R0 = 16, R1 = 16, R2 = 1, NT = 256;
+};
+template <>
+struct ColShape<512> {
+  static constexpr int T = 32, R0 = 16, R1 = 16, R2 = 2, NT = 256;
+};
+template <>
+struct ColShape<1024> {
+  static constexpr int T = 64, R0 = 16, R1 = 16, R2 = 4, NT = 512;
+};
+template <>
+struct ColShape<2048> {
+  static constexpr int T = 128, R0 = 16, R1 = 16, R2 = 8, NT = 512;
+};
+
 // Register-path shapes: transform length -> threads per transform and pass radices.
 template <int N>
 struct RegShape;

@@ -131,14 +131,22 @@ __device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams
   return expf(-d * d * kp.inv_2ls2) / (1.f + p);
 }
 
-// Angular raised-cosine window of orientation (cos_o, sin_o) at frequency (u, v):
-// with c = cos(theta - theta_o), theta = atan2(-v, u), the window (1 + cos(3 dtheta))/2
-// for |dtheta| < pi/3 equals (1 + c)(2c - 1)^2 / 2 (triple-angle identity), 0 beyond.
-__device__ __forceinline__ float lg_angular(float u, float v, float rinv, float co, float so) {
-  float c = (u * co - v * so) * rinv;
+// Angular raised-cosine window of orientation (cos_o, sin_o) at the unit frequency
+// direction (a, b) = (u, v) / r: with c = cos(theta - theta_o) = a cos_o - b sin_o
+// (theta = atan2(-v, u)), the window (1 + cos(3 dtheta)) / 2 for |dtheta| < pi/3 equals
+// (1 + c)(2c - 1)^2 / 2 (triple-angle identity), and 0 beyond.  (a, b) = (0, 0) at DC.
+__device__ __forceinline__ float lg_angular(float a, float b, float co, float so) {
+  const float c = a * co - b * so;
   if (!(c > 0.5f)) return 0.f;
-  float t = 2.f * c - 1.f;
+  const float t = 2.f * c - 1.f;
   return 0.5f * (1.f + c) * t * t;
+}
+
+// Unit direction of DFT bin (u, v): (fu, fv) / r, or (0, 0) at DC.
+__device__ __forceinline__ float2 unit_dir(float fu, float fv) {
+  const float r2 = fu * fu + fv * fv;
+  const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
+  return make_float2(fu * ri, fv * ri);
 }
 
 // Columns u whose angular window is zero on every row: S_o(u, v) = 0 for all v, so the
@@ -153,10 +161,8 @@ __global__ void angular_zero_cols(int H, int W, KParams kp, unsigned char* __res
   const float fu = fftfreq(u, W);
   bool zero = true;
   for (int v = 0; v < H && zero; ++v) {
-    const float fv = fftfreq(v, H);
-    const float r2 = fu * fu + fv * fv;
-    const float g = (r2 > 0.f) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
-    zero = (g == 0.f);
+    const float2 d = unit_dir(fu, fftfreq(v, H));
+    zero = (lg_angular(d.x, d.y, co, so) == 0.f);
   }
   zc[o * W + u] = zero ? 1 : 0;
 }
@@ -196,9 +202,11 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
     const float co = kp.cos_o[o], so = kp.sin_o[o];
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
       int v = i / tc, c = i % tc, u = c0 + c;
-      float fu = fftfreq(u, W), fv = fftfreq(v, H);
-      float r2 = fu * fu + fv * fv;
-      float g = (r2 > 0.f && u < W) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
+      float g = 0.f;
+      if (u < W) {
+        const float2 d = unit_dir(fftfreq(u, W), fftfreq(v, H));
+        g = lg_angular(d.x, d.y, co, so);
+      }
       float2 x = base[i];
       a[i] = make_float2(x.x * g, x.y * g);
     }
@@ -211,6 +219,41 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
     }
     // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
   }
+}
+
+// Per-pixel reductions over the Ns scales of one orientation (phase-congruency model of
+// §II-A; MIM amplitude sum of §II-B).  z[s] = EO_{s,o}(x) before the 1/(HW) scale.
+//   A = sum_s |EO_s|, Er = sum_s (E mE + O mO - |E mO - O mE|) with (mE, mO) the unit mean
+//   phase vector, q = w / A with the frequency-spread weight w, an0 = |EO_0|.
+// Square roots, reciprocals and the exponential use the SFU approximations (relative
+// error a few 1e-7), well inside the 1e-4 value tolerance and the 1e-5 near-tie margin.
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+__device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], float scale, const KParams& kp,
+                                             float& er, float& q, float& an0, float& sum_an) {
+  float e[NS], od[NS];
+  float sum_e = 0.f, sum_o = 0.f, max_an = 0.f;
+  sum_an = 0.f;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    e[s] = z[s].x * scale;
+    od[s] = z[s].y * scale;
+    const float an = fast_sqrt(e[s] * e[s] + od[s] * od[s]);
+    if (s == 0) an0 = an;
+    sum_e += e[s];
+    sum_o += od[s];
+    sum_an += an;
+    max_an = fmaxf(max_an, an);
+  }
+  const float ixe = __fdividef(1.f, fast_sqrt(sum_e * sum_e + sum_o * sum_o) + kp.eps);
+  const float me = sum_e * ixe, mo = sum_o * ixe;
+  float energy = 0.f;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) energy += e[s] * me + od[s] * mo - fabsf(e[s] * mo - od[s] * me);
+  const float width = (sum_an * __fdividef(1.f, max_an + kp.eps) - 1.f) * kp.inv_ns1;
+  const float wgt = __fdividef(1.f, 1.f + __expf((kp.cutoff - width) * kp.g));
+  er = energy;
+  q = (sum_an > 0.f) ? wgt * __fdividef(1.f, sum_an) : 0.f;
 }
 
 // Row pass of the inverse with the fused per-pixel reductions.  One row per CTA;
@@ -251,29 +294,11 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
     for (int k = 0; k < RR_MAXPIX; ++k) {
       int x = threadIdx.x + k * blockDim.x;
       if (x >= W) break;
-      float e[NS], od[NS];
-      float sum_e = 0.f, sum_o = 0.f, sum_an = 0.f, max_an = 0.f, an0 = 0.f;
+      float2 z[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        float2 z = res[s * W + x];
-        e[s] = z.x * scale;
-        od[s] = z.y * scale;
-        float an = sqrtf(e[s] * e[s] + od[s] * od[s]);
-        if (s == 0) an0 = an;
-        sum_e += e[s];
-        sum_o += od[s];
-        sum_an += an;
-        max_an = fmaxf(max_an, an);
-      }
-      float xe = sqrtf(sum_e * sum_e + sum_o * sum_o) + kp.eps;
-      float me = sum_e / xe, mo = sum_o / xe;
-      float energy = 0.f;
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        energy += e[s] * me + od[s] * mo - fabsf(e[s] * mo - od[s] * me);
-      float width = (sum_an / (max_an + kp.eps) - 1.f) * kp.inv_ns1;
-      float wgt = 1.f / (1.f + expf((kp.cutoff - width) * kp.g));
-      float q = (sum_an > 0.f) ? wgt / sum_an : 0.f;
+      for (int s = 0; s < NS; ++s) z[s] = res[s * W + x];
+      float energy, q, an0, sum_an;
+      reduce_pixel(z, scale, kp, energy, q, an0, sum_an);
       size_t off = ((size_t)img * NO + o) * P + (size_t)row * W + x;
       er_out[off] = energy;
       q_out[off] = q;
@@ -299,24 +324,25 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
 constexpr int REG_THREADS = 256;
 
 template <int H>
-__global__ void __launch_bounds__(REG_THREADS) lg_cols_reg(const float2* __restrict__ spec,
-                                                           float2* __restrict__ scratch, int W,
-                                                           const float2* __restrict__ twh,
-                                                           KParams kp,
-                                                           const unsigned char* __restrict__ zc) {
-  using S = RegShape<H>;
-  constexpr int T = S::T;
-  constexpr int COLS = REG_THREADS / T;
+__global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __restrict__ spec,
+                                                              float2* __restrict__ scratch, int W,
+                                                              const float2* __restrict__ twh,
+                                                              KParams kp,
+                                                              const unsigned char* __restrict__ zc) {
+  using S = ColShape<H>;
+  constexpr int T = S::T, NT = S::NT;
+  constexpr int COLS = NT / T;
+  constexpr int E = H / T;
   constexpr int XS = XBuf<H>::SIZE;
   extern __shared__ float2 sm[];
-  float2* base = sm;               // [COLS][XS]
-  float2* xbuf = sm + COLS * XS;   // [COLS][XS]
+  float2* base = sm;               // [COLS][XS]  F * R_s
+  float2* xbuf = sm + COLS * XS;   // [COLS][XS]  exchange buffers
   const int s = blockIdx.y, img = blockIdx.z;
   const int c0 = blockIdx.x * COLS;
   const int tid = threadIdx.x;
   const float2* F = spec + (size_t)img * H * W;
   const float log_fs = kp.log_fs[s];
-  for (int i = tid; i < H * COLS; i += REG_THREADS) {
+  for (int i = tid; i < H * COLS; i += NT) {
     const int v = i / COLS, c = i % COLS, u = c0 + c;
     float2 f = make_float2(0.f, 0.f);
     if (u < W) {
@@ -327,12 +353,19 @@ __global__ void __launch_bounds__(REG_THREADS) lg_cols_reg(const float2* __restr
     }
     base[c * XS + xpad(v)] = f;
   }
-  __syncthreads();
   const int col = tid / T, t = tid % T;
   const int u = c0 + col;
-  const float fu = fftfreq(u, W);
   float2* xb = xbuf + col * XS;
   const float2* bc = base + col * XS;
+  // unit directions of this thread's elements v = t + T k, shared by the six windows
+  float2 dir[E];
+  {
+    const float fu = (u < W) ? fftfreq(u, W) : 0.f;
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+      dir[k] = (u < W) ? unit_dir(fu, fftfreq(t + T * k, H)) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
   auto sync = [] {
     if constexpr (T <= 32) __syncwarp();
     else __syncthreads();
@@ -347,19 +380,20 @@ __global__ void __launch_bounds__(REG_THREADS) lg_cols_reg(const float2* __restr
     if constexpr (T <= 32) skip = __all_sync(0xffffffffu, zcol);
     else skip = __syncthreads_and(zcol);
     if (!skip) {
-      auto ld = [&](int v) -> float2 {
-        const float fv = fftfreq(v, H);
-        const float r2 = fu * fu + fv * fv;
-        const float g = (r2 > 0.f && u < W) ? lg_angular(fu, fv, rsqrtf(r2), co, so) : 0.f;
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const int v = t + T * k;
+        const float g = lg_angular(dir[k].x, dir[k].y, co, so);
         const float2 x = bc[xpad(v)];
-        return make_float2(x.x * g, x.y * g);
-      };
+        xb[xpad(v)] = make_float2(x.x * g, x.y * g);
+      }
+      sync();
       auto st = [&](int v, float2 val) { xb[xpad(v)] = val; };
-      group_fft<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, ld, st, sync);
+      group_fft_xb<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, st, sync);
     }
     __syncthreads();
     float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W;
-    for (int i = tid; i < H * COLS; i += REG_THREADS) {
+    for (int i = tid; i < H * COLS; i += NT) {
       const int v = i / COLS, c = i % COLS;
       if (c0 + c < W && !zc[o * W + c0 + c]) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
     }
@@ -422,29 +456,11 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
       const int pix = tid + REG_THREADS * k;
       const int r2 = pix / WN, x = pix % WN;
       if (row0 + r2 >= H) continue;
-      float e[NS], od[NS];
-      float sum_e = 0.f, sum_o = 0.f, sum_an = 0.f, max_an = 0.f, an0 = 0.f;
+      float2 z[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        const float2 z = sm[(r2 * NS + s) * XS + xpad(x)];
-        e[s] = z.x * scale;
-        od[s] = z.y * scale;
-        const float an = sqrtf(e[s] * e[s] + od[s] * od[s]);
-        if (s == 0) an0 = an;
-        sum_e += e[s];
-        sum_o += od[s];
-        sum_an += an;
-        max_an = fmaxf(max_an, an);
-      }
-      const float xe = sqrtf(sum_e * sum_e + sum_o * sum_o) + kp.eps;
-      const float me = sum_e / xe, mo = sum_o / xe;
-      float energy = 0.f;
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        energy += e[s] * me + od[s] * mo - fabsf(e[s] * mo - od[s] * me);
-      const float width = (sum_an / (max_an + kp.eps) - 1.f) * kp.inv_ns1;
-      const float wgt = 1.f / (1.f + expf((kp.cutoff - width) * kp.g));
-      const float q = (sum_an > 0.f) ? wgt / sum_an : 0.f;
+      for (int s = 0; s < NS; ++s) z[s] = sm[(r2 * NS + s) * XS + xpad(x)];
+      float energy, q, an0, sum_an;
+      reduce_pixel(z, scale, kp, energy, q, an0, sum_an);
       const size_t off = ((size_t)img * NO + o) * P + (size_t)(row0 + r2) * WN + x;
       er_out[off] = energy;
       q_out[off] = q;
@@ -468,11 +484,12 @@ template <int H>
 static cudaError_t cols_reg(const float2* spec, float2* scratch, int nimg, int W,
                             const FftPlan& ph, const KParams& kp, const unsigned char* zc,
                             cudaStream_t st) {
-  constexpr int COLS = REG_THREADS / RegShape<H>::T;
+  constexpr int NT = ColShape<H>::NT;
+  constexpr int COLS = NT / ColShape<H>::T;
   const size_t sm = 2 * (size_t)COLS * XBuf<H>::SIZE * sizeof(float2);
   cudaFuncSetAttribute(lg_cols_reg<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  lg_cols_reg<H><<<dim3((W + COLS - 1) / COLS, NS, nimg), REG_THREADS, sm, st>>>(spec, scratch, W,
-                                                                                ph.tw, kp, zc);
+  lg_cols_reg<H><<<dim3((W + COLS - 1) / COLS, NS, nimg), NT, sm, st>>>(spec, scratch, W, ph.tw,
+                                                                       kp, zc);
   return cudaGetLastError();
 }
 
