@@ -199,6 +199,43 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   }
 }
 
+__global__ void init_detect(unsigned* minmax, unsigned* ccount, int g) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < g) {
+    minmax[2 * i] = 0xFFFFFFFFu;
+    minmax[2 * i + 1] = 0u;
+    ccount[i] = 0u;
+  }
+}
+
+__global__ void minmax_kernel(const float* __restrict__ m, long long P, unsigned* minmax) {
+  const int img = blockIdx.y;
+  float lo = 3.0e38f, hi = -3.0e38f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v = m[(size_t)img * P + i];
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // callers of the stage entry pass non-negative moment maps (M >= eps / 2 > 0)
+    atomicMin(minmax + 2 * img, __float_as_uint(fmaxf(lo, 0.f)));
+    atomicMax(minmax + 2 * img + 1, __float_as_uint(fmaxf(hi, 0.f)));
+  }
+}
+
+void launch_init_detect(unsigned* minmax, unsigned* ccount, int g, cudaStream_t st) {
+  init_detect<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
+}
+
+void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStream_t st) {
+  minmax_kernel<<<dim3(256, g), 256, 0, st>>>(m, P, minmax);
+}
+
 cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st) {
   dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, nimg);

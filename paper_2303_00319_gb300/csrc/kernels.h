@@ -45,6 +45,15 @@ struct DetectWs {
 };
 cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st);
+// min = +inf bits, max = 0, candidate counts = 0 for g images
+void launch_init_detect(unsigned* minmax, unsigned* ccount, int g, cudaStream_t st);
+// image-wide min / max of g non-negative maps [g][P] (ordered-int atomics)
+void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStream_t st);
+// worst-case number of NMS survivors of an H x W map (one per 2 x 2 block)
+inline int detect_cap_candidates(int H, int W) { return ((H + 1) / 2) * ((W + 1) / 2); }
+
+// rift2_api.cu — scalar kernel parameters derived from the public parameter struct
+void derive_kparams(const rift2_params& p, KParams& k);
 
 // k_describe.cu — MIM patch histograms, dominant index, recoded descriptors.
 struct DescribeWs {

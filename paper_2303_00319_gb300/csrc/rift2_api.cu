@@ -14,6 +14,35 @@
 
 using namespace rift2;
 
+namespace rift2 {
+void derive_kparams(const rift2_params& p, KParams& k) {
+  for (int s = 0; s < NS; ++s)
+    k.log_fs[s] = (float)(-std::log((double)p.min_wavelength) - s * std::log((double)p.mult));
+  double ls = std::log((double)p.sigma_onf);
+  k.inv_2ls2 = (float)(1.0 / (2.0 * ls * ls));
+  k.inv_lp_c2 = (float)(1.0 / ((double)p.lp_cutoff * p.lp_cutoff));
+  k.lp_order = p.lp_order;
+  for (int o = 0; o < NO; ++o) {
+    double a = o * M_PI / NO;
+    k.cos_o[o] = (float)std::cos(a);
+    k.sin_o[o] = (float)std::sin(a);
+  }
+  k.eps = p.eps;
+  k.g = p.g;
+  k.cutoff = p.cutoff;
+  k.inv_ns1 = (float)(1.0 / (p.n_scales - 1));
+  double inv_mult = 1.0 / p.mult;
+  double scale_sum = (1.0 - std::pow(inv_mult, p.n_scales)) / (1.0 - inv_mult);
+  k.noise_c = (float)(scale_sum / std::sqrt(std::log(4.0)) *
+                      (std::sqrt(M_PI / 2.0) + p.k * std::sqrt((4.0 - M_PI) / 2.0)));
+  k.fast_t = p.fast_threshold;
+  k.fast_arc = p.fast_arc;
+  k.max_kp = p.max_keypoints;
+  k.ratio_pm = (int)std::lround(p.second_ratio * 1000.0);
+}
+
+}  // namespace rift2
+
 struct rift2_ctx {
   int device = 0;
   rift2_params p{};
@@ -133,32 +162,6 @@ int ensure_ws(rift2_ctx* c, size_t need) {
   return RIFT2_OK;
 }
 
-void derive_kparams(const rift2_params& p, KParams& k) {
-  for (int s = 0; s < NS; ++s)
-    k.log_fs[s] = (float)(-std::log((double)p.min_wavelength) - s * std::log((double)p.mult));
-  double ls = std::log((double)p.sigma_onf);
-  k.inv_2ls2 = (float)(1.0 / (2.0 * ls * ls));
-  k.inv_lp_c2 = (float)(1.0 / ((double)p.lp_cutoff * p.lp_cutoff));
-  k.lp_order = p.lp_order;
-  for (int o = 0; o < NO; ++o) {
-    double a = o * M_PI / NO;
-    k.cos_o[o] = (float)std::cos(a);
-    k.sin_o[o] = (float)std::sin(a);
-  }
-  k.eps = p.eps;
-  k.g = p.g;
-  k.cutoff = p.cutoff;
-  k.inv_ns1 = (float)(1.0 / (p.n_scales - 1));
-  double inv_mult = 1.0 / p.mult;
-  double scale_sum = (1.0 - std::pow(inv_mult, p.n_scales)) / (1.0 - inv_mult);
-  k.noise_c = (float)(scale_sum / std::sqrt(std::log(4.0)) *
-                      (std::sqrt(M_PI / 2.0) + p.k * std::sqrt((4.0 - M_PI) / 2.0)));
-  k.fast_t = p.fast_threshold;
-  k.fast_arc = p.fast_arc;
-  k.max_kp = p.max_keypoints;
-  k.ratio_pm = (int)std::lround(p.second_ratio * 1000.0);
-}
-
 int check_size(int H, int W) {
   if (H < 16 || W < 16) return RIFT2_E_INVAL;
   FftPlan t{};
@@ -244,35 +247,6 @@ Layout extract_layout(int g, int H, int W, int max_kp, bool debug) {
 template <typename T>
 T* at(void* base, size_t off) {
   return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(static_cast<char*>(base) + off);
-}
-
-__global__ void init_group(unsigned* minmax, unsigned* ccount, int g) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < g) {
-    minmax[2 * i] = 0xFFFFFFFFu;
-    minmax[2 * i + 1] = 0u;
-    ccount[i] = 0u;
-  }
-}
-
-__global__ void minmax_kernel(const float* __restrict__ m, long long P, unsigned* minmax) {
-  const int img = blockIdx.y;
-  float lo = 3.0e38f, hi = -3.0e38f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
-       i += (long long)gridDim.x * blockDim.x) {
-    float v = m[(size_t)img * P + i];
-    lo = fminf(lo, v);
-    hi = fmaxf(hi, v);
-  }
-  for (int d = 16; d > 0; d >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, d));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    // callers of the stage entry pass non-negative moment maps (M >= eps / 2 > 0)
-    atomicMin(minmax + 2 * img, __float_as_uint(fmaxf(lo, 0.f)));
-    atomicMax(minmax + 2 * img + 1, __float_as_uint(fmaxf(hi, 0.f)));
-  }
 }
 
 int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int g, int H, int pitch) {
@@ -388,7 +362,7 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   unsigned* minmax = at<unsigned>(ws, L.minmax);
   unsigned* ccount = at<unsigned>(ws, L.ccount);
   c->launches += K_INIT;
-  init_group<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
+  launch_init_detect(minmax, ccount, g, st);
   RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * 2 * 4096 * 4, st));
   float2* spec = at<float2>(ws, L.spec);
   {
@@ -707,9 +681,9 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
     unsigned* minmax = at<unsigned>(c->ws, L.minmax);
     unsigned* ccount = at<unsigned>(c->ws, L.ccount);
     c->launches += K_INIT + 1 + K_DETECT;
-    init_group<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
+    launch_init_detect(minmax, ccount, g, st);
     const float* m = moment + (size_t)i0 * P;
-    minmax_kernel<<<dim3(256, g), 256, 0, st>>>(m, P, minmax);
+    launch_minmax(m, g, P, minmax, st);
     FeatPtrs fp = feat_ptrs(out + i0, g);
     DetectWs dw{minmax, at<unsigned long long>(c->ws, L.cand), ccount, L.cap_cand};
     RIFT2_CU(launch_detect(m, g, H, W, c->kp, dw, fp, st));
