@@ -266,6 +266,32 @@ int rift2_detect(rift2_ctx* ctx, int n, const float* moment, int height, int wid
 int rift2_describe(rift2_ctx* ctx, int n, const unsigned char* mim, int height, int width,
                    rift2_features* feats, void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Allocation-free keypoint detection.  The paper has no counterpart: this is a service
+ * for callers that must not allocate device memory — code whose device memory belongs
+ * to a framework's caching allocator, real-time loops that cannot absorb the implicit
+ * device synchronisation of cudaMalloc / cudaFree, and hosts that budget every byte of
+ * device memory in advance.
+ *
+ * rift2_detect_static does what rift2_detect does for ONE map (min-max normalisation,
+ * FAST, 3x3 NMS, top max_keypoints of moment [H][W], device pointer) without a context:
+ * it calls no cudaMalloc, cudaFree or allocating library routine.  Its only scratch
+ * memory is a fixed file-scope device array of RIFT2_STATIC_MAX_CANDIDATES candidate
+ * slots (about 2 MiB), which every GPU that loads the library holds until the process
+ * exits.  A map needs ceil(H/2) * ceil(W/2) slots (any 1024 x 1024 map fits); larger
+ * maps are refused with RIFT2_E_CAPACITY before anything is enqueued.
+ *  - params: NULL for the defaults; out: kp_xy, kp_score, counts (cap_kp >= max_keypoints).
+ *  - Runs on the calling thread's current device and the given stream.  The first call
+ *    on a device looks up the array's device address; make that first call before any
+ *    CUDA stream capture.
+ *  - Every call shares the one array (it keeps the last call's contents; each call resets
+ *    what must start at zero).  Calls whose work overlaps on the GPU (other streams, other
+ *    host threads, concurrent graph launches) race on it: serialise them.
+ * ---------------------------------------------------------------------------- */
+#define RIFT2_STATIC_MAX_CANDIDATES 262144
+int rift2_detect_static(const rift2_params* params, const float* moment, int height, int width,
+                        rift2_features* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

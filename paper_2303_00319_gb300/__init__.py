@@ -25,7 +25,8 @@ DESC_DIM = CELLS * CELLS * NO
 EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_extract",
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
-           "rift2_describe")
+           "rift2_describe", "rift2_detect_static")
+STATIC_MAX_CANDIDATES = 262144
 STAGES = ("fft_fwd", "lg_cols", "lg_rows", "noise", "moment", "detect", "describe", "match")
 
 
@@ -92,6 +93,8 @@ def lib():
                                    C.POINTER(FeaturesC), C.c_void_p]
         L.rift2_describe.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                      C.POINTER(FeaturesC), C.c_void_p]
+        L.rift2_detect_static.argtypes = [C.POINTER(Params), C.c_void_p, C.c_int, C.c_int,
+                                          C.POINTER(FeaturesC), C.c_void_p]
         _LIB = L
     return _LIB
 
@@ -316,3 +319,16 @@ class Context:
         _check(lib().rift2_describe(self._h, n, _ptr(mim), h, w, fc, _stream(stream)),
                "rift2_describe")
         return feats
+
+
+def detect_static(moment, feats: Features, params: Params | None = None, stream=None):
+    """Keypoints of one moment map [H][W] (float32, CUDA) without any device allocation by
+    the library (rift2_detect_static): for callers that must not allocate device memory.
+    `feats` supplies the output buffers.  Calls that overlap on the GPU share one static
+    scratch array and must be serialised."""
+    h, w = moment.shape
+    fc, _ = feats.to_c()
+    p = C.byref(params) if params is not None else None
+    _check(lib().rift2_detect_static(p, _ptr(moment), h, w, C.byref(fc), _stream(stream)),
+           "rift2_detect_static")
+    return feats
