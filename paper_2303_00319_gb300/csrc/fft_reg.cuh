@@ -87,7 +87,8 @@ struct XBuf {
   static constexpr int SIZE = N + N / 32 + 2;   // +2: staggers consecutive buffers' banks
 };
 
-// One pass.  Inputs come from `ld(index)` (FIRST) or the exchange buffer; outputs go to
+// One pass.  Inputs come from `ld(i, r, index)` (FIRST; i = butterfly of this thread,
+// r = butterfly input, both compile-time) or the exchange buffer; outputs go to
 // `st(index, value)` (LAST) or the exchange buffer.  `sync()` synchronises the group.
 template <int N, int T, int R, int NS, bool INV, bool FIRST, bool LAST, class Ld, class St,
           class Sync>
@@ -100,7 +101,7 @@ __device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __rest
   for (int i = 0; i < B; ++i) {
     const int j = t + T * i;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i][r] = FIRST ? ld(j + r * M) : xb[xpad(j + r * M)];
+    for (int r = 0; r < R; ++r) v[i][r] = FIRST ? ld(i, r, j + r * M) : xb[xpad(j + r * M)];
   }
   if (!FIRST) sync();   // every read of xb is done before this pass overwrites it
 #pragma unroll
@@ -146,7 +147,7 @@ template <int N, int T, int R0, int R1, int R2, bool INV, class St, class Sync>
 __device__ __forceinline__ void group_fft_xb(float2* xb, int t, const float2* __restrict__ tw,
                                              St& st, Sync& sync) {
   static_assert(R0 * R1 * R2 == N, "radices must multiply to N");
-  auto none = [](int) { return make_float2(0.f, 0.f); };
+  auto none = [](int, int, int) { return make_float2(0.f, 0.f); };
   if constexpr (R1 == 1) {
     reg_pass<N, T, R0, 1, INV, false, true>(xb, t, tw, none, st, sync);
   } else if constexpr (R2 == 1) {
@@ -172,7 +173,7 @@ struct ColShape<512> {
 };
 template <>
 struct ColShape<1024> {
-  static constexpr int T = 64, R0 = 16, R1 = 16, R2 = 4, NT = 512;
+  static constexpr int T = 32, R0 = 32, R1 = 32, R2 = 1, NT = 128;
 };
 template <>
 struct ColShape<2048> {

@@ -90,17 +90,26 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
     unsigned w[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) w[i] = wp[i];
+    // bins 0..No-2 by byte-wise compares; the last bin is what remains of the 16 pixels
+    // (MIM values are 0..No-1)
     unsigned cnt[NO] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       unsigned v = __funnelshift_r(w[i], w[i + 1], a8);
 #pragma unroll
-      for (int b = 0; b < NO; ++b) cnt[b] += __popc(__vcmpeq4(v, 0x01010101u * b));
+      for (int b = 0; b < NO - 1; ++b) cnt[b] += __popc(__vcmpeq4(v, 0x01010101u * b));
     }
-    // 8 bits per matching byte; pack two bins per word (cell totals <= 256)
-    unsigned p0 = (cnt[0] >> 3) | ((cnt[1] >> 3) << 16);
-    unsigned p1 = (cnt[2] >> 3) | ((cnt[3] >> 3) << 16);
-    unsigned p2 = (cnt[4] >> 3) | ((cnt[5] >> 3) << 16);
+    unsigned rest = 16;
+#pragma unroll
+    for (int b = 0; b < NO - 1; ++b) {
+      cnt[b] >>= 3;   // 8 bits per matching byte
+      rest -= cnt[b];
+    }
+    cnt[NO - 1] = rest;
+    // pack two bins per word (cell totals <= 256)
+    unsigned p0 = cnt[0] | (cnt[1] << 16);
+    unsigned p1 = cnt[2] | (cnt[3] << 16);
+    unsigned p2 = cnt[4] | (cnt[5] << 16);
 #pragma unroll
     for (int d = 1; d < 16; d <<= 1) {
       p0 += __shfl_xor_sync(0xffffffffu, p0, d);

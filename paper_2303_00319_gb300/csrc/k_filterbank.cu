@@ -115,6 +115,125 @@ __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H
   }
 }
 
+constexpr int REG_NT = 256;   // threads per CTA of the register-tiled row kernels
+
+// ------------------------------------------------------- register-tiled forward DFT
+// Sum over the T threads of one transform group (T <= 32: shuffles inside the group's
+// lanes; T > 32: through shared memory, one slot per thread).
+template <int T>
+__device__ __forceinline__ float2 group_sum(float2 v, float2* red) {
+  if constexpr (T <= 32) {
+#pragma unroll
+    for (int d = 1; d < T; d <<= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, d);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, d);
+    }
+    return v;
+  } else {
+    const int t = threadIdx.x % T, g0 = threadIdx.x - t;
+    red[threadIdx.x] = v;
+    __syncthreads();
+    float2 a = make_float2(0.f, 0.f);
+    for (int k = 0; k < T; ++k) {
+      const float2 b = red[g0 + k];
+      a.x += b.x;
+      a.y += b.y;
+    }
+    __syncthreads();
+    return a;
+  }
+}
+
+// Rows of real images, one group of T threads per row, mean removed and restored.
+template <int WN>
+__global__ void __launch_bounds__(REG_NT) fwd_rows_reg(ImgPtrs ip, const float* __restrict__ dense,
+                                                       float2* __restrict__ spec, int H,
+                                                       const float2* __restrict__ tww) {
+  using S = RegShape<WN>;
+  constexpr int T = S::T, ROWS = REG_NT / T, E = WN / T, XS = XBuf<WN>::SIZE;
+  extern __shared__ float2 sm[];   // [ROWS][XS] exchange + [REG_NT] reduction slots
+  float2* red = sm + ROWS * XS;
+  const int img = blockIdx.y;
+  const int grp = threadIdx.x / T, t = threadIdx.x % T;
+  const int row = blockIdx.x * ROWS + grp;
+  const bool live = row < H;
+  const float* src = dense ? dense + (size_t)img * H * WN : ip.img[img];
+  const long long pitch = dense ? WN : ip.pitch[img];
+  float xr[E];
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {   // the first pass's inputs: x = t + T k
+    xr[k] = live ? __ldg(src + (size_t)row * pitch + t + T * k) : 0.f;
+    sum += xr[k];
+  }
+  const float mean = group_sum<T>(make_float2(sum, 0.f), red).x / WN;
+  float2* xb = sm + grp * XS;
+  auto ld = [&](int, int r, int) -> float2 { return make_float2(xr[r] - mean, 0.f); };
+  float2* dst = spec + ((size_t)img * H + row) * WN;
+  auto st = [&](int x, float2 val) {
+    if (x == 0) val.x += mean * WN;
+    if (live) dst[x] = val;
+  };
+  auto sync = [] {
+    if constexpr (T <= 32) __syncwarp();
+    else __syncthreads();
+  };
+  group_fft<WN, T, S::R0, S::R1, S::R2, false>(xb, t, tww, ld, st, sync);
+}
+
+// Columns of the spectrum in place, COLS columns per CTA, mean removed and restored.
+template <int HN>
+__global__ void __launch_bounds__(ColShape<HN>::NT) fwd_cols_reg(float2* __restrict__ spec, int W,
+                                                                const float2* __restrict__ twh) {
+  using S = ColShape<HN>;
+  constexpr int T = S::T, NT = S::NT, COLS = NT / T, E = HN / T, XS = XBuf<HN>::SIZE;
+  extern __shared__ float2 sm[];   // [COLS][XS] + [NT] reduction slots
+  float2* red = sm + COLS * XS;
+  const int img = blockIdx.y;
+  const int c0 = blockIdx.x * COLS;
+  float2* base = spec + (size_t)img * HN * W;
+  for (int i = threadIdx.x; i < HN * COLS; i += NT) {
+    const int v = i / COLS, c = i % COLS;
+    sm[c * XS + xpad(v)] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int col = threadIdx.x / T, t = threadIdx.x % T;
+  float2* xb = sm + col * XS;
+  float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const float2 v = xb[xpad(t + T * k)];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  const float2 tot = group_sum<T>(s, red);
+  const float2 mean = make_float2(tot.x / HN, tot.y / HN);
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    float2& v = xb[xpad(t + T * k)];
+    v.x -= mean.x;
+    v.y -= mean.y;
+  }
+  auto sync = [] {
+    if constexpr (T <= 32) __syncwarp();
+    else __syncthreads();
+  };
+  sync();
+  auto st = [&](int v, float2 val) {
+    if (v == 0) {
+      val.x += tot.x;
+      val.y += tot.y;
+    }
+    xb[xpad(v)] = val;
+  };
+  group_fft_xb<HN, T, S::R0, S::R1, S::R2, false>(xb, t, twh, st, sync);
+  __syncthreads();
+  for (int i = threadIdx.x; i < HN * COLS; i += NT) {
+    const int v = i / COLS, c = i % COLS;
+    if (c0 + c < W) base[(size_t)v * W + c0 + c] = sm[c * XS + xpad(v)];
+  }
+}
+
 // ------------------------------------------------------------- log-Gabor transfer
 // Radial part of scale s at squared radius r2 (cycles/px)^2:
 //   exp(-(ln r - ln f_s)^2 / (2 ln^2 sigma_onf)) / (1 + (r^2 / c^2)^n), zero at DC.
@@ -321,7 +440,6 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
 // CTA.  F * R_s is staged once per CTA (coalesced rows of COLS columns); each orientation
 // multiplies the angular window in the first FFT pass, and the results are written back
 // through the exchange buffers as coalesced row segments.
-constexpr int REG_THREADS = 256;
 
 template <int H>
 __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __restrict__ spec,
@@ -337,9 +455,14 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   extern __shared__ float2 sm[];
   float2* base = sm;               // [COLS][XS]  F * R_s
   float2* xbuf = sm + COLS * XS;   // [COLS][XS]  exchange buffers
+  __shared__ unsigned char zcs[NO][COLS];   // zero-window flags of this CTA's columns
   const int s = blockIdx.y, img = blockIdx.z;
   const int c0 = blockIdx.x * COLS;
   const int tid = threadIdx.x;
+  for (int i = tid; i < NO * COLS; i += NT) {
+    const int o = i / COLS, c = i % COLS;
+    zcs[o][c] = (c0 + c < W) ? zc[o * W + c0 + c] : 1;
+  }
   const float2* F = spec + (size_t)img * H * W;
   const float log_fs = kp.log_fs[s];
   for (int i = tid; i < H * COLS; i += NT) {
@@ -357,10 +480,12 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   const int u = c0 + col;
   float2* xb = xbuf + col * XS;
   const float2* bc = base + col * XS;
-  // unit directions of this thread's elements v = t + T k, shared by the six windows
-  float2 dir[E];
-  {
-    const float fu = (u < W) ? fftfreq(u, W) : 0.f;
+  const float fu = (u < W) ? fftfreq(u, W) : 0.f;
+  // unit directions of this thread's elements v = t + T k, shared by the six windows:
+  // kept in registers when a thread owns few elements, recomputed otherwise
+  constexpr bool DIR_REGS = E <= 16;
+  float2 dir[DIR_REGS ? E : 1];
+  if constexpr (DIR_REGS) {
 #pragma unroll
     for (int k = 0; k < E; ++k)
       dir[k] = (u < W) ? unit_dir(fu, fftfreq(t + T * k, H)) : make_float2(0.f, 0.f);
@@ -375,15 +500,18 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
     // a column whose window is zero everywhere transforms to zero: skip it, and leave it
     // unwritten (the row pass reads the same table and substitutes zeros).  The skip is
     // taken per synchronisation domain of the FFT: a warp, or the CTA when T > 32.
-    const bool zcol = (u >= W) || zc[o * W + u];
+    const bool zcol = zcs[o][col] != 0;
     bool skip;
     if constexpr (T <= 32) skip = __all_sync(0xffffffffu, zcol);
     else skip = __syncthreads_and(zcol);
     if (!skip) {
-#pragma unroll
+#pragma unroll 8
       for (int k = 0; k < E; ++k) {
         const int v = t + T * k;
-        const float g = lg_angular(dir[k].x, dir[k].y, co, so);
+        float2 d;
+        if constexpr (DIR_REGS) d = dir[k];
+        else d = (u < W) ? unit_dir(fu, fftfreq(v, H)) : make_float2(0.f, 0.f);
+        const float g = lg_angular(d.x, d.y, co, so);
         const float2 x = bc[xpad(v)];
         xb[xpad(v)] = make_float2(x.x * g, x.y * g);
       }
@@ -395,7 +523,7 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
     float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W;
     for (int i = tid; i < H * COLS; i += NT) {
       const int v = i / COLS, c = i % COLS;
-      if (c0 + c < W && !zc[o * W + c0 + c]) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
+      if (!zcs[o][c]) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
     }
     __syncthreads();
   }
@@ -405,7 +533,7 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
 // after each orientation's four scales are in shared memory every thread reduces its
 // pixels (same formulas as lg_rows_reduce).
 template <int WN>
-__global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restrict__ scratch, int H,
+__global__ void __launch_bounds__(REG_NT) lg_rows_reg(const float2* __restrict__ scratch, int H,
                                                            const float2* __restrict__ tww,
                                                            KParams kp, float* __restrict__ er_out,
                                                            float* __restrict__ q_out,
@@ -416,14 +544,14 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
                                                            const unsigned char* __restrict__ zc) {
   using S = RegShape<WN>;
   constexpr int T = S::T;
-  constexpr int GROUPS = REG_THREADS / T;
+  constexpr int GROUPS = REG_NT / T;
   constexpr int ROWS = GROUPS / NS;
   constexpr int XS = XBuf<WN>::SIZE;
-  constexpr int PIX = ROWS * WN / REG_THREADS;
+  constexpr int PIX = ROWS * WN / REG_NT;
   static_assert(ROWS >= 1 && PIX >= 1, "row tile");
   extern __shared__ float2 sm[];   // [GROUPS][XS], group g = (row g / NS, scale g % NS)
   __shared__ unsigned char zcs[NO * WN];
-  for (int i = threadIdx.x; i < NO * WN; i += REG_THREADS) zcs[i] = zc[i];
+  for (int i = threadIdx.x; i < NO * WN; i += REG_NT) zcs[i] = zc[i];
   __syncthreads();
   const int img = blockIdx.y;
   const int row0 = blockIdx.x * ROWS;
@@ -445,7 +573,7 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
   for (int o = 0; o < NO; ++o) {
     const float2* src = scratch + (((size_t)img * NS + sc) * NO + o) * P + (size_t)row * WN;
     const unsigned char* zco = zcs + o * WN;
-    auto ld = [&](int x) -> float2 {
+    auto ld = [&](int, int, int x) -> float2 {
       return (row < H && !zco[x]) ? __ldg(src + x) : make_float2(0.f, 0.f);
     };
     auto st = [&](int x, float2 val) { xb[xpad(x)] = val; };
@@ -453,7 +581,7 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
-      const int pix = tid + REG_THREADS * k;
+      const int pix = tid + REG_NT * k;
       const int r2 = pix / WN, x = pix % WN;
       if (row0 + r2 >= H) continue;
       float2 z[NS];
@@ -472,7 +600,7 @@ __global__ void __launch_bounds__(REG_THREADS) lg_rows_reg(const float2* __restr
   }
 #pragma unroll
   for (int k = 0; k < PIX; ++k) {
-    const int pix = tid + REG_THREADS * k;
+    const int pix = tid + REG_NT * k;
     const int r2 = pix / WN, x = pix % WN;
     if (row0 + r2 < H)
       mim_out[(size_t)img * H * mim_pitch + (size_t)(row0 + r2) * mim_pitch + x] =
@@ -498,11 +626,11 @@ static cudaError_t rows_reg(const float2* scratch, int nimg, int H, const FftPla
                             const KParams& kp, float* er, float* q, float* an0, float* amp,
                             unsigned char* mim, int mim_pitch, const unsigned char* zc,
                             cudaStream_t st) {
-  constexpr int GROUPS = REG_THREADS / RegShape<WN>::T;
+  constexpr int GROUPS = REG_NT / RegShape<WN>::T;
   constexpr int ROWS = GROUPS / NS;
   const size_t sm = (size_t)GROUPS * XBuf<WN>::SIZE * sizeof(float2);
   cudaFuncSetAttribute(lg_rows_reg<WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  lg_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_THREADS, sm, st>>>(
+  lg_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_NT, sm, st>>>(
       scratch, H, pw.tw, kp, er, q, an0, amp, mim, mim_pitch, zc);
   return cudaGetLastError();
 }
@@ -520,19 +648,52 @@ static int cols_tile(int H) {
   return tc;
 }
 
+template <int WN>
+static void rows_fwd_reg(const ImgPtrs& ip, const float* dense, float2* spec, int nimg, int H,
+                         const FftPlan& pw, cudaStream_t st) {
+  constexpr int ROWS = REG_NT / RegShape<WN>::T;
+  const size_t sm = ((size_t)ROWS * XBuf<WN>::SIZE + REG_NT) * sizeof(float2);
+  cudaFuncSetAttribute(fwd_rows_reg<WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  fwd_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_NT, sm, st>>>(ip, dense, spec, H, pw.tw);
+}
+
+template <int HN>
+static void cols_fwd_reg(float2* spec, int nimg, int W, const FftPlan& ph, cudaStream_t st) {
+  constexpr int NT = ColShape<HN>::NT, COLS = NT / ColShape<HN>::T;
+  const size_t sm = ((size_t)COLS * XBuf<HN>::SIZE + NT) * sizeof(float2);
+  cudaFuncSetAttribute(fwd_cols_reg<HN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  fwd_cols_reg<HN><<<dim3((W + COLS - 1) / COLS, nimg), NT, sm, st>>>(spec, W, ph.tw);
+}
+
 cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
                                 int H, int W, const FftPlan& ph, const FftPlan& pw,
                                 cudaStream_t st) {
-  int tr = rows_tile(W);
-  size_t smr = 2 * (size_t)tr * W * sizeof(float2);
-  cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
   ImgPtrs none{};
-  fwd_rows<<<dim3((H + tr - 1) / tr, nimg), 512, smr, st>>>(ip ? *ip : none, dense, spec, H, W,
-                                                           tr, pw);
-  int tc = cols_tile(H);
-  size_t smc = 2 * (size_t)tc * H * sizeof(float2);
-  cudaFuncSetAttribute(fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  fwd_cols<<<dim3((W + tc - 1) / tc, nimg), 512, smc, st>>>(spec, H, W, tc, ph);
+  const ImgPtrs& ipr = ip ? *ip : none;
+  switch (W) {
+    case 256: rows_fwd_reg<256>(ipr, dense, spec, nimg, H, pw, st); break;
+    case 512: rows_fwd_reg<512>(ipr, dense, spec, nimg, H, pw, st); break;
+    case 1024: rows_fwd_reg<1024>(ipr, dense, spec, nimg, H, pw, st); break;
+    case 2048: rows_fwd_reg<2048>(ipr, dense, spec, nimg, H, pw, st); break;
+    default: {
+      int tr = rows_tile(W);
+      size_t smr = 2 * (size_t)tr * W * sizeof(float2);
+      cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+      fwd_rows<<<dim3((H + tr - 1) / tr, nimg), 512, smr, st>>>(ipr, dense, spec, H, W, tr, pw);
+    }
+  }
+  switch (H) {
+    case 256: cols_fwd_reg<256>(spec, nimg, W, ph, st); break;
+    case 512: cols_fwd_reg<512>(spec, nimg, W, ph, st); break;
+    case 1024: cols_fwd_reg<1024>(spec, nimg, W, ph, st); break;
+    case 2048: cols_fwd_reg<2048>(spec, nimg, W, ph, st); break;
+    default: {
+      int tc = cols_tile(H);
+      size_t smc = 2 * (size_t)tc * H * sizeof(float2);
+      cudaFuncSetAttribute(fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+      fwd_cols<<<dim3((W + tc - 1) / tc, nimg), 512, smc, st>>>(spec, H, W, tc, ph);
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -3,9 +3,9 @@
 Stage tests feed the oracle's upstream outputs to the GPU stage, so a near tie upstream
 cannot cascade.  End-to-end tests compare the whole path on the seeded pairs.
 
-Tolerances (float maps): the CUDA path computes the filter bank in FP32; its FFT has an
-error of ~1e-7 of the spectrum's scale, so element-wise errors are measured against
-max(|oracle|, floor * max|oracle|).  Integer outputs (MIM, keypoints, dominant indices,
+Tolerances (float maps): the CUDA path computes the filter bank in FP32; its FFT leaves an
+absolute error of a few ulp of a map's maximum, so element-wise errors are measured
+against max(|oracle|, floor * max|oracle|).  Integer outputs (MIM, keypoints, dominant indices,
 descriptor counts, NN indices) must be identical except at oracle-certified near ties
 (relative top-two margin below 1e-5).
 """
@@ -20,6 +20,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TIE = 1e-5
+# An FP32 transform of 2^20 points leaves an absolute error of a few ulp of a map's
+# maximum; 1e-4 relative is asserted down to 2.5e-3 of the maximum (4 ulp / 1e-4).
+AMP_FLOOR = 2.5e-3
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +70,7 @@ def test_fft2_matches_numpy(pkg, dev, h, w):
 # ------------------------------------------------------------------------- maps
 def test_amplitude_sums(small):
     d = small["fa"].debug
-    assert rel_err(d["amp"].cpu().numpy(), small["oa"].maps["A"], 1e-3) < 1e-4
+    assert rel_err(d["amp"].cpu().numpy(), small["oa"].maps["A"], AMP_FLOOR) < 1e-4
 
 
 def test_mim_exact_except_near_ties(small):
@@ -246,7 +249,7 @@ def test_end_to_end_1024(pkg, dev):
     d = {k: v.cpu().numpy() for k, v in fa.debug.items()}
     mis = d["mim"] != oa.maps["mim"]
     assert np.all(oa.maps["mim_margin"][mis] < TIE)
-    assert rel_err(d["amp"], oa.maps["A"], 1e-3) < 1e-4
+    assert rel_err(d["amp"], oa.maps["A"], AMP_FLOOR) < 1e-4
     np.testing.assert_allclose(d["noise_t"], oa.maps["T"], rtol=1e-5)
     mo = oa.maps["M"]
     assert np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min()) < 5e-6
