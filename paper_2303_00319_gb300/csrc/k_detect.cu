@@ -108,16 +108,18 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
 
 constexpr int SORT_CAP = 16384;
 
+// Ascending bitonic sort of n (a power of two) keys in shared memory; every thread
+// iteration performs one compare-exchange (n / 2 per stage).
 __device__ void bitonic_sort(unsigned long long* s, int n) {
+  const int half = n >> 1;
   for (int k = 2; k <= n; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long a = s[i], b = s[ixj];
-          bool up = (i & k) == 0;
-          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
-        }
+      for (int p = threadIdx.x; p < half; p += blockDim.x) {
+        const int i = 2 * j * (p / j) + (p % j);
+        const int l = i + j;
+        const unsigned long long a = s[i], b = s[l];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) { s[i] = b; s[l] = a; }
       }
       __syncthreads();
     }
@@ -133,10 +135,12 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   unsigned n = ws.cand_count[img];
   if (n > (unsigned)ws.cap_cand) n = ws.cap_cand;
   const unsigned K = kp.max_kp;
+  unsigned kcap = 256;                 // sort size: the smallest power of two >= K
+  while (kcap < K) kcap <<= 1;
   int pbits = 0;
   unsigned long long prefix = 0;
   unsigned nsel = n;   // keys to gather: those whose top pbits bits are <= prefix
-  if (n > SORT_CAP) {
+  if (n > kcap) {
     unsigned below = 0, rank = K - 1;
     while (true) {
       for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
       prefix = (prefix << 8) | d;
       pbits += 8;
       __syncthreads();
-      if (below + hd <= SORT_CAP || pbits >= 64) { nsel = below + hd; break; }
+      if (below + hd <= kcap || pbits >= 64) { nsel = below + hd; break; }
     }
   }
   int nsort = 1;

@@ -9,10 +9,11 @@
 //               warps read the accumulators with tcgen05.ld (double-buffered in TMEM so
 //               the next tile's MMAs overlap) and keep each query's 8 best candidates by
 //               the FP32 score dot / |b|.  No score matrix ever reaches HBM.
-//   nn_rerank : one warp per query: exact integer dot products for its candidates, the
-//               exact comparison of match_common.cuh, distances and near-tie flags.
-// The products and sums of integer counts stay below 2^24, so the tensor-core dot
-// products are exact; the re-rank recomputes them anyway from the integer counts.
+//   nn_rerank : one thread per query: the exact comparison of match_common.cuh over its
+//               candidates, distances and near-tie flags.
+// The products and partial sums of integer counts stay below 2^24, so every FP32 addition
+// in the tensor-core accumulation is exact: the accumulators hold the exact integer dot
+// products, which the epilogue stores with each candidate for the re-rank.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -166,7 +167,7 @@ struct TcArgs {
   const int* counts_a[MAXB];
   const int* counts_b[MAXB];
   const float* rinv_b;   // [pairs][cap]
-  int* cand;             // [pairs][nsplit * TC_HALVES][cap][TOPK]
+  int2* cand;            // [pairs][nsplit * TC_HALVES][cap][TOPK] (index, dot bits)
   int cap, nsplit;
   int* status;
 };
@@ -314,10 +315,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
     const int half = (warp - 2) >> 2;
     const int etid = threadIdx.x - 64;
     const int row = m0 + q * 32 + lane;
-    float sc[TC_TOPK];
+    float sc[TC_TOPK], dt[TC_TOPK];
     int id[TC_TOPK];
 #pragma unroll
-    for (int k = 0; k < TC_TOPK; ++k) { sc[k] = -1.f; id[k] = -1; }
+    for (int k = 0; k < TC_TOPK; ++k) { sc[k] = -1.f; dt[k] = 0.f; id[k] = -1; }
     const float* rinv = args.rinv_b + (size_t)pr * args.cap;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     // 1/|b| of the next tile, prefetched one tile ahead into registers, staged in smem
@@ -349,7 +350,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
         const float* rs = rinv_s + col0;
         uint32_t r[32];
         tmem_ld32(lane_base + (uint32_t)col0, r);
-        float sv[32];
+        float sv[32], dv[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) dv[e] = __uint_as_float(r[e]);
         const float thr = sc[TC_TOPK - 1];
         unsigned m = 0;
 #pragma unroll
@@ -370,11 +373,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
           const float s = pick32(sv, e);
           if (s > sc[TC_TOPK - 1]) {
             sc[TC_TOPK - 1] = s;
+            dt[TC_TOPK - 1] = pick32(dv, e);
             id[TC_TOPK - 1] = j0 + e;
 #pragma unroll
             for (int k = TC_TOPK - 1; k > 0; --k) {
               if (sc[k] > sc[k - 1]) {
                 const float ts = sc[k]; sc[k] = sc[k - 1]; sc[k - 1] = ts;
+                const float td = dt[k]; dt[k] = dt[k - 1]; dt[k - 1] = td;
                 const int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
               }
             }
@@ -386,11 +391,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
       mbar_arrive(tempty0 + 8 * acc);
     }
     if (row < nA) {
-      int* out = args.cand +
-                 (((size_t)pr * args.nsplit * TC_HALVES + split * TC_HALVES + half) * args.cap + row) *
-                     TC_TOPK;
+      int2* out = args.cand +
+                  (((size_t)pr * args.nsplit * TC_HALVES + split * TC_HALVES + half) * args.cap + row) *
+                      TC_TOPK;
 #pragma unroll
-      for (int k = 0; k < TC_TOPK; ++k) out[k] = id[k];
+      for (int k = 0; k < TC_TOPK; ++k) out[k] = make_int2(id[k], __float_as_int(dt[k]));
     }
   }
   __syncthreads();
@@ -408,69 +413,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
 }
 
 // ------------------------------------------------------------------------ re-rank
-// One warp per query.  A descriptor row is 216 uint16 = 54 uint2 words; lane l holds words
-// l and l + 32.  Exact integer dot products for every candidate of every list.
-__device__ __forceinline__ unsigned dot4(uint2 a, uint2 b) {
-  return (a.x & 0xFFFFu) * (b.x & 0xFFFFu) + (a.x >> 16) * (b.x >> 16) +
-         (a.y & 0xFFFFu) * (b.y & 0xFFFFu) + (a.y >> 16) * (b.y >> 16);
-}
-
-__global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int* __restrict__ cand,
+__global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int2* __restrict__ cand,
                                                  const int* __restrict__ n2_a,
                                                  const int* __restrict__ n2_b, int cap,
                                                  int nsplit) {
-  constexpr int WORDS = DESC_DIM / 4;   // 54
   const int pr = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q = blockIdx.x * 8 + warp;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int nA = mp.counts_a[pr][1], nB = mp.counts_b[pr][1];
   if (blockIdx.x == 0 && threadIdx.x == 0) *mp.count[pr] = nA;
   if (q >= nA) return;
-  const uint2* a = reinterpret_cast<const uint2*>(mp.desc_a[pr] + (size_t)q * DESC_DIM);
-  const uint2 z = make_uint2(0u, 0u);
-  const uint2 a0 = a[lane], a1 = (lane + 32 < WORDS) ? a[lane + 32] : z;
-  Cand c1{0.f, 1.f, 0x7fffffff}, c2 = c1;
   const int nl = nsplit * TC_HALVES;
-  for (int sp = 0; sp < nl; ++sp) {
-    const int* cl = cand + (((size_t)pr * nl + sp) * cap + q) * TC_TOPK;
-    int js[TC_TOPK];
-    uint2 b0[TC_TOPK], b1[TC_TOPK];
+  Cand c1{0.f, 1.f, 0x7fffffff}, c2 = c1;
+  for (int l = 0; l < nl; ++l) {
+    const int4* cl = reinterpret_cast<const int4*>(cand + (((size_t)pr * nl + l) * cap + q) * TC_TOPK);
+    int2 e[TC_TOPK];
 #pragma unroll
-    for (int k = 0; k < TC_TOPK; ++k) {
-      js[k] = cl[k];
-      const bool ok = js[k] >= 0 && js[k] < nB;
-      const uint2* b = reinterpret_cast<const uint2*>(mp.desc_b[pr] + (size_t)(ok ? js[k] : 0) * DESC_DIM);
-      b0[k] = ok ? b[lane] : z;
-      b1[k] = (ok && lane + 32 < WORDS) ? b[lane + 32] : z;
-      if (!ok) js[k] = -1;
+    for (int k = 0; k < TC_TOPK / 2; ++k) {
+      const int4 v = __ldg(cl + k);
+      e[2 * k] = make_int2(v.x, v.y);
+      e[2 * k + 1] = make_int2(v.z, v.w);
     }
+    float n2[TC_TOPK];
 #pragma unroll
-    for (int k = 0; k < TC_TOPK; ++k) {
-      unsigned dot = dot4(a0, b0[k]) + dot4(a1, b1[k]);
-      for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);
-      if (js[k] >= 0) push2(c1, c2, Cand{(float)dot, (float)n2_b[(size_t)pr * cap + js[k]], js[k]});
-    }
+    for (int k = 0; k < TC_TOPK; ++k)
+      n2[k] = (e[k].x >= 0 && e[k].x < nB) ? (float)__ldg(n2_b + (size_t)pr * cap + e[k].x) : 0.f;
+#pragma unroll
+    for (int k = 0; k < TC_TOPK; ++k)
+      if (e[k].x >= 0 && e[k].x < nB) push2(c1, c2, Cand{__int_as_float(e[k].y), n2[k], e[k].x});
   }
-  if (lane == 0) {
-    const float na2 = (float)n2_a[(size_t)pr * cap + q];
-    const bool ok1 = c1.j != 0x7fffffff, ok2 = c2.j != 0x7fffffff;
-    const float d1 = ok1 ? exact_dist(na2, c1) : __int_as_float(0x7f800000);
-    const float d2 = ok2 ? exact_dist(na2, c2) : __int_as_float(0x7f800000);
-    mp.q_desc[pr][q] = q;
-    mp.nn_desc[pr][q] = ok1 ? c1.j : -1;
-    mp.kp_a[pr][q] = mp.desc_kp_a[pr][q];
-    mp.kp_b[pr][q] = ok1 ? mp.desc_kp_b[pr][c1.j] : -1;
-    mp.d1[pr][q] = d1;
-    mp.d2[pr][q] = d2;
-    mp.near_tie[pr][q] = (ok2 && (d2 - d1) < 1e-5f * fmaxf(d1, 1e-12f)) ? 1 : 0;
-  }
+  const float na2 = (float)n2_a[(size_t)pr * cap + q];
+  const bool ok1 = c1.j != 0x7fffffff, ok2 = c2.j != 0x7fffffff;
+  const float d1 = ok1 ? exact_dist(na2, c1) : __int_as_float(0x7f800000);
+  const float d2 = ok2 ? exact_dist(na2, c2) : __int_as_float(0x7f800000);
+  mp.q_desc[pr][q] = q;
+  mp.nn_desc[pr][q] = ok1 ? c1.j : -1;
+  mp.kp_a[pr][q] = mp.desc_kp_a[pr][q];
+  mp.kp_b[pr][q] = ok1 ? mp.desc_kp_b[pr][c1.j] : -1;
+  mp.d1[pr][q] = d1;
+  mp.d2[pr][q] = d2;
+  mp.near_tie[pr][q] = (ok2 && (d2 - d1) < 1e-5f * fmaxf(d1, 1e-12f)) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------- launcher
 size_t match_tc_ws_bytes(int npairs, int cap, int nsplit) {
   size_t bf = (size_t)npairs * cap * TC_KP * 2;
   size_t per = (size_t)npairs * cap * 4;
-  return 2 * bf + 3 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 4 + 4096;
+  return 2 * bf + 3 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8 + 4096;
 }
 
 int match_tc_nsplit(int npairs, int cap) {
@@ -493,7 +481,7 @@ cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
   p += (size_t)npairs * cap * 4;
   int* n2b = reinterpret_cast<int*>(p);
   p += (size_t)npairs * cap * 4;
-  int* cand = reinterpret_cast<int*>(p);
+  int2* cand = reinterpret_cast<int2*>(p);
   nn_prep<<<dim3((cap + 7) / 8, 2, npairs), 256, 0, st>>>(mp, abf, bbf, rinv, n2a, n2b, cap);
   TcArgs ta{};
   for (int i = 0; i < npairs; ++i) {
@@ -508,7 +496,7 @@ cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
   const size_t sm = TC_SMEM;
   cudaFuncSetAttribute(nn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   nn_tc<<<dim3((cap + TC_BM - 1) / TC_BM, nsplit, npairs), TC_THREADS, sm, st>>>(*tmA, *tmB, ta);
-  nn_rerank<<<dim3((cap + 7) / 8, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, cap, nsplit);
+  nn_rerank<<<dim3((cap + 255) / 256, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, cap, nsplit);
   return cudaGetLastError();
 }
 

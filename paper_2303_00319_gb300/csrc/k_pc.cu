@@ -21,20 +21,20 @@ __device__ __forceinline__ void med_digit(unsigned bits, int round, unsigned& pr
   else { pre = bits >> 8; dig = bits & 0xFFu; }
 }
 
-__global__ void __launch_bounds__(256) median_hist(const float* __restrict__ an0, long long P,
+__global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0, long long P,
                                                    int round, MedianWs ws) {
   __shared__ unsigned h[2][MED_BINS];
+  const int nslot = (round == 0) ? 1 : 2;   // round 0: both ranks share one histogram
   const int o = blockIdx.y, img = blockIdx.z;
-  for (int i = threadIdx.x; i < 2 * MED_BINS; i += blockDim.x) (&h[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < nslot * MED_BINS; i += blockDim.x) (&h[0][0])[i] = 0;
   const unsigned* st = ws.state + ((size_t)img * NO + o) * 4;
   const unsigned pre0 = st[0], pre1 = st[2];
   __syncthreads();
   const float* src = an0 + ((size_t)img * NO + o) * P;
-  const long long chunk = (P + gridDim.x - 1) / gridDim.x;
+  const long long chunk = ((P + gridDim.x - 1) / gridDim.x + 3) & ~3ll;
   const long long beg = blockIdx.x * chunk;
   const long long end = min(P, beg + chunk);
-  for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    unsigned bits = __float_as_uint(__ldg(src + i));
+  auto one = [&](unsigned bits) {
     unsigned pre, dig;
     med_digit(bits, round, pre, dig);
     if (round == 0) {
@@ -43,10 +43,23 @@ __global__ void __launch_bounds__(256) median_hist(const float* __restrict__ an0
       if (pre == pre0) atomicAdd(&h[0][dig], 1u);
       if (pre == pre1) atomicAdd(&h[1][dig], 1u);
     }
+  };
+  // 16-byte loads when the slice is 16-byte aligned (P % 4 == 0), scalar otherwise
+  if ((P & 3) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (long long i = beg / 4 + threadIdx.x; i < end / 4; i += blockDim.x) {
+      const float4 v = __ldg(s4 + i);
+      one(__float_as_uint(v.x));
+      one(__float_as_uint(v.y));
+      one(__float_as_uint(v.z));
+      one(__float_as_uint(v.w));
+    }
+  } else {
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) one(__float_as_uint(__ldg(src + i)));
   }
   __syncthreads();
   unsigned* gh = ws.hist + ((size_t)img * NO + o) * 2 * MED_BINS;
-  for (int i = threadIdx.x; i < 2 * MED_BINS; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nslot * MED_BINS; i += blockDim.x) {
     unsigned c = (&h[0][0])[i];
     if (c) atomicAdd(gh + i, c);
   }
@@ -112,11 +125,12 @@ __global__ void __launch_bounds__(64) median_select(long long P, int round, floa
 
 cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, const KParams& kp,
                                    MedianWs ws, cudaStream_t st) {
-  int chunks = (int)((P + 16383) / 16384);
+  // ~64K values per CTA: the histogram set-up and flush stay small next to the scan
+  int chunks = (int)((P + 65535) / 65536);
   if (chunks > 64) chunks = 64;
   if (chunks < 1) chunks = 1;
   for (int r = 0; r < 3; ++r) {
-    median_hist<<<dim3(chunks, NO, nimg), 256, 0, st>>>(an0, P, r, ws);
+    median_hist<<<dim3(chunks, NO, nimg), 512, 0, st>>>(an0, P, r, ws);
     median_select<<<dim3(NO, nimg), 64, 0, st>>>(P, r, kp.noise_c, ws);
   }
   return cudaGetLastError();
