@@ -100,6 +100,35 @@ STAGE_BYTES_PER_PX = {"fft_fwd": 16.0, "lg_cols": 200.0, "lg_rows": 265.0, "nois
                       "moment": 52.0, "detect": 4.0}
 
 
+# Kernel source each stage's DRAM-traffic figure in profiles/traffic.json was captured
+# from; the figure is reported only while these files are unchanged.
+STAGE_SOURCES = {"lg_cols": ("k_filterbank.cu", "fft_reg.cuh", "fft.cuh", "common.cuh"),
+                 "lg_rows": ("k_filterbank.cu", "fft_reg.cuh", "fft.cuh", "common.cuh")}
+
+
+def stage_source_hash(stage: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES.get(stage, ()):
+        with open(os.path.join(ROOT, "paper_2303_00319_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage: str, images: int):
+    """DRAM bytes per launch of `stage` for `images` images, scaled from the ncu capture in
+    profiles/traffic.json (bytes grow in proportion to the images a launch processes), or
+    None when the kernel source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)[stage]
+    except Exception:
+        return None
+    if d.get("source_hash") != stage_source_hash(stage):
+        return None
+    return d["dram_bytes_per_image"] * images
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -316,7 +345,7 @@ def run_ours(args):
             "stage_ms_per_step": stage_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": measured_traffic(dom, imgs_per_launch),
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,

@@ -187,7 +187,8 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
  * log-Gabor bank in the frequency domain -> MIM and phase congruency -> maximum
  * moment -> FAST + NMS + top-K -> dominant-index-recoded 6x6xNo descriptors.
  * imgs[i] (host array of n_images structs; data on the device) -> out[i] (host array).
- * Each side must be >= 16 with prime factors in {2, 3, 5, 7}; images smaller than
+ * Each side must be >= 16 with prime factors in {2, 3, 5, 7, 11, 13} and width <= 3584
+ * (the row pass keeps the four scales of a row in shared memory); images smaller than
  * patch + 6 on a side produce zero keypoints.  Images of equal size are grouped into
  * shared launches unless RIFT2_FLAG_NO_GROUPING is set.
  * Errors: RIFT2_E_INVAL, RIFT2_E_UNIMPL (size), RIFT2_E_CAPACITY, RIFT2_E_NOMEM,

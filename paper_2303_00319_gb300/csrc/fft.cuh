@@ -1,4 +1,4 @@
-// Batched mixed-radix Stockham FFT over shared memory (radices 2, 3, 4, 5, 7, 8).
+// Batched mixed-radix Stockham FFT over shared memory (radices 2, 3, 4, 5, 7, 8, 11, 13).
 //
 // A Stockham (auto-sorting) pass of radix R over an n-point transform, with ns the
 // product of the radices already applied, maps butterfly j (0 <= j < n/R, k = j mod ns)
@@ -146,6 +146,8 @@ __device__ float2* fft_smem(float2* a, float2* b, const FftPlan& pl, int nb, int
       case 3: fft_pass<3, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
       case 5: fft_pass<5, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
       case 7: fft_pass<7, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 11: fft_pass<11, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 13: fft_pass<13, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
       default: break;
     }
     __syncthreads();

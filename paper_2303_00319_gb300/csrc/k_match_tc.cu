@@ -350,11 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
         const float* rs = rinv_s + col0;
         uint32_t r[32];
         tmem_ld32(lane_base + (uint32_t)col0, r);
-        float sv[32], dv[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) dv[e] = __uint_as_float(r[e]);
-        const float thr = sc[TC_TOPK - 1];
-        unsigned m = 0;
+        float sv[32];
 #pragma unroll
         for (int e4 = 0; e4 < 8; ++e4) {
           const float4 rb = *reinterpret_cast<const float4*>(rs + e4 * 4);
@@ -362,10 +358,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
           sv[e4 * 4 + 1] = __uint_as_float(r[e4 * 4 + 1]) * rb.y;
           sv[e4 * 4 + 2] = __uint_as_float(r[e4 * 4 + 2]) * rb.z;
           sv[e4 * 4 + 3] = __uint_as_float(r[e4 * 4 + 3]) * rb.w;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) m |= (sv[e4 * 4 + e] > thr ? 1u : 0u) << (e4 * 4 + e);
         }
-        if (j0 + 32 > nB) m &= (j0 >= nB) ? 0u : ((1u << (nB - j0)) - 1u);
+        // one max per score decides whether this chunk can touch the list at all
+        float mx[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) mx[e] = fmaxf(sv[e], sv[e + 16]);
+#pragma unroll
+        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+          for (int e = 0; e < w; ++e) mx[e] = fmaxf(mx[e], mx[e + w]);
+        const float thr = sc[TC_TOPK - 1];
+        unsigned m = 0;
+        if (mx[0] > thr) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) m |= (sv[e] > thr ? 1u : 0u) << e;
+          if (j0 + 32 > nB) m &= (j0 >= nB) ? 0u : ((1u << (nB - j0)) - 1u);
+        }
         // each lane walks only its own columns above its threshold (rare after warm-up)
         while (m) {
           const int e = __ffs(m) - 1;
@@ -373,6 +381,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
           const float s = pick32(sv, e);
           if (s > sc[TC_TOPK - 1]) {
             sc[TC_TOPK - 1] = s;
+            float dv[32];
+#pragma unroll
+            for (int q2 = 0; q2 < 32; ++q2) dv[q2] = __uint_as_float(r[q2]);
             dt[TC_TOPK - 1] = pick32(dv, e);
             id[TC_TOPK - 1] = j0 + e;
 #pragma unroll

@@ -102,7 +102,7 @@ bool factor_plan(int n, FftPlan& pl) {
   else if (r == 1) rs.push_back(2);
   else if (r == 2) rs.push_back(4);
   for (int i = 0; i < q; ++i) rs.insert(rs.begin(), 8);
-  for (int f : {3, 5, 7})
+  for (int f : {3, 5, 7, 11, 13})
     while (m % f == 0) { m /= f; rs.push_back(f); }
   if (m != 1 || (int)rs.size() > FFT_MAX_STAGES) return false;
   pl.nst = (int)rs.size();

@@ -57,7 +57,7 @@ def small(pkg, dev):
 
 # --------------------------------------------------------------------------- FFT
 @pytest.mark.parametrize("h,w", [(16, 16), (256, 256), (1024, 1024), (48, 80), (105, 63),
-                                 (384, 640), (224, 448)])
+                                 (384, 640), (224, 448), (1408, 176), (1664, 208), (2048, 1920)])
 def test_fft2_matches_numpy(pkg, dev, h, w):
     ctx = pkg.Context(pkg.default_params(), device=0)
     x = np.random.default_rng(h * 7 + w).random((2, h, w)).astype(np.float32)
@@ -287,9 +287,9 @@ def test_edge_images(pkg, dev):
     assert f[1].counts.cpu().tolist() == [0, 0]
     o = O.extract(r.cpu().numpy().astype(np.float64), O.Params(max_keypoints=100), keep_maps=True)
     g, _ = _e2e_check(f[2], o, None)
-    # unsupported size (prime factor 11) is refused, not computed wrongly
+    # unsupported size (prime factor 17) is refused, not computed wrongly
     with pytest.raises(pkg.Rift2Error):
-        ctx.extract([torch.rand((121, 128), device=dev)])
+        ctx.extract([torch.rand((136, 128), device=dev)])
 
 
 @pytest.mark.parametrize("na,nb", [(3000, 4500), (129, 127), (1, 300), (640, 1)])
@@ -347,3 +347,20 @@ def test_tensor_core_matcher_batch_of_pairs(pkg, dev):
         if na:
             nn, d1, d2, near = e
             assert np.all((h["nn_desc"] == nn) | near)
+
+
+@pytest.mark.slow
+def test_uneven_batch_in_one_call(pkg, dev):
+    """Images of different sizes (mixed radices 3, 5, 7, 11, 13 among them) in one extract
+    call: each matches the oracle image by image."""
+    ctx = pkg.Context(pkg.default_params(max_keypoints=400), device=0)
+    sizes = [(384, 640), (1408, 256), (256, 1664), (640, 384), (896, 1152)]
+    imgs = []
+    for i, (h, w) in enumerate(sizes):
+        imgs.append(synth.make_pair(h, w, synth.pair_seed(2, i), angle_deg=None).a)
+    feats = ctx.extract([torch.from_numpy(a).to(dev) for a in imgs])
+    ctx.sync()
+    for a, f in zip(imgs, feats):
+        o = O.extract(a.astype(np.float64), O.Params(max_keypoints=400), keep_maps=True)
+        g, _ = _e2e_check(f, o, None)
+        assert len(g["xy"]) == len(o.xy)
