@@ -187,6 +187,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- multi-rank timing
+def max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time: every rank's value, MAX-reduced (no-op on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, pairs_per_step: int, steps: int, max_ms: float) -> float:
+    """Pairs per second over all ranks: each rank (replica) processed pairs_per_step pairs
+    in each of `steps` steps, and the job took as long as its slowest rank."""
+    return world * pairs_per_step * steps / (max_ms / 1000.0)
+
+
 # --------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -254,13 +272,9 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     prof = ctx.profile_read()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = world * B * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, B, args.steps, total_ms)
 
     # end to end through the public API with host buffers
     e2e_ms = []
@@ -280,10 +294,7 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     barrier()
-    e2e_total = torch.tensor([sum(e2e_ms)], device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_total, op=dist.ReduceOp.MAX)
-    e2e_value = world * B * args.steps / (float(e2e_total.item()) / 1000.0)
+    e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(sum(e2e_ms), dev))
     h2d = int(host[0].numel() * 4)
     d2h = int(B * (2 * MAX_KP * 2 + 1) * 4)
 
@@ -322,6 +333,10 @@ def run_ours(args):
     achieved = bytes_per_launch / (ms_dom / n_dom / 1000.0) / 1e9
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(args, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tcpu = oracle_pair_seconds(H, MAX_KP, synth.pair_seed(1, 0))
@@ -342,6 +357,7 @@ def run_ours(args):
                              "each step streams ~0.3 GB of workspace per image, > L2"},
             "mpix_per_s": value * 2 * H * W / 1e6,
             "plain_form": plain,
+            "serving": serving,
             "stage_ms_per_step": stage_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -360,6 +376,31 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving(args, device: int):
+    """Open-loop Poisson arrivals of pairs of mixed sizes (each side log-uniform in
+    [256, 4096], snapped to transform-friendly sizes) through the continuous-batching loop;
+    a pool of distinct pairs is generated once and cycled."""
+    import synth
+    from paper_2303_00319_gb300 import serve
+    sizes = synth.serving_sizes(args.serve_pool, seed=synth.pair_seed(4, 0))
+    pool = [synth.make_pair(h, w, synth.pair_seed(4, i + 1), angle_deg=None)
+            for i, (h, w) in enumerate(sizes)]
+    srv = serve.Server(device=device, max_keypoints=MAX_KP, max_batch_pairs=8,
+                       hbm_budget=96 << 30, lanes=2)
+    warm = [serve.PairRequest(-1 - i, p.a, p.b) for i, p in enumerate(pool)]
+    for r in warm:
+        srv.submit(r)
+    srv.drain()                           # plans, tables and workspaces for every size
+    reqs = [serve.PairRequest(i, pool[i % len(pool)].a, pool[i % len(pool)].b)
+            for i in range(args.serve_requests)]
+    stats = serve.run_open_loop(srv, reqs, rate=args.serve_rate, seed=7)
+    srv.close()
+    stats["workload"] = (f"{len(pool)} distinct pairs cycled, sides log-uniform 256..4096 "
+                         f"(13-smooth, width <= 3584), mean {np.mean([p.a.size for p in pool]) / 1e6:.2f} "
+                         "MPix per image, <= 5000 keypoints")
+    return stats
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,6 +410,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the open-loop serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="offered pairs/s")
+    ap.add_argument("--serve-pool", type=int, default=8, help="distinct pairs generated")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -162,3 +162,32 @@ def batch_sizes(n: int, seed: int, lo: int = 384, hi: int = 2048, step: int = 12
         if max(h, w) <= 2 * min(h, w):
             out.append((h, w))
     return out
+
+
+def smooth_sizes(lo: int = 16, hi: int = 8192, primes=(2, 3, 5, 7, 11, 13)):
+    """Integers in [lo, hi] whose prime factors all lie in `primes` (sizes the FFT takes)."""
+    out = []
+    for n in range(lo, hi + 1):
+        m = n
+        for p in primes:
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            out.append(n)
+    return np.array(out)
+
+
+def serving_sizes(n: int, seed: int, lo: int = 256, hi: int = 4096, max_width: int = 3584):
+    """Pair sizes of the serving workload: each side log-uniform in [lo, hi], snapped to the
+    nearest size the transforms take (13-smooth; width at most max_width)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ok = smooth_sizes(lo, hi)
+    out = []
+    for _ in range(n):
+        side = []
+        for lim in (hi, max_width):
+            x = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+            cand = ok[ok <= lim]
+            side.append(int(cand[np.argmin(np.abs(cand - x))]))
+        out.append((side[0], side[1]))
+    return out
