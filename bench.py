@@ -333,6 +333,41 @@ def run_ours(args):
     achieved = bytes_per_launch / (ms_dom / n_dom / 1000.0) / 1e9
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
 
+    # RIFT's own rotation handling on the same batches (§II-C): template descriptors for A,
+    # the six-member convolution ring for B, matching A against all ring members
+    rift = None
+    if not args.no_rift:
+        rt = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=pkg.FLAG_RIFT_TEMPLATE),
+                         device=local, hbm_budget=48 << 30)
+        rr = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=pkg.FLAG_RIFT_RING),
+                         device=local, hbm_budget=48 << 30)
+        fa_t = [rt.alloc_features() for _ in range(B)]
+        fb_r = [rr.alloc_features() for _ in range(B)]
+        mr = [rr.alloc_matches() for _ in range(B)]
+
+        def rift_step(imgs):
+            rt.extract([imgs[2 * i] for i in range(B)], fa_t, stream=stream)
+            rr.extract([imgs[2 * i + 1] for i in range(B)], fb_r, stream=stream)
+            rr.match(fa_t, fb_r, mr, stream=stream)
+
+        for i in range(2):
+            rift_step(devb[i % ROTATE])
+        torch.cuda.synchronize()
+        rms = []
+        for i in range(min(args.steps, 10)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rift_step(devb[i % ROTATE])
+            e1.record(stream)
+            e1.synchronize()
+            rms.append(e0.elapsed_time(e1))
+        rift_ms = statistics.mean(rms)
+        rift = {"pairs_per_s": B / (rift_ms / 1000.0), "ms_per_step": rift_ms,
+                "rift2_speedup": rift_ms / ms_per_step,
+                "form": "RIFT baseline: template descriptors for A, six-member ring for B"}
+        rt.close()
+        rr.close()
+
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(args, local)
@@ -358,6 +393,7 @@ def run_ours(args):
             "mpix_per_s": value * 2 * H * W / 1e6,
             "plain_form": plain,
             "serving": serving,
+            "rift_baseline": rift,
             "stage_ms_per_step": stage_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -410,6 +446,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-rift", action="store_true", help="skip the RIFT-ring baseline")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the open-loop serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="offered pairs/s")

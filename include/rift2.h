@@ -57,6 +57,13 @@ enum {
 /* Flags (rift2_params.flags). */
 #define RIFT2_FLAG_PLAIN_MATCH 0x1   /* CUDA-core matcher instead of the tcgen05 one */
 #define RIFT2_FLAG_NO_GROUPING 0x2   /* one image / pair per launch (plain form) */
+/* RIFT's own rotation handling (§II-C), the baseline RIFT2 replaces: a "template" image gets
+ * one descriptor per keypoint from the unshifted MIM, a "reference" image gets the No
+ * descriptors of the convolution-sequence ring, one per initial layer w = 0..No-1, i.e. the
+ * MIM recoded by (MIM - w) mod No.  Without either flag: RIFT2's dominant-index descriptors
+ * (§III).  The ring needs cap_desc >= No * max_keypoints. */
+#define RIFT2_FLAG_RIFT_TEMPLATE 0x4
+#define RIFT2_FLAG_RIFT_RING 0x8
 
 /*
  * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
@@ -128,10 +135,12 @@ typedef struct rift2_debug_maps {
  *                                    minor, bins recoded by the dominant index (Eq. 2)
  *   desc_norm float [cap_desc]       L2 norm of the count vector (descriptor = desc/norm)
  *   desc_kp   int32 [cap_desc]       keypoint each descriptor belongs to
- *   desc_dom  uint8 [cap_desc]       dominant index used to recode it (0..No-1)
+ *   desc_dom  uint8 [cap_desc]       index the MIM was recoded by (dominant index, or the
+ *                                    ring's initial layer; 0..No-1)
  *   counts    int32 [2]              written on the device: n_kp, n_desc
  * cap_kp >= max_keypoints and cap_desc >= 2 * max_keypoints are required (each keypoint
- * yields one or two descriptors, §III), otherwise RIFT2_E_CAPACITY.
+ * yields one or two descriptors, §III; No * max_keypoints with RIFT2_FLAG_RIFT_RING),
+ * otherwise RIFT2_E_CAPACITY.
  */
 typedef struct rift2_features {
   int cap_kp, cap_desc;
@@ -152,7 +161,7 @@ typedef struct rift2_features {
  *   d1 / d2 = smallest and second-smallest ||a/|a| - b/|b|||^2 (d2 = +inf if B has one
  *   descriptor), near_tie = 1 if (d2 - d1) < 1e-5 * max(d1, 1e-12).
  *   count = number of rows (= n_desc of A), written on the device.
- * cap >= 2 * max_keypoints is required.
+ * cap >= 2 * max_keypoints is required (No * max_keypoints with RIFT2_FLAG_RIFT_RING).
  */
 typedef struct rift2_matches {
   int cap;

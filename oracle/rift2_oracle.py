@@ -390,23 +390,33 @@ def descriptor_from_cells(cells, s: int, p: Params = DEFAULT):
     return d
 
 
-def describe(mim, xy, p: Params = DEFAULT):
-    """One descriptor per keypoint plus a second one where the secondary index qualifies
-    (both images, §III).  Returns (desc int64 [n][216], desc_kp, desc_dom, per-keypoint
-    (s, s2, has2, whole-patch histogram))."""
+def describe(mim, xy, p: Params = DEFAULT, mode: str = "rift2"):
+    """Descriptors of the keypoints xy on the MIM.
+
+    mode "rift2" (§III): one descriptor per keypoint recoded by its dominant index, plus a
+    second one where the secondary index qualifies (both images).
+    mode "rift_template" (§II-C, RIFT's baseline): one descriptor from the unshifted MIM.
+    mode "rift_ring" (§II-C): the No descriptors of the convolution-sequence ring, the MIM
+    with each layer w = 0..No-1 as the initial one, i.e. recoded by w.
+    Returns (desc int64 [n][216], desc_kp, desc_dom, per-keypoint (s, s2, has2, whole))."""
     cells = cell_histograms(mim, xy, p)
     descs, dkp, ddom, info = [], [], [], []
     for kidx in range(len(xy)):
         whole = cells[kidx].sum(axis=0)
         s, s2, has2 = dominant_indices(whole, p)
         info.append((s, s2, has2, whole))
-        descs.append(descriptor_from_cells(cells[kidx], s, p))
-        dkp.append(kidx)
-        ddom.append(s)
-        if has2:
-            descs.append(descriptor_from_cells(cells[kidx], s2, p))
+        if mode == "rift2":
+            shifts = [s, s2] if has2 else [s]
+        elif mode == "rift_template":
+            shifts = [0]
+        elif mode == "rift_ring":
+            shifts = list(range(p.n_orient))
+        else:
+            raise ValueError(mode)
+        for w in shifts:
+            descs.append(descriptor_from_cells(cells[kidx], w, p))
             dkp.append(kidx)
-            ddom.append(s2)
+            ddom.append(w)
     d = np.array(descs, dtype=np.int64).reshape(-1, p.desc_dim)
     return d, np.array(dkp, dtype=np.int64), np.array(ddom, dtype=np.int64), info
 
@@ -475,18 +485,45 @@ def detect(m_map, p: Params = DEFAULT, tie_eps: float = 1e-5):
     return xy, v, unc, btie
 
 
-def extract(img, p: Params = DEFAULT, keep_maps: bool = False) -> Features:
-    """Whole single-image path: responses -> (MIM, PC -> M -> keypoints) -> descriptors."""
+def extract(img, p: Params = DEFAULT, keep_maps: bool = False, mode: str = "rift2") -> Features:
+    """Whole single-image path: responses -> (MIM, PC -> M -> keypoints) -> descriptors
+    (`mode` as in describe)."""
     eo = responses(img, p)
     a = amplitude_sums(eo)
     mim, mim_margin = max_index_map(a)
     pc, t = phase_congruency(eo, p)
     m_max, m_min = moments(pc, p)
     xy, v, unc, btie = detect(m_max, p)
-    desc, dkp, ddom, _ = describe(mim, xy, p)
+    desc, dkp, ddom, _ = describe(mim, xy, p, mode)
     maps = {}
     if keep_maps:
         er, q, an0, _ = pc_terms(eo, p)
         maps = dict(A=a, mim=mim, mim_margin=mim_margin, pc=pc, T=t, M=m_max, m=m_min,
                     Er=er, q=q, An0=an0, kp_uncertain=unc, kp_boundary_tie=btie)
     return Features(xy, v, desc, dkp, ddom, maps)
+
+
+# ------------------------------------------------------ ground-truth evaluation (§IV)
+def evaluate(xy_a, xy_b, nn, desc_kp_a, desc_kp_b, angle_deg, shape, tol: float = 3.0,
+             rmse_cap: float = 20.0, min_correct: int = 10):
+    """Correct matches, RMSE and success of one pair against the known rotation (§IV:
+    a match is correct if its residual is below 3 px; RMSE over the correct matches,
+    capped at 20 px; a pair succeeds with at least 10 correct matches).  Image B is image A
+    rotated by angle_deg about ((W-1)/2, (H-1)/2), so a point p of A appears in B at
+    R^-1 (p - c) + c with R the sampling rotation [[cos, -sin], [sin, cos]]."""
+    h, w = shape
+    cy, cx = (h - 1) / 2.0, (w - 1) / 2.0
+    a = math.radians(angle_deg)
+    ca, sa = math.cos(a), math.sin(a)
+    ok = nn >= 0
+    pa = np.asarray(xy_a, dtype=np.float64)[np.asarray(desc_kp_a)[ok]]
+    pb = np.asarray(xy_b, dtype=np.float64)[np.asarray(desc_kp_b)[nn[ok]]]
+    dx, dy = pa[:, 0] - cx, pa[:, 1] - cy
+    ex = ca * dx + sa * dy + cx
+    ey = -sa * dx + ca * dy + cy
+    res = np.hypot(ex - pb[:, 0], ey - pb[:, 1])
+    good = res < tol
+    n = int(good.sum())
+    rmse = float(np.sqrt(np.mean(res[good] ** 2))) if n else rmse_cap
+    return {"correct": n, "rmse": min(rmse, rmse_cap), "success": n >= min_correct,
+            "matches": int(ok.sum())}

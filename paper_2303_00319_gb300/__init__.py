@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "librift2.so")
 OK, E_INVAL, E_NOMEM, E_CAPACITY, E_CUDA, E_TIMEOUT, E_UNIMPL = 0, -1, -2, -3, -4, -5, -6
 FLAG_PLAIN_MATCH = 0x1
 FLAG_NO_GROUPING = 0x2
+FLAG_RIFT_TEMPLATE = 0x4   # RIFT baseline: one descriptor per keypoint, unshifted MIM
+FLAG_RIFT_RING = 0x8       # RIFT baseline: the No descriptors of the convolution ring
 NS, NO, PATCH, CELLS = 4, 6, 96, 6
 DESC_DIM = CELLS * CELLS * NO
 
@@ -140,15 +142,16 @@ class Features:
     debug: dict | None = None
 
     @staticmethod
-    def alloc(max_kp: int, device, debug_shape=None):
+    def alloc(max_kp: int, device, debug_shape=None, desc_per_kp: int = 2):
         dev = torch.device(device)
+        nd = desc_per_kp * max_kp
         f = Features(
             kp_xy=torch.zeros((max_kp, 2), dtype=torch.int32, device=dev),
             kp_score=torch.zeros(max_kp, dtype=torch.float32, device=dev),
-            desc=torch.zeros((2 * max_kp, DESC_DIM), dtype=torch.int16, device=dev),
-            desc_norm=torch.zeros(2 * max_kp, dtype=torch.float32, device=dev),
-            desc_kp=torch.zeros(2 * max_kp, dtype=torch.int32, device=dev),
-            desc_dom=torch.zeros(2 * max_kp, dtype=torch.uint8, device=dev),
+            desc=torch.zeros((nd, DESC_DIM), dtype=torch.int16, device=dev),
+            desc_norm=torch.zeros(nd, dtype=torch.float32, device=dev),
+            desc_kp=torch.zeros(nd, dtype=torch.int32, device=dev),
+            desc_dom=torch.zeros(nd, dtype=torch.uint8, device=dev),
             counts=torch.zeros(2, dtype=torch.int32, device=dev))
         if debug_shape is not None:
             h, w = debug_shape
@@ -237,11 +240,15 @@ class Context:
     def max_kp(self) -> int:
         return int(self.params.max_keypoints)
 
+    @property
+    def desc_per_kp(self) -> int:
+        return NO if self.params.flags & FLAG_RIFT_RING else 2
+
     def alloc_features(self, debug_shape=None) -> Features:
-        return Features.alloc(self.max_kp, f"cuda:{self.device}", debug_shape)
+        return Features.alloc(self.max_kp, f"cuda:{self.device}", debug_shape, self.desc_per_kp)
 
     def alloc_matches(self) -> Matches:
-        return Matches.alloc(2 * self.max_kp, f"cuda:{self.device}")
+        return Matches.alloc(self.desc_per_kp * self.max_kp, f"cuda:{self.device}")
 
     def extract(self, images, feats=None, stream=None, debug=False):
         """images: list of float32 CUDA tensors [H][W] (rows may be strided)."""

@@ -34,7 +34,12 @@ struct KParams {
   int fast_arc;
   int max_kp;
   int ratio_pm;          // dominant ratio in per mille (integer comparison)
+  int desc_mode;         // DESC_RIFT2, DESC_RIFT_TEMPLATE or DESC_RIFT_RING
 };
+
+// Descriptor modes: RIFT2's dominant index (one or two per keypoint), RIFT's template
+// (unshifted MIM, one per keypoint) and RIFT's reference ring (No per keypoint).
+constexpr int DESC_RIFT2 = 0, DESC_RIFT_TEMPLATE = 1, DESC_RIFT_RING = 2;
 
 // Per-launch-group pointers to the caller's buffers (passed by value).
 struct FeatPtrs {

@@ -9,7 +9,9 @@
 //                counts 16-byte cell rows with byte-wise compares (__vcmpeq4 + popc) and
 //                the cell totals are reduced over the 16 lanes of a half-warp.  Writes the
 //                unrecoded cell counts, s, s2 and the second-descriptor flag.
-//   desc_scan  : one CTA per image: exclusive scan of descriptors per keypoint (1 or 2).
+//   desc_scan  : one CTA per image: exclusive scan of descriptors per keypoint (1 or 2;
+//                for RIFT's baseline modes 1 from the unshifted MIM, or the No members of
+//                the convolution-sequence ring, §II-C).
 //   desc_write : one warp per keypoint: the recoded count vectors (a cyclic shift of the
 //                bins of every cell) and their L2 norms.
 #include "kernels.h"
@@ -137,6 +139,22 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
   }
 }
 
+// Descriptors of keypoint info `inf` under the mode: count, and the recoding shift of each.
+__device__ __forceinline__ int desc_shifts(unsigned inf, int mode, int (&sh)[NO]) {
+  if (mode == DESC_RIFT_RING) {
+#pragma unroll
+    for (int w = 0; w < NO; ++w) sh[w] = w;
+    return NO;
+  }
+  if (mode == DESC_RIFT_TEMPLATE) {
+    sh[0] = 0;
+    return 1;
+  }
+  sh[0] = inf & 15u;
+  sh[1] = (inf >> 4) & 15u;
+  return 1 + (int)((inf >> 8) & 1u);
+}
+
 __global__ void __launch_bounds__(1024) desc_scan(KParams kp, DescribeWs ws, FeatPtrs fp) {
   __shared__ int wsum[32];
   const int img = blockIdx.x;
@@ -147,7 +165,10 @@ __global__ void __launch_bounds__(1024) desc_scan(KParams kp, DescribeWs ws, Fea
   int local = 0;
   for (int i = 0; i < per; ++i) {
     int kk = beg + i;
-    if (kk < nkp) local += 1 + (int)((info[kk] >> 8) & 1u);
+    if (kk < nkp) {
+      int sh[NO];
+      local += desc_shifts(info[kk], kp.desc_mode, sh);
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int incl = local;
@@ -172,14 +193,12 @@ __global__ void __launch_bounds__(1024) desc_scan(KParams kp, DescribeWs ws, Fea
   for (int i = 0; i < per; ++i) {
     int kk = beg + i;
     if (kk >= nkp) break;
-    unsigned inf = info[kk];
+    int sh[NO];
+    const int nd = desc_shifts(info[kk], kp.desc_mode, sh);
     off[kk] = run;
-    fp.desc_kp[img][run] = kk;
-    fp.desc_dom[img][run] = (unsigned char)(inf & 15u);
-    ++run;
-    if ((inf >> 8) & 1u) {
+    for (int d = 0; d < nd; ++d) {
       fp.desc_kp[img][run] = kk;
-      fp.desc_dom[img][run] = (unsigned char)((inf >> 4) & 15u);
+      fp.desc_dom[img][run] = (unsigned char)sh[d];
       ++run;
     }
   }
@@ -192,27 +211,20 @@ __global__ void __launch_bounds__(256) desc_write(KParams kp, DescribeWs ws, Fea
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * 8 + warp;
   if (k >= fp.counts[img][0]) return;
-  const unsigned inf = ws.info[(size_t)img * kp.max_kp + k];
-  const int s = inf & 15u, s2 = (inf >> 4) & 15u;
-  const bool has2 = (inf >> 8) & 1u;
+  int sh[NO];
+  const int nd = desc_shifts(ws.info[(size_t)img * kp.max_kp + k], kp.desc_mode, sh);
   const int off = ws.off[(size_t)img * kp.max_kp + k];
   const unsigned short* raw = ws.raw + ((size_t)img * kp.max_kp + k) * DESC_DIM;
   unsigned short* d0 = fp.desc[img] + (size_t)off * DESC_DIM;
-  unsigned short* d1 = d0 + DESC_DIM;
   unsigned n2 = 0;
   for (int e = lane; e < DESC_DIM; e += 32) {
-    unsigned v = raw[e];
+    const unsigned v = raw[e];
     n2 += v * v;
-    int c = e / NO, b = e - c * NO;
-    d0[c * NO + (b - s + NO) % NO] = (unsigned short)v;
-    if (has2) d1[c * NO + (b - s2 + NO) % NO] = (unsigned short)v;
+    const int c = e / NO, b = e - c * NO;
+    for (int d = 0; d < nd; ++d) d0[(size_t)d * DESC_DIM + c * NO + (b - sh[d] + NO) % NO] = (unsigned short)v;
   }
   for (int d = 16; d > 0; d >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, d);
-  if (lane == 0) {
-    float nrm = sqrtf((float)n2);   // n2 <= 36 * 256^2 < 2^24: exact in float
-    fp.desc_norm[img][off] = nrm;
-    if (has2) fp.desc_norm[img][off + 1] = nrm;
-  }
+  if (lane < nd) fp.desc_norm[img][off + lane] = sqrtf((float)n2);   // exact: n2 < 2^24
 }
 
 cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,

@@ -39,6 +39,9 @@ void derive_kparams(const rift2_params& p, KParams& k) {
   k.fast_arc = p.fast_arc;
   k.max_kp = p.max_keypoints;
   k.ratio_pm = (int)std::lround(p.second_ratio * 1000.0);
+  k.desc_mode = (p.flags & RIFT2_FLAG_RIFT_RING)       ? DESC_RIFT_RING
+                : (p.flags & RIFT2_FLAG_RIFT_TEMPLATE) ? DESC_RIFT_TEMPLATE
+                                                       : DESC_RIFT2;
 }
 
 }  // namespace rift2
@@ -280,12 +283,15 @@ int make_operand_map(rift2_ctx* c, CUtensorMap* tm, void* base, int npairs, int 
   return RIFT2_OK;
 }
 
+// Most descriptors one image can produce per keypoint under the context's mode.
+int desc_per_kp(const rift2_ctx* c) { return (c->p.flags & RIFT2_FLAG_RIFT_RING) ? NO : 2; }
+
 int check_features(const rift2_ctx* c, const rift2_features& f, bool need_desc) {
   if (!f.kp_xy || !f.kp_score || !f.counts) return RIFT2_E_INVAL;
   if (f.cap_kp < c->p.max_keypoints) return RIFT2_E_CAPACITY;
   if (need_desc) {
     if (!f.desc || !f.desc_norm || !f.desc_kp || !f.desc_dom) return RIFT2_E_INVAL;
-    if (f.cap_desc < 2 * c->p.max_keypoints) return RIFT2_E_CAPACITY;
+    if (f.cap_desc < desc_per_kp(c) * c->p.max_keypoints) return RIFT2_E_CAPACITY;
   }
   return RIFT2_OK;
 }
@@ -462,6 +468,7 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
   if (!(p.min_wavelength > 0) || !(p.mult > 1) || !(p.sigma_onf > 0 && p.sigma_onf < 1) ||
       !(p.lp_cutoff > 0) || p.lp_order < 1 || p.fast_arc < 1 || p.fast_arc > 16 ||
       p.max_keypoints < 1 || p.max_keypoints > 16384 || !(p.fast_threshold >= 0) ||
+      ((p.flags & RIFT2_FLAG_RIFT_RING) && (p.flags & RIFT2_FLAG_RIFT_TEMPLATE)) ||
       !(p.second_ratio >= 0) || !(p.eps > 0))
     return RIFT2_E_INVAL;
   int ndev = 0;
@@ -593,7 +600,7 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
     if (!m.q_desc || !m.nn_desc || !m.kp_a || !m.kp_b || !m.d1 || !m.d2 || !m.near_tie ||
         !m.count)
       return RIFT2_E_INVAL;
-    if (m.cap < 2 * c->p.max_keypoints) return RIFT2_E_CAPACITY;
+    if (m.cap < desc_per_kp(c) * c->p.max_keypoints) return RIFT2_E_CAPACITY;
   }
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -622,9 +629,9 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
     }
     if (c->p.flags & RIFT2_FLAG_PLAIN_MATCH) {
       StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH);
-      RIFT2_CU(launch_match_simt(mp, g, 2 * c->p.max_keypoints, st));
+      RIFT2_CU(launch_match_simt(mp, g, desc_per_kp(c) * c->p.max_keypoints, st));
     } else {
-      const int cap = (2 * c->p.max_keypoints + 127) / 128 * 128;
+      const int cap = (desc_per_kp(c) * c->p.max_keypoints + 127) / 128 * 128;
       const int nsplit = match_tc_nsplit(g, cap);
       int rc = ensure_ws(c, match_tc_ws_bytes(g, cap, nsplit));
       if (rc) return rc;

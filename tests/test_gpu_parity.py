@@ -364,3 +364,56 @@ def test_uneven_batch_in_one_call(pkg, dev):
         o = O.extract(a.astype(np.float64), O.Params(max_keypoints=400), keep_maps=True)
         g, _ = _e2e_check(f, o, None)
         assert len(g["xy"]) == len(o.xy)
+
+
+# ------------------------------------------------------ RIFT ring baseline (§II-C)
+def test_rift_ring_and_template_descriptors_bit_exact(pkg, dev, small):
+    o = small["oa"]
+    n = len(o.xy)
+    for flag, mode, per in ((pkg.FLAG_RIFT_RING, "rift_ring", 6),
+                            (pkg.FLAG_RIFT_TEMPLATE, "rift_template", 1)):
+        ctx = pkg.Context(pkg.default_params(max_keypoints=500, flags=flag), device=0)
+        f = ctx.alloc_features()
+        assert f.desc.shape[0] >= per * 500
+        f.kp_xy[:n] = torch.from_numpy(o.xy.astype(np.int32)).to(dev)
+        f.counts[0] = n
+        ctx.describe(torch.from_numpy(o.maps["mim"][None].copy()).to(dev), [f])
+        g = f.host()
+        desc, dkp, ddom, _ = O.describe(o.maps["mim"], o.xy, O.Params(max_keypoints=500), mode)
+        assert len(g["desc"]) == per * n
+        assert np.array_equal(g["desc"].astype(np.int64), desc)
+        assert np.array_equal(g["desc_kp"], dkp) and np.array_equal(g["desc_dom"], ddom)
+
+
+def test_rift_baseline_matching_and_ground_truth(pkg, dev, small):
+    """RIFT baseline end to end (template A against the ring of B) and the ground-truth
+    metrics of both methods: GPU matches scored by the library's host-side evaluation
+    against oracle matches scored by the oracle's."""
+    from paper_2303_00319_gb300 import evaluate as ev
+    pr, p = small["pr"], small["p"]
+    ring = pkg.Context(pkg.default_params(max_keypoints=500, flags=pkg.FLAG_RIFT_RING), device=0)
+    tmpl = pkg.Context(pkg.default_params(max_keypoints=500, flags=pkg.FLAG_RIFT_TEMPLATE), device=0)
+    fa = tmpl.extract([torch.from_numpy(pr.a).to(dev)])[0]
+    fb = ring.extract([torch.from_numpy(pr.b).to(dev)])[0]
+    m = ring.match([fa], [fb])[0]
+    ring.sync()
+    ga, gb, gm = fa.host(), fb.host(), m.host()
+    assert len(gb["desc"]) == 6 * len(gb["xy"]) and len(ga["desc"]) == len(ga["xy"])
+    oa = O.extract(pr.a.astype(np.float64), p, mode="rift_template")
+    ob = O.extract(pr.b.astype(np.float64), p, mode="rift_ring")
+    if np.array_equal(ga["desc"].astype(np.int64), oa.desc) and \
+            np.array_equal(gb["desc"].astype(np.int64), ob.desc):
+        nn, d1, d2, near = O.match(oa.desc, ob.desc)
+        assert np.all((gm["nn_desc"] == nn) | near)
+    for gpu, orc in (((ga, gb, gm), (oa, ob)),
+                     ((small["fa"].host(), small["fb"].host(), small["m"].host()),
+                      (small["oa"], small["ob"]))):
+        g_a, g_b, g_m = gpu
+        res = ev.rotation_residuals(g_a["xy"], g_b["xy"], g_m["nn_desc"], g_a["desc_kp"],
+                                    g_b["desc_kp"], pr.angle_deg, pr.a.shape)
+        mg = ev.pair_metrics(res)
+        o_a, o_b = orc
+        nn, _, _, _ = O.match(o_a.desc, o_b.desc)
+        mo = O.evaluate(o_a.xy, o_b.xy, nn, o_a.desc_kp, o_b.desc_kp, pr.angle_deg, pr.a.shape)
+        assert abs(mg["correct"] - mo["correct"]) <= 2, (mg, mo)
+        assert mg["matches"] == mo["matches"]

@@ -386,3 +386,40 @@ def test_moments_of_single_orientation():
     pc[:] = 0.5
     mx, mn = O.moments(pc)
     assert math.isclose(mx.item(), mn.item() + 1e-4, rel_tol=1e-9)
+
+
+# ------------------------------------------------------------ RIFT ring baseline (§II-C)
+def test_ring_members_are_the_cyclic_shifts_and_contain_rift2():
+    rng = np.random.default_rng(21)
+    mim = rng.integers(0, 6, size=(160, 170)).astype(np.uint8)
+    xy = np.array([[60, 70], [100, 100], [121, 111]])
+    ring, rkp, rdom, info = O.describe(mim, xy, mode="rift_ring")
+    tmpl, tkp, tdom, _ = O.describe(mim, xy, mode="rift_template")
+    r2, r2kp, r2dom, _ = O.describe(mim, xy, mode="rift2")
+    assert len(ring) == 6 * len(xy) and len(tmpl) == len(xy)
+    for k in range(len(xy)):
+        members = ring[rkp == k]
+        assert list(rdom[rkp == k]) == list(range(6))
+        # member w: every cell's bins rotated by w relative to the unshifted template
+        for w in range(6):
+            np.testing.assert_array_equal(
+                members[w].reshape(36, 6), np.roll(tmpl[k].reshape(36, 6), -w, axis=1))
+        # RIFT2's descriptor is the ring member whose initial layer is the dominant index
+        for d, s in zip(r2[r2kp == k], r2dom[r2kp == k]):
+            np.testing.assert_array_equal(d, members[s])
+
+
+def test_ground_truth_evaluation_on_exact_correspondences():
+    # identity transform: a keypoint matched to itself has residual 0
+    xy = np.array([[10, 20], [30, 40], [55, 65]])
+    ev = O.evaluate(xy, xy, np.array([0, 1, 2]), np.arange(3), np.arange(3), 0.0, (100, 100))
+    assert ev["correct"] == 3 and ev["rmse"] == 0.0 and not ev["success"]
+    # quarter turn: the point p maps to R^-1 (p - c) + c
+    h = w = 101
+    c = 50.0
+    pa = np.array([[60.0, 50.0]])                      # dx = 10, dy = 0
+    pb = np.array([[50.0, 40.0]])                      # 90 deg sampling rotation sends it here
+    ev = O.evaluate(pa, pb, np.array([0]), np.array([0]), np.array([0]), 90.0, (h, w))
+    assert ev["correct"] == 1 and ev["rmse"] < 1e-9
+    ev = O.evaluate(pa, pb + 5, np.array([0]), np.array([0]), np.array([0]), 90.0, (h, w))
+    assert ev["correct"] == 0 and ev["rmse"] == 20.0
