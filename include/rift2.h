@@ -88,7 +88,7 @@ typedef struct rift2_params {
   int   lp_order;        /* low-pass order n: 1 / (1 + (r/c)^(2n)) */
   float fast_threshold;  /* FAST threshold on the min-max normalised moment map */
   int   fast_arc;        /* contiguous circle pixels required (9 of 16) */
-  int   max_keypoints;   /* strongest keypoints kept per image */
+  int   max_keypoints;   /* strongest keypoints kept per image (1..32768) */
   int   patch;           /* descriptor patch side, px */
   int   cells;           /* cells per patch side */
   float second_ratio;    /* second dominant bin kept if >= ratio * peak (integer test) */

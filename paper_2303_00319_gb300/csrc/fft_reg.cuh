@@ -179,25 +179,33 @@ template <>
 struct ColShape<2048> {
   static constexpr int T = 128, R0 = 16, R1 = 16, R2 = 8, NT = 512;
 };
+template <>
+struct ColShape<4096> {
+  static constexpr int T = 128, R0 = 32, R1 = 8, R2 = 16, NT = 256;
+};
 
 // Register-path shapes: transform length -> threads per transform and pass radices.
 template <int N>
 struct RegShape;
 template <>
 struct RegShape<256> {
-  static constexpr int T = 16, R0 = 16, R1 = 16, R2 = 1;
+  static constexpr int T = 16, R0 = 16, R1 = 16, R2 = 1, NT = 256;
 };
 template <>
 struct RegShape<512> {
-  static constexpr int T = 16, R0 = 32, R1 = 16, R2 = 1;
+  static constexpr int T = 16, R0 = 32, R1 = 16, R2 = 1, NT = 256;
 };
 template <>
 struct RegShape<1024> {
-  static constexpr int T = 32, R0 = 32, R1 = 32, R2 = 1;
+  static constexpr int T = 32, R0 = 32, R1 = 32, R2 = 1, NT = 256;
 };
 template <>
 struct RegShape<2048> {
-  static constexpr int T = 64, R0 = 32, R1 = 8, R2 = 8;
+  static constexpr int T = 64, R0 = 32, R1 = 8, R2 = 8, NT = 256;
+};
+template <>
+struct RegShape<4096> {
+  static constexpr int T = 128, R0 = 32, R1 = 8, R2 = 16, NT = 512;
 };
 
 }  // namespace rift2

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
   }
 }
 
-constexpr int SORT_CAP = 16384;
+constexpr int SORT_CAP = TOPK_SMEM_CAP;
 
 // Ascending bitonic sort of n (a power of two) keys in shared memory; every thread
 // iteration performs one compare-exchange (n / 2 per stage).
@@ -127,7 +127,7 @@ __device__ void bitonic_sort(unsigned long long* s, int n) {
 }
 
 __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws, FeatPtrs fp) {
-  extern __shared__ unsigned long long keys[];
+  extern __shared__ unsigned long long skeys[];
   __shared__ unsigned hist[256];
   __shared__ unsigned s_sel[4];
   const int img = blockIdx.x;
@@ -137,6 +137,10 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   const unsigned K = kp.max_kp;
   unsigned kcap = 256;                 // sort size: the smallest power of two >= K
   while (kcap < K) kcap <<= 1;
+  // keys live in shared memory, or (K above the shared capacity) in this image's global
+  // sort buffer; the block-wide barriers order the global accesses the same way
+  unsigned long long* keys =
+      (kcap <= (unsigned)SORT_CAP) ? skeys : ws.sortbuf + (size_t)img * kcap;
   int pbits = 0;
   unsigned long long prefix = 0;
   unsigned nsel = n;   // keys to gather: those whose top pbits bits are <= prefix
@@ -244,7 +248,8 @@ cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KPa
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st) {
   dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, nimg);
   fast_nms<<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
-  size_t sm = SORT_CAP * sizeof(unsigned long long);
+  const int kc = topk_sort_cap(kp.max_kp);
+  size_t sm = (kc <= SORT_CAP ? kc : 0) * sizeof(unsigned long long);
   cudaFuncSetAttribute(topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   topk_sort<<<nimg, 1024, sm, st>>>(W, kp, ws, fp);
   return cudaGetLastError();

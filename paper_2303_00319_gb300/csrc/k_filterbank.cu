@@ -146,12 +146,12 @@ __device__ __forceinline__ float2 group_sum(float2 v, float2* red) {
 
 // Rows of real images, one group of T threads per row, mean removed and restored.
 template <int WN>
-__global__ void __launch_bounds__(REG_NT) fwd_rows_reg(ImgPtrs ip, const float* __restrict__ dense,
+__global__ void __launch_bounds__(RegShape<WN>::NT) fwd_rows_reg(ImgPtrs ip, const float* __restrict__ dense,
                                                        float2* __restrict__ spec, int H,
                                                        const float2* __restrict__ tww) {
   using S = RegShape<WN>;
-  constexpr int T = S::T, ROWS = REG_NT / T, E = WN / T, XS = XBuf<WN>::SIZE;
-  extern __shared__ float2 sm[];   // [ROWS][XS] exchange + [REG_NT] reduction slots
+  constexpr int T = S::T, ROWS = S::NT / T, E = WN / T, XS = XBuf<WN>::SIZE;
+  extern __shared__ float2 sm[];   // [ROWS][XS] exchange + [NT] reduction slots
   float2* red = sm + ROWS * XS;
   const int img = blockIdx.y;
   const int grp = threadIdx.x / T, t = threadIdx.x % T;
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
 // after each orientation's four scales are in shared memory every thread reduces its
 // pixels (same formulas as lg_rows_reduce).
 template <int WN>
-__global__ void __launch_bounds__(REG_NT) lg_rows_reg(const float2* __restrict__ scratch, int H,
+__global__ void __launch_bounds__(RegShape<WN>::NT) lg_rows_reg(const float2* __restrict__ scratch, int H,
                                                            const float2* __restrict__ tww,
                                                            KParams kp, float* __restrict__ er_out,
                                                            float* __restrict__ q_out,
@@ -543,15 +543,15 @@ __global__ void __launch_bounds__(REG_NT) lg_rows_reg(const float2* __restrict__
                                                            int mim_pitch,
                                                            const unsigned char* __restrict__ zc) {
   using S = RegShape<WN>;
-  constexpr int T = S::T;
-  constexpr int GROUPS = REG_NT / T;
+  constexpr int T = S::T, NT = S::NT;
+  constexpr int GROUPS = NT / T;
   constexpr int ROWS = GROUPS / NS;
   constexpr int XS = XBuf<WN>::SIZE;
-  constexpr int PIX = ROWS * WN / REG_NT;
+  constexpr int PIX = ROWS * WN / NT;
   static_assert(ROWS >= 1 && PIX >= 1, "row tile");
   extern __shared__ float2 sm[];   // [GROUPS][XS], group g = (row g / NS, scale g % NS)
   __shared__ unsigned char zcs[NO * WN];
-  for (int i = threadIdx.x; i < NO * WN; i += REG_NT) zcs[i] = zc[i];
+  for (int i = threadIdx.x; i < NO * WN; i += NT) zcs[i] = zc[i];
   __syncthreads();
   const int img = blockIdx.y;
   const int row0 = blockIdx.x * ROWS;
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(REG_NT) lg_rows_reg(const float2* __restrict__
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
-      const int pix = tid + REG_NT * k;
+      const int pix = tid + NT * k;
       const int r2 = pix / WN, x = pix % WN;
       if (row0 + r2 >= H) continue;
       float2 z[NS];
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(REG_NT) lg_rows_reg(const float2* __restrict__
   }
 #pragma unroll
   for (int k = 0; k < PIX; ++k) {
-    const int pix = tid + REG_NT * k;
+    const int pix = tid + NT * k;
     const int r2 = pix / WN, x = pix % WN;
     if (row0 + r2 < H)
       mim_out[(size_t)img * H * mim_pitch + (size_t)(row0 + r2) * mim_pitch + x] =
@@ -626,11 +626,11 @@ static cudaError_t rows_reg(const float2* scratch, int nimg, int H, const FftPla
                             const KParams& kp, float* er, float* q, float* an0, float* amp,
                             unsigned char* mim, int mim_pitch, const unsigned char* zc,
                             cudaStream_t st) {
-  constexpr int GROUPS = REG_NT / RegShape<WN>::T;
+  constexpr int NT = RegShape<WN>::NT, GROUPS = NT / RegShape<WN>::T;
   constexpr int ROWS = GROUPS / NS;
   const size_t sm = (size_t)GROUPS * XBuf<WN>::SIZE * sizeof(float2);
   cudaFuncSetAttribute(lg_rows_reg<WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  lg_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_NT, sm, st>>>(
+  lg_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), NT, sm, st>>>(
       scratch, H, pw.tw, kp, er, q, an0, amp, mim, mim_pitch, zc);
   return cudaGetLastError();
 }
@@ -651,10 +651,10 @@ static int cols_tile(int H) {
 template <int WN>
 static void rows_fwd_reg(const ImgPtrs& ip, const float* dense, float2* spec, int nimg, int H,
                          const FftPlan& pw, cudaStream_t st) {
-  constexpr int ROWS = REG_NT / RegShape<WN>::T;
-  const size_t sm = ((size_t)ROWS * XBuf<WN>::SIZE + REG_NT) * sizeof(float2);
+  constexpr int NT = RegShape<WN>::NT, ROWS = NT / RegShape<WN>::T;
+  const size_t sm = ((size_t)ROWS * XBuf<WN>::SIZE + NT) * sizeof(float2);
   cudaFuncSetAttribute(fwd_rows_reg<WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  fwd_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), REG_NT, sm, st>>>(ip, dense, spec, H, pw.tw);
+  fwd_rows_reg<WN><<<dim3((H + ROWS - 1) / ROWS, nimg), NT, sm, st>>>(ip, dense, spec, H, pw.tw);
 }
 
 template <int HN>
@@ -675,6 +675,7 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
     case 512: rows_fwd_reg<512>(ipr, dense, spec, nimg, H, pw, st); break;
     case 1024: rows_fwd_reg<1024>(ipr, dense, spec, nimg, H, pw, st); break;
     case 2048: rows_fwd_reg<2048>(ipr, dense, spec, nimg, H, pw, st); break;
+    case 4096: rows_fwd_reg<4096>(ipr, dense, spec, nimg, H, pw, st); break;
     default: {
       int tr = rows_tile(W);
       size_t smr = 2 * (size_t)tr * W * sizeof(float2);
@@ -687,6 +688,7 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
     case 512: cols_fwd_reg<512>(spec, nimg, W, ph, st); break;
     case 1024: cols_fwd_reg<1024>(spec, nimg, W, ph, st); break;
     case 2048: cols_fwd_reg<2048>(spec, nimg, W, ph, st); break;
+    case 4096: cols_fwd_reg<4096>(spec, nimg, W, ph, st); break;
     default: {
       int tc = cols_tile(H);
       size_t smc = 2 * (size_t)tc * H * sizeof(float2);
@@ -705,6 +707,7 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H,
     case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
     case 1024: return cols_reg<1024>(spec, scratch, nimg, W, ph, kp, zc, st);
     case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, zc, st);
+    case 4096: return cols_reg<4096>(spec, scratch, nimg, W, ph, kp, zc, st);
     default: break;
   }
   int tc = cols_tile(H);
@@ -724,6 +727,7 @@ cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const 
     case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     case 1024: return rows_reg<1024>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     case 2048: return rows_reg<2048>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
+    case 4096: return rows_reg<4096>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     default: break;
   }
   size_t sm3 = 2 * (size_t)NS * W * sizeof(float2);

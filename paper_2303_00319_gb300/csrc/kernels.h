@@ -42,7 +42,16 @@ struct DetectWs {
   unsigned long long* cand;     // [nimg][cap_cand]
   unsigned* cand_count;         // [nimg]
   int cap_cand;
+  unsigned long long* sortbuf;  // [nimg][topk_sort_cap(max_kp)] when that exceeds the
+                                // shared-memory sort (max_kp > 16384), else unused
 };
+// Keys the top-K sort holds: the smallest power of two >= max_kp (at least 256).
+inline int topk_sort_cap(int max_kp) {
+  int c = 256;
+  while (c < max_kp) c <<= 1;
+  return c;
+}
+constexpr int TOPK_SMEM_CAP = 16384;
 cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st);
 // min = +inf bits, max = 0, candidate counts = 0 for g images

@@ -169,7 +169,10 @@ int check_size(int H, int W) {
   if (H < 16 || W < 16) return RIFT2_E_INVAL;
   FftPlan t{};
   if (!factor_plan(H, t) || !factor_plan(W, t)) return RIFT2_E_UNIMPL;
-  if ((size_t)2 * NS * W * sizeof(float2) > 227 * 1024) return RIFT2_E_UNIMPL;   // row pass
+  // the generic row pass keeps the four scales of a row in shared memory; power-of-two
+  // widths up to 4096 take the register-tiled path
+  const bool pow2_w = (W & (W - 1)) == 0 && W >= 256 && W <= 4096;
+  if (!pow2_w && (size_t)2 * NS * W * sizeof(float2) > 227 * 1024) return RIFT2_E_UNIMPL;
   if (W > 4096 || H > 8192) return RIFT2_E_UNIMPL;
   return RIFT2_OK;
 }
@@ -214,7 +217,7 @@ struct StageScope {
 // ------------------------------------------------------------------ workspace layout
 struct Layout {
   size_t spec, scratch, er, q, an0, amp, pc, moment, mim, mhist, mstate, noise, minmax, ccount,
-      cand, raw, info, off, total;
+      cand, sortbuf, raw, info, off, total;
   int mim_pitch, cap_cand;
 };
 
@@ -240,6 +243,8 @@ Layout extract_layout(int g, int H, int W, int max_kp, bool debug) {
   L.minmax = take((size_t)g * 2 * 4);
   L.ccount = take((size_t)g * 4);
   L.cand = take((size_t)g * L.cap_cand * 8);
+  const int kc = topk_sort_cap(max_kp);
+  L.sortbuf = take(kc > TOPK_SMEM_CAP ? (size_t)g * kc * 8 : 0);
   L.raw = take((size_t)g * max_kp * DESC_DIM * 2);
   L.info = take((size_t)g * max_kp * 4);
   L.off = take((size_t)g * max_kp * 4);
@@ -400,7 +405,8 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
     RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, g, P, c->kp, moment, minmax, at<float>(ws, L.pc),
                               st));
   }
-  DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand};
+  DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand,
+              at<unsigned long long>(ws, L.sortbuf)};
   {
     StageScope sc(c, RIFT2_STAGE_DETECT, st, K_DETECT);
     RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
@@ -467,7 +473,7 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
     return RIFT2_E_UNIMPL;
   if (!(p.min_wavelength > 0) || !(p.mult > 1) || !(p.sigma_onf > 0 && p.sigma_onf < 1) ||
       !(p.lp_cutoff > 0) || p.lp_order < 1 || p.fast_arc < 1 || p.fast_arc > 16 ||
-      p.max_keypoints < 1 || p.max_keypoints > 16384 || !(p.fast_threshold >= 0) ||
+      p.max_keypoints < 1 || p.max_keypoints > 32768 || !(p.fast_threshold >= 0) ||
       ((p.flags & RIFT2_FLAG_RIFT_RING) && (p.flags & RIFT2_FLAG_RIFT_TEMPLATE)) ||
       !(p.second_ratio >= 0) || !(p.eps > 0))
     return RIFT2_E_INVAL;
@@ -692,7 +698,8 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
     const float* m = moment + (size_t)i0 * P;
     launch_minmax(m, g, P, minmax, st);
     FeatPtrs fp = feat_ptrs(out + i0, g);
-    DetectWs dw{minmax, at<unsigned long long>(c->ws, L.cand), ccount, L.cap_cand};
+    DetectWs dw{minmax, at<unsigned long long>(c->ws, L.cand), ccount, L.cap_cand,
+                at<unsigned long long>(c->ws, L.sortbuf)};
     RIFT2_CU(launch_detect(m, g, H, W, c->kp, dw, fp, st));
   }
   return RIFT2_OK;

@@ -87,7 +87,7 @@ extern "C" int rift2_detect_static(const rift2_params* params, const float* mome
   fp.kp_xy[0] = out->kp_xy;
   fp.kp_score[0] = out->kp_score;
   fp.counts[0] = out->counts;
-  DetectWs dw{minmax, cand, ccount, RIFT2_STATIC_MAX_CANDIDATES};
+  DetectWs dw{minmax, cand, ccount, RIFT2_STATIC_MAX_CANDIDATES, nullptr};
   if (launch_detect(moment, 1, height, width, kp, dw, fp, st) != cudaSuccess) return RIFT2_E_CUDA;
   return RIFT2_OK;
 }

@@ -417,3 +417,56 @@ def test_rift_baseline_matching_and_ground_truth(pkg, dev, small):
         mo = O.evaluate(o_a.xy, o_b.xy, nn, o_a.desc_kp, o_b.desc_kp, pr.angle_deg, pr.a.shape)
         assert abs(mg["correct"] - mo["correct"]) <= 2, (mg, mo)
         assert mg["matches"] == mo["matches"]
+
+
+@pytest.mark.slow
+def test_large_scene_4096(pkg, dev):
+    """Large scene (4096^2, up to 20000 keypoints, 20000 x 20000-class matching).  The
+    oracle computes orientation 0 of the filter bank in full (amplitude sum and noise
+    threshold); keypoints, descriptors and matches are checked by properties that hold at
+    any size, and sampled queries by exhaustive search over the returned descriptors."""
+    pr = synth.config_pair(3)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=20000), device=0, hbm_budget=48 << 30)
+    fa, fb = ctx.extract([torch.from_numpy(pr.a).to(dev), torch.from_numpy(pr.b).to(dev)],
+                         debug=True)
+    m = ctx.match([fa], [fb])[0]
+    ctx.sync()
+    # orientation 0 against the oracle's definition
+    img = pr.a.astype(np.float64)
+    F = np.fft.fft2(img)
+    r, th = O.frequency_grid(*img.shape)
+    ang = O.angular(th, 0)
+    amp0 = np.zeros(img.shape)
+    an0 = None
+    for s in range(4):
+        e = np.abs(np.fft.ifft2(F * (O.radial(r, s) * ang)))
+        amp0 += e
+        if s == 0:
+            an0 = e
+    got = fa.debug["amp"][0].cpu().numpy()
+    assert rel_err(got, amp0, AMP_FLOOR) < 1e-4
+    t0 = O.noise_threshold(an0)
+    assert abs(float(fa.debug["noise_t"][0].cpu()) - t0) <= 1e-5 * t0
+    # keypoints / descriptors / matches: properties
+    g, gb, mh = fa.host(), fb.host(), m.host()
+    h, w = img.shape
+    assert len(g["xy"]) == 20000
+    assert np.all(np.diff(g["score"]) <= 0)
+    x, y = g["xy"][:, 0], g["xy"][:, 1]
+    assert np.all((x >= 48) & (y >= 48) & (x < w - 48) & (y < h - 48))
+    d = g["desc"].astype(np.int64).reshape(len(g["desc"]), 36, 6)
+    assert np.all(d.sum(axis=2) == 256)
+    assert np.all(np.diff(g["desc_kp"]) >= 0) and np.all(g["desc_dom"] < 6)
+    assert len(mh["nn_desc"]) == len(g["desc"])
+    assert np.all((mh["nn_desc"] >= 0) & (mh["nn_desc"] < len(gb["desc"])))
+    assert np.all(mh["d1"] <= mh["d2"])
+    A = g["desc"].astype(np.float64)
+    B = gb["desc"].astype(np.float64)
+    nb = np.sqrt((B * B).sum(axis=1))
+    for q in np.random.default_rng(3).choice(len(A), size=64, replace=False):
+        dist = 2.0 - 2.0 * (B @ A[q]) / (nb * np.sqrt(A[q] @ A[q]))
+        j = int(np.argmin(dist))
+        srt = np.sort(dist)
+        if srt[1] - srt[0] >= 1e-5 * max(srt[0], 1e-12):
+            assert mh["nn_desc"][q] == j
+        assert abs(mh["d1"][q] - srt[0]) <= 1e-5 * max(srt[0], 1e-6) + 1e-9
