@@ -5,6 +5,11 @@ synthetic 1024^2 pairs (400 blobs, 200 segments, random rotation, intensity rema
 gamma speckle; at most 5000 keypoints per image).  Prints one JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--pairs B] [--impl ours|reference]
+                  [--workload 1|2|3]
+
+--workload 2 times the uneven batch (64 pairs, sides 384..2048 step 128, <= 4000
+keypoints) and --workload 3 the 4096^2 scene (<= 20000 keypoints); the default line also
+carries an open-loop serving sweep (Poisson arrivals at 50..400 pairs/s).
 
 Multi-GPU: independent replicas (the pairs shard with no exchange step); launched with
 torch.distributed.run, one rank per GPU, timing = max over ranks.
@@ -27,6 +32,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pairs/s at 1024x1024 (extract A + extract B + NN match A->B)"
+
+
+def _uneven(n, rank):
+    import synth
+    return synth.batch_sizes(n, seed=20232001 + rank)
+
+
+WORKLOADS = {
+    1: {"metric": METRIC, "max_kp": 5000, "pairs": 8,
+        "sizes": lambda n, rank: [(1024, 1024)] * n,
+        "desc": "1024x1024 synthetic multimodal pairs (400 blobs, 200 segments, random rotation, "
+                "1-v^0.6 remap, gamma speckle), <=5000 kp"},
+    2: {"metric": "pairs/s, uneven batch (sides 384..2048 step 128, aspect <= 2)", "max_kp": 4000,
+        "pairs": 64, "sizes": _uneven,
+        "desc": "64 pairs per step, sides uniform on 384..2048 step 128 (aspect <= 2), random "
+                "rotation, <=4000 kp"},
+    3: {"metric": "pairs/s, 4096x4096 large scene", "max_kp": 20000, "pairs": 1,
+        "sizes": lambda n, rank: [(4096, 4096)] * n,
+        "desc": "4096x4096 pair, <=20000 kp, ~20000x20000x216 matching"},
+}
 H = W = 1024
 MAX_KP = 5000
 ROTATE = 4   # input batches rotated between steps
@@ -129,6 +154,15 @@ def measured_traffic(stage: str, images: int):
     return d["dram_bytes_per_image"] * images
 
 
+def load_tensor_peak():
+    """Sustained dense BF16 TFLOP/s (a kernel timed inside a long step)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -220,23 +254,30 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     _build.build()
-    B = args.pairs
-    ctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP), device=local,
+    wl = WORKLOADS[args.workload]
+    B = args.pairs if args.workload == 1 else wl["pairs"]
+    rot = ROTATE if args.workload == 1 else 1
+    max_kp = wl["max_kp"]
+    ctx = pkg.Context(pkg.default_params(max_keypoints=max_kp), device=local,
                       hbm_budget=96 << 30)
 
-    # inputs: ROTATE batches of B pairs, distinct per rank; pinned host copies for e2e
+    # inputs: `rot` batches of B pairs, distinct per rank; pinned host copies for e2e
     host = []
-    for r in range(ROTATE):
+    sizes = wl["sizes"](B, rank)
+    for r in range(rot):
         batch = []
         for b in range(B):
-            pr = synth.make_pair(H, W, synth.pair_seed(1, 100000 * rank + r * B + b),
-                                 angle_deg=None, n_blobs=400, n_segments=200)
-            batch += [pr.a, pr.b]
-        host.append(torch.from_numpy(np.stack(batch)).pin_memory())
-    devb = [h.to(dev) for h in host]
+            h, w = sizes[b]
+            kw = dict(n_blobs=400, n_segments=200) if (h, w) == (1024, 1024) else {}
+            pr = synth.make_pair(h, w, synth.pair_seed(args.workload, 100000 * rank + r * B + b),
+                                 angle_deg=None, **kw)
+            batch += [torch.from_numpy(pr.a).pin_memory(), torch.from_numpy(pr.b).pin_memory()]
+        host.append(batch)
+    devb = [[t.to(dev) for t in batch] for batch in host]
     feats = [ctx.alloc_features() for _ in range(2 * B)]
     matches = [ctx.alloc_matches() for _ in range(B)]
     stream = torch.cuda.current_stream()
+    px_per_step = sum(2 * h * w for h, w in sizes)
 
     def step(imgs):
         ctx.extract([imgs[i] for i in range(2 * B)], feats, stream=stream)
@@ -248,7 +289,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for i in range(args.warmup):
-        step(devb[i % ROTATE])
+        step(devb[i % rot])
     ctx.sync()
     ctx.profile_read()
     barrier()
@@ -263,7 +304,7 @@ def run_ours(args):
     wall0 = time.perf_counter()
     for i in range(args.steps):
         evs[i][0].record(stream)
-        step(devb[i % ROTATE])
+        step(devb[i % rot])
         evs[i][1].record(stream)
     barrier()
     wall = time.perf_counter() - wall0
@@ -278,29 +319,30 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e_ms = []
-    out_h = [torch.empty(2 * MAX_KP * 2 + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
+    ncap = matches[0].nn_desc.shape[0]
+    out_h = [torch.empty(2 * ncap + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
     barrier()
     for i in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        imgs = host[i % ROTATE].to(dev, non_blocking=True)
+        imgs = [t.to(dev, non_blocking=True) for t in host[i % rot]]
         step(imgs)
         for b in range(B):
             m = matches[b]
-            out_h[b][:2 * MAX_KP].copy_(m.nn_desc, non_blocking=True)
-            out_h[b][2 * MAX_KP:4 * MAX_KP].copy_(m.d1.view(torch.int32), non_blocking=True)
-            out_h[b][4 * MAX_KP:].copy_(m.count, non_blocking=True)
+            out_h[b][:ncap].copy_(m.nn_desc, non_blocking=True)
+            out_h[b][ncap:2 * ncap].copy_(m.d1.view(torch.int32), non_blocking=True)
+            out_h[b][2 * ncap:].copy_(m.count, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     barrier()
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(sum(e2e_ms), dev))
-    h2d = int(host[0].numel() * 4)
-    d2h = int(B * (2 * MAX_KP * 2 + 1) * 4)
+    h2d = int(sum(t.numel() for t in host[0]) * 4)
+    d2h = int(B * (2 * ncap + 1) * 4)
 
     # plain form: one pair per call, no grouping, CUDA-core matcher
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and args.workload == 1:
         pctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP,
                                               flags=pkg.FLAG_PLAIN_MATCH | pkg.FLAG_NO_GROUPING),
                            device=local, hbm_budget=16 << 30)
@@ -309,7 +351,7 @@ def run_ours(args):
         lat = []
         for i in range(2 + min(args.steps, 8)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            imgs = devb[i % ROTATE]
+            imgs = devb[i % rot]
             e0.record(stream)
             pctx.extract([imgs[0], imgs[1]], pf, stream=stream)
             pctx.match([pf[0]], [pf[1]], pm, stream=stream)
@@ -329,14 +371,27 @@ def run_ours(args):
     dom = max((k for k in STAGE_BYTES_PER_PX if prof[k][1] > 0), key=lambda k: prof[k][0])
     ms_dom, n_dom = prof[dom]
     imgs_per_launch = 2 * B
-    bytes_per_launch = STAGE_BYTES_PER_PX[dom] * H * W * imgs_per_launch
+    # one launch per same-size group; the bytes of one step's launches over their time
+    n_dom = max(1, n_dom // args.steps) * args.steps if args.workload != 2 else args.steps
+    bytes_per_launch = STAGE_BYTES_PER_PX[dom] * px_per_step / (n_dom / args.steps)
     achieved = bytes_per_launch / (ms_dom / n_dom / 1000.0) / 1e9
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
+    # the matching GEMM against the tensor roofline: 2 nA nB 216 flop per pair
+    na = [int(f.counts[1].item()) for f in feats[0::2]]
+    nb = [int(f.counts[1].item()) for f in feats[1::2]]
+    gemm_flop = sum(2.0 * a * b * 216 for a, b in zip(na, nb))
+    tpeak, tkind = load_tensor_peak()
+    match_s = prof["match"][0] / prof["match"][1] / 1000.0 if prof["match"][1] else float("nan")
+    match_tensor = {"bound": "tensor", "achieved": gemm_flop / match_s / 1e12, "peak": tpeak,
+                    "peak_kind": tkind, "unit": "TFLOP/s",
+                    "frac": gemm_flop / match_s / 1e12 / tpeak,
+                    "flop_per_launch": gemm_flop, "descriptors": [na, nb],
+                    "note": "whole match stage (BF16 prep, tcgen05 GEMM + top-8, exact re-rank)"}
 
     # RIFT's own rotation handling on the same batches (§II-C): template descriptors for A,
     # the six-member convolution ring for B, matching A against all ring members
     rift = None
-    if not args.no_rift:
+    if not args.no_rift and args.workload == 1:
         rt = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=pkg.FLAG_RIFT_TEMPLATE),
                          device=local, hbm_budget=48 << 30)
         rr = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=pkg.FLAG_RIFT_RING),
@@ -351,13 +406,13 @@ def run_ours(args):
             rr.match(fa_t, fb_r, mr, stream=stream)
 
         for i in range(2):
-            rift_step(devb[i % ROTATE])
+            rift_step(devb[i % rot])
         torch.cuda.synchronize()
         rms = []
         for i in range(min(args.steps, 10)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rift_step(devb[i % ROTATE])
+            rift_step(devb[i % rot])
             e1.record(stream)
             e1.synchronize()
             rms.append(e0.elapsed_time(e1))
@@ -369,11 +424,11 @@ def run_ours(args):
         rr.close()
 
     serving = None
-    if args.serve_requests > 0:
+    if args.serve_requests > 0 and args.workload == 1:
         serving = run_serving(args, local)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == 1:
         tcpu = oracle_pair_seconds(H, MAX_KP, synth.pair_seed(1, 0))
         cpu = {"value": 1.0 / tcpu, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "one 1024x1024 pair (2 FP64 oracle extracts + brute-force match); "
@@ -381,24 +436,24 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "metric": wl["metric"], "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "1024x1024 synthetic multimodal pairs (400 blobs, 200 segments, "
-                                   "random rotation, 1-v^0.6 remap, gamma speckle), <=5000 kp",
-                       "pairs_per_step": B, "parallelism": f"replicas x{world}",
-                       "l2": f"inputs rotate over {ROTATE} batches ({ROTATE * 2 * B * 4} MB) and "
-                             "each step streams ~0.3 GB of workspace per image, > L2"},
-            "mpix_per_s": value * 2 * H * W / 1e6,
+            "config": {"workload": wl["desc"], "pairs_per_step": B,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs rotate over {rot} batch(es) ({rot * px_per_step * 4 / 1e6:.0f} MB)"
+                             " and each step streams ~0.3 KB of workspace per pixel, > L2"},
+            "mpix_per_s": value * px_per_step / B / 1e6,
             "plain_form": plain,
             "serving": serving,
             "rift_baseline": rift,
             "stage_ms_per_step": stage_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": measured_traffic(dom, imgs_per_launch),
+                         "traffic": measured_traffic(dom, imgs_per_launch) if args.workload == 1 else None,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
+            "match_tensor": match_tensor,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -422,19 +477,22 @@ def run_serving(args, device: int):
     pool = [synth.make_pair(h, w, synth.pair_seed(4, i + 1), angle_deg=None)
             for i, (h, w) in enumerate(sizes)]
     srv = serve.Server(device=device, max_keypoints=MAX_KP, max_batch_pairs=8,
-                       hbm_budget=96 << 30, lanes=2)
+                       hbm_budget=120 << 30, lanes=2)
     warm = [serve.PairRequest(-1 - i, p.a, p.b) for i, p in enumerate(pool)]
     for r in warm:
         srv.submit(r)
     srv.drain()                           # plans, tables and workspaces for every size
-    reqs = [serve.PairRequest(i, pool[i % len(pool)].a, pool[i % len(pool)].b)
-            for i in range(args.serve_requests)]
-    stats = serve.run_open_loop(srv, reqs, rate=args.serve_rate, seed=7)
+    runs = []
+    for k, rate in enumerate(float(x) for x in str(args.serve_rate).split(",")):
+        reqs = [serve.PairRequest(i, pool[i % len(pool)].a, pool[i % len(pool)].b)
+                for i in range(args.serve_requests)]
+        runs.append(serve.run_open_loop(srv, reqs, rate=rate, seed=7 + k))
     srv.close()
-    stats["workload"] = (f"{len(pool)} distinct pairs cycled, sides log-uniform 256..4096 "
-                         f"(13-smooth, width <= 3584), mean {np.mean([p.a.size for p in pool]) / 1e6:.2f} "
-                         "MPix per image, <= 5000 keypoints")
-    return stats
+    return {"workload": (f"{len(pool)} distinct pairs cycled, sides log-uniform 256..4096 "
+                         f"(13-smooth, width <= 3584), mean "
+                         f"{np.mean([p.a.size for p in pool]) / 1e6:.2f} MPix per image, "
+                         "<= 5000 keypoints, HBM admission budget 120 GB"),
+            "rates": runs}
 
 
 def main():
@@ -442,14 +500,17 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--pairs", type=int, default=8)
+    ap.add_argument("--pairs", type=int, default=8, help="pairs per step (1024^2 workload)")
+    ap.add_argument("--workload", type=int, default=1, choices=(1, 2, 3),
+                    help="1: 1024^2 pairs (headline); 2: uneven batch; 3: 4096^2 scene")
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-rift", action="store_true", help="skip the RIFT-ring baseline")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the open-loop serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=100.0, help="offered pairs/s")
+    ap.add_argument("--serve-rate", default="50,100,200,400",
+                    help="offered pairs/s, comma-separated for a sweep")
     ap.add_argument("--serve-pool", type=int, default=8, help="distinct pairs generated")
     args = ap.parse_args()
     if args.impl == "reference":
