@@ -250,22 +250,21 @@ __device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams
   return expf(-d * d * kp.inv_2ls2) / (1.f + p);
 }
 
-// Angular raised-cosine window of orientation (cos_o, sin_o) at the unit frequency
-// direction (a, b) = (u, v) / r: with c = cos(theta - theta_o) = a cos_o - b sin_o
-// (theta = atan2(-v, u)), the window (1 + cos(3 dtheta)) / 2 for |dtheta| < pi/3 equals
-// (1 + c)(2c - 1)^2 / 2 (triple-angle identity), and 0 beyond.  (a, b) = (0, 0) at DC.
-__device__ __forceinline__ float lg_angular(float a, float b, float co, float so) {
-  const float c = a * co - b * so;
+// Angular raised-cosine window.  With c = cos(theta - theta_o) (theta = atan2(-v, u)),
+// the window (1 + cos(3 dtheta)) / 2 for |dtheta| < pi/3 equals (1 + c)(2c - 1)^2 / 2
+// (triple-angle identity), and 0 beyond.  c = (fu cos_o - fv sin_o) / r is formed from
+// fuco = fu cos_o, fv, sin_o and ri = 1/r (0 at DC).  Every kernel that evaluates the
+// window, and the zero-column table, goes through lg_rinv and lg_window with explicitly
+// rounded products, so they agree bit for bit on which bins are zero.
+__device__ __forceinline__ float lg_rinv(float fu, float fv) {
+  const float r2 = fmaf(fv, fv, __fmul_rn(fu, fu));
+  return (r2 > 0.f) ? rsqrtf(r2) : 0.f;
+}
+__device__ __forceinline__ float lg_window(float fuco, float fv, float so, float ri) {
+  const float c = __fmul_rn(fmaf(-fv, so, fuco), ri);
   if (!(c > 0.5f)) return 0.f;
   const float t = 2.f * c - 1.f;
   return 0.5f * (1.f + c) * t * t;
-}
-
-// Unit direction of DFT bin (u, v): (fu, fv) / r, or (0, 0) at DC.
-__device__ __forceinline__ float2 unit_dir(float fu, float fv) {
-  const float r2 = fu * fu + fv * fv;
-  const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
-  return make_float2(fu * ri, fv * ri);
 }
 
 // Columns u whose angular window is zero on every row: S_o(u, v) = 0 for all v, so the
@@ -276,12 +275,12 @@ __global__ void angular_zero_cols(int H, int W, KParams kp, unsigned char* __res
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int o = blockIdx.y;
   if (u >= W) return;
-  const float co = kp.cos_o[o], so = kp.sin_o[o];
   const float fu = fftfreq(u, W);
+  const float fuco = __fmul_rn(fu, kp.cos_o[o]), so = kp.sin_o[o];
   bool zero = true;
   for (int v = 0; v < H && zero; ++v) {
-    const float2 d = unit_dir(fu, fftfreq(v, H));
-    zero = (lg_angular(d.x, d.y, co, so) == 0.f);
+    const float fv = fftfreq(v, H);
+    zero = (lg_window(fuco, fv, so, lg_rinv(fu, fv)) == 0.f);
   }
   zc[o * W + u] = zero ? 1 : 0;
 }
@@ -323,8 +322,8 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
       int v = i / tc, c = i % tc, u = c0 + c;
       float g = 0.f;
       if (u < W) {
-        const float2 d = unit_dir(fftfreq(u, W), fftfreq(v, H));
-        g = lg_angular(d.x, d.y, co, so);
+        const float fu = fftfreq(u, W), fv = fftfreq(v, H);
+        g = lg_window(__fmul_rn(fu, co), fv, so, lg_rinv(fu, fv));
       }
       float2 x = base[i];
       a[i] = make_float2(x.x * g, x.y * g);
@@ -481,22 +480,20 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   float2* xb = xbuf + col * XS;
   const float2* bc = base + col * XS;
   const float fu = (u < W) ? fftfreq(u, W) : 0.f;
-  // unit directions of this thread's elements v = t + T k, shared by the six windows:
-  // kept in registers when a thread owns few elements, recomputed otherwise
-  constexpr bool DIR_REGS = E <= 16;
-  float2 dir[DIR_REGS ? E : 1];
-  if constexpr (DIR_REGS) {
+  // The first FFT pass reads this thread's elements v = t + T r (r < E, one butterfly of
+  // radix E): 1/r of those bins stays in registers across the six windows, and each
+  // window is applied as the pass loads its input.
+  static_assert(E == S::R0, "first pass: one butterfly of radix E per thread");
+  float ri[E];
 #pragma unroll
-    for (int k = 0; k < E; ++k)
-      dir[k] = (u < W) ? unit_dir(fu, fftfreq(t + T * k, H)) : make_float2(0.f, 0.f);
-  }
+  for (int r = 0; r < E; ++r) ri[r] = (u < W) ? lg_rinv(fu, fftfreq(t + T * r, H)) : 0.f;
   __syncthreads();
   auto sync = [] {
     if constexpr (T <= 32) __syncwarp();
     else __syncthreads();
   };
   for (int o = 0; o < NO; ++o) {
-    const float co = kp.cos_o[o], so = kp.sin_o[o];
+    const float fuco = __fmul_rn(fu, kp.cos_o[o]), so = kp.sin_o[o];
     // a column whose window is zero everywhere transforms to zero: skip it, and leave it
     // unwritten (the row pass reads the same table and substitutes zeros).  The skip is
     // taken per synchronisation domain of the FFT: a warp, or the CTA when T > 32.
@@ -505,19 +502,13 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
     if constexpr (T <= 32) skip = __all_sync(0xffffffffu, zcol);
     else skip = __syncthreads_and(zcol);
     if (!skip) {
-#pragma unroll 8
-      for (int k = 0; k < E; ++k) {
-        const int v = t + T * k;
-        float2 d;
-        if constexpr (DIR_REGS) d = dir[k];
-        else d = (u < W) ? unit_dir(fu, fftfreq(v, H)) : make_float2(0.f, 0.f);
-        const float g = lg_angular(d.x, d.y, co, so);
+      auto ld = [&](int, int r, int v) -> float2 {
+        const float g = lg_window(fuco, fftfreq(v, H), so, ri[r]);
         const float2 x = bc[xpad(v)];
-        xb[xpad(v)] = make_float2(x.x * g, x.y * g);
-      }
-      sync();
+        return make_float2(x.x * g, x.y * g);
+      };
       auto st = [&](int v, float2 val) { xb[xpad(v)] = val; };
-      group_fft_xb<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, st, sync);
+      group_fft<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, ld, st, sync);
     }
     __syncthreads();
     float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W;
