@@ -5,10 +5,12 @@
 //               in BF16), exact squared norms, 1/|b| for the screening scores.
 //   nn_tc     : per CTA 128 queries x a range of 128-wide tiles of B.  One thread issues
 //               TMA loads (128-byte swizzle), one issues tcgen05.mma (BF16 x BF16 -> FP32
-//               in TMEM, M = 128, N = 128, 14 K-steps of 16 cover K = 216); four epilogue
-//               warps read the accumulators with tcgen05.ld (double-buffered in TMEM so
-//               the next tile's MMAs overlap) and keep each query's 8 best candidates by
-//               the FP32 score dot / |b|.  No score matrix ever reaches HBM.
+//               in TMEM, M = 128, N = 128, 14 K-steps of 16 cover K = 216); eight epilogue
+//               warps (two per TMEM lane quadrant, one column half each) read the
+//               accumulators with tcgen05.ld (double-buffered in TMEM so the next tile's
+//               MMAs overlap) and keep each query's 8 best candidates per half by the FP32
+//               score dot / |b|, screening 32 columns at a time against the larger of the
+//               two halves' 8th-best scores.  No score matrix ever reaches HBM.
 //   nn_rerank : one thread per query: the exact comparison of match_common.cuh over its
 //               candidates, distances and near-tie flags.
 // The products and partial sums of integer counts stay below 2^24, so every FP32 addition
@@ -21,23 +23,26 @@
 
 namespace rift2 {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_KP = 256, TC_KATOM = 64, TC_NATOM = 4;
+constexpr int TC_BM = 128, TC_BN = 256, TC_KP = 256, TC_KATOM = 64, TC_NATOM = 4;
 constexpr int TC_KSTEPS = 14;                             // 14 x 16 = 224 >= 216
 constexpr int TC_A_ATOM = TC_BM * 128;                    // 128 rows x 128 bytes = 16 KB
-constexpr int TC_B_ATOM = TC_BN * 128;                    // 16 KB: one K-atom of a B tile
+constexpr int TC_B_ATOM = TC_BN * 128;                    // 32 KB: one K-atom of a B tile
 constexpr int TC_A_BYTES = TC_NATOM * TC_A_ATOM;          // 64 KB
-constexpr int TC_SLOTS = 8;                               // B K-atoms in flight (2 tiles)
+constexpr int TC_SLOTS = 3;                               // B K-atoms in flight
 constexpr int TC_ACC = 2;                                 // accumulators in TMEM
-constexpr int TC_TOPK = 8;
+constexpr int TC_TOPK = 4;
 constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;        // warp 0 TMA, warp 1 MMA, epilogue
 constexpr int TC_HALVES = TC_EPI_WARPS / 4;               // column slices per quadrant
-constexpr int TC_SLICE = TC_BN / TC_HALVES;               // 64 columns per epilogue warp
-constexpr int TC_TMEM_COLS = TC_ACC * TC_BN;              // 256
+constexpr int TC_SLICE = TC_BN / TC_HALVES;               // 128 columns per epilogue warp
+constexpr int TC_TMEM_COLS = TC_ACC * TC_BN;              // 512: all of TMEM
 constexpr long long TC_WAIT = 1ll << 26;                  // bounded mbarrier polls
 constexpr int TC_NBARS = 1 + 2 * TC_SLOTS + 3 * TC_ACC;
+// per epilogue warp: 32 lanes x 32 accumulator values, the chunk a lane is screening
+constexpr int TC_STAGE_FLOATS = TC_EPI_WARPS * 32 * 32;
 constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_SLOTS * TC_B_ATOM + 256 +
-                           TC_ACC * TC_BN * sizeof(float);
+                           (TC_ACC * TC_BN + TC_HALVES * TC_BM + TC_STAGE_FLOATS) * sizeof(float);
+static_assert(TC_HALVES == 2, "threshold sharing pairs the two column halves of a row");
 static_assert(TC_NBARS * 8 + 8 <= 256, "barrier block");
 static_assert(TC_SMEM <= 232448, "shared memory");
 
@@ -112,8 +117,9 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane, without the wait
+// (several loads share one tcgen05.wait::ld).
+__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
       "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
@@ -124,7 +130,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// Largest of 32 values with three-input maxima (17 instructions).
+__device__ __forceinline__ float max32(const float (&v)[32]) {
+  float a[11];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) a[k] = max3f(v[3 * k], v[3 * k + 1], v[3 * k + 2]);
+  a[10] = fmaxf(v[30], v[31]);
+  const float b0 = max3f(a[0], a[1], a[2]), b1 = max3f(a[3], a[4], a[5]);
+  const float b2 = max3f(a[6], a[7], a[8]), b3 = fmaxf(a[9], a[10]);
+  return fmaxf(max3f(b0, b1, b2), b3);
+}
+// Two IEEE round-to-nearest products in one packed instruction.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  const unsigned long long x = ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+  const unsigned long long y = ((unsigned long long)__float_as_uint(b.y) << 32) | __float_as_uint(b.x);
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+  return make_float2(__uint_as_float((unsigned)d), __uint_as_float((unsigned)(d >> 32)));
 }
 
 // --------------------------------------------------------------------------- prep
@@ -133,8 +165,9 @@ __global__ void __launch_bounds__(256) nn_prep(MatchPtrs mp, __nv_bfloat16* __re
                                                __nv_bfloat16* __restrict__ bbf,
                                                float* __restrict__ rinv_b,
                                                int* __restrict__ n2_a, int* __restrict__ n2_b,
-                                               int cap) {
+                                               int cap, int* __restrict__ n_unsure) {
   const int pr = blockIdx.z, side = blockIdx.y;
+  if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *n_unsure = 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + warp;
   const int n = side ? mp.counts_b[pr][1] : mp.counts_a[pr][1];
@@ -172,33 +205,6 @@ struct TcArgs {
   int* status;
 };
 
-__device__ __forceinline__ void topk_insert(float (&sc)[TC_TOPK], int (&id)[TC_TOPK], float s,
-                                            int j) {
-  sc[TC_TOPK - 1] = s;
-  id[TC_TOPK - 1] = j;
-#pragma unroll
-  for (int k = TC_TOPK - 1; k > 0; --k) {
-    if (sc[k] > sc[k - 1]) {
-      const float ts = sc[k]; sc[k] = sc[k - 1]; sc[k - 1] = ts;
-      const int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
-    }
-  }
-}
-
-// v[e] for a run-time e in 0..31 without indexing registers dynamically: a select tree.
-__device__ __forceinline__ float pick32(const float (&v)[32], int e) {
-  float a[16], b[8], c[4], d[2];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) a[k] = (e & 1) ? v[2 * k + 1] : v[2 * k];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) b[k] = (e & 2) ? a[2 * k + 1] : a[2 * k];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) c[k] = (e & 4) ? b[2 * k + 1] : b[2 * k];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) d[k] = (e & 8) ? c[2 * k + 1] : c[2 * k];
-  return (e & 16) ? d[1] : d[0];
-}
-
 __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ CUtensorMap tmA,
                                                        const __grid_constant__ CUtensorMap tmB,
                                                        TcArgs args) {
@@ -228,6 +234,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(&bars[TC_NBARS]);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* rinv_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 256);
+  float* thr_s = rinv_s + TC_ACC * TC_BN;          // [half][row]: 8th-best score of a list
+  float* stage_s = thr_s + TC_HALVES * TC_BM;      // [epilogue warp][lane][32], swizzled
+  for (int i = threadIdx.x; i < TC_HALVES * TC_BM; i += TC_THREADS) thr_s[i] = -1.f;
 
   if (threadIdx.x == 0) {
     mbar_init(full_a, 1);
@@ -310,15 +319,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
   } else {
     // ----------------------------------------------------------------- epilogue
     // Warp w reads TMEM lanes 32 (w % 4) .. +31 (the quadrant the hardware lets it access)
-    // and one slice of TC_SLICE columns of every accumulator tile.
+    // and one half (TC_SLICE columns) of every accumulator tile.  Each lane keeps the 8
+    // best candidates of its row within its half.  The two halves of a row publish their
+    // 8th-best score in shared memory and each screens against the larger of the two: a
+    // candidate below the partner's 8th best has 8 better ones in the partner's half and
+    // cannot be among the row's 8 best, so the union of the two lists still holds them.
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const int etid = threadIdx.x - 64;
-    const int row = m0 + q * 32 + lane;
+    const int rl = q * 32 + lane;
+    const int row = m0 + rl;
     float sc[TC_TOPK], dt[TC_TOPK];
     int id[TC_TOPK];
 #pragma unroll
     for (int k = 0; k < TC_TOPK; ++k) { sc[k] = -1.f; dt[k] = 0.f; id[k] = -1; }
+    volatile float* my_thr = thr_s + half * TC_BM + rl;
+    const volatile float* pa_thr = thr_s + (half ^ 1) * TC_BM + rl;
+    // this lane's row of the staging area: 8 float4 slots, slot k stored at k ^ (lane & 7)
+    float4* stg = reinterpret_cast<float4*>(stage_s + ((warp - 2) * 32 + lane) * 32);
+    const int swz = lane & 7;
     const float* rinv = args.rinv_b + (size_t)pr * args.cap;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     // 1/|b| of the next tile, prefetched one tile ahead into registers, staged in smem
@@ -343,60 +362,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
         break;
       }
       tc_fence_after();
+      // two rounds of two 32-column chunks: one tcgen05.wait::ld per round
 #pragma unroll 1
-      for (int c = 0; c < TC_SLICE / 32; ++c) {
-        const int col0 = acc * TC_BN + half * TC_SLICE + c * 32;
-        const int j0 = (t0 + i) * TC_BN + half * TC_SLICE + c * 32;
-        const float* rs = rinv_s + col0;
-        uint32_t r[32];
-        tmem_ld32(lane_base + (uint32_t)col0, r);
-        float sv[32];
+      for (int rd = 0; rd < TC_SLICE / 64; ++rd) {
+        uint32_t r[2][32];
+        const uint32_t cb = (uint32_t)(acc * TC_BN + half * TC_SLICE + rd * 64);
+        tmem_ld32_nw(lane_base + cb, r[0]);
+        tmem_ld32_nw(lane_base + cb + 32, r[1]);
+        tmem_wait_ld();
 #pragma unroll
-        for (int e4 = 0; e4 < 8; ++e4) {
-          const float4 rb = *reinterpret_cast<const float4*>(rs + e4 * 4);
-          sv[e4 * 4 + 0] = __uint_as_float(r[e4 * 4 + 0]) * rb.x;
-          sv[e4 * 4 + 1] = __uint_as_float(r[e4 * 4 + 1]) * rb.y;
-          sv[e4 * 4 + 2] = __uint_as_float(r[e4 * 4 + 2]) * rb.z;
-          sv[e4 * 4 + 3] = __uint_as_float(r[e4 * 4 + 3]) * rb.w;
-        }
-        // one max per score decides whether this chunk can touch the list at all
-        float mx[16];
+        for (int c = 0; c < 2; ++c) {
+          const int j0 = (t0 + i) * TC_BN + half * TC_SLICE + rd * 64 + c * 32;
+          const float* rs = rinv_s + acc * TC_BN + half * TC_SLICE + rd * 64 + c * 32;
+          float sv[32];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) mx[e] = fmaxf(sv[e], sv[e + 16]);
+          for (int e4 = 0; e4 < 8; ++e4) {
+            const float4 rb = *reinterpret_cast<const float4*>(rs + e4 * 4);
+            const float2 lo = mul2(make_float2(__uint_as_float(r[c][4 * e4]), __uint_as_float(r[c][4 * e4 + 1])),
+                                   make_float2(rb.x, rb.y));
+            const float2 hi = mul2(make_float2(__uint_as_float(r[c][4 * e4 + 2]), __uint_as_float(r[c][4 * e4 + 3])),
+                                   make_float2(rb.z, rb.w));
+            sv[4 * e4] = lo.x; sv[4 * e4 + 1] = lo.y; sv[4 * e4 + 2] = hi.x; sv[4 * e4 + 3] = hi.y;
+          }
+          float thr = fmaxf(sc[TC_TOPK - 1], *pa_thr);
+          if (max32(sv) > thr) {
+            // stage this lane's 32 exact dots, then visit only the groups of four whose
+            // maximum passes; scores are recomputed with the same rounded product
 #pragma unroll
-        for (int w = 8; w > 0; w >>= 1)
+            for (int k = 0; k < 8; ++k)
+              stg[k ^ swz] = make_float4(__uint_as_float(r[c][4 * k]), __uint_as_float(r[c][4 * k + 1]),
+                                         __uint_as_float(r[c][4 * k + 2]), __uint_as_float(r[c][4 * k + 3]));
+            unsigned gm = 0;
 #pragma unroll
-          for (int e = 0; e < w; ++e) mx[e] = fmaxf(mx[e], mx[e + w]);
-        const float thr = sc[TC_TOPK - 1];
-        unsigned m = 0;
-        if (mx[0] > thr) {
+            for (int k = 0; k < 8; ++k)
+              gm |= (fmaxf(fmaxf(sv[4 * k], sv[4 * k + 1]), fmaxf(sv[4 * k + 2], sv[4 * k + 3])) > thr ? 1u : 0u) << k;
+            while (gm) {
+              const int k = __ffs(gm) - 1;
+              gm &= gm - 1;
+              const float4 d4 = stg[k ^ swz];
+              const float4 r4 = *reinterpret_cast<const float4*>(rs + 4 * k);
+              const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+              const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
-          for (int e = 0; e < 32; ++e) m |= (sv[e] > thr ? 1u : 0u) << e;
-          if (j0 + 32 > nB) m &= (j0 >= nB) ? 0u : ((1u << (nB - j0)) - 1u);
-        }
-        // each lane walks only its own columns above its threshold (rare after warm-up)
-        while (m) {
-          const int e = __ffs(m) - 1;
-          m &= m - 1;
-          const float s = pick32(sv, e);
-          if (s > sc[TC_TOPK - 1]) {
-            sc[TC_TOPK - 1] = s;
-            float dv[32];
+              for (int e = 0; e < 4; ++e) {
+                const float s = __fmul_rn(dv[e], rv[e]);
+                const int j = j0 + 4 * k + e;
+                if (s > thr && j < nB) {
+                  sc[TC_TOPK - 1] = s;
+                  dt[TC_TOPK - 1] = dv[e];
+                  id[TC_TOPK - 1] = j;
 #pragma unroll
-            for (int q2 = 0; q2 < 32; ++q2) dv[q2] = __uint_as_float(r[q2]);
-            dt[TC_TOPK - 1] = pick32(dv, e);
-            id[TC_TOPK - 1] = j0 + e;
-#pragma unroll
-            for (int k = TC_TOPK - 1; k > 0; --k) {
-              if (sc[k] > sc[k - 1]) {
-                const float ts = sc[k]; sc[k] = sc[k - 1]; sc[k - 1] = ts;
-                const float td = dt[k]; dt[k] = dt[k - 1]; dt[k - 1] = td;
-                const int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
+                  for (int k2 = TC_TOPK - 1; k2 > 0; --k2) {
+                    if (sc[k2] > sc[k2 - 1]) {
+                      const float ts = sc[k2]; sc[k2] = sc[k2 - 1]; sc[k2 - 1] = ts;
+                      const float td = dt[k2]; dt[k2] = dt[k2 - 1]; dt[k2 - 1] = td;
+                      const int ti = id[k2]; id[k2] = id[k2 - 1]; id[k2 - 1] = ti;
+                    }
+                  }
+                  thr = fmaxf(sc[TC_TOPK - 1], thr);
+                }
               }
             }
+            *my_thr = sc[TC_TOPK - 1];
           }
         }
-        __syncwarp();
       }
       tc_fence_before();
       mbar_arrive(tempty0 + 8 * acc);
@@ -424,10 +453,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
 }
 
 // ------------------------------------------------------------------------ re-rank
+// One thread per query.  The exact comparison of match_common.cuh over the candidates of
+// all its lists gives c1, c2.  The screen is certified afterwards: every column left out
+// of a list scored at most that list's last (4th) FP32 score s, and the exact similarity
+// dot / |b| of any column is at most its FP32 score times (1 + 3 * 2^-24) (one rounding
+// each in sqrt, reciprocal and product; dots and squared norms are exact).  If the
+// second-best similarity beats the largest such s by more than a factor 1 + 2^-21, no
+// column outside the lists can displace c1 or c2; otherwise the query goes to the
+// exhaustive pass below (it needs several columns within FP32 rounding of c2).
+__device__ __forceinline__ void write_match(const MatchPtrs& mp, int pr, int q, float na2,
+                                            const Cand& c1, const Cand& c2) {
+  const bool ok1 = c1.j != 0x7fffffff, ok2 = c2.j != 0x7fffffff;
+  const float d1 = ok1 ? exact_dist(na2, c1) : __int_as_float(0x7f800000);
+  const float d2 = ok2 ? exact_dist(na2, c2) : __int_as_float(0x7f800000);
+  mp.q_desc[pr][q] = q;
+  mp.nn_desc[pr][q] = ok1 ? c1.j : -1;
+  mp.kp_a[pr][q] = mp.desc_kp_a[pr][q];
+  mp.kp_b[pr][q] = ok1 ? mp.desc_kp_b[pr][c1.j] : -1;
+  mp.d1[pr][q] = d1;
+  mp.d2[pr][q] = d2;
+  mp.near_tie[pr][q] = (ok2 && (d2 - d1) < 1e-5f * fmaxf(d1, 1e-12f)) ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int2* __restrict__ cand,
                                                  const int* __restrict__ n2_a,
-                                                 const int* __restrict__ n2_b, int cap,
-                                                 int nsplit) {
+                                                 const int* __restrict__ n2_b,
+                                                 const float* __restrict__ rinv_b, int cap,
+                                                 int nsplit, int* __restrict__ unsure,
+                                                 int* __restrict__ n_unsure) {
   const int pr = blockIdx.y;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int nA = mp.counts_a[pr][1], nB = mp.counts_b[pr][1];
@@ -435,6 +488,7 @@ __global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int2* __res
   if (q >= nA) return;
   const int nl = nsplit * TC_HALVES;
   Cand c1{0.f, 1.f, 0x7fffffff}, c2 = c1;
+  float s_cut = -1.f;   // largest last score of a full list
   for (int l = 0; l < nl; ++l) {
     const int4* cl = reinterpret_cast<const int4*>(cand + (((size_t)pr * nl + l) * cap + q) * TC_TOPK);
     int2 e[TC_TOPK];
@@ -451,25 +505,65 @@ __global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int2* __res
 #pragma unroll
     for (int k = 0; k < TC_TOPK; ++k)
       if (e[k].x >= 0 && e[k].x < nB) push2(c1, c2, Cand{__int_as_float(e[k].y), n2[k], e[k].x});
+    const int2 last = e[TC_TOPK - 1];
+    if (last.x >= 0 && last.x < nB)
+      s_cut = fmaxf(s_cut, __fmul_rn(__int_as_float(last.y), __ldg(rinv_b + (size_t)pr * cap + last.x)));
   }
-  const float na2 = (float)n2_a[(size_t)pr * cap + q];
-  const bool ok1 = c1.j != 0x7fffffff, ok2 = c2.j != 0x7fffffff;
-  const float d1 = ok1 ? exact_dist(na2, c1) : __int_as_float(0x7f800000);
-  const float d2 = ok2 ? exact_dist(na2, c2) : __int_as_float(0x7f800000);
-  mp.q_desc[pr][q] = q;
-  mp.nn_desc[pr][q] = ok1 ? c1.j : -1;
-  mp.kp_a[pr][q] = mp.desc_kp_a[pr][q];
-  mp.kp_b[pr][q] = ok1 ? mp.desc_kp_b[pr][c1.j] : -1;
-  mp.d1[pr][q] = d1;
-  mp.d2[pr][q] = d2;
-  mp.near_tie[pr][q] = (ok2 && (d2 - d1) < 1e-5f * fmaxf(d1, 1e-12f)) ? 1 : 0;
+  if (s_cut >= 0.f) {
+    const Cand& w = (c2.j != 0x7fffffff) ? c2 : c1;
+    const double bound = (double)s_cut * (1.0 + 1.0 / (double)(1 << 21));
+    if (!(w.j != 0x7fffffff && (double)w.dot / sqrt((double)w.n2) > bound)) {
+      const int slot = atomicAdd(n_unsure, 1);
+      unsure[slot] = pr * cap + q;
+      return;
+    }
+  }
+  write_match(mp, pr, q, (float)n2_a[(size_t)pr * cap + q], c1, c2);
+}
+
+// Exhaustive exact search for the queries the screen could not certify: one CTA per
+// query, integer dots against every descriptor of B, the exact order of match_common.cuh.
+constexpr int NN_EXACT_THREADS = 256;
+__global__ void __launch_bounds__(NN_EXACT_THREADS) nn_exact(MatchPtrs mp,
+                                                             const int* __restrict__ n2_a,
+                                                             const int* __restrict__ n2_b,
+                                                             int cap,
+                                                             const int* __restrict__ unsure,
+                                                             const int* __restrict__ n_unsure) {
+  __shared__ int qa[DESC_DIM];
+  __shared__ Cand best[2 * NN_EXACT_THREADS];
+  const int nu = *n_unsure;
+  for (int f = blockIdx.x; f < nu; f += gridDim.x) {
+    const int pr = unsure[f] / cap, q = unsure[f] % cap;
+    const int nB = mp.counts_b[pr][1];
+    __syncthreads();   // qa / best of the previous query are no longer read
+    for (int k = threadIdx.x; k < DESC_DIM; k += blockDim.x)
+      qa[k] = mp.desc_a[pr][(size_t)q * DESC_DIM + k];
+    __syncthreads();
+    Cand c1{0.f, 1.f, 0x7fffffff}, c2 = c1;
+    for (int j = threadIdx.x; j < nB; j += blockDim.x) {
+      const unsigned short* bj = mp.desc_b[pr] + (size_t)j * DESC_DIM;
+      int dot = 0;
+      for (int k = 0; k < DESC_DIM; ++k) dot += qa[k] * (int)bj[k];
+      push2(c1, c2, Cand{(float)dot, (float)n2_b[(size_t)pr * cap + j], j});
+    }
+    best[2 * threadIdx.x] = c1;
+    best[2 * threadIdx.x + 1] = c2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Cand b1{0.f, 1.f, 0x7fffffff}, b2 = b1;
+      for (int i = 0; i < 2 * NN_EXACT_THREADS; ++i)
+        if (best[i].j != 0x7fffffff) push2(b1, b2, best[i]);
+      write_match(mp, pr, q, (float)n2_a[(size_t)pr * cap + q], b1, b2);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------- launcher
 size_t match_tc_ws_bytes(int npairs, int cap, int nsplit) {
   size_t bf = (size_t)npairs * cap * TC_KP * 2;
   size_t per = (size_t)npairs * cap * 4;
-  return 2 * bf + 3 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8 + 4096;
+  return 2 * bf + 4 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8 + 4096;
 }
 
 int match_tc_nsplit(int npairs, int cap) {
@@ -492,8 +586,12 @@ cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
   p += (size_t)npairs * cap * 4;
   int* n2b = reinterpret_cast<int*>(p);
   p += (size_t)npairs * cap * 4;
+  int* unsure = reinterpret_cast<int*>(p);
+  p += (size_t)npairs * cap * 4;
   int2* cand = reinterpret_cast<int2*>(p);
-  nn_prep<<<dim3((cap + 7) / 8, 2, npairs), 256, 0, st>>>(mp, abf, bbf, rinv, n2a, n2b, cap);
+  p += (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8;
+  int* n_unsure = reinterpret_cast<int*>(p);
+  nn_prep<<<dim3((cap + 7) / 8, 2, npairs), 256, 0, st>>>(mp, abf, bbf, rinv, n2a, n2b, cap, n_unsure);
   TcArgs ta{};
   for (int i = 0; i < npairs; ++i) {
     ta.counts_a[i] = mp.counts_a[i] + 1;
@@ -507,7 +605,9 @@ cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
   const size_t sm = TC_SMEM;
   cudaFuncSetAttribute(nn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   nn_tc<<<dim3((cap + TC_BM - 1) / TC_BM, nsplit, npairs), TC_THREADS, sm, st>>>(*tmA, *tmB, ta);
-  nn_rerank<<<dim3((cap + 255) / 256, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, cap, nsplit);
+  nn_rerank<<<dim3((cap + 255) / 256, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, rinv, cap, nsplit,
+                                                             unsure, n_unsure);
+  nn_exact<<<152, NN_EXACT_THREADS, 0, st>>>(mp, n2a, n2b, cap, unsure, n_unsure);
   return cudaGetLastError();
 }
 

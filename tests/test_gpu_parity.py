@@ -210,6 +210,31 @@ def test_match_stage_duplicates_and_single(pkg, dev):
     assert int(m0.count.cpu()[0]) == 0
 
 
+def test_match_stage_screen_fallback(pkg, dev):
+    """Ten exact copies of a query's descriptor spread over B's tiles and column halves
+    fill every candidate list with equal scores: the screen cannot certify the top two and
+    the exhaustive pass must return the lowest copy, as the oracle does."""
+    ctx = pkg.Context(pkg.default_params(max_keypoints=700), device=0)
+    rng = np.random.default_rng(11)
+    a = rng.integers(0, 40, size=(300, 216))
+    b = rng.integers(0, 40, size=(1300, 216))
+    copies = [37, 130, 131, 300, 555, 700, 901, 1024, 1100, 1299]
+    for j in copies:
+        b[j] = a[0]
+    for j in (12, 400, 800, 1250, 1251, 1252):   # a second query with six copies
+        b[j] = a[7]
+    fa = _features_from(ctx, dev, a, np.arange(300))
+    fb = _features_from(ctx, dev, b, np.arange(1300))
+    m = ctx.match([fa], [fb])[0].host()
+    nn, d1, d2, near = O.match(a, b)
+    assert nn[0] == 37 and m["nn_desc"][0] == 37 and m["d1"][0] == 0 and m["d2"][0] == 0
+    assert nn[7] == 12 and m["nn_desc"][7] == 12
+    assert np.all((m["nn_desc"] == nn) | near)
+    np.testing.assert_allclose(m["d1"], d1, rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(m["d2"], d2, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(m["near_tie"].astype(bool), near)
+
+
 # -------------------------------------------------------------------- end to end
 def _e2e_check(f, o, ctx_p):
     g = f.host()
