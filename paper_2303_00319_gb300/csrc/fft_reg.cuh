@@ -87,6 +87,17 @@ struct XBuf {
   static constexpr int SIZE = N + N / 32 + 2;   // +2: staggers consecutive buffers' banks
 };
 
+// Stride between the exchange buffers of the COLS columns a CTA transposes through shared
+// memory (row segments of COLS columns in global memory <-> one buffer per column): a
+// stride of 16 / COLS (mod 16) float2 puts the COLS columns of the (16 / COLS) rows a
+// half-warp touches on 32 distinct banks.
+template <int N, int COLS>
+struct ColStride {
+  static_assert(COLS >= 1 && COLS <= 16 && 16 % COLS == 0, "columns per CTA");
+  static constexpr int BASE = XBuf<N>::SIZE;
+  static constexpr int SIZE = BASE + ((16 / COLS - BASE % 16) % 16 + 16) % 16;
+};
+
 // One pass.  Inputs come from `ld(i, r, index)` (FIRST; i = butterfly of this thread,
 // r = butterfly input, both compile-time) or the exchange buffer; outputs go to
 // `st(index, value)` (LAST) or the exchange buffer.  `sync()` synchronises the group.

@@ -186,7 +186,7 @@ template <int HN>
 __global__ void __launch_bounds__(ColShape<HN>::NT) fwd_cols_reg(float2* __restrict__ spec, int W,
                                                                 const float2* __restrict__ twh) {
   using S = ColShape<HN>;
-  constexpr int T = S::T, NT = S::NT, COLS = NT / T, E = HN / T, XS = XBuf<HN>::SIZE;
+  constexpr int T = S::T, NT = S::NT, COLS = NT / T, E = HN / T, XS = ColStride<HN, COLS>::SIZE;
   extern __shared__ float2 sm[];   // [COLS][XS] + [NT] reduction slots
   float2* red = sm + COLS * XS;
   const int img = blockIdx.y;
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   constexpr int T = S::T, NT = S::NT;
   constexpr int COLS = NT / T;
   constexpr int E = H / T;
-  constexpr int XS = XBuf<H>::SIZE;
+  constexpr int XS = ColStride<H, COLS>::SIZE;
   extern __shared__ float2 sm[];
   float2* base = sm;               // [COLS][XS]  F * R_s
   float2* xbuf = sm + COLS * XS;   // [COLS][XS]  exchange buffers
@@ -605,7 +605,7 @@ static cudaError_t cols_reg(const float2* spec, float2* scratch, int nimg, int W
                             cudaStream_t st) {
   constexpr int NT = ColShape<H>::NT;
   constexpr int COLS = NT / ColShape<H>::T;
-  const size_t sm = 2 * (size_t)COLS * XBuf<H>::SIZE * sizeof(float2);
+  const size_t sm = 2 * (size_t)COLS * ColStride<H, COLS>::SIZE * sizeof(float2);
   cudaFuncSetAttribute(lg_cols_reg<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   lg_cols_reg<H><<<dim3((W + COLS - 1) / COLS, NS, nimg), NT, sm, st>>>(spec, scratch, W, ph.tw,
                                                                        kp, zc);
@@ -651,7 +651,7 @@ static void rows_fwd_reg(const ImgPtrs& ip, const float* dense, float2* spec, in
 template <int HN>
 static void cols_fwd_reg(float2* spec, int nimg, int W, const FftPlan& ph, cudaStream_t st) {
   constexpr int NT = ColShape<HN>::NT, COLS = NT / ColShape<HN>::T;
-  const size_t sm = ((size_t)COLS * XBuf<HN>::SIZE + NT) * sizeof(float2);
+  const size_t sm = ((size_t)COLS * ColStride<HN, COLS>::SIZE + NT) * sizeof(float2);
   cudaFuncSetAttribute(fwd_cols_reg<HN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   fwd_cols_reg<HN><<<dim3((W + COLS - 1) / COLS, nimg), NT, sm, st>>>(spec, W, ph.tw);
 }
