@@ -317,24 +317,39 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, B, args.steps, total_ms)
 
-    # end to end through the public API with host buffers
-    e2e_ms = []
+    # end to end through the public API with host buffers: every step copies its pinned
+    # input images in on a copy stream (overlapping the previous step's kernels through
+    # two device input buffers), runs extract + match, and copies its matches out; all K
+    # steps' copies lie inside the timed region
+    copy_stream = torch.cuda.Stream(device=dev)
+    dbuf = [[torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host[0]] for _ in range(2)]
     ncap = matches[0].nn_desc.shape[0]
     out_h = [torch.empty(2 * ncap + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
+    ev_copied = [torch.cuda.Event() for _ in range(args.steps)]
+    ev_done = [torch.cuda.Event() for _ in range(args.steps)]
     barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    copy_stream.wait_stream(stream)
     for i in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        imgs = [t.to(dev, non_blocking=True) for t in host[i % rot]]
-        step(imgs)
+        buf = dbuf[i % 2]
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(ev_done[i - 2])   # this buffer's previous step is done
+            for d, h in zip(buf, host[i % rot]):
+                d.copy_(h, non_blocking=True)
+            ev_copied[i].record(copy_stream)
+        stream.wait_event(ev_copied[i])
+        step(buf)
         for b in range(B):
             m = matches[b]
             out_h[b][:ncap].copy_(m.nn_desc, non_blocking=True)
             out_h[b][ncap:2 * ncap].copy_(m.d1.view(torch.int32), non_blocking=True)
             out_h[b][2 * ncap:].copy_(m.count, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
+        ev_done[i].record(stream)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = [e0.elapsed_time(e1)]
     barrier()
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(sum(e2e_ms), dev))
     h2d = int(sum(t.numel() for t in host[0]) * 4)
@@ -456,6 +471,8 @@ def run_ours(args):
             "match_tensor": match_tensor,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "form": "pinned host images in on a copy stream (step i+1's copy overlaps "
+                            "step i's kernels), matches out every step",
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
