@@ -120,9 +120,28 @@ __device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __rest
     const int j = t + T * i;
     const int k = j % NS;
     if constexpr (NS > 1) {
+      // W^(k r TSTEP), r = 1..R-1: the powers r = 2^b come from the table (generated in
+      // FP64); every other r is the product of the powers of its set bits, taken from the
+      // lowest bit up, so each shares its prefix product with a smaller r.  log2(R) table
+      // reads instead of R - 1, at most log2(R) - 1 extra roundings per twiddle (relative
+      // error below 1e-6).
       constexpr int TSTEP = N / (NS * R);
+      constexpr int LOGR = (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : 1;
+      float2 wp[LOGR];
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle<INV>(tw, k * r * TSTEP));
+      for (int b = 0; b < LOGR; ++b) wp[b] = twiddle<INV>(tw, k * (1 << b) * TSTEP);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = make_float2(1.f, 0.f);
+        bool first = true;
+#pragma unroll
+        for (int b = 0; b < LOGR; ++b)
+          if (r & (1 << b)) {
+            w = first ? wp[b] : cmul(w, wp[b]);
+            first = false;
+          }
+        v[i][r] = cmul(v[i][r], w);
+      }
     }
     dft_reg<R, INV>(v[i]);
     const int base = (j - k) * R + k;
