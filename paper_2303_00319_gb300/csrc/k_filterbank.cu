@@ -237,9 +237,11 @@ __global__ void __launch_bounds__(ColShape<HN>::NT) fwd_cols_reg(float2* __restr
 // ------------------------------------------------------------- log-Gabor transfer
 // Radial part of scale s at squared radius r2 (cycles/px)^2:
 //   exp(-(ln r - ln f_s)^2 / (2 ln^2 sigma_onf)) / (1 + (r^2 / c^2)^n), zero at DC.
+// The logarithm, exponential and quotient use the SFU approximations (relative error of
+// the filter value a few 1e-7; (r/c)^(2n) stays below 1e6 on the grid).
 __device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams& kp) {
   if (r2 <= 0.f) return 0.f;
-  float lr = 0.5f * logf(r2);
+  float lr = 0.5f * __logf(r2);
   float d = lr - log_fs;
   float x = r2 * kp.inv_lp_c2;   // (r/c)^2
   float p = 1.f, base = x;
@@ -247,7 +249,7 @@ __device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams
     if (e & 1) p *= base;
     base *= base;
   }
-  return expf(-d * d * kp.inv_2ls2) / (1.f + p);
+  return __fdividef(__expf(-d * d * kp.inv_2ls2), 1.f + p);
 }
 
 // Angular raised-cosine window.  With c = cos(theta - theta_o) (theta = atan2(-v, u)),
@@ -541,8 +543,17 @@ __global__ void __launch_bounds__(RegShape<WN>::NT) lg_rows_reg(const float2* __
   constexpr int PIX = ROWS * WN / NT;
   static_assert(ROWS >= 1 && PIX >= 1, "row tile");
   extern __shared__ float2 sm[];   // [GROUPS][XS], group g = (row g / NS, scale g % NS)
-  __shared__ unsigned char zcs[NO * WN];
-  for (int i = threadIdx.x; i < NO * WN; i += NT) zcs[i] = zc[i];
+  // bit r of zmask[o][t]: column t + T r has a zero window for orientation o (the first
+  // FFT pass reads exactly those columns, one radix-E butterfly per thread)
+  constexpr int E = WN / T;
+  static_assert(E == S::R0 && E <= 32, "first pass: one butterfly of radix E per thread");
+  __shared__ unsigned zmask[NO][T];
+  for (int i = threadIdx.x; i < NO * T; i += NT) {
+    const int o = i / T, tt = i % T;
+    unsigned m = 0;
+    for (int r = 0; r < E; ++r) m |= (zc[o * WN + tt + T * r] ? 1u : 0u) << r;
+    zmask[o][tt] = m;
+  }
   __syncthreads();
   const int img = blockIdx.y;
   const int row0 = blockIdx.x * ROWS;
@@ -563,9 +574,9 @@ __global__ void __launch_bounds__(RegShape<WN>::NT) lg_rows_reg(const float2* __
   };
   for (int o = 0; o < NO; ++o) {
     const float2* src = scratch + (((size_t)img * NS + sc) * NO + o) * P + (size_t)row * WN;
-    const unsigned char* zco = zcs + o * WN;
-    auto ld = [&](int, int, int x) -> float2 {
-      return (row < H && !zco[x]) ? __ldg(src + x) : make_float2(0.f, 0.f);
+    const unsigned zm = (row < H) ? ~zmask[o][t] : 0u;   // bit r set: load element r
+    auto ld = [&](int, int r, int x) -> float2 {
+      return ((zm >> r) & 1u) ? __ldg(src + x) : make_float2(0.f, 0.f);
     };
     auto st = [&](int x, float2 val) { xb[xpad(x)] = val; };
     group_fft<WN, T, S::R0, S::R1, S::R2, true>(xb, t, tww, ld, st, sync);
