@@ -306,12 +306,13 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
   float2* b = sm + 2 * nel;
   const float2* F = spec + (size_t)img * H * W;
   const float log_fs = kp.log_fs[s];
+  const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     int v = i / tc, c = i % tc, u = c0 + c;
     float2 f = make_float2(0.f, 0.f);
     if (u < W) {
       float fu = fftfreq(u, W), fv = fftfreq(v, H);
-      float rs = lg_radial(fu * fu + fv * fv, log_fs, kp);
+      float rs = lg_radial(fu * fu + fv * fv, log_fs, kp) * inv_hw;
       float2 x = __ldg(F + (size_t)v * W + u);
       f = make_float2(x.x * rs, x.y * rs);
     }
@@ -342,22 +343,23 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
 }
 
 // Per-pixel reductions over the Ns scales of one orientation (phase-congruency model of
-// §II-A; MIM amplitude sum of §II-B).  z[s] = EO_{s,o}(x) before the 1/(HW) scale.
+// §II-A; MIM amplitude sum of §II-B).  z[s] = EO_{s,o}(x): the column pass applies the
+// inverse DFT's 1/(HW) to the filtered spectrum, so the row pass output is EO itself.
 //   A = sum_s |EO_s|, Er = sum_s (E mE + O mO - |E mO - O mE|) with (mE, mO) the unit mean
 //   phase vector, q = w / A with the frequency-spread weight w, an0 = |EO_0|.
 // Square roots, reciprocals and the exponential use the SFU approximations (relative
 // error a few 1e-7), well inside the 1e-4 value tolerance and the 1e-5 near-tie margin.
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
-__device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], float scale, const KParams& kp,
+__device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParams& kp,
                                              float& er, float& q, float& an0, float& sum_an) {
   float e[NS], od[NS];
   float sum_e = 0.f, sum_o = 0.f, max_an = 0.f;
   sum_an = 0.f;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    e[s] = z[s].x * scale;
-    od[s] = z[s].y * scale;
+    e[s] = z[s].x;
+    od[s] = z[s].y;
     const float an = fast_sqrt(e[s] * e[s] + od[s] * od[s]);
     if (s == 0) an0 = an;
     sum_e += e[s];
@@ -396,7 +398,6 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
   float2* a = sm;
   float2* b = sm + nel;
   const size_t P = (size_t)H * W;
-  const float scale = 1.f / ((float)H * (float)W);
   float best[RR_MAXPIX];
   int besto[RR_MAXPIX];
 #pragma unroll
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
 #pragma unroll
       for (int s = 0; s < NS; ++s) z[s] = res[s * W + x];
       float energy, q, an0, sum_an;
-      reduce_pixel(z, scale, kp, energy, q, an0, sum_an);
+      reduce_pixel(z, kp, energy, q, an0, sum_an);
       size_t off = ((size_t)img * NO + o) * P + (size_t)row * W + x;
       er_out[off] = energy;
       q_out[off] = q;
@@ -466,12 +467,17 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   }
   const float2* F = spec + (size_t)img * H * W;
   const float log_fs = kp.log_fs[s];
-  for (int i = tid; i < H * COLS; i += NT) {
+  const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
+  static_assert((H * COLS) % NT == 0, "fill tile");
+  // unrolled so that several spectrum loads are in flight per thread
+#pragma unroll 8
+  for (int k = 0; k < H * COLS / NT; ++k) {
+    const int i = tid + k * NT;
     const int v = i / COLS, c = i % COLS, u = c0 + c;
     float2 f = make_float2(0.f, 0.f);
     if (u < W) {
       const float fu = fftfreq(u, W), fv = fftfreq(v, H);
-      const float rs = lg_radial(fu * fu + fv * fv, log_fs, kp);
+      const float rs = lg_radial(fu * fu + fv * fv, log_fs, kp) * inv_hw;
       const float2 x = __ldg(F + (size_t)v * W + u);
       f = make_float2(x.x * rs, x.y * rs);
     }
@@ -563,7 +569,6 @@ __global__ void __launch_bounds__(RegShape<WN>::NT) lg_rows_reg(const float2* __
   const int row = row0 + rr;
   float2* xb = sm + grp * XS;
   const size_t P = (size_t)H * WN;
-  const float scale = 1.f / ((float)H * (float)WN);
   float best[PIX];
   int besto[PIX];
 #pragma unroll
@@ -590,7 +595,7 @@ __global__ void __launch_bounds__(RegShape<WN>::NT) lg_rows_reg(const float2* __
 #pragma unroll
       for (int s = 0; s < NS; ++s) z[s] = sm[(r2 * NS + s) * XS + xpad(x)];
       float energy, q, an0, sum_an;
-      reduce_pixel(z, scale, kp, energy, q, an0, sum_an);
+      reduce_pixel(z, kp, energy, q, an0, sum_an);
       const size_t off = ((size_t)img * NO + o) * P + (size_t)(row0 + r2) * WN + x;
       er_out[off] = energy;
       q_out[off] = q;
