@@ -495,6 +495,9 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   float ri[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) ri[r] = (u < W) ? lg_rinv(fu, fftfreq(t + T * r, H)) : 0.f;
+  // fftfreq(t + T r, H) as t / H plus a constant per r (exact: H is a power of two and
+  // t + T r < H / 2 exactly when r < E / 2)
+  const float fv0 = (float)t * (1.f / H);
   __syncthreads();
   auto sync = [] {
     if constexpr (T <= 32) __syncwarp();
@@ -511,7 +514,8 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
     else skip = __syncthreads_and(zcol);
     if (!skip) {
       auto ld = [&](int, int r, int v) -> float2 {
-        const float g = lg_window(fuco, fftfreq(v, H), so, ri[r]);
+        const float fv = fv0 + (float)(T * r - (2 * r >= E ? H : 0)) * (1.f / H);
+        const float g = lg_window(fuco, fv, so, ri[r]);
         const float2 x = bc[xpad(v)];
         return make_float2(x.x * g, x.y * g);
       };
@@ -519,10 +523,20 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
       group_fft<H, T, S::R0, S::R1, S::R2, true>(xb, t, twh, ld, st, sync);
     }
     __syncthreads();
-    float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W;
-    for (int i = tid; i < H * COLS; i += NT) {
-      const int v = i / COLS, c = i % COLS;
-      if (!zcs[o][c]) dst[(size_t)v * W + c0 + c] = xbuf[c * XS + xpad(v)];
+    {
+      // thread (row v0 = tid / COLS, column c = tid % COLS) copies rows v0 + RSTEP k: a
+      // warp stores row segments of COLS columns
+      constexpr int RSTEP = NT / COLS;
+      const int c = tid % COLS, v0 = tid / COLS;
+      if (!zcs[o][c]) {
+        const float2* srcb = xbuf + c * XS;
+        float2* dstc = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W + c0 + c;
+#pragma unroll 8
+        for (int k = 0; k < H / RSTEP; ++k) {
+          const int v = v0 + RSTEP * k;
+          dstc[(size_t)v * W] = srcb[xpad(v)];
+        }
+      }
     }
     __syncthreads();
   }
