@@ -98,12 +98,43 @@ struct ColStride {
   static constexpr int SIZE = BASE + ((16 / COLS - BASE % 16) % 16 + 16) % 16;
 };
 
+// log2 of a power-of-two radix.
+template <int R>
+constexpr int log2_radix() { return R >= 32 ? 5 : R >= 16 ? 4 : R >= 8 ? 3 : R >= 4 ? 2 : 1; }
+
+// The twiddle powers one thread's butterflies of a pass need: for butterfly i (k = the
+// butterfly's index modulo NS) the table values W^(k 2^b TSTEP), b < log2(R).  They depend
+// only on the thread, so a transform loads them before its first pass runs and the loads'
+// latency hides behind that pass.
+template <int N, int T, int R, int NS>
+struct PassTw {
+  static constexpr int B = (N / T) / R, LOGR = log2_radix<R>();
+  float2 w[B][LOGR];
+  template <bool INV>
+  __device__ __forceinline__ void load(int t, const float2* __restrict__ tw) {
+    if constexpr (NS > 1) {
+      constexpr int TSTEP = N / (NS * R);
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        const int k = (t + T * i) % NS;
+#pragma unroll
+        for (int b = 0; b < LOGR; ++b) w[i][b] = twiddle<INV>(tw, k * (1 << b) * TSTEP);
+      }
+    }
+  }
+};
+
 // One pass.  Inputs come from `ld(i, r, index)` (FIRST; i = butterfly of this thread,
 // r = butterfly input, both compile-time) or the exchange buffer; outputs go to
 // `st(index, value)` (LAST) or the exchange buffer.  `sync()` synchronises the group.
+// Twiddles W^(k r TSTEP), r = 1..R-1: the powers r = 2^b come from `tp` (table values
+// generated in FP64); every other r is the product of the powers of its set bits, taken
+// from the lowest bit up, so each shares its prefix product with a smaller r: log2(R)
+// table reads instead of R - 1, at most log2(R) - 1 extra roundings per twiddle (relative
+// error below 1e-6).
 template <int N, int T, int R, int NS, bool INV, bool FIRST, bool LAST, class Ld, class St,
           class Sync>
-__device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __restrict__ tw,
+__device__ __forceinline__ void reg_pass(float2* xb, int t, const PassTw<N, T, R, NS>& tp,
                                          Ld& ld, St& st, Sync& sync) {
   constexpr int E = N / T, B = E / R, M = N / R;
   static_assert(E % R == 0, "radix must divide the elements per thread");
@@ -120,16 +151,7 @@ __device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __rest
     const int j = t + T * i;
     const int k = j % NS;
     if constexpr (NS > 1) {
-      // W^(k r TSTEP), r = 1..R-1: the powers r = 2^b come from the table (generated in
-      // FP64); every other r is the product of the powers of its set bits, taken from the
-      // lowest bit up, so each shares its prefix product with a smaller r.  log2(R) table
-      // reads instead of R - 1, at most log2(R) - 1 extra roundings per twiddle (relative
-      // error below 1e-6).
-      constexpr int TSTEP = N / (NS * R);
-      constexpr int LOGR = (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : 1;
-      float2 wp[LOGR];
-#pragma unroll
-      for (int b = 0; b < LOGR; ++b) wp[b] = twiddle<INV>(tw, k * (1 << b) * TSTEP);
+      constexpr int LOGR = PassTw<N, T, R, NS>::LOGR;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         float2 w = make_float2(1.f, 0.f);
@@ -137,7 +159,7 @@ __device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __rest
 #pragma unroll
         for (int b = 0; b < LOGR; ++b)
           if (r & (1 << b)) {
-            w = first ? wp[b] : cmul(w, wp[b]);
+            w = first ? tp.w[i][b] : cmul(w, tp.w[i][b]);
             first = false;
           }
         v[i][r] = cmul(v[i][r], w);
@@ -154,20 +176,28 @@ __device__ __forceinline__ void reg_pass(float2* xb, int t, const float2* __rest
   if (!LAST) sync();
 }
 
-// Full transform as up to three passes of radices R0, R1, R2 (1 = unused).
+// Full transform as up to three passes of radices R0, R1, R2 (1 = unused).  The later
+// passes' twiddle powers are loaded before the first pass.
 template <int N, int T, int R0, int R1, int R2, bool INV, class Ld, class St, class Sync>
 __device__ __forceinline__ void group_fft(float2* xb, int t, const float2* __restrict__ tw, Ld& ld,
                                           St& st, Sync& sync) {
   static_assert(R0 * R1 * R2 == N, "radices must multiply to N");
+  PassTw<N, T, R0, 1> p0;
   if constexpr (R1 == 1) {
-    reg_pass<N, T, R0, 1, INV, true, true>(xb, t, tw, ld, st, sync);
+    reg_pass<N, T, R0, 1, INV, true, true>(xb, t, p0, ld, st, sync);
   } else if constexpr (R2 == 1) {
-    reg_pass<N, T, R0, 1, INV, true, false>(xb, t, tw, ld, st, sync);
-    reg_pass<N, T, R1, R0, INV, false, true>(xb, t, tw, ld, st, sync);
+    PassTw<N, T, R1, R0> p1;
+    p1.template load<INV>(t, tw);
+    reg_pass<N, T, R0, 1, INV, true, false>(xb, t, p0, ld, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, true>(xb, t, p1, ld, st, sync);
   } else {
-    reg_pass<N, T, R0, 1, INV, true, false>(xb, t, tw, ld, st, sync);
-    reg_pass<N, T, R1, R0, INV, false, false>(xb, t, tw, ld, st, sync);
-    reg_pass<N, T, R2, R0 * R1, INV, false, true>(xb, t, tw, ld, st, sync);
+    PassTw<N, T, R1, R0> p1;
+    PassTw<N, T, R2, R0 * R1> p2;
+    p1.template load<INV>(t, tw);
+    p2.template load<INV>(t, tw);
+    reg_pass<N, T, R0, 1, INV, true, false>(xb, t, p0, ld, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, false>(xb, t, p1, ld, st, sync);
+    reg_pass<N, T, R2, R0 * R1, INV, false, true>(xb, t, p2, ld, st, sync);
   }
 }
 
@@ -178,15 +208,22 @@ __device__ __forceinline__ void group_fft_xb(float2* xb, int t, const float2* __
                                              St& st, Sync& sync) {
   static_assert(R0 * R1 * R2 == N, "radices must multiply to N");
   auto none = [](int, int, int) { return make_float2(0.f, 0.f); };
+  PassTw<N, T, R0, 1> p0;
   if constexpr (R1 == 1) {
-    reg_pass<N, T, R0, 1, INV, false, true>(xb, t, tw, none, st, sync);
+    reg_pass<N, T, R0, 1, INV, false, true>(xb, t, p0, none, st, sync);
   } else if constexpr (R2 == 1) {
-    reg_pass<N, T, R0, 1, INV, false, false>(xb, t, tw, none, st, sync);
-    reg_pass<N, T, R1, R0, INV, false, true>(xb, t, tw, none, st, sync);
+    PassTw<N, T, R1, R0> p1;
+    p1.template load<INV>(t, tw);
+    reg_pass<N, T, R0, 1, INV, false, false>(xb, t, p0, none, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, true>(xb, t, p1, none, st, sync);
   } else {
-    reg_pass<N, T, R0, 1, INV, false, false>(xb, t, tw, none, st, sync);
-    reg_pass<N, T, R1, R0, INV, false, false>(xb, t, tw, none, st, sync);
-    reg_pass<N, T, R2, R0 * R1, INV, false, true>(xb, t, tw, none, st, sync);
+    PassTw<N, T, R1, R0> p1;
+    PassTw<N, T, R2, R0 * R1> p2;
+    p1.template load<INV>(t, tw);
+    p2.template load<INV>(t, tw);
+    reg_pass<N, T, R0, 1, INV, false, false>(xb, t, p0, none, st, sync);
+    reg_pass<N, T, R1, R0, INV, false, false>(xb, t, p1, none, st, sync);
+    reg_pass<N, T, R2, R0 * R1, INV, false, true>(xb, t, p2, none, st, sync);
   }
 }
 
