@@ -461,27 +461,21 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   const int s = blockIdx.y, img = blockIdx.z;
   const int c0 = blockIdx.x * COLS;
   const int tid = threadIdx.x;
+  // The CTA's spectrum tile (H rows x COLS columns) is loaded into registers first, all
+  // loads in flight together; their latency hides behind the set-up below.
+  const float2* F = spec + (size_t)img * H * W;
+  static_assert((H * COLS) % NT == 0, "fill tile");
+  constexpr int NF = H * COLS / NT;
+  float2 fx[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const int i = tid + k * NT;
+    const int v = i / COLS, c = i % COLS, u = c0 + c;
+    fx[k] = (u < W) ? __ldg(F + (size_t)v * W + u) : make_float2(0.f, 0.f);
+  }
   for (int i = tid; i < NO * COLS; i += NT) {
     const int o = i / COLS, c = i % COLS;
     zcs[o][c] = (c0 + c < W) ? zc[o * W + c0 + c] : 1;
-  }
-  const float2* F = spec + (size_t)img * H * W;
-  const float log_fs = kp.log_fs[s];
-  const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
-  static_assert((H * COLS) % NT == 0, "fill tile");
-  // unrolled so that several spectrum loads are in flight per thread
-#pragma unroll 8
-  for (int k = 0; k < H * COLS / NT; ++k) {
-    const int i = tid + k * NT;
-    const int v = i / COLS, c = i % COLS, u = c0 + c;
-    float2 f = make_float2(0.f, 0.f);
-    if (u < W) {
-      const float fu = fftfreq(u, W), fv = fftfreq(v, H);
-      const float rs = lg_radial(fu * fu + fv * fv, log_fs, kp) * inv_hw;
-      const float2 x = __ldg(F + (size_t)v * W + u);
-      f = make_float2(x.x * rs, x.y * rs);
-    }
-    base[c * XS + xpad(v)] = f;
   }
   const int col = tid / T, t = tid % T;
   const int u = c0 + col;
@@ -498,6 +492,21 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   // fftfreq(t + T r, H) as t / H plus a constant per r (exact: H is a power of two and
   // t + T r < H / 2 exactly when r < E / 2)
   const float fv0 = (float)t * (1.f / H);
+  // F * R_s * 1/(HW) into shared memory
+  const float log_fs = kp.log_fs[s];
+  const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const int i = tid + k * NT;
+    const int v = i / COLS, c = i % COLS, uu = c0 + c;
+    float2 f = make_float2(0.f, 0.f);
+    if (uu < W) {
+      const float fuu = fftfreq(uu, W), fv = fftfreq(v, H);
+      const float rs = lg_radial(fuu * fuu + fv * fv, log_fs, kp) * inv_hw;
+      f = make_float2(fx[k].x * rs, fx[k].y * rs);
+    }
+    base[c * XS + xpad(v)] = f;
+  }
   __syncthreads();
   auto sync = [] {
     if constexpr (T <= 32) __syncwarp();
