@@ -3,12 +3,14 @@
 // and a second descriptor when the second-highest bin is within the dominant ratio of
 // the peak).
 //
-//   desc_hist  : one warp per keypoint.  The 96x96 MIM patch (rows y-48..y+47, columns
-//                x-48..x+47) is staged into shared memory by a TMA tensor copy whose x
-//                start is rounded down to 16 bytes (a 112-byte wide box); each lane
-//                counts 16-byte cell rows with byte-wise compares (__vcmpeq4 + popc) and
-//                the cell totals are reduced over the 16 lanes of a half-warp.  Writes the
-//                unrecoded cell counts, s, s2 and the second-descriptor flag.
+//   desc_hist  : each warp takes several keypoints.  The 96x96 MIM patch (rows
+//                y-48..y+47, columns x-48..x+47) is staged into shared memory in two
+//                halves by TMA tensor copies whose x start is rounded down to 16 bytes
+//                (112 x 48 boxes), the next half in flight while the current one is
+//                counted; each lane counts a 16-pixel cell row through three bit planes
+//                and popc, and the cell totals are reduced over the 16 lanes of a
+//                half-warp.  Writes the unrecoded cell counts, s, s2 and the
+//                second-descriptor flag.
 //   desc_scan  : one CTA per image: exclusive scan of descriptors per keypoint (1 or 2;
 //                for RIFT's baseline modes 1 from the unshifted MIM, or the No members of
 //                the convolution-sequence ring, §II-C).
@@ -19,8 +21,11 @@
 namespace rift2 {
 
 constexpr int BOX_W = PATCH + 16;                 // 112 bytes: x start rounded down to 16
-constexpr int WARP_BUF = BOX_W * PATCH + 128;     // + slack for the 4-byte realignment reads
+constexpr int HALF_ROWS = PATCH / 2;              // one job stages half a patch (3 cell rows)
+constexpr int HBUF = (BOX_W * HALF_ROWS + 128 + 127) / 128 * 128;   // + slack for the
+                                                                    // 4-byte realignment reads
 constexpr int DH_WARPS = 8;
+constexpr int DH_KPW = 4;                         // keypoints per warp
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -40,102 +45,130 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long lon
   return false;
 }
 
+// Each warp takes the keypoints gw, gw + stride, ... of its image (gw its global warp
+// index).  Every keypoint is two jobs, the upper and lower half of its patch; a job's
+// 112 x 48 box is staged while the previous job is counted (two buffers per warp).
 __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant__ CUtensorMap tmap,
                                                            int H, int W, KParams kp,
                                                            DescribeWs ws, FeatPtrs fp) {
-  // [DH_WARPS patch buffers][DH_WARPS mbarriers]; no static shared memory, so the dynamic
-  // block starts at the (16-byte aligned) base the TMA destination needs.
+  // [DH_WARPS][2 half-patch buffers][DH_WARPS][2 mbarriers]; no static shared memory, so
+  // the dynamic block starts at the (16-byte aligned) base the TMA destination needs.
   extern __shared__ __align__(128) unsigned char dsm[];
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(dsm + DH_WARPS * WARP_BUF);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(dsm + DH_WARPS * 2 * HBUF);
   const int img = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * DH_WARPS + warp;
   const int nkp = fp.counts[img][0];
-  if (k >= nkp) return;   // warp-uniform
-  const int x = fp.kp_xy[img][2 * k], y = fp.kp_xy[img][2 * k + 1];
-  const int px = x - HALF_PATCH;          // first patch column
-  const int x0 = px & ~15;                // TMA x start: 16-byte aligned (u8 elements)
-  const int sh = px - x0;
-  unsigned char* buf = dsm + warp * WARP_BUF;
-  const unsigned bar = smem_u32(&bars[warp]);
+  const int gw = blockIdx.x * DH_WARPS + warp, gstride = gridDim.x * DH_WARPS;
+  if (gw >= nkp) return;   // warp-uniform
+  const int njobs = 2 * ((nkp - gw + gstride - 1) / gstride);
+  unsigned char* buf0 = dsm + warp * 2 * HBUF;
+  const unsigned bar0 = smem_u32(&bars[2 * warp]);
+  const int* kxy = fp.kp_xy[img];
   if (lane == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncwarp();
-  if (lane == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(BOX_W * PATCH)
+  // lane 0: stage job q into buffer q & 1 (its previous contents were read before the
+  // warp's last __syncwarp; the proxy fence orders those reads before the async write)
+  auto issue = [&](int q) {
+    const int k = gw + (q >> 1) * gstride;
+    const int x = kxy[2 * k], y = kxy[2 * k + 1];
+    const unsigned b = bar0 + 8 * (q & 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                 "r"(BOX_W * HALF_ROWS)
                  : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(buf)),
-        "l"(&tmap), "r"(x0), "r"(y - HALF_PATCH), "r"(img), "r"(bar)
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(buf0 + (q & 1) * HBUF)),
+        "l"(&tmap), "r"((x - HALF_PATCH) & ~15), "r"(y - HALF_PATCH + (q & 1) * HALF_ROWS),
+        "r"(img), "r"(b)
         : "memory");
-  }
-  if (!mbar_wait(bar, 0, 1ll << 24)) {
-    if (lane == 0) atomicExch(ws.status, ST_TIMEOUT);
-    mbar_wait(bar, 0, 1ll << 24);   // the copy may still land: give it a bounded chance
-    return;
-  }
+  };
+  if (lane == 0) issue(0);
   const int rho = lane & 15, half = lane >> 4;
-  unsigned whole[NO] = {0, 0, 0, 0, 0, 0};
-  unsigned short* raw = ws.raw + ((size_t)img * kp.max_kp + k) * DESC_DIM;
-#pragma unroll 2
-  for (int m = 0; m < CELLS * CELLS / 2; ++m) {
-    const int c = 2 * m + half;
-    const int ci = c / CELLS, cj = c % CELLS;
-    const int s0 = (ci * CELL + rho) * BOX_W + sh + cj * CELL;
-    const unsigned* wp = reinterpret_cast<const unsigned*>(buf + (s0 & ~3));
-    const int a8 = (s0 & 3) * 8;
-    unsigned w[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) w[i] = wp[i];
-    // bins 0..No-2 by byte-wise compares; the last bin is what remains of the 16 pixels
-    // (MIM values are 0..No-1)
-    unsigned cnt[NO] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      unsigned v = __funnelshift_r(w[i], w[i + 1], a8);
-#pragma unroll
-      for (int b = 0; b < NO - 1; ++b) cnt[b] += __popc(__vcmpeq4(v, 0x01010101u * b));
+  unsigned wsum[3] = {0, 0, 0};   // whole-patch bins as u16 pairs (each total <= 9216)
+  for (int q = 0; q < njobs; ++q) {
+    if (lane == 0 && q + 1 < njobs) issue(q + 1);
+    const int k = gw + (q >> 1) * gstride, hh = q & 1;
+    const int px = kxy[2 * k] - HALF_PATCH;
+    const int sh = px - (px & ~15);
+    if (!mbar_wait(bar0 + 8 * (q & 1), (q >> 1) & 1, 1ll << 24)) {
+      if (lane == 0) atomicExch(ws.status, ST_TIMEOUT);
+      // the copies in flight may still land: give them a bounded chance before exiting
+      mbar_wait(bar0 + 8 * (q & 1), (q >> 1) & 1, 1ll << 24);
+      if (q + 1 < njobs) mbar_wait(bar0 + 8 * ((q + 1) & 1), ((q + 1) >> 1) & 1, 1ll << 24);
+      return;
     }
-    unsigned rest = 16;
+    const unsigned char* buf = buf0 + (q & 1) * HBUF;
+    unsigned short* raw = ws.raw + ((size_t)img * kp.max_kp + k) * DESC_DIM;
+#pragma unroll 3
+    for (int m = 0; m < CELLS * CELLS / 4; ++m) {
+      const int cl = 2 * m + half;                 // cell within this half: 3 rows of 6
+      const int ci = cl / CELLS, cj = cl % CELLS;
+      const int c = hh * (CELLS * CELLS / 2) + cl;
+      const int s0 = (ci * CELL + rho) * BOX_W + sh + cj * CELL;
+      const unsigned* wp = reinterpret_cast<const unsigned*>(buf + (s0 & ~3));
+      const int a8 = (s0 & 3) * 8;
+      unsigned w[5];
 #pragma unroll
-    for (int b = 0; b < NO - 1; ++b) {
-      cnt[b] >>= 3;   // 8 bits per matching byte
-      rest -= cnt[b];
+      for (int i = 0; i < 5; ++i) w[i] = wp[i];
+      // bit planes of the 16 pixels (MIM values 0..5 need three bits): bit i of byte j of
+      // plane k is bit k of pixel 4i + j; a bin count is one 3-input logic op and a popc
+      // (values 6 and 7 never occur, so 5 = b2 b0 and 4 = b2 !b0)
+      static_assert(NO == 6, "bit-plane counting covers the values 0..5");
+      unsigned p0b = 0, p1b = 0, p2b = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned v = __funnelshift_r(w[i], w[i + 1], a8);
+        p0b |= (v & 0x01010101u) << i;
+        p1b |= ((v >> 1) & 0x01010101u) << i;
+        p2b |= ((v >> 2) & 0x01010101u) << i;
+      }
+      unsigned cnt[NO];
+      cnt[5] = __popc(p2b & p0b);
+      cnt[4] = __popc(p2b & ~p0b);
+      cnt[3] = __popc(~p2b & p1b & p0b);
+      cnt[2] = __popc(~p2b & p1b & ~p0b);
+      cnt[1] = __popc(~p2b & ~p1b & p0b);
+      cnt[0] = 16u - cnt[1] - cnt[2] - cnt[3] - cnt[4] - cnt[5];
+      // pack two bins per word (cell totals <= 256)
+      unsigned p0 = cnt[0] | (cnt[1] << 16);
+      unsigned p1 = cnt[2] | (cnt[3] << 16);
+      unsigned p2 = cnt[4] | (cnt[5] << 16);
+#pragma unroll
+      for (int d = 1; d < 16; d <<= 1) {
+        p0 += __shfl_xor_sync(0xffffffffu, p0, d);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, d);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, d);
+      }
+      // p0, p1, p2 are the cell's bins (0,1), (2,3), (4,5) as u16 pairs: the raw layout
+      wsum[0] += p0;
+      wsum[1] += p1;
+      wsum[2] += p2;
+      if (rho < 3)
+        reinterpret_cast<unsigned*>(raw + c * NO)[rho] = (rho == 0) ? p0 : (rho == 1) ? p1 : p2;
     }
-    cnt[NO - 1] = rest;
-    // pack two bins per word (cell totals <= 256)
-    unsigned p0 = cnt[0] | (cnt[1] << 16);
-    unsigned p1 = cnt[2] | (cnt[3] << 16);
-    unsigned p2 = cnt[4] | (cnt[5] << 16);
+    if (hh == 1) {
 #pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-      p0 += __shfl_xor_sync(0xffffffffu, p0, d);
-      p1 += __shfl_xor_sync(0xffffffffu, p1, d);
-      p2 += __shfl_xor_sync(0xffffffffu, p2, d);
+      for (int i = 0; i < 3; ++i) wsum[i] += __shfl_xor_sync(0xffffffffu, wsum[i], 16);
+      const unsigned whole[NO] = {wsum[0] & 0xFFFFu, wsum[0] >> 16, wsum[1] & 0xFFFFu,
+                                  wsum[1] >> 16, wsum[2] & 0xFFFFu, wsum[2] >> 16};
+      if (lane == 0) {
+        int s = 0;
+        for (int b = 1; b < NO; ++b)
+          if (whole[b] > whole[s]) s = b;
+        int s2 = (s == 0) ? 1 : 0;
+        for (int b = 0; b < NO; ++b)
+          if (b != s && whole[b] > whole[s2]) s2 = b;
+        unsigned has2 = (1000u * whole[s2] >= (unsigned)kp.ratio_pm * whole[s]) ? 1u : 0u;
+        ws.info[(size_t)img * kp.max_kp + k] = (unsigned)s | ((unsigned)s2 << 4) | (has2 << 8);
+      }
+      wsum[0] = wsum[1] = wsum[2] = 0;
     }
-    unsigned tot[NO] = {p0 & 0xFFFFu, p0 >> 16, p1 & 0xFFFFu, p1 >> 16, p2 & 0xFFFFu, p2 >> 16};
-#pragma unroll
-    for (int b = 0; b < NO; ++b) {
-      whole[b] += tot[b];
-      if (rho == b) raw[c * NO + b] = (unsigned short)tot[b];
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < NO; ++b) whole[b] += __shfl_xor_sync(0xffffffffu, whole[b], 16);
-  if (lane == 0) {
-    int s = 0;
-    for (int b = 1; b < NO; ++b)
-      if (whole[b] > whole[s]) s = b;
-    int s2 = (s == 0) ? 1 : 0;
-    for (int b = 0; b < NO; ++b)
-      if (b != s && whole[b] > whole[s2]) s2 = b;
-    unsigned has2 = (1000u * whole[s2] >= (unsigned)kp.ratio_pm * whole[s]) ? 1u : 0u;
-    ws.info[(size_t)img * kp.max_kp + k] = (unsigned)s | ((unsigned)s2 << 4) | (has2 << 8);
+    __syncwarp();   // every lane's reads of this buffer precede its next staging
   }
 }
 
@@ -227,12 +260,14 @@ __global__ void __launch_bounds__(256) desc_write(KParams kp, DescribeWs ws, Fea
   if (lane < nd) fp.desc_norm[img][off + lane] = sqrtf((float)n2);   // exact: n2 < 2^24
 }
 
+int describe_box_rows() { return HALF_ROWS; }
+
 cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
                             const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
                             cudaStream_t st) {
-  size_t sm = (size_t)DH_WARPS * WARP_BUF + DH_WARPS * sizeof(unsigned long long);
+  size_t sm = (size_t)DH_WARPS * 2 * HBUF + DH_WARPS * 2 * sizeof(unsigned long long);
   cudaFuncSetAttribute(desc_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int blocks = (kp.max_kp + DH_WARPS - 1) / DH_WARPS;
+  int blocks = (kp.max_kp + DH_WARPS * DH_KPW - 1) / (DH_WARPS * DH_KPW);
   desc_hist<<<dim3(blocks, nimg), DH_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
   desc_scan<<<nimg, 1024, 0, st>>>(kp, ws, fp);
   desc_write<<<dim3((kp.max_kp + 7) / 8, nimg), 256, 0, st>>>(kp, ws, fp);

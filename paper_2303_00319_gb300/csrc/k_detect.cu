@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   __shared__ unsigned hist[256];
   __shared__ unsigned s_sel[4];
   const int img = blockIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
   const unsigned long long* cand = ws.cand + (size_t)img * ws.cap_cand;
   unsigned n = ws.cand_count[img];
   if (n > (unsigned)ws.cap_cand) n = ws.cap_cand;
@@ -149,10 +150,17 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
     while (true) {
       for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
       __syncthreads();
-      for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-        unsigned long long k = cand[i];
-        if (pbits == 0 || (k >> (64 - pbits)) == prefix)
-          atomicAdd(&hist[(unsigned)(k >> (56 - pbits)) & 0xFFu], 1u);
+      // warp-aggregated: most keys share the leading digits, so lanes with equal digits
+      // add their count with one atomic
+      for (unsigned b0 = threadIdx.x & ~31u; b0 < n; b0 += blockDim.x) {
+        const unsigned i = b0 + lane;
+        unsigned dig = 256u;   // not counted
+        if (i < n) {
+          const unsigned long long k = cand[i];
+          if (pbits == 0 || (k >> (64 - pbits)) == prefix) dig = (unsigned)(k >> (56 - pbits)) & 0xFFu;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        if (dig < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], (unsigned)__popc(peers));
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -182,10 +190,20 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   if (threadIdx.x == 0) s_sel[3] = 0;
   for (int i = threadIdx.x; i < nsort; i += blockDim.x) keys[i] = ~0ull;
   __syncthreads();
-  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-    unsigned long long k = cand[i];
-    if (pbits == 0 || (k >> (64 - pbits)) <= prefix) {
-      unsigned pos = atomicAdd(&s_sel[3], 1u);
+  for (unsigned b0 = threadIdx.x & ~31u; b0 < n; b0 += blockDim.x) {
+    const unsigned i = b0 + lane;
+    unsigned long long k = 0;
+    bool take = false;
+    if (i < n) {
+      k = cand[i];
+      take = pbits == 0 || (k >> (64 - pbits)) <= prefix;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    unsigned base = 0;
+    if (lane == 0 && bal) base = atomicAdd(&s_sel[3], (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) {
+      const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
       if (pos < (unsigned)nsort) keys[pos] = k;
     }
   }

@@ -71,6 +71,7 @@ struct DescribeWs {
   int* off;              // [nimg][max_kp]
   int* status;           // device status word
 };
+int describe_box_rows();   // rows of the MIM tensor map's box (k_describe.cu)
 cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
                             const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
                             cudaStream_t st);

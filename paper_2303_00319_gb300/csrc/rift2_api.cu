@@ -260,7 +260,7 @@ T* at(void* base, size_t off) {
 int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int g, int H, int pitch) {
   cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)H, (cuuint64_t)g};
   cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * H};
-  cuuint32_t box[3] = {RIFT2_PATCH + 16, RIFT2_PATCH, 1};
+  cuuint32_t box[3] = {RIFT2_PATCH + 16, (cuuint32_t)describe_box_rows(), 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, mim, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
