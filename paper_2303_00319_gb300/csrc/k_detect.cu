@@ -21,10 +21,19 @@ constexpr int VS = FT + 2;      // score map side (1-pixel halo)
 __constant__ int c_circle_dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
 __constant__ int c_circle_dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
 
+// A run of >= arc cyclically contiguous set bits in the 16-bit circle mask (1 <= arc <= 16).
+// acc holds the AND of r >> 0 .. h-1 (bit i set: bits i .. i+h-1 of r all set); doubling h
+// and one final shift by arc - h (<= h) extend it to arc.
 __device__ __forceinline__ bool has_arc(unsigned m16, int arc) {
-  unsigned r = m16 | (m16 << 16);   // cyclic: any run of length <= 16 appears linearly
+  if (__popc(m16) < arc) return false;
+  const unsigned r = m16 | (m16 << 16);   // cyclic: any run of length <= 16 appears linearly
   unsigned acc = r;
-  for (int k = 1; k < arc; ++k) acc &= (r >> k);
+  int h = 1;
+  while (2 * h <= arc) {
+    acc &= acc >> h;
+    h *= 2;
+  }
+  if (h < arc) acc &= acc >> (arc - h);
   return acc != 0;
 }
 
@@ -126,6 +135,60 @@ __device__ void bitonic_sort(unsigned long long* s, int n) {
   }
 }
 
+// The same sort for n = 1024 E keys in shared memory with 1024 threads: warp w owns
+// positions w 32E .. +32E-1, lane l the positions w 32E + l + 32 e (e < E).  Compare-exchange
+// distances j < 32 run as lane shuffles, 32 <= j < 32E inside a thread's registers, and only
+// j >= 32E through shared memory (15 block-wide barriers instead of 91 for n = 8192).
+template <int E>
+__device__ void bitonic_sort_reg(unsigned long long* s, int n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int base = warp * 32 * E + lane;
+  unsigned long long v[E];
+  for (int k = 2; k <= n; k <<= 1) {
+    int j = k >> 1;
+    for (; j >= 32 * E; j >>= 1) {   // partners in another warp
+      for (int p = threadIdx.x; p < (n >> 1); p += blockDim.x) {
+        const int i = 2 * j * (p / j) + (p % j);
+        const int l = i + j;
+        const unsigned long long a = s[i], b = s[l];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) { s[i] = b; s[l] = a; }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = s[base + 32 * e];
+    for (; j > 0; j >>= 1) {
+      if (j >= 32) {   // partner e ^ (j / 32) in this thread (static register indices)
+#pragma unroll
+        for (int sb = 1; sb < E; sb <<= 1) {
+          if ((j >> 5) == sb) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              if ((e & sb) == 0) {
+                const bool up = ((base + 32 * e) & k) == 0;
+                const unsigned long long a = v[e], b = v[e | sb];
+                if ((a > b) == up) { v[e] = b; v[e | sb] = a; }
+              }
+            }
+          }
+        }
+      } else {         // partner lane ^ j
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int pos = base + 32 * e;
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[e], j);
+          const bool keep_min = ((pos & j) == 0) == ((pos & k) == 0);
+          v[e] = keep_min ? (v[e] < o ? v[e] : o) : (v[e] > o ? v[e] : o);
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) s[base + 32 * e] = v[e];
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws, FeatPtrs fp) {
   extern __shared__ unsigned long long skeys[];
   __shared__ unsigned hist[256];
@@ -208,7 +271,11 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
     }
   }
   __syncthreads();
-  bitonic_sort(keys, nsort);
+  // keys in shared memory with 2048 .. 8192 of them: the register / shuffle form
+  if (keys == skeys && nsort == 2048) bitonic_sort_reg<2>(keys, nsort);
+  else if (keys == skeys && nsort == 4096) bitonic_sort_reg<4>(keys, nsort);
+  else if (keys == skeys && nsort == 8192) bitonic_sort_reg<8>(keys, nsort);
+  else bitonic_sort(keys, nsort);
   unsigned nout = n < K ? n : K;
   int* xy = fp.kp_xy[img];
   float* sc = fp.kp_score[img];
