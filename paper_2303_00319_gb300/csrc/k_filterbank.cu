@@ -192,9 +192,21 @@ __global__ void __launch_bounds__(ColShape<HN>::NT) fwd_cols_reg(float2* __restr
   const int img = blockIdx.y;
   const int c0 = blockIdx.x * COLS;
   float2* base = spec + (size_t)img * HN * W;
-  for (int i = threadIdx.x; i < HN * COLS; i += NT) {
-    const int v = i / COLS, c = i % COLS;
-    sm[c * XS + xpad(v)] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
+  {
+    // the tile's loads all in flight together, then into the exchange buffers
+    constexpr int NF = HN * COLS / NT;
+    float2 fx[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const int i = threadIdx.x + k * NT;
+      const int v = i / COLS, c = i % COLS;
+      fx[k] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const int i = threadIdx.x + k * NT;
+      sm[(i % COLS) * XS + xpad(i / COLS)] = fx[k];
+    }
   }
   __syncthreads();
   const int col = threadIdx.x / T, t = threadIdx.x % T;
@@ -228,9 +240,17 @@ __global__ void __launch_bounds__(ColShape<HN>::NT) fwd_cols_reg(float2* __restr
   };
   group_fft_xb<HN, T, S::R0, S::R1, S::R2, false>(xb, t, twh, st, sync);
   __syncthreads();
-  for (int i = threadIdx.x; i < HN * COLS; i += NT) {
-    const int v = i / COLS, c = i % COLS;
-    if (c0 + c < W) base[(size_t)v * W + c0 + c] = sm[c * XS + xpad(v)];
+  {
+    // thread (row v0, column c) writes rows v0 + RSTEP k: a warp stores row segments
+    constexpr int RSTEP = NT / COLS;
+    const int c = threadIdx.x % COLS, v0 = threadIdx.x / COLS;
+    if (c0 + c < W) {
+#pragma unroll 8
+      for (int k = 0; k < HN / RSTEP; ++k) {
+        const int v = v0 + RSTEP * k;
+        base[(size_t)v * W + c0 + c] = sm[c * XS + xpad(v)];
+      }
+    }
   }
 }
 
