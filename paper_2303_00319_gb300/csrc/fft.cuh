@@ -5,7 +5,8 @@
 //     v_r = in[j + r n/R] * W_{ns R}^{k r},   v = DFT_R(v),
 //     out[(j / ns) ns R + k + r ns] = v_r,
 // and leaves the result in natural order after the last pass.  Twiddles come from one
-// table per length, tw[e] = exp(-2 pi i e / n), generated in double precision.
+// table per length, tw[e] = exp(-2 pi i e / n), generated in double precision; the odd
+// radices' own roots are compile-time constants.
 #pragma once
 
 #include "common.cuh"
@@ -73,31 +74,88 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[7] = csub(e[3], o3);
 }
 
-// Odd radix: direct R-point DFT with roots of unity read from the length-n table.
-template <int R, bool INV>
-__device__ __forceinline__ void dft_odd(float2* v, const float2* __restrict__ tw, int n) {
-  float2 out[R];
-  const int step = n / R;
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    float2 acc = v[0];
-#pragma unroll
-    for (int m = 1; m < R; ++m) {
-      float2 w = twiddle<INV>(tw, ((m * k) % R) * step);
-      acc = cadd(acc, cmul(v[m], w));
-    }
-    out[k] = acc;
-  }
-#pragma unroll
-  for (int k = 0; k < R; ++k) v[k] = out[k];
+// cos / sin (2 pi j / R) of the odd radices (written out to 10 significant digits).
+__device__ constexpr float kCos3[3] = {1.000000000e+00f, -5.000000000e-01f, -5.000000000e-01f};
+__device__ constexpr float kSin3[3] = {0.000000000e+00f, 8.660254038e-01f, -8.660254038e-01f};
+__device__ constexpr float kCos5[5] = {1.000000000e+00f, 3.090169944e-01f, -8.090169944e-01f, -8.090169944e-01f, 3.090169944e-01f};
+__device__ constexpr float kSin5[5] = {0.000000000e+00f, 9.510565163e-01f, 5.877852523e-01f, -5.877852523e-01f, -9.510565163e-01f};
+__device__ constexpr float kCos7[7] = {1.000000000e+00f, 6.234898019e-01f, -2.225209340e-01f, -9.009688679e-01f, -9.009688679e-01f, -2.225209340e-01f, 6.234898019e-01f};
+__device__ constexpr float kSin7[7] = {0.000000000e+00f, 7.818314825e-01f, 9.749279122e-01f, 4.338837391e-01f, -4.338837391e-01f, -9.749279122e-01f, -7.818314825e-01f};
+__device__ constexpr float kCos11[11] = {1.000000000e+00f, 8.412535328e-01f, 4.154150130e-01f, -1.423148383e-01f, -6.548607339e-01f, -9.594929736e-01f, -9.594929736e-01f, -6.548607339e-01f, -1.423148383e-01f, 4.154150130e-01f, 8.412535328e-01f};
+__device__ constexpr float kSin11[11] = {0.000000000e+00f, 5.406408175e-01f, 9.096319954e-01f, 9.898214419e-01f, 7.557495744e-01f, 2.817325568e-01f, -2.817325568e-01f, -7.557495744e-01f, -9.898214419e-01f, -9.096319954e-01f, -5.406408175e-01f};
+__device__ constexpr float kCos13[13] = {1.000000000e+00f, 8.854560257e-01f, 5.680647467e-01f, 1.205366803e-01f, -3.546048870e-01f, -7.485107482e-01f, -9.709418174e-01f, -9.709418174e-01f, -7.485107482e-01f, -3.546048870e-01f, 1.205366803e-01f, 5.680647467e-01f, 8.854560257e-01f};
+__device__ constexpr float kSin13[13] = {0.000000000e+00f, 4.647231720e-01f, 8.229838659e-01f, 9.927088741e-01f, 9.350162427e-01f, 6.631226582e-01f, 2.393156643e-01f, -2.393156643e-01f, -6.631226582e-01f, -9.350162427e-01f, -9.927088741e-01f, -8.229838659e-01f, -4.647231720e-01f};
+template <int R>
+__device__ __forceinline__ float odd_cos(int j) {
+  if constexpr (R == 3) return kCos3[j];
+  else if constexpr (R == 5) return kCos5[j];
+  else if constexpr (R == 7) return kCos7[j];
+  else if constexpr (R == 11) return kCos11[j];
+  else return kCos13[j];
+}
+template <int R>
+__device__ __forceinline__ float odd_sin(int j) {
+  if constexpr (R == 3) return kSin3[j];
+  else if constexpr (R == 5) return kSin5[j];
+  else if constexpr (R == 7) return kSin7[j];
+  else if constexpr (R == 11) return kSin11[j];
+  else return kSin13[j];
 }
 
+// Odd radix R: with a_m = x_m + x_{R-m}, b_m = x_m - x_{R-m} (m = 1 .. (R-1)/2),
+//     X_0 = x_0 + sum a_m,   C_k = x_0 + sum a_m cos(2 pi m k / R),   S_k = sum b_m sin(..),
+//     X_k = C_k -+ i S_k,  X_{R-k} = C_k +- i S_k   (upper signs forward, lower inverse),
+// about a third of the direct form's multiplications; the roots fold into constants.
 template <int R, bool INV>
-__device__ __forceinline__ void dft_r(float2* v, const float2* __restrict__ tw, int n) {
+__device__ __forceinline__ void dft_odd(float2* v) {
+  constexpr int h = (R - 1) / 2;
+  const float2 x0 = v[0];
+  float2 a[h + 1], b[h + 1];
+  float2 sum = x0;
+#pragma unroll
+  for (int m = 1; m <= h; ++m) {
+    a[m] = cadd(v[m], v[R - m]);
+    b[m] = csub(v[m], v[R - m]);
+    sum = cadd(sum, a[m]);
+  }
+#pragma unroll
+  for (int k = 1; k <= h; ++k) {
+    float2 c = x0, sn = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 1; m <= h; ++m) {
+      const int e = (m * k) % R;
+      c.x = fmaf(a[m].x, odd_cos<R>(e), c.x);
+      c.y = fmaf(a[m].y, odd_cos<R>(e), c.y);
+      sn.x = fmaf(b[m].x, odd_sin<R>(e), sn.x);
+      sn.y = fmaf(b[m].y, odd_sin<R>(e), sn.y);
+    }
+    const float2 minus_is = make_float2(c.x + sn.y, c.y - sn.x);   // C - i S
+    const float2 plus_is = make_float2(c.x - sn.y, c.y + sn.x);    // C + i S
+    v[k] = INV ? plus_is : minus_is;
+    v[R - k] = INV ? minus_is : plus_is;
+  }
+  v[0] = sum;
+}
+
+// Unsigned division by a run-time divisor d >= 1 for dividends below 2^31: the
+// multiply-shift method (Granlund and Montgomery), q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  unsigned m, s, d;
+  __host__ __device__ explicit FastDiv(unsigned dv) : d(dv) {
+    s = 0;
+    while ((1u << s) < dv) ++s;
+    m = (unsigned)(((1ull << 32) * ((1ull << s) - dv)) / dv + 1);
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> s; }
+};
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2* v) {
   if constexpr (R == 2) dft2<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
   else if constexpr (R == 8) dft8<INV>(v);
-  else dft_odd<R, INV>(v, tw, n);
+  else dft_odd<R, INV>(v);
 }
 
 // One Stockham pass over nb transforms; element k of transform b at buf[b*bs + k*ks].
@@ -110,20 +168,40 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* 
   const int m = n / R;
   const int tstep = n / (ns * R);
   const int total = nb * m;
+  const FastDiv dnb((unsigned)nb), dm((unsigned)m), dns((unsigned)ns);
   for (int idx = tid; idx < total; idx += nthr) {
     int b, j;
-    if (BFAST) { j = idx / nb; b = idx - j * nb; }
-    else       { b = idx / m;  j = idx - b * m; }
-    const int k = j % ns;
+    if (BFAST) { j = (int)dnb.div((unsigned)idx); b = idx - j * nb; }
+    else       { b = (int)dm.div((unsigned)idx); j = idx - b * m; }
+    const int k = j - (int)dns.div((unsigned)j) * ns;
     const float2* src = in + b * bs;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * ks];
     if (ns > 1) {
+      if constexpr ((R & (R - 1)) == 0) {
+        // powers of two: the table gives W^(k 2^q tstep); other r are products of those
+        float2 wp[3];
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(tw, k * r * tstep));
+        for (int q = 0; (1 << q) < R; ++q) wp[q] = twiddle<INV>(tw, k * (1 << q) * tstep);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = make_float2(1.f, 0.f);
+          bool first = true;
+#pragma unroll
+          for (int q = 0; (1 << q) < R; ++q)
+            if (r & (1 << q)) {
+              w = first ? wp[q] : cmul(w, wp[q]);
+              first = false;
+            }
+          v[r] = cmul(v[r], w);
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(tw, k * r * tstep));
+      }
     }
-    dft_r<R, INV>(v, tw, n);
+    dft_r<R, INV>(v);
     float2* dst = out + b * bs;
     const int base = (j - k) * R + k;
 #pragma unroll

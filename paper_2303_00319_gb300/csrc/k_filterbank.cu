@@ -59,22 +59,23 @@ __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restr
   float2* b = sm + nel;
   const float* src = dense ? dense + (size_t)img * H * W : ip.img[img];
   const long long pitch = dense ? W : ip.pitch[img];
+  const FastDiv dW((unsigned)W);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    int r = r0 + i / W, x = i % W;
+    const int rr = (int)dW.div((unsigned)i), x = i - rr * W, r = r0 + rr;
     float v = (r < H) ? __ldg(src + (size_t)r * pitch + x) : 0.f;
     a[i] = make_float2(v, 0.f);
   }
   __syncthreads();
   seg_means(a, tr, W, 1, W, mean);
   __syncthreads();
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) a[i].x -= mean[i / W].x;
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) a[i].x -= mean[dW.div((unsigned)i)].x;
   __syncthreads();
   float2* res = fft_smem<false, false>(a, b, pw, tr, W, 1);
   float2* dst = spec + (size_t)img * H * W;
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    int r = r0 + i / W, x = i % W;
+    const int rr = (int)dW.div((unsigned)i), x = i - rr * W, r = r0 + rr;
     float2 v = res[i];
-    if (x == 0) v.x += mean[i / W].x * W;
+    if (x == 0) v.x += mean[rr].x * W;
     if (r < H) dst[(size_t)r * W + x] = v;
   }
 }
@@ -90,22 +91,23 @@ __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H
   float2* a = sm;
   float2* b = sm + nel;
   float2* base = spec + (size_t)img * H * W;
+  const FastDiv dtc((unsigned)tc);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    int v = i / tc, c = i % tc;
+    const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
     a[i] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   seg_means(a, tc, H, tc, 1, mean);
   __syncthreads();
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    float2 m = mean[i % tc];
+    float2 m = mean[i - (int)dtc.div((unsigned)i) * tc];
     a[i].x -= m.x;
     a[i].y -= m.y;
   }
   __syncthreads();
   float2* res = fft_smem<false, true>(a, b, ph, tc, 1, tc);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    int v = i / tc, c = i % tc;
+    const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
     float2 r = res[i];
     if (v == 0) {
       r.x += mean[c].x * H;
@@ -324,16 +326,22 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
   float2* base = sm;
   float2* a = sm + nel;
   float2* b = sm + 2 * nel;
+  float* fvt = reinterpret_cast<float*>(sm + 3 * nel);   // fftfreq(v, H) per row
+  __shared__ float fut[16];                               // fftfreq(u, W) per column
   const float2* F = spec + (size_t)img * H * W;
   const float log_fs = kp.log_fs[s];
   const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
+  const FastDiv dtc((unsigned)tc);
+  for (int v = threadIdx.x; v < H; v += blockDim.x) fvt[v] = fftfreq(v, H);
+  if (threadIdx.x < tc) fut[threadIdx.x] = fftfreq(c0 + threadIdx.x, W);
+  __syncthreads();
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    int v = i / tc, c = i % tc, u = c0 + c;
+    const int v = (int)dtc.div((unsigned)i), c = i - v * tc, u = c0 + c;
     float2 f = make_float2(0.f, 0.f);
     if (u < W) {
-      float fu = fftfreq(u, W), fv = fftfreq(v, H);
-      float rs = lg_radial(fu * fu + fv * fv, log_fs, kp) * inv_hw;
-      float2 x = __ldg(F + (size_t)v * W + u);
+      const float fu = fut[c], fv = fvt[v];
+      const float rs = lg_radial(fu * fu + fv * fv, log_fs, kp) * inv_hw;
+      const float2 x = __ldg(F + (size_t)v * W + u);
       f = make_float2(x.x * rs, x.y * rs);
     }
     base[i] = f;
@@ -342,10 +350,10 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
     __syncthreads();
     const float co = kp.cos_o[o], so = kp.sin_o[o];
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-      int v = i / tc, c = i % tc, u = c0 + c;
+      const int v = (int)dtc.div((unsigned)i), c = i - v * tc, u = c0 + c;
       float g = 0.f;
       if (u < W) {
-        const float fu = fftfreq(u, W), fv = fftfreq(v, H);
+        const float fu = fut[c], fv = fvt[v];
         g = lg_window(__fmul_rn(fu, co), fv, so, lg_rinv(fu, fv));
       }
       float2 x = base[i];
@@ -355,7 +363,7 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
     float2* res = fft_smem<true, true>(a, b, ph, tc, 1, tc);
     float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * H * W;
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-      int v = i / tc, c = i % tc;
+      const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
       if (c0 + c < W) dst[(size_t)v * W + c0 + c] = res[i];
     }
     // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
@@ -424,10 +432,10 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
   for (int k = 0; k < RR_MAXPIX; ++k) { best[k] = -1.f; besto[k] = 0; }
 
   for (int o = 0; o < NO; ++o) {
-    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-      int s = i / W, x = i - s * W;
-      a[i] = zc[o * W + x] ? make_float2(0.f, 0.f)
-                           : __ldg(scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W + x);
+    for (int s = 0; s < NS; ++s) {
+      const float2* src = scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W;
+      for (int x = threadIdx.x; x < W; x += blockDim.x)
+        a[s * W + x] = zc[o * W + x] ? make_float2(0.f, 0.f) : __ldg(src + x);
     }
     __syncthreads();
     float2* res = fft_smem<true, false>(a, b, pw, NS, W, 1);
@@ -761,7 +769,7 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H,
     default: break;
   }
   int tc = cols_tile(H);
-  size_t sm2 = 3 * (size_t)tc * H * sizeof(float2);
+  size_t sm2 = 3 * (size_t)tc * H * sizeof(float2) + (size_t)H * sizeof(float);
   cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   lg_cols_inverse<<<dim3((W + tc - 1) / tc, NS, nimg), 512, sm2, st>>>(spec, scratch, H, W, tc,
                                                                        ph, kp);
