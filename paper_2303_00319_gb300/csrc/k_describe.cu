@@ -16,6 +16,8 @@
 //                the convolution-sequence ring, §II-C).
 //   desc_write : one warp per keypoint: the recoded count vectors (a cyclic shift of the
 //                bins of every cell) and their L2 norms.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace rift2 {
@@ -104,52 +106,63 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
     }
     const unsigned char* buf = buf0 + (q & 1) * HBUF;
     unsigned short* raw = ws.raw + ((size_t)img * kp.max_kp + k) * DESC_DIM;
+    // A lane's 16 pixels start sh bytes into a 16-byte aligned 32-byte window, read with
+    // two 16-byte loads (the 112-byte row pitch puts a quarter-warp's loads on distinct
+    // banks); the window's words d .. d+4, d = sh / 4 (uniform over the warp), feed the
+    // byte realignment through a uniform switch so that every index is static.
+    const int a8 = (sh & 3) * 8;
+    auto count_cells = [&](auto dc) {
+      constexpr int d = decltype(dc)::value;
 #pragma unroll 3
-    for (int m = 0; m < CELLS * CELLS / 4; ++m) {
-      const int cl = 2 * m + half;                 // cell within this half: 3 rows of 6
-      const int ci = cl / CELLS, cj = cl % CELLS;
-      const int c = hh * (CELLS * CELLS / 2) + cl;
-      const int s0 = (ci * CELL + rho) * BOX_W + sh + cj * CELL;
-      const unsigned* wp = reinterpret_cast<const unsigned*>(buf + (s0 & ~3));
-      const int a8 = (s0 & 3) * 8;
-      unsigned w[5];
+      for (int m = 0; m < CELLS * CELLS / 4; ++m) {
+        const int cl = 2 * m + half;                 // cell within this half: 3 rows of 6
+        const int ci = cl / CELLS, cj = cl % CELLS;
+        const int c = hh * (CELLS * CELLS / 2) + cl;
+        const uint4* wp = reinterpret_cast<const uint4*>(buf + (ci * CELL + rho) * BOX_W + cj * CELL);
+        const uint4 lo = wp[0], hi = wp[1];
+        const unsigned qw[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        // bit planes of the 16 pixels (MIM values 0..5 need three bits): bit i of byte j of
+        // plane k is bit k of pixel 4i + j; a bin count is one 3-input logic op and a popc
+        // (values 6 and 7 never occur, so 5 = b2 b0 and 4 = b2 !b0)
+        static_assert(NO == 6, "bit-plane counting covers the values 0..5");
+        unsigned p0b = 0, p1b = 0, p2b = 0;
 #pragma unroll
-      for (int i = 0; i < 5; ++i) w[i] = wp[i];
-      // bit planes of the 16 pixels (MIM values 0..5 need three bits): bit i of byte j of
-      // plane k is bit k of pixel 4i + j; a bin count is one 3-input logic op and a popc
-      // (values 6 and 7 never occur, so 5 = b2 b0 and 4 = b2 !b0)
-      static_assert(NO == 6, "bit-plane counting covers the values 0..5");
-      unsigned p0b = 0, p1b = 0, p2b = 0;
+        for (int i = 0; i < 4; ++i) {
+          const unsigned v = __funnelshift_r(qw[d + i], qw[d + i + 1], a8);
+          p0b |= (v & 0x01010101u) << i;
+          p1b |= ((v >> 1) & 0x01010101u) << i;
+          p2b |= ((v >> 2) & 0x01010101u) << i;
+        }
+        unsigned cnt[NO];
+        cnt[5] = __popc(p2b & p0b);
+        cnt[4] = __popc(p2b & ~p0b);
+        cnt[3] = __popc(~p2b & p1b & p0b);
+        cnt[2] = __popc(~p2b & p1b & ~p0b);
+        cnt[1] = __popc(~p2b & ~p1b & p0b);
+        cnt[0] = 16u - cnt[1] - cnt[2] - cnt[3] - cnt[4] - cnt[5];
+        // pack two bins per word (cell totals <= 256)
+        unsigned p0 = cnt[0] | (cnt[1] << 16);
+        unsigned p1 = cnt[2] | (cnt[3] << 16);
+        unsigned p2 = cnt[4] | (cnt[5] << 16);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const unsigned v = __funnelshift_r(w[i], w[i + 1], a8);
-        p0b |= (v & 0x01010101u) << i;
-        p1b |= ((v >> 1) & 0x01010101u) << i;
-        p2b |= ((v >> 2) & 0x01010101u) << i;
+        for (int dd = 1; dd < 16; dd <<= 1) {
+          p0 += __shfl_xor_sync(0xffffffffu, p0, dd);
+          p1 += __shfl_xor_sync(0xffffffffu, p1, dd);
+          p2 += __shfl_xor_sync(0xffffffffu, p2, dd);
+        }
+        // p0, p1, p2 are the cell's bins (0,1), (2,3), (4,5) as u16 pairs: the raw layout
+        wsum[0] += p0;
+        wsum[1] += p1;
+        wsum[2] += p2;
+        if (rho < 3)
+          reinterpret_cast<unsigned*>(raw + c * NO)[rho] = (rho == 0) ? p0 : (rho == 1) ? p1 : p2;
       }
-      unsigned cnt[NO];
-      cnt[5] = __popc(p2b & p0b);
-      cnt[4] = __popc(p2b & ~p0b);
-      cnt[3] = __popc(~p2b & p1b & p0b);
-      cnt[2] = __popc(~p2b & p1b & ~p0b);
-      cnt[1] = __popc(~p2b & ~p1b & p0b);
-      cnt[0] = 16u - cnt[1] - cnt[2] - cnt[3] - cnt[4] - cnt[5];
-      // pack two bins per word (cell totals <= 256)
-      unsigned p0 = cnt[0] | (cnt[1] << 16);
-      unsigned p1 = cnt[2] | (cnt[3] << 16);
-      unsigned p2 = cnt[4] | (cnt[5] << 16);
-#pragma unroll
-      for (int d = 1; d < 16; d <<= 1) {
-        p0 += __shfl_xor_sync(0xffffffffu, p0, d);
-        p1 += __shfl_xor_sync(0xffffffffu, p1, d);
-        p2 += __shfl_xor_sync(0xffffffffu, p2, d);
-      }
-      // p0, p1, p2 are the cell's bins (0,1), (2,3), (4,5) as u16 pairs: the raw layout
-      wsum[0] += p0;
-      wsum[1] += p1;
-      wsum[2] += p2;
-      if (rho < 3)
-        reinterpret_cast<unsigned*>(raw + c * NO)[rho] = (rho == 0) ? p0 : (rho == 1) ? p1 : p2;
+    };
+    switch (sh >> 2) {
+      case 0: count_cells(std::integral_constant<int, 0>{}); break;
+      case 1: count_cells(std::integral_constant<int, 1>{}); break;
+      case 2: count_cells(std::integral_constant<int, 2>{}); break;
+      default: count_cells(std::integral_constant<int, 3>{}); break;
     }
     if (hh == 1) {
 #pragma unroll
