@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
       if (!zcs[o][c]) {
         const float2* srcb = xbuf + c * XS;
         float2* dstc = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W + c0 + c;
-#pragma unroll 8
+#pragma unroll 2
         for (int k = 0; k < H / RSTEP; ++k) {
           const int v = v0 + RSTEP * k;
           dstc[(size_t)v * W] = srcb[xpad(v)];
