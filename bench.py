@@ -279,9 +279,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     px_per_step = sum(2 * h * w for h, w in sizes)
 
-    def step(imgs):
-        ctx.extract([imgs[i] for i in range(2 * B)], feats, stream=stream)
-        ctx.match(feats[0::2], feats[1::2], matches, stream=stream)
+    def step(imgs, st=None):
+        st = stream if st is None else st
+        ctx.extract([imgs[i] for i in range(2 * B)], feats, stream=st)
+        ctx.match(feats[0::2], feats[1::2], matches, stream=st)
 
     def barrier():
         if world > 1:
@@ -354,6 +355,36 @@ def run_ours(args):
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(sum(e2e_ms), dev))
     h2d = int(sum(t.numel() for t in host[0]) * 4)
     d2h = int(B * (2 * ncap + 1) * 4)
+
+    # graph form: the step's launches (extract + match of the whole batch, every size
+    # group) captured once into a CUDA graph and replayed; the context's plans, tables and
+    # workspace already exist from the steps above, so the capture makes no allocation
+    graph = None
+    if not args.no_graph:
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream(device=dev)
+        gs.wait_stream(stream)
+        torch.cuda.synchronize()
+        launches_g0 = ctx.launch_count()
+        with torch.cuda.graph(g, stream=gs):
+            step(devb[0], st=torch.cuda.current_stream())
+        glaunches = ctx.launch_count() - launches_g0
+        torch.cuda.synchronize()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        e1.synchronize()
+        gms = e0.elapsed_time(e1)
+        graph = {"value": whole_job_rate(world, B, args.steps, max_over_ranks(gms, dev)),
+                 "unit": "pairs/s", "ms_per_step": gms / args.steps,
+                 "kernels_per_graph": glaunches,
+                 "form": "one CUDA graph per batch (extract + match of every pair), replayed"}
+        del g
 
     # plain form: one pair per call, no grouping, CUDA-core matcher
     plain = None
@@ -463,6 +494,7 @@ def run_ours(args):
                              " and each step streams ~0.3 KB of workspace per pixel, > L2"},
             "mpix_per_s": value * px_per_step / B / 1e6,
             "plain_form": plain,
+            "graph_form": graph,
             "serving": serving,
             "rift_baseline": rift,
             "stage_ms_per_step": stage_ms,
@@ -526,6 +558,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-rift", action="store_true", help="skip the RIFT-ring baseline")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay form")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the open-loop serving run (0: skip)")
     ap.add_argument("--serve-rate", default="50,100,200,400",

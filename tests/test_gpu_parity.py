@@ -391,6 +391,45 @@ def test_uneven_batch_in_one_call(pkg, dev):
         assert len(g["xy"]) == len(o.xy)
 
 
+def test_graph_capture_replays_the_calls(pkg, dev):
+    """extract + match of a mixed-size batch captured into a CUDA graph (after the calls
+    that create plans and workspace) and replayed: the outputs equal the direct calls'."""
+    ctx = pkg.Context(pkg.default_params(max_keypoints=300), device=0)
+    sizes = [(256, 256), (256, 256), (384, 320), (384, 320)]
+    imgs = [torch.from_numpy(synth.make_pair(h, w, synth.pair_seed(5, i), angle_deg=None).a).to(dev)
+            for i, (h, w) in enumerate(sizes)]
+    feats = [ctx.alloc_features() for _ in imgs]
+    matches = [ctx.alloc_matches() for _ in range(2)]
+
+    def run(st):
+        ctx.extract(imgs, feats, stream=st)
+        ctx.match(feats[0::2], feats[1::2], matches, stream=st)
+
+    run(torch.cuda.current_stream())
+    ctx.sync()
+    ref_f = [f.host() for f in feats]
+    ref_m = [m.host() for m in matches]
+    for f in feats:   # clear the outputs so the replay has to write them again
+        f.kp_xy.zero_(); f.desc.zero_(); f.counts.zero_()
+    for m in matches:
+        m.nn_desc.fill_(-7); m.count.zero_()
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream(device=dev)
+    gs.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=gs):
+        run(torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.sync()
+    for f, r in zip(feats, ref_f):
+        h = f.host()
+        assert np.array_equal(h["xy"], r["xy"]) and np.array_equal(h["desc"], r["desc"])
+    for m, r in zip(matches, ref_m):
+        h = m.host()
+        assert np.array_equal(h["nn_desc"], r["nn_desc"]) and np.array_equal(h["d1"], r["d1"])
+
+
 # ------------------------------------------------------ RIFT ring baseline (§II-C)
 def test_rift_ring_and_template_descriptors_bit_exact(pkg, dev, small):
     o = small["oa"]
