@@ -64,6 +64,13 @@ enum {
  * (§III).  The ring needs cap_desc >= No * max_keypoints. */
 #define RIFT2_FLAG_RIFT_TEMPLATE 0x4
 #define RIFT2_FLAG_RIFT_RING 0x8
+/* RIFT's corner keypoints (§II-A: FAST on the minimum moment, which measures cornerness,
+ * beside the edge keypoints on the maximum moment): FAST with the same threshold, NMS and
+ * ordering on the min-max normalised minimum moment, at most max_keypoints of them,
+ * appended after the edge keypoints with pixels already among the edge keypoints left out.
+ * The keypoint capacity doubles: cap_kp >= 2 * max_keypoints, and cap_desc / the match
+ * capacity double with it.  rift2_detect (the stage entry) ignores the flag. */
+#define RIFT2_FLAG_CORNERS 0x10
 
 /*
  * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
@@ -139,8 +146,8 @@ typedef struct rift2_debug_maps {
  *                                    ring's initial layer; 0..No-1)
  *   counts    int32 [2]              written on the device: n_kp, n_desc
  * cap_kp >= max_keypoints and cap_desc >= 2 * max_keypoints are required (each keypoint
- * yields one or two descriptors, §III; No * max_keypoints with RIFT2_FLAG_RIFT_RING),
- * otherwise RIFT2_E_CAPACITY.
+ * yields one or two descriptors, §III; No * max_keypoints with RIFT2_FLAG_RIFT_RING; both
+ * doubled with RIFT2_FLAG_CORNERS), otherwise RIFT2_E_CAPACITY.
  */
 typedef struct rift2_features {
   int cap_kp, cap_desc;
@@ -161,7 +168,8 @@ typedef struct rift2_features {
  *   d1 / d2 = smallest and second-smallest ||a/|a| - b/|b|||^2 (d2 = +inf if B has one
  *   descriptor), near_tie = 1 if (d2 - d1) < 1e-5 * max(d1, 1e-12).
  *   count = number of rows (= n_desc of A), written on the device.
- * cap >= 2 * max_keypoints is required (No * max_keypoints with RIFT2_FLAG_RIFT_RING).
+ * cap >= 2 * max_keypoints is required (No * max_keypoints with RIFT2_FLAG_RIFT_RING;
+ * doubled with RIFT2_FLAG_CORNERS).
  */
 typedef struct rift2_matches {
   int cap;

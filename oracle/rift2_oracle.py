@@ -24,6 +24,9 @@ Where the paper is silent the module takes a reading, tagged [R1]..[R9]:
   R7 patch rows y-48..y+47 and columns x-48..x+47; keypoints only where it fits.
   R8 secondary descriptor iff 1000*H[s2] >= round(1000*ratio)*H[s] (ratio 0.8).
   R9 matching A -> B, lowest index on ties, duplicates kept.
+  R13 RIFT's corner keypoints (§II-A): FAST on the min-max normalised minimum moment with
+     the edge detector's threshold, NMS and ordering, capped at max_keypoints; merged after
+     the edge keypoints, pixels already in the edge list dropped.
 
 Pins (tests/test_oracle_*.py): FFT vs a direct DFT; filter properties (peak, bandwidth,
 low-pass half point, raised-cosine window values, partition of unity, one-sidedness);
@@ -63,6 +66,7 @@ class Params:
     patch: int = 96
     cells: int = 6
     second_ratio: float = 0.8
+    corners: bool = False          # RIFT's corner keypoints on the minimum moment too [R13]
 
     @property
     def half_patch(self) -> int:
@@ -485,21 +489,41 @@ def detect(m_map, p: Params = DEFAULT, tie_eps: float = 1e-5):
     return xy, v, unc, btie
 
 
+def merge_keypoints(xy_edge, v_edge, xy_corner, v_corner):
+    """Edge keypoints (maximum moment) followed by the corner keypoints (minimum moment)
+    that are not already edge keypoints, each list in its own (score desc, index asc)
+    order [R13]: RIFT takes both kinds, corners for repeatability and edges for number
+    (§II-A)."""
+    have = {(int(x), int(y)) for x, y in xy_edge}
+    keep = np.array([(int(x), int(y)) not in have for x, y in xy_corner], dtype=bool)
+    xy = np.concatenate([np.asarray(xy_edge).reshape(-1, 2), np.asarray(xy_corner).reshape(-1, 2)[keep]])
+    v = np.concatenate([np.asarray(v_edge, dtype=np.float64), np.asarray(v_corner, dtype=np.float64)[keep]])
+    return xy.astype(np.int64), v
+
+
 def extract(img, p: Params = DEFAULT, keep_maps: bool = False, mode: str = "rift2") -> Features:
     """Whole single-image path: responses -> (MIM, PC -> M -> keypoints) -> descriptors
-    (`mode` as in describe)."""
+    (`mode` as in describe).  With p.corners the keypoints are merge_keypoints of FAST on
+    the maximum moment and FAST on the minimum moment, each capped at max_keypoints."""
     eo = responses(img, p)
     a = amplitude_sums(eo)
     mim, mim_margin = max_index_map(a)
     pc, t = phase_congruency(eo, p)
     m_max, m_min = moments(pc, p)
     xy, v, unc, btie = detect(m_max, p)
+    n_edge = len(xy)
+    if p.corners:
+        xy_c, v_c, unc_c, btie_c = detect(m_min, p)
+        xy, v = merge_keypoints(xy, v, xy_c, v_c)
     desc, dkp, ddom, _ = describe(mim, xy, p, mode)
     maps = {}
     if keep_maps:
         er, q, an0, _ = pc_terms(eo, p)
         maps = dict(A=a, mim=mim, mim_margin=mim_margin, pc=pc, T=t, M=m_max, m=m_min,
-                    Er=er, q=q, An0=an0, kp_uncertain=unc, kp_boundary_tie=btie)
+                    Er=er, q=q, An0=an0, kp_uncertain=unc, kp_boundary_tie=btie, n_edge=n_edge)
+        if p.corners:
+            maps.update(corner_xy=xy_c, corner_score=v_c, corner_uncertain=unc_c,
+                        corner_boundary_tie=btie_c)
     return Features(xy, v, desc, dkp, ddom, maps)
 
 

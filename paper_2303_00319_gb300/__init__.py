@@ -20,6 +20,7 @@ FLAG_PLAIN_MATCH = 0x1
 FLAG_NO_GROUPING = 0x2
 FLAG_RIFT_TEMPLATE = 0x4   # RIFT baseline: one descriptor per keypoint, unshifted MIM
 FLAG_RIFT_RING = 0x8       # RIFT baseline: the No descriptors of the convolution ring
+FLAG_CORNERS = 0x10        # RIFT's corner keypoints on the minimum moment, after the edge ones
 NS, NO, PATCH, CELLS = 4, 6, 96, 6
 DESC_DIM = CELLS * CELLS * NO
 
@@ -241,14 +242,19 @@ class Context:
         return int(self.params.max_keypoints)
 
     @property
+    def kp_cap(self) -> int:
+        """Keypoint list capacity per image: max_keypoints, twice that with corners."""
+        return self.max_kp * (2 if self.params.flags & FLAG_CORNERS else 1)
+
+    @property
     def desc_per_kp(self) -> int:
         return NO if self.params.flags & FLAG_RIFT_RING else 2
 
     def alloc_features(self, debug_shape=None) -> Features:
-        return Features.alloc(self.max_kp, f"cuda:{self.device}", debug_shape, self.desc_per_kp)
+        return Features.alloc(self.kp_cap, f"cuda:{self.device}", debug_shape, self.desc_per_kp)
 
     def alloc_matches(self) -> Matches:
-        return Matches.alloc(self.desc_per_kp * self.max_kp, f"cuda:{self.device}")
+        return Matches.alloc(self.desc_per_kp * self.kp_cap, f"cuda:{self.device}")
 
     def extract(self, images, feats=None, stream=None, debug=False):
         """images: list of float32 CUDA tensors [H][W] (rows may be strided)."""

@@ -32,7 +32,8 @@ struct KParams {
   float noise_c;         // T_o = median * noise_c (tau, scale sum and Rayleigh stats)
   float fast_t;
   int fast_arc;
-  int max_kp;
+  int max_kp;            // keypoints one detector pass keeps
+  int kp_cap;            // keypoint list capacity per image (2 max_kp with corners)
   int ratio_pm;          // dominant ratio in per mille (integer comparison)
   int desc_mode;         // DESC_RIFT2, DESC_RIFT_TEMPLATE or DESC_RIFT_RING
 };

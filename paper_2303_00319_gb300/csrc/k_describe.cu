@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
       return;
     }
     const unsigned char* buf = buf0 + (q & 1) * HBUF;
-    unsigned short* raw = ws.raw + ((size_t)img * kp.max_kp + k) * DESC_DIM;
+    unsigned short* raw = ws.raw + ((size_t)img * kp.kp_cap + k) * DESC_DIM;
     // A lane's 16 pixels start sh bytes into a 16-byte aligned 32-byte window, read with
     // two 16-byte loads (the 112-byte row pitch puts a quarter-warp's loads on distinct
     // banks); the window's words d .. d+4, d = sh / 4 (uniform over the warp), feed the
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
         for (int b = 0; b < NO; ++b)
           if (b != s && whole[b] > whole[s2]) s2 = b;
         unsigned has2 = (1000u * whole[s2] >= (unsigned)kp.ratio_pm * whole[s]) ? 1u : 0u;
-        ws.info[(size_t)img * kp.max_kp + k] = (unsigned)s | ((unsigned)s2 << 4) | (has2 << 8);
+        ws.info[(size_t)img * kp.kp_cap + k] = (unsigned)s | ((unsigned)s2 << 4) | (has2 << 8);
       }
       wsum[0] = wsum[1] = wsum[2] = 0;
     }
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(1024) desc_scan(KParams kp, DescribeWs ws, Fea
   const int nkp = fp.counts[img][0];
   const int per = (nkp + blockDim.x - 1) / blockDim.x;
   const int beg = threadIdx.x * per;
-  const unsigned* info = ws.info + (size_t)img * kp.max_kp;
+  const unsigned* info = ws.info + (size_t)img * kp.kp_cap;
   int local = 0;
   for (int i = 0; i < per; ++i) {
     int kk = beg + i;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(1024) desc_scan(KParams kp, DescribeWs ws, Fea
   }
   __syncthreads();
   int run = wsum[warp] + incl - local;
-  int* off = ws.off + (size_t)img * kp.max_kp;
+  int* off = ws.off + (size_t)img * kp.kp_cap;
   for (int i = 0; i < per; ++i) {
     int kk = beg + i;
     if (kk >= nkp) break;
@@ -258,9 +258,9 @@ __global__ void __launch_bounds__(256) desc_write(KParams kp, DescribeWs ws, Fea
   const int k = blockIdx.x * 8 + warp;
   if (k >= fp.counts[img][0]) return;
   int sh[NO];
-  const int nd = desc_shifts(ws.info[(size_t)img * kp.max_kp + k], kp.desc_mode, sh);
-  const int off = ws.off[(size_t)img * kp.max_kp + k];
-  const unsigned short* raw = ws.raw + ((size_t)img * kp.max_kp + k) * DESC_DIM;
+  const int nd = desc_shifts(ws.info[(size_t)img * kp.kp_cap + k], kp.desc_mode, sh);
+  const int off = ws.off[(size_t)img * kp.kp_cap + k];
+  const unsigned short* raw = ws.raw + ((size_t)img * kp.kp_cap + k) * DESC_DIM;
   unsigned short* d0 = fp.desc[img] + (size_t)off * DESC_DIM;
   unsigned n2 = 0;
   for (int e = lane; e < DESC_DIM; e += 32) {
@@ -280,10 +280,10 @@ cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
                             cudaStream_t st) {
   size_t sm = (size_t)DH_WARPS * 2 * HBUF + DH_WARPS * 2 * sizeof(unsigned long long);
   cudaFuncSetAttribute(desc_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int blocks = (kp.max_kp + DH_WARPS * DH_KPW - 1) / (DH_WARPS * DH_KPW);
+  int blocks = (kp.kp_cap + DH_WARPS * DH_KPW - 1) / (DH_WARPS * DH_KPW);
   desc_hist<<<dim3(blocks, nimg), DH_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
   desc_scan<<<nimg, 1024, 0, st>>>(kp, ws, fp);
-  desc_write<<<dim3((kp.max_kp + 7) / 8, nimg), 256, 0, st>>>(kp, ws, fp);
+  desc_write<<<dim3((kp.kp_cap + 7) / 8, nimg), 256, 0, st>>>(kp, ws, fp);
   return cudaGetLastError();
 }
 

@@ -321,6 +321,81 @@ __global__ void minmax_kernel(const float* __restrict__ m, long long P, unsigned
   }
 }
 
+// Corner keypoints after the edge keypoints (RIFT's corner and edge features, §II-A): one
+// CTA per image marks the edge keypoints' pixels in a bitmap, then compacts the corner
+// list (already in (score desc, index asc) order) without the marked pixels, block-wide
+// scans keeping the order.
+__global__ void __launch_bounds__(1024) merge_corners(int H, int W, KParams kp, FeatPtrs fp,
+                                                      const int* __restrict__ cxy,
+                                                      const float* __restrict__ csc,
+                                                      const int* __restrict__ ccnt,
+                                                      unsigned* __restrict__ bits) {
+  __shared__ unsigned wsum[32];
+  __shared__ int s_base;
+  const int img = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const size_t nw = ((size_t)H * W + 31) / 32;
+  unsigned* bm = bits + (size_t)img * nw;
+  for (size_t i = threadIdx.x; i < nw; i += blockDim.x) bm[i] = 0u;
+  __syncthreads();
+  int* xy = fp.kp_xy[img];
+  float* sc = fp.kp_score[img];
+  const int ne = fp.counts[img][0];
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    const unsigned idx = (unsigned)xy[2 * i + 1] * (unsigned)W + (unsigned)xy[2 * i];
+    atomicOr(bm + idx / 32, 1u << (idx % 32));
+  }
+  if (threadIdx.x == 0) s_base = ne;
+  __syncthreads();
+  const int nc = ccnt[2 * img];
+  const int* cx = cxy + (size_t)img * kp.max_kp * 2;
+  const float* cs = csc + (size_t)img * kp.max_kp;
+  for (int c0 = 0; c0 < nc; c0 += blockDim.x) {
+    const int i = c0 + threadIdx.x;
+    int x = 0, y = 0;
+    float v = 0.f;
+    bool keep = false;
+    if (i < nc) {
+      x = cx[2 * i];
+      y = cx[2 * i + 1];
+      v = cs[i];
+      const unsigned idx = (unsigned)y * (unsigned)W + (unsigned)x;
+      keep = ((bm[idx / 32] >> (idx % 32)) & 1u) == 0u;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[warp] = (unsigned)__popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned own = lane < nwarp ? wsum[lane] : 0u;
+      unsigned inc = own;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+      }
+      wsum[lane] = inc - own;   // exclusive prefix over warps
+    }
+    __syncthreads();
+    const int base = s_base;
+    const int pos = base + (int)wsum[warp] + __popc(bal & ((1u << lane) - 1u));
+    if (keep) {
+      xy[2 * pos] = x;
+      xy[2 * pos + 1] = y;
+      sc[pos] = v;
+    }
+    __syncthreads();   // every thread has read s_base
+    if (threadIdx.x == blockDim.x - 1) s_base = pos + (keep ? 1 : 0);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) fp.counts[img][0] = s_base;
+}
+
+cudaError_t launch_merge_corners(int nimg, int H, int W, const KParams& kp, const FeatPtrs& fp,
+                                 const int* cxy, const float* csc, const int* ccnt,
+                                 unsigned* bits, cudaStream_t st) {
+  merge_corners<<<nimg, 1024, 0, st>>>(H, W, kp, fp, cxy, csc, ccnt, bits);
+  return cudaGetLastError();
+}
+
 void launch_init_detect(unsigned* minmax, unsigned* ccount, int g, cudaStream_t st) {
   init_detect<<<(g + 127) / 128, 128, 0, st>>>(minmax, ccount, g);
 }

@@ -137,10 +137,11 @@ cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, cons
 }
 
 // ------------------------------------------------------------------ PC and moments
-// Maximum moment of one pixel from its six (q_o, Er_o).
+// Maximum moment of one pixel from its six (q_o, Er_o); mc = the minimum moment plus eps/2,
+// clamped at 0 (the covariance's smaller eigenvalue).
 __device__ __forceinline__ float moment_px(const float (&qv)[NO], const float (&ev)[NO],
                                            const float (&tn)[NO], const KParams& kp,
-                                           float (&pc)[NO]) {
+                                           float (&pc)[NO], float& mc) {
   float sxx = 0.f, syy = 0.f, sxy = 0.f;
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
@@ -154,7 +155,9 @@ __device__ __forceinline__ float moment_px(const float (&qv)[NO], const float (&
   syy *= 2.f / NO;
   sxy *= 4.f / NO;
   const float d = sxx - syy;
-  const float den = sqrtf(sxy * sxy + d * d) + kp.eps;
+  const float sq = sqrtf(sxy * sxy + d * d);
+  const float den = sq + kp.eps;
+  mc = fmaxf(0.5f * (sxx + syy - sq), 0.f);
   return 0.5f * (sxx + syy + den);
 }
 
@@ -163,12 +166,14 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
                                                  const float* __restrict__ noise_t, long long P,
                                                  KParams kp, float* __restrict__ moment,
                                                  unsigned* __restrict__ minmax,
-                                                 float* __restrict__ pc_out) {
+                                                 float* __restrict__ pc_out,
+                                                 float* __restrict__ mcorner,
+                                                 unsigned* __restrict__ minmax_c) {
   const int img = blockIdx.y;
   float tn[NO];
 #pragma unroll
   for (int o = 0; o < NO; ++o) tn[o] = __ldg(noise_t + img * NO + o);
-  float lo = 3.0e38f, hi = 0.f;
+  float lo = 3.0e38f, hi = 0.f, loc = 3.0e38f, hic = 0.f;
   const size_t ib = (size_t)img * NO * P;
   if ((P & 3) == 0) {
     // four pixels per thread and step: twelve 16-byte loads in flight
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
         q4[o] = __ldg(reinterpret_cast<const float4*>(q + ib + (size_t)o * P) + i);
         e4[o] = __ldg(reinterpret_cast<const float4*>(er + ib + (size_t)o * P) + i);
       }
-      float mv[4];
+      float mv[4], mcv[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float qv[NO], ev[NO], pc[NO];
@@ -190,7 +195,9 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
           qv[o] = c == 0 ? q4[o].x : c == 1 ? q4[o].y : c == 2 ? q4[o].z : q4[o].w;
           ev[o] = c == 0 ? e4[o].x : c == 1 ? e4[o].y : c == 2 ? e4[o].z : e4[o].w;
         }
-        mv[c] = moment_px(qv, ev, tn, kp, pc);
+        mv[c] = moment_px(qv, ev, tn, kp, pc, mcv[c]);
+        loc = fminf(loc, mcv[c]);
+        hic = fmaxf(hic, mcv[c]);
         if (pc_out) {
 #pragma unroll
           for (int o = 0; o < NO; ++o) pc_out[ib + (size_t)o * P + 4 * i + c] = pc[o];
@@ -199,6 +206,8 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
         hi = fmaxf(hi, mv[c]);
       }
       reinterpret_cast<float4*>(moment + (size_t)img * P)[i] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+      if (mcorner)
+        reinterpret_cast<float4*>(mcorner + (size_t)img * P)[i] = make_float4(mcv[0], mcv[1], mcv[2], mcv[3]);
     }
   } else {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
@@ -209,7 +218,11 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
         qv[o] = __ldg(q + ib + (size_t)o * P + i);
         ev[o] = __ldg(er + ib + (size_t)o * P + i);
       }
-      const float m = moment_px(qv, ev, tn, kp, pc);
+      float mc;
+      const float m = moment_px(qv, ev, tn, kp, pc, mc);
+      if (mcorner) mcorner[(size_t)img * P + i] = mc;
+      loc = fminf(loc, mc);
+      hic = fmaxf(hic, mc);
       if (pc_out) {
 #pragma unroll
         for (int o = 0; o < NO; ++o) pc_out[ib + (size_t)o * P + i] = pc[o];
@@ -222,27 +235,38 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
   for (int d = 16; d > 0; d >>= 1) {
     lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, d));
     hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    loc = fminf(loc, __shfl_xor_sync(0xffffffffu, loc, d));
+    hic = fmaxf(hic, __shfl_xor_sync(0xffffffffu, hic, d));
   }
-  __shared__ float slo[8], shi[8];
+  __shared__ float slo[8], shi[8], sloc[8], shic[8];
   int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { slo[w] = lo; shi[w] = hi; }
+  if ((threadIdx.x & 31) == 0) { slo[w] = lo; shi[w] = hi; sloc[w] = loc; shic[w] = hic; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { lo = fminf(lo, slo[k]); hi = fmaxf(hi, shi[k]); }
-    // M > 0, so the bit patterns order like the values
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      lo = fminf(lo, slo[k]);
+      hi = fmaxf(hi, shi[k]);
+      loc = fminf(loc, sloc[k]);
+      hic = fmaxf(hic, shic[k]);
+    }
+    // M > 0 and the corner map >= 0, so the bit patterns order like the values
     atomicMin(minmax + 2 * img, __float_as_uint(lo));
     atomicMax(minmax + 2 * img + 1, __float_as_uint(hi));
+    if (minmax_c) {
+      atomicMin(minmax_c + 2 * img, __float_as_uint(loc));
+      atomicMax(minmax_c + 2 * img + 1, __float_as_uint(hic));
+    }
   }
 }
 
 cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t, int nimg,
                              long long P, const KParams& kp, float* moment, unsigned* minmax,
-                             float* pc_out, cudaStream_t st) {
+                             float* pc_out, float* mcorner, unsigned* minmax_c, cudaStream_t st) {
   long long blocks = (P / 4 + 255) / 256;
   if (blocks < 1) blocks = 1;
   if (blocks > 1216) blocks = 1216;   // 8 per SM on 152 SMs; grid-stride beyond
   pc_moment<<<dim3((unsigned)blocks, nimg), 256, 0, st>>>(er, q, noise_t, P, kp, moment, minmax,
-                                                          pc_out);
+                                                          pc_out, mcorner, minmax_c);
   return cudaGetLastError();
 }
 

@@ -32,9 +32,11 @@ struct MedianWs {
 };
 cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, const KParams& kp,
                                    MedianWs ws, cudaStream_t st);
+// mcorner / minmax_c (both NULL unless corners are wanted): the minimum moment without its
+// -eps/2 offset (>= 0, the same FAST input up to the min-max normalisation) and its min / max.
 cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t, int nimg,
                              long long P, const KParams& kp, float* moment, unsigned* minmax,
-                             float* pc_out, cudaStream_t st);
+                             float* pc_out, float* mcorner, unsigned* minmax_c, cudaStream_t st);
 
 // k_detect.cu — FAST + NMS on the normalised moment map, then top-K.
 struct DetectWs {
@@ -56,6 +58,12 @@ cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KPa
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st);
 // min = +inf bits, max = 0, candidate counts = 0 for g images
 void launch_init_detect(unsigned* minmax, unsigned* ccount, int g, cudaStream_t st);
+// Appends each image's corner keypoints (cxy / csc / ccnt[2 i], max_kp per image) after its
+// edge keypoints in fp, leaving out pixels already among the edge keypoints (order kept);
+// bits: scratch of ceil(H W / 32) words per image.
+cudaError_t launch_merge_corners(int nimg, int H, int W, const KParams& kp, const FeatPtrs& fp,
+                                 const int* cxy, const float* csc, const int* ccnt,
+                                 unsigned* bits, cudaStream_t st);
 // image-wide min / max of g non-negative maps [g][P] (ordered-int atomics)
 void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStream_t st);
 // worst-case number of NMS survivors of an H x W map (one per 2 x 2 block)

@@ -38,6 +38,7 @@ void derive_kparams(const rift2_params& p, KParams& k) {
   k.fast_t = p.fast_threshold;
   k.fast_arc = p.fast_arc;
   k.max_kp = p.max_keypoints;
+  k.kp_cap = p.max_keypoints * ((p.flags & RIFT2_FLAG_CORNERS) ? 2 : 1);
   k.ratio_pm = (int)std::lround(p.second_ratio * 1000.0);
   k.desc_mode = (p.flags & RIFT2_FLAG_RIFT_RING)       ? DESC_RIFT_RING
                 : (p.flags & RIFT2_FLAG_RIFT_TEMPLATE) ? DESC_RIFT_TEMPLATE
@@ -180,7 +181,8 @@ int check_size(int H, int W) {
 // ------------------------------------------------------------------ tracing
 // Kernels enqueued by each launcher (kept next to the launch sequences they count).
 constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_LG_ROWS = 1, K_NOISE = 6, K_MOMENT = 1,
-              K_DETECT = 2, K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1;
+              K_DETECT = 2, K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1,
+              K_MERGE = 1;
 
 cudaEvent_t take_event(rift2_ctx* c) {
   if (!c->free_events.empty()) {
@@ -218,10 +220,14 @@ struct StageScope {
 struct Layout {
   size_t spec, scratch, er, q, an0, amp, pc, moment, mim, mhist, mstate, noise, minmax, ccount,
       cand, sortbuf, raw, info, off, total;
+  // corner keypoints (RIFT2_FLAG_CORNERS): minimum-moment map, its min / max, candidate
+  // count, the corner list before the merge, and the bitmap of edge-keypoint pixels
+  size_t mcorner, minmax_c, ccount_c, cxy, csc, ccnt, bits;
   int mim_pitch, cap_cand;
 };
 
-Layout extract_layout(int g, int H, int W, int max_kp, bool debug) {
+// max_kp: keypoints one detector pass keeps; kp_cap: keypoint list capacity per image.
+Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners, bool debug) {
   Layout L{};
   const size_t P = (size_t)H * W;
   L.mim_pitch = (int)align_up((size_t)(W > 112 ? W : 112), 16);
@@ -245,11 +251,24 @@ Layout extract_layout(int g, int H, int W, int max_kp, bool debug) {
   L.cand = take((size_t)g * L.cap_cand * 8);
   const int kc = topk_sort_cap(max_kp);
   L.sortbuf = take(kc > TOPK_SMEM_CAP ? (size_t)g * kc * 8 : 0);
-  L.raw = take((size_t)g * max_kp * DESC_DIM * 2);
-  L.info = take((size_t)g * max_kp * 4);
-  L.off = take((size_t)g * max_kp * 4);
+  L.raw = take((size_t)g * kp_cap * DESC_DIM * 2);
+  L.info = take((size_t)g * kp_cap * 4);
+  L.off = take((size_t)g * kp_cap * 4);
+  const size_t none = (size_t)-1;
+  L.mcorner = corners ? take((size_t)g * P * 4) : none;
+  L.minmax_c = corners ? take((size_t)g * 2 * 4) : none;
+  L.ccount_c = corners ? take((size_t)g * 4) : none;
+  L.cxy = corners ? take((size_t)g * max_kp * 2 * 4) : none;
+  L.csc = corners ? take((size_t)g * max_kp * 4) : none;
+  L.ccnt = corners ? take((size_t)g * 2 * 4) : none;
+  L.bits = corners ? take((size_t)g * ((P + 31) / 32) * 4) : none;
   L.total = o;
   return L;
+}
+
+Layout ctx_layout(const rift2_ctx* c, int g, int H, int W, bool debug) {
+  return extract_layout(g, H, W, c->kp.max_kp, c->kp.kp_cap,
+                        (c->p.flags & RIFT2_FLAG_CORNERS) != 0, debug);
 }
 
 template <typename T>
@@ -293,10 +312,10 @@ int desc_per_kp(const rift2_ctx* c) { return (c->p.flags & RIFT2_FLAG_RIFT_RING)
 
 int check_features(const rift2_ctx* c, const rift2_features& f, bool need_desc) {
   if (!f.kp_xy || !f.kp_score || !f.counts) return RIFT2_E_INVAL;
-  if (f.cap_kp < c->p.max_keypoints) return RIFT2_E_CAPACITY;
+  if (f.cap_kp < c->kp.kp_cap) return RIFT2_E_CAPACITY;
   if (need_desc) {
     if (!f.desc || !f.desc_norm || !f.desc_kp || !f.desc_dom) return RIFT2_E_INVAL;
-    if (f.cap_desc < desc_per_kp(c) * c->p.max_keypoints) return RIFT2_E_CAPACITY;
+    if (f.cap_desc < desc_per_kp(c) * c->kp.kp_cap) return RIFT2_E_CAPACITY;
   }
   return RIFT2_OK;
 }
@@ -360,7 +379,7 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   rc = get_zero_cols(c, H, W, st, &zc);
   if (rc) return rc;
   const bool dbg = wants_debug(out, g);
-  Layout L = extract_layout(g, H, W, c->p.max_keypoints, dbg);
+  Layout L = ctx_layout(c, g, H, W, dbg);
   rc = ensure_ws(c, L.total);
   if (rc) return rc;
   void* ws = c->ws;
@@ -374,6 +393,13 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   unsigned* ccount = at<unsigned>(ws, L.ccount);
   c->launches += K_INIT;
   launch_init_detect(minmax, ccount, g, st);
+  const bool corners = (c->p.flags & RIFT2_FLAG_CORNERS) != 0;
+  unsigned* minmax_c = corners ? at<unsigned>(ws, L.minmax_c) : nullptr;
+  unsigned* ccount_c = corners ? at<unsigned>(ws, L.ccount_c) : nullptr;
+  if (corners) {
+    c->launches += K_INIT;
+    launch_init_detect(minmax_c, ccount_c, g, st);
+  }
   RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * 2 * 4096 * 4, st));
   float2* spec = at<float2>(ws, L.spec);
   {
@@ -403,13 +429,29 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   {
     StageScope sc(c, RIFT2_STAGE_MOMENT, st, K_MOMENT);
     RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, g, P, c->kp, moment, minmax, at<float>(ws, L.pc),
-                              st));
+                              corners ? at<float>(ws, L.mcorner) : nullptr, minmax_c, st));
   }
   DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand,
               at<unsigned long long>(ws, L.sortbuf)};
   {
-    StageScope sc(c, RIFT2_STAGE_DETECT, st, K_DETECT);
+    StageScope sc(c, RIFT2_STAGE_DETECT, st, corners ? 2 * K_DETECT + K_MERGE : K_DETECT);
     RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
+    if (corners) {
+      // corner keypoints on the minimum moment into the side list, then appended
+      FeatPtrs fc{};
+      int* cxy = at<int>(ws, L.cxy);
+      float* csc = at<float>(ws, L.csc);
+      int* ccnt = at<int>(ws, L.ccnt);
+      for (int i = 0; i < g; ++i) {
+        fc.kp_xy[i] = cxy + (size_t)i * c->kp.max_kp * 2;
+        fc.kp_score[i] = csc + (size_t)i * c->kp.max_kp;
+        fc.counts[i] = ccnt + 2 * i;
+      }
+      DetectWs dwc{minmax_c, at<unsigned long long>(ws, L.cand), ccount_c, L.cap_cand,
+                   at<unsigned long long>(ws, L.sortbuf)};
+      RIFT2_CU(launch_detect(at<float>(ws, L.mcorner), g, H, W, c->kp, dwc, fc, st));
+      RIFT2_CU(launch_merge_corners(g, H, W, c->kp, fp, cxy, csc, ccnt, at<unsigned>(ws, L.bits), st));
+    }
   }
   if (H >= RIFT2_PATCH && W >= RIFT2_PATCH) {
     CUtensorMap tm;
@@ -585,8 +627,8 @@ int rift2_extract(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* 
       ++j;
     // shrink the group until its workspace fits the budget
     int g = j - i;
-    while (g > 1 && extract_layout(g, imgs[i].height, imgs[i].width, c->p.max_keypoints,
-                                   wants_debug(out + i, g)).total > c->budget)
+    while (g > 1 && ctx_layout(c, g, imgs[i].height, imgs[i].width, wants_debug(out + i, g)).total >
+                        c->budget)
       g = (g + 1) / 2;
     int rc = extract_group(c, g, imgs + i, out + i, st);
     if (rc) return rc;
@@ -606,7 +648,7 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
     if (!m.q_desc || !m.nn_desc || !m.kp_a || !m.kp_b || !m.d1 || !m.d2 || !m.near_tie ||
         !m.count)
       return RIFT2_E_INVAL;
-    if (m.cap < desc_per_kp(c) * c->p.max_keypoints) return RIFT2_E_CAPACITY;
+    if (m.cap < desc_per_kp(c) * c->kp.kp_cap) return RIFT2_E_CAPACITY;
   }
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -635,9 +677,9 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
     }
     if (c->p.flags & RIFT2_FLAG_PLAIN_MATCH) {
       StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH);
-      RIFT2_CU(launch_match_simt(mp, g, desc_per_kp(c) * c->p.max_keypoints, st));
+      RIFT2_CU(launch_match_simt(mp, g, desc_per_kp(c) * c->kp.kp_cap, st));
     } else {
-      const int cap = (desc_per_kp(c) * c->p.max_keypoints + 127) / 128 * 128;
+      const int cap = (desc_per_kp(c) * c->kp.kp_cap + 127) / 128 * 128;
       const int nsplit = match_tc_nsplit(g, cap);
       int rc = ensure_ws(c, match_tc_ws_bytes(g, cap, nsplit));
       if (rc) return rc;
@@ -688,7 +730,7 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
   const long long P = (long long)H * W;
   for (int i0 = 0; i0 < n; i0 += MAXB) {
     int g = n - i0 < MAXB ? n - i0 : MAXB;
-    Layout L = extract_layout(g, H, W, c->p.max_keypoints, false);
+    Layout L = ctx_layout(c, g, H, W, false);
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
     unsigned* minmax = at<unsigned>(c->ws, L.minmax);
@@ -716,7 +758,7 @@ int rift2_describe(rift2_ctx* c, int n, const unsigned char* mim, int H, int W,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i0 = 0; i0 < n; i0 += MAXB) {
     int g = n - i0 < MAXB ? n - i0 : MAXB;
-    Layout L = extract_layout(g, H, W, c->p.max_keypoints, false);
+    Layout L = ctx_layout(c, g, H, W, false);
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
     unsigned char* wm = at<unsigned char>(c->ws, L.mim);

@@ -430,6 +430,34 @@ def test_graph_capture_replays_the_calls(pkg, dev):
         assert np.array_equal(h["nn_desc"], r["nn_desc"]) and np.array_equal(h["d1"], r["d1"])
 
 
+def test_corner_keypoints_merge(pkg, dev):
+    """With corner keypoints (FAST on the minimum moment, reading R13) the keypoint list is
+    the edge list followed by the corners not already in it: each part matches the
+    oracle's (up to certified near ties), and the descriptors cover the merged list."""
+    pr = synth.config_pair(0)
+    p = O.Params(max_keypoints=300, corners=True)
+    o = O.extract(pr.a.astype(np.float64), p, keep_maps=True)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=300, flags=pkg.FLAG_CORNERS), device=0)
+    f = ctx.extract([torch.from_numpy(pr.a).to(dev)])[0]
+    ctx.sync()
+    g = f.host()
+    ne = o.maps["n_edge"]
+    r = compare_keypoints(g["xy"][:ne], g["score"][:ne], o.xy[:ne], o.score[:ne],
+                          o.maps["kp_uncertain"], o.maps["kp_boundary_tie"])
+    assert not r["bad"] and r["inversions"] == 0, r
+    if r["flips"] == 0:
+        edge = {tuple(map(int, q)) for q in o.xy[:ne]}
+        keep = np.array([tuple(map(int, q)) not in edge for q in o.maps["corner_xy"]], dtype=bool)
+        unc = o.maps["corner_uncertain"]
+        rc = compare_keypoints(g["xy"][ne:], g["score"][ne:], o.xy[ne:], o.score[ne:], unc,
+                               o.maps["corner_boundary_tie"])
+        assert not rc["bad"] and rc["inversions"] == 0, rc
+        assert keep.sum() == len(o.xy) - ne
+    assert len(g["xy"]) > ne   # the synthetic scene has corner keypoints beyond the edge ones
+    # every keypoint got 1 or 2 descriptors
+    assert set(np.unique(g["desc_kp"])) == set(range(len(g["xy"])))
+
+
 # ------------------------------------------------------ RIFT ring baseline (§II-C)
 def test_rift_ring_and_template_descriptors_bit_exact(pkg, dev, small):
     o = small["oa"]

@@ -423,3 +423,44 @@ def test_ground_truth_evaluation_on_exact_correspondences():
     assert ev["correct"] == 1 and ev["rmse"] < 1e-9
     ev = O.evaluate(pa, pb + 5, np.array([0]), np.array([0]), np.array([0]), 90.0, (h, w))
     assert ev["correct"] == 0 and ev["rmse"] == 20.0
+
+
+# ----------------------------------------------- corner keypoints (§II-A, reading R13)
+def test_corner_keypoints_on_the_minimum_moment():
+    """A bright square: the minimum moment (cornerness) peaks at its four corners and stays
+    small along its sides, where the maximum moment (edgeness) is large; FAST on the
+    normalised minimum moment ranks exactly the four corners first, far ahead of the rest."""
+    img = np.zeros((160, 160))
+    img[56:104, 56:104] = 1.0
+    p = O.Params(max_keypoints=50, corners=True)
+    pc, _ = O.phase_congruency(O.responses(img, p), p)
+    m_max, m_min = O.moments(pc, p)
+    corners = ((56, 56), (56, 103), (103, 56), (103, 103))
+    mids = ((56, 80), (80, 56), (103, 80), (80, 103))
+    assert min(m_min[y, x] for y, x in corners) > 3 * max(m_min[y, x] for y, x in mids)
+    assert min(m_max[y, x] for y, x in mids) > 3 * max(m_min[y, x] for y, x in mids)
+    xy, v, _, _ = O.detect(m_min, p)
+    assert {tuple(map(int, q)) for q in xy[:4]} == {(x, y) for y, x in corners}
+    assert v[3] > 3 * v[4]
+
+
+def test_merge_keypoints_brute_force():
+    """Edge keypoints unchanged and first; then the corner keypoints in their order, minus
+    the pixels already present; no pixel twice."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        pts = rng.integers(0, 12, size=(40, 2))
+        _, first = np.unique(pts, axis=0, return_index=True)
+        pts = pts[np.sort(first)]
+        ne = int(rng.integers(0, len(pts)))
+        nc = int(rng.integers(0, len(pts)))
+        edge = pts[:ne]
+        corner = rng.permutation(pts)[:nc]
+        ve, vc = rng.random(ne), rng.random(nc)
+        xy, v = O.merge_keypoints(edge, ve, corner, vc)
+        assert np.array_equal(xy[:ne], edge) and np.array_equal(v[:ne], ve)
+        seen = {tuple(q) for q in edge}
+        exp = [(tuple(q), w) for q, w in zip(corner, vc) if tuple(q) not in seen]
+        assert [tuple(q) for q in xy[ne:]] == [q for q, _ in exp]
+        assert np.array_equal(v[ne:], np.array([w for _, w in exp]))
+        assert len({tuple(q) for q in xy}) == len(xy)
