@@ -471,6 +471,37 @@ def run_ours(args):
         rt.close()
         rr.close()
 
+    # RIFT's corner keypoints on the minimum moment beside the edge ones (up to twice the
+    # keypoints, so more descriptors and a larger matching problem) on the same batches
+    corners = None
+    if not args.no_rift and args.workload == 1:
+        cc = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=pkg.FLAG_CORNERS),
+                         device=local, hbm_budget=96 << 30)
+        fc = [cc.alloc_features() for _ in range(2 * B)]
+        mc = [cc.alloc_matches() for _ in range(B)]
+
+        def corner_step(imgs):
+            cc.extract([imgs[i] for i in range(2 * B)], fc, stream=stream)
+            cc.match(fc[0::2], fc[1::2], mc, stream=stream)
+
+        for i in range(2):
+            corner_step(devb[i % rot])
+        torch.cuda.synchronize()
+        cms = []
+        for i in range(min(args.steps, 10)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            corner_step(devb[i % rot])
+            e1.record(stream)
+            e1.synchronize()
+            cms.append(e0.elapsed_time(e1))
+        nkp = [int(f.counts[0].item()) for f in fc]
+        corners = {"pairs_per_s": B / (statistics.mean(cms) / 1000.0),
+                   "ms_per_step": statistics.mean(cms),
+                   "keypoints_per_image": statistics.mean(nkp),
+                   "form": "edge keypoints (maximum moment) + corner keypoints (minimum moment)"}
+        cc.close()
+
     serving = None
     if args.serve_requests > 0 and args.workload == 1:
         serving = run_serving(args, local)
@@ -497,6 +528,7 @@ def run_ours(args):
             "graph_form": graph,
             "serving": serving,
             "rift_baseline": rift,
+            "corners_form": corners,
             "stage_ms_per_step": stage_ms,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
