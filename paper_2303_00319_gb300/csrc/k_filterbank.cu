@@ -410,7 +410,7 @@ __device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParam
 // for each orientation the four scales are transformed together.
 constexpr int RR_MAXPIX = 8;   // pixels per thread: W <= 8 * blockDim.x
 
-__global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__ scratch, int H,
+__global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restrict__ scratch, int H,
                                                       int W, FftPlan pw, KParams kp,
                                                       float* __restrict__ er_out,
                                                       float* __restrict__ q_out,
@@ -434,8 +434,12 @@ __global__ void __launch_bounds__(512) lg_rows_reduce(const float2* __restrict__
   for (int o = 0; o < NO; ++o) {
     for (int s = 0; s < NS; ++s) {
       const float2* src = scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W;
-      for (int x = threadIdx.x; x < W; x += blockDim.x)
-        a[s * W + x] = zc[o * W + x] ? make_float2(0.f, 0.f) : __ldg(src + x);
+      // unconditional loads (a zero-window column's data is not used), several in flight
+#pragma unroll 4
+      for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const float2 v = __ldg(src + x);
+        a[s * W + x] = zc[o * W + x] ? make_float2(0.f, 0.f) : v;
+      }
     }
     __syncthreads();
     float2* res = fft_smem<true, false>(a, b, pw, NS, W, 1);
