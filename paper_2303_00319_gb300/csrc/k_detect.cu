@@ -18,8 +18,10 @@ constexpr int FH = 4;           // halo: 3 for the circle + 1 for the NMS
 constexpr int FS = FT + 2 * FH; // 40
 constexpr int VS = FT + 2;      // score map side (1-pixel halo)
 
-__constant__ int c_circle_dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
-__constant__ int c_circle_dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
+// The 16-pixel Bresenham circle of radius 3 in cyclic order; compile-time offsets, so the
+// unrolled segment test reads the tile at immediate displacements.
+__device__ constexpr int kCircleDx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
+__device__ constexpr int kCircleDy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
 
 // A run of >= arc cyclically contiguous set bits in the 16-bit circle mask (1 <= arc <= 16).
 // acc holds the AND of r >> 0 .. h-1 (bit i set: bits i .. i+h-1 of r all set); doubling h
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
       float vb = 0.f, vd = 0.f;
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        float q = mn[sy + c_circle_dy[k]][sx + c_circle_dx[k]];
+        float q = mn[sy + kCircleDy[k]][sx + kCircleDx[k]];
         if (q > p + t) { bright |= 1u << k; vb += q - p - t; }
         if (q < p - t) { dark |= 1u << k; vd += p - q - t; }
       }
