@@ -71,6 +71,12 @@ enum {
  * The keypoint capacity doubles: cap_kp >= 2 * max_keypoints, and cap_desc / the match
  * capacity double with it.  rift2_detect (the stage entry) ignores the flag. */
 #define RIFT2_FLAG_CORNERS 0x10
+/* Tune per image size (no counterpart in the paper): the first extraction of a size whose
+ * column transforms run in shared memory times each candidate column tile (columns per
+ * CTA) on that call's own data, synchronising the stream once, and keeps the fastest for
+ * the context; every tile computes bit-identical results.  Without the flag the default
+ * tile is used.  rift2_tuned_tile reports the choice. */
+#define RIFT2_FLAG_AUTOTUNE 0x20
 
 /*
  * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
@@ -229,6 +235,11 @@ int rift2_sync(rift2_ctx* ctx, void* stream);
 
 /* Frees the context and its workspace (waits for the device first). */
 int rift2_destroy(rift2_ctx* ctx);
+
+/* The column tile the autotuner chose for images of H x W in this context: the tile (>= 1),
+ * 0 if none was tuned (flag off, the size not seen yet, or a register-tiled height), or
+ * RIFT2_E_INVAL for a NULL context.  No counterpart in the paper. */
+int rift2_tuned_tile(const rift2_ctx* ctx, int height, int width);
 
 /* ------------------------------------------------------------------------------
  * Tracing.  With profiling on, the context brackets every stage of every launch group

@@ -21,6 +21,7 @@ FLAG_NO_GROUPING = 0x2
 FLAG_RIFT_TEMPLATE = 0x4   # RIFT baseline: one descriptor per keypoint, unshifted MIM
 FLAG_RIFT_RING = 0x8       # RIFT baseline: the No descriptors of the convolution ring
 FLAG_CORNERS = 0x10        # RIFT's corner keypoints on the minimum moment, after the edge ones
+FLAG_AUTOTUNE = 0x20       # time the column tiles of a new image size once, keep the fastest
 NS, NO, PATCH, CELLS = 4, 6, 96, 6
 DESC_DIM = CELLS * CELLS * NO
 
@@ -28,7 +29,7 @@ DESC_DIM = CELLS * CELLS * NO
 EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_extract",
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
-           "rift2_describe", "rift2_detect_static")
+           "rift2_describe", "rift2_detect_static", "rift2_tuned_tile")
 STATIC_MAX_CANDIDATES = 262144
 STAGES = ("fft_fwd", "lg_cols", "lg_rows", "noise", "moment", "detect", "describe", "match")
 
@@ -90,6 +91,7 @@ def lib():
                                          C.POINTER(C.c_longlong)]
         L.rift2_launch_count.argtypes = [C.c_void_p]
         L.rift2_launch_count.restype = C.c_longlong
+        L.rift2_tuned_tile.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.rift2_fft2.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                  C.c_void_p]
         L.rift2_detect.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
@@ -303,6 +305,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().rift2_launch_count(self._h))
+
+    def tuned_tile(self, height: int, width: int) -> int:
+        """Column tile the autotuner kept for this size (0: none tuned)."""
+        return int(lib().rift2_tuned_tile(self._h, height, width))
 
     # ---- stage entry points
     def fft2(self, img, stream=None):

@@ -761,9 +761,19 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
   return cudaGetLastError();
 }
 
+int lg_cols_tile_candidates(int H, int* out, int max_n) {
+  switch (H) {
+    case 256: case 512: case 1024: case 2048: case 4096: return 0;   // register path
+    default: break;
+  }
+  int n = 0;
+  for (int tc = cols_tile(H); tc >= 1 && n < max_n; tc /= 2) out[n++] = tc;
+  return n;
+}
+
 cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
                            const FftPlan& ph, const KParams& kp, const unsigned char* zc,
-                           cudaStream_t st) {
+                           cudaStream_t st, int tile) {
   switch (H) {
     case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, zc, st);
     case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
@@ -773,6 +783,7 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H,
     default: break;
   }
   int tc = cols_tile(H);
+  if (tile >= 1 && tile <= tc) tc = tile;   // a tuned (smaller) tile; any tile gives the same result
   size_t sm2 = 3 * (size_t)tc * H * sizeof(float2) + (size_t)H * sizeof(float);
   cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   lg_cols_inverse<<<dim3((W + tc - 1) / tc, NS, nimg), 512, sm2, st>>>(spec, scratch, H, W, tc,

@@ -16,9 +16,13 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
                                 cudaStream_t st);
 // zc [NO][W]: 1 where orientation o's angular window is zero on the whole column u.
 void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaStream_t st);
+// Column tiles (columns per CTA) the shared-memory column pass can use for height H, the
+// default first; none for the register-tiled heights.  `tile` of launch_lg_cols picks one
+// (0: the default); every tile computes the same result.
+int lg_cols_tile_candidates(int H, int* out, int max_n);
 cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
                            const FftPlan& ph, const KParams& kp, const unsigned char* zc,
-                           cudaStream_t st);
+                           cudaStream_t st, int tile = 0);
 cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
                            unsigned char* mim, int mim_pitch, const unsigned char* zc,

@@ -57,6 +57,7 @@ struct rift2_ctx {
   int* status = nullptr;
   std::map<int, FftPlan> plans;
   std::map<std::pair<int, int>, unsigned char*> zero_cols;   // (H, W) -> [NO][W]
+  std::map<std::pair<int, int>, int> col_tiles;              // (H, W) -> tuned column tile
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   // tracing
   long long launches = 0;
@@ -215,6 +216,42 @@ struct StageScope {
     }
   }
 };
+
+// ------------------------------------------------------------------ autotuning
+// First extraction of a size with a shared-memory column pass: run that pass once per
+// candidate tile on the call's own spectrum (two timed repetitions each, events on the
+// stream, one synchronisation), keep the fastest.  The outputs of every candidate are
+// identical, so the scratch the last run leaves is as good as any.
+int tune_col_tile(rift2_ctx* c, const float2* spec, float2* scratch, int g, int H, int W,
+                  const FftPlan& ph, const unsigned char* zc, cudaStream_t st, int* tile) {
+  const auto key = std::make_pair(H, W);
+  auto it = c->col_tiles.find(key);
+  if (it != c->col_tiles.end()) { *tile = it->second; return RIFT2_OK; }
+  int cand[8];
+  const int n = lg_cols_tile_candidates(H, cand, 8);
+  if (n <= 1) { *tile = n ? cand[0] : 0; c->col_tiles[key] = *tile; return RIFT2_OK; }
+  cudaEvent_t ev[9];
+  for (int i = 0; i <= n; ++i) RIFT2_CU(cudaEventCreate(&ev[i]));
+  RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, cand[0]));   // warm-up
+  c->launches += 1 + 2 * n;
+  RIFT2_CU(cudaEventRecord(ev[0], st));
+  for (int i = 0; i < n; ++i) {
+    for (int r = 0; r < 2; ++r) RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, cand[i]));
+    RIFT2_CU(cudaEventRecord(ev[i + 1], st));
+  }
+  RIFT2_CU(cudaEventSynchronize(ev[n]));
+  int best = cand[0];
+  float best_ms = 1e30f;
+  for (int i = 0; i < n; ++i) {
+    float ms = 0.f;
+    RIFT2_CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    if (ms < best_ms) { best_ms = ms; best = cand[i]; }
+  }
+  for (int i = 0; i <= n; ++i) cudaEventDestroy(ev[i]);
+  c->col_tiles[key] = best;
+  *tile = best;
+  return RIFT2_OK;
+}
 
 // ------------------------------------------------------------------ workspace layout
 struct Layout {
@@ -411,9 +448,14 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   float* an0 = at<float>(ws, L.an0);
   unsigned char* mim = at<unsigned char>(ws, L.mim);
   float2* scratch = at<float2>(ws, L.scratch);
+  int tile = 0;
+  if (c->p.flags & RIFT2_FLAG_AUTOTUNE) {
+    rc = tune_col_tile(c, spec, scratch, g, H, W, ph, zc, st, &tile);
+    if (rc) return rc;
+  }
   {
     StageScope sc(c, RIFT2_STAGE_LG_COLS, st, K_LG_COLS);
-    RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st));
+    RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, tile));
   }
   {
     StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, K_LG_ROWS);
@@ -590,6 +632,12 @@ int rift2_profile_read(rift2_ctx* c, int n, double* ms, long long* count) {
 }
 
 long long rift2_launch_count(const rift2_ctx* c) { return c ? c->launches : -1; }
+
+int rift2_tuned_tile(const rift2_ctx* c, int height, int width) {
+  if (!c) return RIFT2_E_INVAL;
+  auto it = c->col_tiles.find(std::make_pair(height, width));
+  return it == c->col_tiles.end() ? 0 : it->second;
+}
 
 int rift2_sync(rift2_ctx* c, void* stream) {
   if (!c) return RIFT2_E_INVAL;

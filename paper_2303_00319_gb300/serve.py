@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import Context, default_params
+from . import FLAG_AUTOTUNE, Context, default_params
 
 # Workspace bytes per pixel of one image in an extract launch (spectrum, 24 responses,
 # PC terms, maps, candidates) plus a margin; used for admission against the budget.
@@ -64,7 +64,8 @@ class Server:
         self.budget = hbm_budget
         self.dev = torch.device(f"cuda:{device}")
         per_lane = hbm_budget // lanes
-        self.lanes = [_Lane(Context(default_params(max_keypoints=max_keypoints), device, per_lane),
+        self.lanes = [_Lane(Context(default_params(max_keypoints=max_keypoints, flags=FLAG_AUTOTUNE),
+                                    device, per_lane),
                             torch.cuda.Stream(device=self.dev)) for _ in range(lanes)]
         self.per_lane_budget = per_lane
         self.queue: deque[PairRequest] = deque()

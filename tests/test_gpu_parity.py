@@ -458,6 +458,27 @@ def test_corner_keypoints_merge(pkg, dev):
     assert set(np.unique(g["desc_kp"])) == set(range(len(g["xy"])))
 
 
+def test_autotuned_column_tile_gives_identical_features(pkg, dev):
+    """With AUTOTUNE the first call of a size whose columns run in shared memory times the
+    candidate tiles and keeps one; the features equal those of the default tile bit for bit."""
+    sizes = [(640, 384), (640, 384)]
+    imgs = [torch.from_numpy(synth.make_pair(h, w, synth.pair_seed(6, i), angle_deg=None).a).to(dev)
+            for i, (h, w) in enumerate(sizes)]
+    ref = pkg.Context(pkg.default_params(max_keypoints=300), device=0)
+    tuned = pkg.Context(pkg.default_params(max_keypoints=300, flags=pkg.FLAG_AUTOTUNE), device=0)
+    fr = ref.extract(imgs)
+    ft = tuned.extract(imgs)
+    ft2 = tuned.extract(imgs)   # the kept tile
+    ref.sync(); tuned.sync()
+    tile = tuned.tuned_tile(640, 384)
+    assert tile >= 1 and ref.tuned_tile(640, 384) == 0
+    for a, b, c in zip(fr, ft, ft2):
+        ha, hb, hc = a.host(), b.host(), c.host()
+        for k in ("xy", "desc"):
+            assert np.array_equal(ha[k], hb[k]) and np.array_equal(ha[k], hc[k])
+    assert tuned.tuned_tile(1024, 1024) == 0   # never seen
+
+
 # ------------------------------------------------------ RIFT ring baseline (§II-C)
 def test_rift_ring_and_template_descriptors_bit_exact(pkg, dev, small):
     o = small["oa"]
