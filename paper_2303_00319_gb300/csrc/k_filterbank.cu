@@ -275,9 +275,10 @@ __device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams
 }
 
 // Angular raised-cosine window.  With c = cos(theta - theta_o) (theta = atan2(-v, u)),
-// the window (1 + cos(3 dtheta)) / 2 for |dtheta| < pi/3 equals (1 + c)(2c - 1)^2 / 2
-// (triple-angle identity), and 0 beyond.  c = (fu cos_o - fv sin_o) / r is formed from
-// fuco = fu cos_o, fv, sin_o and ri = 1/r (0 at DC).  Every kernel that evaluates the
+// the window (1 + cos(3 dtheta)) / 2 for |dtheta| < pi/3 equals (1 + c)(2c - 1)^2 / 2 =
+// 2c^3 - 1.5c + 0.5 (triple-angle identity, cos 3x = 4c^3 - 3c), evaluated as
+// c (2c^2 - 1.5) + 0.5 with two fused multiply-adds, and 0 beyond.  c = (fu cos_o -
+// fv sin_o) / r is formed from fuco = fu cos_o, fv, sin_o and ri = 1/r (0 at DC).  Every kernel that evaluates the
 // window, and the zero-column table, goes through lg_rinv and lg_window with explicitly
 // rounded products, so they agree bit for bit on which bins are zero.
 __device__ __forceinline__ float lg_rinv(float fu, float fv) {
@@ -287,8 +288,7 @@ __device__ __forceinline__ float lg_rinv(float fu, float fv) {
 __device__ __forceinline__ float lg_window(float fuco, float fv, float so, float ri) {
   const float c = __fmul_rn(fmaf(-fv, so, fuco), ri);
   if (!(c > 0.5f)) return 0.f;
-  const float t = 2.f * c - 1.f;
-  return 0.5f * (1.f + c) * t * t;
+  return fmaf(c, fmaf(2.f * c, c, -1.5f), 0.5f);
 }
 
 // Columns u whose angular window is zero on every row: S_o(u, v) = 0 for all v, so the
@@ -382,7 +382,8 @@ __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrt
 __device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParams& kp,
                                              float& er, float& q, float& an0, float& sum_an) {
   float e[NS], od[NS];
-  float sum_e = 0.f, sum_o = 0.f, max_an = 0.f;
+  float2 sum_eo = z[0];
+  float max_an = 0.f;
   sum_an = 0.f;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -390,11 +391,11 @@ __device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParam
     od[s] = z[s].y;
     const float an = fast_sqrt(e[s] * e[s] + od[s] * od[s]);
     if (s == 0) an0 = an;
-    sum_e += e[s];
-    sum_o += od[s];
+    if (s > 0) sum_eo = cadd(sum_eo, z[s]);
     sum_an += an;
     max_an = fmaxf(max_an, an);
   }
+  const float sum_e = sum_eo.x, sum_o = sum_eo.y;
   const float ixe = __fdividef(1.f, fast_sqrt(sum_e * sum_e + sum_o * sum_o) + kp.eps);
   const float me = sum_e * ixe, mo = sum_o * ixe;
   float energy = 0.f;
