@@ -1,7 +1,9 @@
 // Keypoint detection on the maximum-moment map (§II-A: FAST "detects edge features on
 // the maximum moment map"; Table 1: FAST threshold 0.001, at most 5000 keypoints).
 //
-//   fast_nms  : min-max normalisation of M, FAST segment test (>= arc contiguous pixels of
+//   fast_nms  : min-max normalisation of M (times one reciprocal of the range per tile;
+//               1.5 ulp, far inside the 1e-5 near-tie margin), FAST segment test (a
+//               compass-pixel precheck, then >= arc contiguous pixels of
 //               the radius-3 Bresenham circle all brighter than p + t or all darker than
 //               p - t), sum-of-differences score V, 3x3 non-maximum suppression on
 //               (V, -raster index); survivors are appended as 64-bit keys
@@ -13,10 +15,10 @@
 
 namespace rift2 {
 
-constexpr int FT = 32;          // output tile side
-constexpr int FH = 4;           // halo: 3 for the circle + 1 for the NMS
-constexpr int FS = FT + 2 * FH; // 40
-constexpr int VS = FT + 2;      // score map side (1-pixel halo)
+constexpr int FTX = 64, FTY = 32;   // output tile
+constexpr int FH = 4;                // halo: 3 for the circle + 1 for the NMS
+constexpr int FSX = FTX + 2 * FH, FSY = FTY + 2 * FH;
+constexpr int VSX = FTX + 2, VSY = FTY + 2;   // score map (1-pixel halo)
 
 // The 16-pixel Bresenham circle of radius 3 in cyclic order; compile-time offsets, so the
 // unrolled segment test reads the tile at immediate displacements.
@@ -41,48 +43,60 @@ __device__ __forceinline__ bool has_arc(unsigned m16, int arc) {
 
 __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment, int H, int W,
                                                 KParams kp, DetectWs ws) {
-  __shared__ float mn[FS][FS];
-  __shared__ float vs[VS][VS];
+  __shared__ float mn[FSY][FSX];
+  __shared__ float vs[VSY][VSX];
   const int img = blockIdx.z;
-  const int tx0 = blockIdx.x * FT, ty0 = blockIdx.y * FT;
+  const int tx0 = blockIdx.x * FTX, ty0 = blockIdx.y * FTY;
   const int ylo = HALF_PATCH, yhi = H - HALF_PATCH, xlo = HALF_PATCH, xhi = W - HALF_PATCH;
   // tiles with no candidate pixel in or next to them do nothing
-  if (tx0 - 1 >= xhi || tx0 + FT + 1 <= xlo || ty0 - 1 >= yhi || ty0 + FT + 1 <= ylo) return;
+  if (tx0 - 1 >= xhi || tx0 + FTX + 1 <= xlo || ty0 - 1 >= yhi || ty0 + FTY + 1 <= ylo) return;
   const float lo = __uint_as_float(ws.minmax[2 * img]);
   const float hi = __uint_as_float(ws.minmax[2 * img + 1]);
   if (!(hi > lo)) return;   // constant map: no keypoints
-  const float range = hi - lo;
+  const float rinv = 1.f / (hi - lo);
   const float* M = moment + (size_t)img * H * W;
-  for (int i = threadIdx.x; i < FS * FS; i += blockDim.x) {
-    int y = ty0 - FH + i / FS, x = tx0 - FH + i % FS;
+  for (int i = threadIdx.x; i < FSX * FSY; i += blockDim.x) {
+    int y = ty0 - FH + i / FSX, x = tx0 - FH + i % FSX;
     float v = 0.f;
-    if (y >= 0 && y < H && x >= 0 && x < W) v = (__ldg(M + (size_t)y * W + x) - lo) / range;
-    mn[i / FS][i % FS] = v;
+    if (y >= 0 && y < H && x >= 0 && x < W) v = (__ldg(M + (size_t)y * W + x) - lo) * rinv;
+    mn[i / FSX][i % FSX] = v;
   }
   __syncthreads();
   const float t = kp.fast_t;
-  for (int i = threadIdx.x; i < VS * VS; i += blockDim.x) {
-    int ly = i / VS, lx = i % VS;
+  for (int i = threadIdx.x; i < VSX * VSY; i += blockDim.x) {
+    int ly = i / VSX, lx = i % VSX;
     int y = ty0 - 1 + ly, x = tx0 - 1 + lx;
     float score = 0.f;
     if (y >= ylo && y < yhi && x >= xlo && x < xhi) {
       int sy = ly + FH - 1, sx = lx + FH - 1;
       float p = mn[sy][sx];
-      unsigned bright = 0, dark = 0;
-      float vb = 0.f, vd = 0.f;
+      // any run of >= arc contiguous circle pixels holds >= arc / 4 of the compass pixels
+      // 0, 4, 8, 12 (every 4 consecutive positions hold one): a pixel without that many
+      // brighter or that many darker compass pixels fails the segment test
+      int nb = 0, nd = 0;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        float q = mn[sy + kCircleDy[k]][sx + kCircleDx[k]];
-        if (q > p + t) { bright |= 1u << k; vb += q - p - t; }
-        if (q < p - t) { dark |= 1u << k; vd += p - q - t; }
+      for (int k = 0; k < 16; k += 4) {
+        const float q = mn[sy + kCircleDy[k]][sx + kCircleDx[k]];
+        nb += (q > p + t) ? 1 : 0;
+        nd += (q < p - t) ? 1 : 0;
       }
-      if (has_arc(bright, kp.fast_arc) || has_arc(dark, kp.fast_arc)) score = fmaxf(vb, vd);
+      if (max(nb, nd) >= (kp.fast_arc >> 2)) {
+        unsigned bright = 0, dark = 0;
+        float vb = 0.f, vd = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          float q = mn[sy + kCircleDy[k]][sx + kCircleDx[k]];
+          if (q > p + t) { bright |= 1u << k; vb += q - p - t; }
+          if (q < p - t) { dark |= 1u << k; vd += p - q - t; }
+        }
+        if (has_arc(bright, kp.fast_arc) || has_arc(dark, kp.fast_arc)) score = fmaxf(vb, vd);
+      }
     }
     vs[ly][lx] = score;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < FT * FT; i += blockDim.x) {
-    int ly = i / FT + 1, lx = i % FT + 1;
+  for (int i = threadIdx.x; i < FTX * FTY; i += blockDim.x) {
+    int ly = i / FTX + 1, lx = i % FTX + 1;
     float v = vs[ly][lx];
     bool keep = v > 0.f;
     if (keep) {
@@ -408,7 +422,7 @@ void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStr
 
 cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st) {
-  dim3 grid((W + FT - 1) / FT, (H + FT - 1) / FT, nimg);
+  dim3 grid((W + FTX - 1) / FTX, (H + FTY - 1) / FTY, nimg);
   fast_nms<<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
   const int kc = topk_sort_cap(kp.max_kp);
   size_t sm = (kc <= SORT_CAP ? kc : 0) * sizeof(unsigned long long);
