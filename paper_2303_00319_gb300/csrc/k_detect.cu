@@ -10,7 +10,9 @@
 //               (~bits(V) << 32 | raster index), whose ascending order is (V desc, index asc).
 //   topk_sort : one CTA per image keeps the max_keypoints smallest keys: radix refinement
 //               on 8-bit digits until the boundary bucket fits in shared memory, then a
-//               bitonic sort.  The result order is deterministic.
+//               bitonic sort (a power-of-two size up to 16384 keys; any size up to 26624
+//               keys with the missing tail treated as +inf; global memory beyond that).
+//               The result order is deterministic.
 #include "kernels.h"
 
 namespace rift2 {
@@ -151,6 +153,30 @@ __device__ void bitonic_sort(unsigned long long* s, int n) {
   }
 }
 
+// Ascending sort of n keys (any n) in shared memory as a bitonic network over the next
+// power of two N >= n, positions >= n standing for +inf keys that are never stored.  Each
+// stage k merges with the mirrored comparison (i against i ^ (k - 1)) followed by
+// half-cleaners (i against i + j), every comparator ascending; a comparator whose upper
+// position is >= n would only confirm that +inf stays on top, so it is skipped.
+__device__ void bitonic_sort_any(unsigned long long* s, int n) {
+  int N = 1;
+  while (N < n) N <<= 1;
+  const int half = N >> 1;
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int p = threadIdx.x; p < half; p += blockDim.x) {
+        const int i = 2 * j * (p / j) + (p % j);
+        const int l = (j == (k >> 1)) ? (i ^ (k - 1)) : (i + j);
+        if (l < n) {
+          const unsigned long long a = s[i], b = s[l];
+          if (a > b) { s[i] = b; s[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // The same sort for n = 1024 E keys in shared memory with 1024 threads: warp w owns
 // positions w 32E .. +32E-1, lane l the positions w 32E + l + 32 e (e < E).  Compare-exchange
 // distances j < 32 run as lane shuffles, 32 <= j < 32E inside a thread's registers, and only
@@ -217,10 +243,14 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   const unsigned K = kp.max_kp;
   unsigned kcap = 256;                 // sort size: the smallest power of two >= K
   while (kcap < K) kcap <<= 1;
-  // keys live in shared memory, or (K above the shared capacity) in this image's global
-  // sort buffer; the block-wide barriers order the global accesses the same way
+  // keys live in shared memory (a power-of-two sort of kcap keys, or K above that but
+  // within TOPK_SMEM_ANY_CAP: an any-size sort of at most that many keys), or in this
+  // image's global sort buffer; the block-wide barriers order the global accesses the
+  // same way
+  const bool any = kcap > (unsigned)SORT_CAP && K <= (unsigned)TOPK_SMEM_ANY_CAP;
+  if (any) kcap = TOPK_SMEM_ANY_CAP;
   unsigned long long* keys =
-      (kcap <= (unsigned)SORT_CAP) ? skeys : ws.sortbuf + (size_t)img * kcap;
+      (kcap <= (unsigned)SORT_CAP || any) ? skeys : ws.sortbuf + (size_t)img * kcap;
   int pbits = 0;
   unsigned long long prefix = 0;
   unsigned nsel = n;   // keys to gather: those whose top pbits bits are <= prefix
@@ -266,6 +296,7 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   int nsort = 1;
   while (nsort < (int)nsel) nsort <<= 1;
   if (nsort < 2) nsort = 2;
+  if (any) nsort = (int)nsel;   // exactly the gathered keys, no padding
   if (threadIdx.x == 0) s_sel[3] = 0;
   for (int i = threadIdx.x; i < nsort; i += blockDim.x) keys[i] = ~0ull;
   __syncthreads();
@@ -291,6 +322,7 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   if (keys == skeys && nsort == 2048) bitonic_sort_reg<2>(keys, nsort);
   else if (keys == skeys && nsort == 4096) bitonic_sort_reg<4>(keys, nsort);
   else if (keys == skeys && nsort == 8192) bitonic_sort_reg<8>(keys, nsort);
+  else if (any) bitonic_sort_any(keys, nsort);
   else bitonic_sort(keys, nsort);
   unsigned nout = n < K ? n : K;
   int* xy = fp.kp_xy[img];
@@ -425,7 +457,8 @@ cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KPa
   dim3 grid((W + FTX - 1) / FTX, (H + FTY - 1) / FTY, nimg);
   fast_nms<<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
   const int kc = topk_sort_cap(kp.max_kp);
-  size_t sm = (kc <= SORT_CAP ? kc : 0) * sizeof(unsigned long long);
+  const int skeys = kc <= SORT_CAP ? kc : (kp.max_kp <= TOPK_SMEM_ANY_CAP ? TOPK_SMEM_ANY_CAP : 0);
+  size_t sm = (size_t)skeys * sizeof(unsigned long long);
   cudaFuncSetAttribute(topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   topk_sort<<<nimg, 1024, sm, st>>>(W, kp, ws, fp);
   return cudaGetLastError();

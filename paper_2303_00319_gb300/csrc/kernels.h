@@ -48,8 +48,8 @@ struct DetectWs {
   unsigned long long* cand;     // [nimg][cap_cand]
   unsigned* cand_count;         // [nimg]
   int cap_cand;
-  unsigned long long* sortbuf;  // [nimg][topk_sort_cap(max_kp)] when that exceeds the
-                                // shared-memory sort (max_kp > 16384), else unused
+  unsigned long long* sortbuf;  // [nimg][topk_sort_cap(max_kp)] when max_kp exceeds both
+                                // shared-memory sorts (max_kp > TOPK_SMEM_ANY_CAP), else unused
 };
 // Keys the top-K sort holds: the smallest power of two >= max_kp (at least 256).
 inline int topk_sort_cap(int max_kp) {
@@ -57,7 +57,11 @@ inline int topk_sort_cap(int max_kp) {
   while (c < max_kp) c <<= 1;
   return c;
 }
-constexpr int TOPK_SMEM_CAP = 16384;
+constexpr int TOPK_SMEM_CAP = 16384;       // power-of-two sort in shared memory
+constexpr int TOPK_SMEM_ANY_CAP = 26624;   // any-size sort in shared memory (208 KB)
+inline bool topk_needs_sortbuf(int max_kp) {
+  return topk_sort_cap(max_kp) > TOPK_SMEM_CAP && max_kp > TOPK_SMEM_ANY_CAP;
+}
 cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st);
 // min = +inf bits, max = 0, candidate counts = 0 for g images

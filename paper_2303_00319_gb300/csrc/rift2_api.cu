@@ -287,7 +287,7 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   L.ccount = take((size_t)g * 4);
   L.cand = take((size_t)g * L.cap_cand * 8);
   const int kc = topk_sort_cap(max_kp);
-  L.sortbuf = take(kc > TOPK_SMEM_CAP ? (size_t)g * kc * 8 : 0);
+  L.sortbuf = take(topk_needs_sortbuf(max_kp) ? (size_t)g * kc * 8 : 0);
   L.raw = take((size_t)g * kp_cap * DESC_DIM * 2);
   L.info = take((size_t)g * kp_cap * 4);
   L.off = take((size_t)g * kp_cap * 4);

@@ -131,6 +131,22 @@ def test_detect_stage_edge_cases(pkg, dev):
     assert not r["bad"], r
 
 
+@pytest.mark.parametrize("k", [20000, 30000])
+def test_detect_stage_large_top_k(pkg, dev, k):
+    """More than 16384 keypoints per image: the any-size shared-memory sort (k <= 26624)
+    and the global-memory sort beyond it, against the oracle's detection on a noise map
+    with more NMS survivors than k."""
+    rng = np.random.default_rng(11)
+    m = rng.random((640, 800)).astype(np.float32)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=k), device=0)
+    f, = ctx.detect(torch.from_numpy(m[None].copy()).to(dev))
+    g = f.host()
+    xy, v, unc, btie = O.detect(m.astype(np.float64), O.Params(max_keypoints=k))
+    assert len(g["xy"]) == len(xy) == k
+    r = compare_keypoints(g["xy"], g["score"], xy, v, unc, btie)
+    assert not r["bad"] and r["inversions"] == 0, r
+
+
 def test_describe_stage_bit_exact(pkg, dev, small):
     ctx = small["ctx"]
     for o in (small["oa"], small["ob"]):
