@@ -7,8 +7,13 @@
 //               the radius-3 Bresenham circle all brighter than p + t or all darker than
 //               p - t), sum-of-differences score V, 3x3 non-maximum suppression on
 //               (V, -raster index); survivors are appended as 64-bit keys
-//               (~bits(V) << 32 | raster index), whose ascending order is (V desc, index asc).
-//   topk_sort : one CTA per image keeps the max_keypoints smallest keys: radix refinement
+//               (~bits(V) << 32 | raster index), whose ascending order is (V desc, index asc),
+//               and counted in a histogram of their leading 16 bits.
+//   topk_select / topk_gather : from that histogram, the digit holding rank K - 1; the keys
+//               up to it (the K smallest and the rest of that digit's bucket) compacted by
+//               many CTAs when they fit the shared-memory sort.
+//   topk_sort : one CTA per image sorts the compacted keys; without a fast selection it
+//               keeps the max_keypoints smallest keys itself: radix refinement
 //               on 8-bit digits until the boundary bucket fits in shared memory, then a
 //               bitonic sort (a power-of-two size up to 16384 keys; any size up to 26624
 //               keys with the missing tail treated as +inf; global memory beyond that).
@@ -122,12 +127,21 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(ws.cand_count + img, (unsigned)__popc(ballot));
       base = __shfl_sync(0xffffffffu, base, leader);
+      unsigned dig = 0xFFFFFFFFu;   // top 16 key bits of a stored key, else none
       if (keep) {
         unsigned pos = base + __popc(ballot & ((1u << lane) - 1));
         int y = ty0 + ly - 1, x = tx0 + lx - 1;
         unsigned long long key = ((unsigned long long)(~__float_as_uint(v)) << 32) |
                                  (unsigned)(y * W + x);
-        if (pos < (unsigned)ws.cap_cand) ws.cand[(size_t)img * ws.cap_cand + pos] = key;
+        if (pos < (unsigned)ws.cap_cand) {
+          ws.cand[(size_t)img * ws.cap_cand + pos] = key;
+          dig = (unsigned)(key >> (64 - TOPK_DIGIT_BITS));
+        }
+      }
+      if (ws.cand_hist) {   // histogram of the stored keys' leading digits (warp-aggregated)
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        if (dig != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+          atomicAdd(ws.cand_hist + ((size_t)img << TOPK_DIGIT_BITS) + dig, (unsigned)__popc(peers));
       }
     }
   }
@@ -231,6 +245,99 @@ __device__ void bitonic_sort_reg(unsigned long long* s, int n) {
   }
 }
 
+// Top-K selection from the leading-digit histogram fast_nms built: one CTA per image finds
+// the digit d holding rank K - 1 of the stored keys (or takes every digit when at most
+// topk_fast_cap keys are stored).  The keys with digit <= d are exactly the K smallest
+// plus the rest of d's bucket; when they fit the sort (below + bucket <= topk_fast_cap) the
+// gather kernel compacts them and the sort reads only those, else the sort refines on the
+// full candidate list.  sel[img] = {d, below + bucket, fast, gathered count}.
+__global__ void __launch_bounds__(1024) topk_select(KParams kp, DetectWs ws) {
+  __shared__ unsigned part[1024];
+  __shared__ unsigned s_d, s_below, s_found;
+  const int img = blockIdx.x;
+  const unsigned* h = ws.cand_hist + ((size_t)img << TOPK_DIGIT_BITS);
+  unsigned n = ws.cand_count[img];
+  if (n > (unsigned)ws.cap_cand) n = ws.cap_cand;
+  const unsigned capf = (unsigned)topk_fast_cap(kp.max_kp);
+  unsigned* sel = ws.sel + 4 * img;
+  if (n <= capf) {   // every stored key fits: no selection
+    if (threadIdx.x == 0) {
+      sel[0] = (1u << TOPK_DIGIT_BITS) - 1;
+      sel[1] = n;
+      sel[2] = 1;
+      sel[3] = 0;
+    }
+    return;
+  }
+  constexpr int PER = (1 << TOPK_DIGIT_BITS) / 1024;
+  if (threadIdx.x == 0) s_found = 0;
+  unsigned loc = 0;
+  for (int i = 0; i < PER; ++i) loc += h[threadIdx.x * PER + i];
+  part[threadIdx.x] = loc;
+  __syncthreads();
+  // inclusive block scan (Hillis-Steele in shared memory)
+  for (int d = 1; d < 1024; d <<= 1) {
+    const unsigned add = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  const unsigned rank = (unsigned)kp.max_kp - 1;
+  const unsigned incl = part[threadIdx.x], excl = incl - loc;
+  if (excl <= rank && rank < incl) {   // exactly one thread holds the rank
+    unsigned acc = excl;
+    int i = 0;
+    for (; i < PER - 1; ++i) {
+      const unsigned c = h[threadIdx.x * PER + i];
+      if (rank < acc + c) break;
+      acc += c;
+    }
+    s_d = threadIdx.x * PER + i;
+    s_below = acc;
+    s_found = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned d = s_found ? s_d : 0u, tot = s_found ? s_below + h[d] : 0u;
+    sel[0] = d;
+    sel[1] = tot;
+    sel[2] = (s_found && tot <= capf) ? 1u : 0u;
+    sel[3] = 0;
+  }
+}
+
+// Compacts the keys whose leading digit is <= sel.d into ws.comp (fast selections only).
+__global__ void __launch_bounds__(256) topk_gather(KParams kp, DetectWs ws) {
+  const int img = blockIdx.y;
+  unsigned* sel = ws.sel + 4 * img;
+  if (!sel[2]) return;
+  const unsigned d = sel[0];
+  unsigned n = ws.cand_count[img];
+  if (n > (unsigned)ws.cap_cand) n = ws.cap_cand;
+  const unsigned capf = (unsigned)topk_fast_cap(kp.max_kp);
+  const unsigned long long* cand = ws.cand + (size_t)img * ws.cap_cand;
+  unsigned long long* comp = ws.comp + (size_t)img * capf;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned b0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b0 < n; b0 += stride) {
+    const unsigned i = b0 + lane;
+    unsigned long long k = 0;
+    bool take = false;
+    if (i < n) {
+      k = cand[i];
+      take = (unsigned)(k >> (64 - TOPK_DIGIT_BITS)) <= d;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    unsigned base = 0;
+    if (lane == 0 && bal) base = atomicAdd(sel + 3, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) {
+      const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
+      if (pos < capf) comp[pos] = k;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws, FeatPtrs fp) {
   extern __shared__ unsigned long long skeys[];
   __shared__ unsigned hist[256];
@@ -254,7 +361,10 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   int pbits = 0;
   unsigned long long prefix = 0;
   unsigned nsel = n;   // keys to gather: those whose top pbits bits are <= prefix
-  if (n > kcap) {
+  // a fast selection already compacted the keys to sort (topk_select / topk_gather)
+  const bool fast = ws.sel && ws.sel[4 * img + 2];
+  if (fast) nsel = ws.sel[4 * img + 1];
+  if (!fast && n > kcap) {
     unsigned below = 0, rank = K - 1;
     while (true) {
       for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
@@ -300,7 +410,11 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   if (threadIdx.x == 0) s_sel[3] = 0;
   for (int i = threadIdx.x; i < nsort; i += blockDim.x) keys[i] = ~0ull;
   __syncthreads();
-  for (unsigned b0 = threadIdx.x & ~31u; b0 < n; b0 += blockDim.x) {
+  if (fast) {
+    const unsigned long long* comp = ws.comp + (size_t)img * topk_fast_cap(kp.max_kp);
+    for (unsigned i = threadIdx.x; i < nsel; i += blockDim.x) keys[i] = comp[i];
+  }
+  for (unsigned b0 = threadIdx.x & ~31u; !fast && b0 < n; b0 += blockDim.x) {
     const unsigned i = b0 + lane;
     unsigned long long k = 0;
     bool take = false;
@@ -455,7 +569,19 @@ void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStr
 cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
                           DetectWs ws, const FeatPtrs& fp, cudaStream_t st) {
   dim3 grid((W + FTX - 1) / FTX, (H + FTY - 1) / FTY, nimg);
+  if (!ws.cand_hist || !ws.sel || !ws.comp || !topk_multi(kp.max_kp, H, W)) {
+    ws.cand_hist = nullptr;   // single-CTA refinement only
+    ws.sel = nullptr;
+    ws.comp = nullptr;
+  } else {
+    cudaError_t e = cudaMemsetAsync(ws.cand_hist, 0, ((size_t)nimg << TOPK_DIGIT_BITS) * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
   fast_nms<<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
+  if (ws.cand_hist) {
+    topk_select<<<nimg, 1024, 0, st>>>(kp, ws);
+    topk_gather<<<dim3(16, nimg), 256, 0, st>>>(kp, ws);
+  }
   const int kc = topk_sort_cap(kp.max_kp);
   const int skeys = kc <= SORT_CAP ? kc : (kp.max_kp <= TOPK_SMEM_ANY_CAP ? TOPK_SMEM_ANY_CAP : 0);
   size_t sm = (size_t)skeys * sizeof(unsigned long long);

@@ -50,15 +50,31 @@ struct DetectWs {
   int cap_cand;
   unsigned long long* sortbuf;  // [nimg][topk_sort_cap(max_kp)] when max_kp exceeds both
                                 // shared-memory sorts (max_kp > TOPK_SMEM_ANY_CAP), else unused
+  // Multi-CTA selection (all NULL: topk_sort refines on the full list by itself):
+  unsigned* cand_hist;          // [nimg][2^TOPK_DIGIT_BITS] counts of the stored keys' leading digits
+  unsigned* sel;                // [nimg][4] digit, keys selected, fast flag, gathered count
+  unsigned long long* comp;     // [nimg][topk_fast_cap(max_kp)] the compacted selection
 };
 // Keys the top-K sort holds: the smallest power of two >= max_kp (at least 256).
-inline int topk_sort_cap(int max_kp) {
+__host__ __device__ inline int topk_sort_cap(int max_kp) {
   int c = 256;
   while (c < max_kp) c <<= 1;
   return c;
 }
 constexpr int TOPK_SMEM_CAP = 16384;       // power-of-two sort in shared memory
 constexpr int TOPK_SMEM_ANY_CAP = 26624;   // any-size sort in shared memory (208 KB)
+constexpr int TOPK_DIGIT_BITS = 16;       // leading key bits of the selection histogram
+// Keys a fast selection may hand to the shared-memory sort (0: the global-memory sort
+// always refines on the full list).
+__host__ __device__ inline int topk_fast_cap(int max_kp) {
+  const int kc = topk_sort_cap(max_kp);
+  return kc <= TOPK_SMEM_CAP ? kc : (max_kp <= TOPK_SMEM_ANY_CAP ? TOPK_SMEM_ANY_CAP : 0);
+}
+// The multi-CTA selection pays for its histogram and two extra launches only when an image
+// can hold many more candidates than one CTA scans quickly: maps above 4 MPix.
+inline bool topk_multi(int max_kp, int H, int W) {
+  return topk_fast_cap(max_kp) > 0 && (long long)H * W > (1ll << 22);
+}
 inline bool topk_needs_sortbuf(int max_kp) {
   return topk_sort_cap(max_kp) > TOPK_SMEM_CAP && max_kp > TOPK_SMEM_ANY_CAP;
 }

@@ -182,7 +182,7 @@ int check_size(int H, int W) {
 // ------------------------------------------------------------------ tracing
 // Kernels enqueued by each launcher (kept next to the launch sequences they count).
 constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_LG_ROWS = 1, K_NOISE = 6, K_MOMENT = 1,
-              K_DETECT = 2, K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1,
+              K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1,
               K_MERGE = 1;
 
 cudaEvent_t take_event(rift2_ctx* c) {
@@ -254,9 +254,13 @@ int tune_col_tile(rift2_ctx* c, const float2* spec, float2* scratch, int g, int 
 }
 
 // ------------------------------------------------------------------ workspace layout
+// Kernels one launch_detect issues: FAST + sort, plus the multi-CTA selection's two
+// kernels when it runs for this keypoint budget and map size.
+static int detect_launches(int max_kp, int H, int W) { return topk_multi(max_kp, H, W) ? 4 : 2; }
+
 struct Layout {
   size_t spec, scratch, er, q, an0, amp, pc, moment, mim, mhist, mstate, noise, minmax, ccount,
-      cand, sortbuf, raw, info, off, total;
+      cand, sortbuf, chist, sel, comp, raw, info, off, total;
   // corner keypoints (RIFT2_FLAG_CORNERS): minimum-moment map, its min / max, candidate
   // count, the corner list before the merge, and the bitmap of edge-keypoint pixels
   size_t mcorner, minmax_c, ccount_c, cxy, csc, ccnt, bits;
@@ -288,6 +292,10 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   L.cand = take((size_t)g * L.cap_cand * 8);
   const int kc = topk_sort_cap(max_kp);
   L.sortbuf = take(topk_needs_sortbuf(max_kp) ? (size_t)g * kc * 8 : 0);
+  const bool multi = topk_multi(max_kp, H, W);
+  L.chist = take(multi ? (size_t)g * ((size_t)1 << TOPK_DIGIT_BITS) * 4 : 0);
+  L.sel = take(multi ? (size_t)g * 4 * 4 : 0);
+  L.comp = take(multi ? (size_t)g * topk_fast_cap(max_kp) * 8 : 0);
   L.raw = take((size_t)g * kp_cap * DESC_DIM * 2);
   L.info = take((size_t)g * kp_cap * 4);
   L.off = take((size_t)g * kp_cap * 4);
@@ -474,9 +482,11 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
                               corners ? at<float>(ws, L.mcorner) : nullptr, minmax_c, st));
   }
   DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand,
-              at<unsigned long long>(ws, L.sortbuf)};
+              at<unsigned long long>(ws, L.sortbuf), at<unsigned>(ws, L.chist),
+              at<unsigned>(ws, L.sel), at<unsigned long long>(ws, L.comp)};
   {
-    StageScope sc(c, RIFT2_STAGE_DETECT, st, corners ? 2 * K_DETECT + K_MERGE : K_DETECT);
+    const int kd = detect_launches(c->kp.max_kp, H, W);
+    StageScope sc(c, RIFT2_STAGE_DETECT, st, corners ? 2 * kd + K_MERGE : kd);
     RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
     if (corners) {
       // corner keypoints on the minimum moment into the side list, then appended
@@ -490,7 +500,8 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
         fc.counts[i] = ccnt + 2 * i;
       }
       DetectWs dwc{minmax_c, at<unsigned long long>(ws, L.cand), ccount_c, L.cap_cand,
-                   at<unsigned long long>(ws, L.sortbuf)};
+                   at<unsigned long long>(ws, L.sortbuf), at<unsigned>(ws, L.chist),
+                   at<unsigned>(ws, L.sel), at<unsigned long long>(ws, L.comp)};
       RIFT2_CU(launch_detect(at<float>(ws, L.mcorner), g, H, W, c->kp, dwc, fc, st));
       RIFT2_CU(launch_merge_corners(g, H, W, c->kp, fp, cxy, csc, ccnt, at<unsigned>(ws, L.bits), st));
     }
@@ -783,13 +794,14 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
     if (rc) return rc;
     unsigned* minmax = at<unsigned>(c->ws, L.minmax);
     unsigned* ccount = at<unsigned>(c->ws, L.ccount);
-    c->launches += K_INIT + 1 + K_DETECT;
+    c->launches += K_INIT + 1 + detect_launches(c->kp.max_kp, H, W);
     launch_init_detect(minmax, ccount, g, st);
     const float* m = moment + (size_t)i0 * P;
     launch_minmax(m, g, P, minmax, st);
     FeatPtrs fp = feat_ptrs(out + i0, g);
     DetectWs dw{minmax, at<unsigned long long>(c->ws, L.cand), ccount, L.cap_cand,
-                at<unsigned long long>(c->ws, L.sortbuf)};
+                at<unsigned long long>(c->ws, L.sortbuf), at<unsigned>(c->ws, L.chist),
+                at<unsigned>(c->ws, L.sel), at<unsigned long long>(c->ws, L.comp)};
     RIFT2_CU(launch_detect(m, g, H, W, c->kp, dw, fp, st));
   }
   return RIFT2_OK;

@@ -147,6 +147,30 @@ def test_detect_stage_large_top_k(pkg, dev, k):
     assert not r["bad"] and r["inversions"] == 0, r
 
 
+@pytest.mark.parametrize("k,pattern", [(5000, "noise"), (20000, "noise"), (300, "dots")])
+def test_detect_stage_multi_cta_selection(pkg, dev, k, pattern):
+    """Maps above 4 MPix select the top K from a histogram of the candidates' leading key
+    bits with many CTAs: against the oracle on a 2048 x 2112 noise map (the boundary
+    bucket fits the sort), and on a grid of isolated bright pixels, ~250000 corners with
+    one and the same score, whose bucket overflows the sort and sends it back to refining
+    on the full list (ties ordered by raster index)."""
+    if pattern == "noise":
+        m = np.random.default_rng(12).random((2048, 2112)).astype(np.float32)
+    else:
+        m = np.zeros((2048, 2112), np.float32)
+        m[2::4, 3::4] = 1.0
+    ctx = pkg.Context(pkg.default_params(max_keypoints=k), device=0)
+    f, = ctx.detect(torch.from_numpy(m[None].copy()).to(dev))
+    g = f.host()
+    xy, v, unc, btie = O.detect(m.astype(np.float64), O.Params(max_keypoints=k))
+    assert len(g["xy"]) == len(xy) == k
+    r = compare_keypoints(g["xy"], g["score"], xy, v, unc, btie)
+    assert not r["bad"] and r["inversions"] == 0, r
+    if pattern == "dots":   # equal FP32 scores: raster order
+        ridx = g["xy"][:, 1].astype(np.int64) * m.shape[1] + g["xy"][:, 0]
+        assert np.all(np.diff(ridx) > 0) and np.all(g["score"] == g["score"][0])
+
+
 def test_describe_stage_bit_exact(pkg, dev, small):
     ctx = small["ctx"]
     for o in (small["oa"], small["ob"]):
