@@ -263,8 +263,8 @@ struct RegShape<512> {
   static constexpr int T = 16, R0 = 32, R1 = 16, R2 = 1, NT = 256;
 };
 template <>
-struct RegShape<1024> {
-  static constexpr int T = 32, R0 = 32, R1 = 32, R2 = 1, NT = 256;
+struct RegShape<1024> {   // one row (its four scale transforms) per 128-thread CTA
+  static constexpr int T = 32, R0 = 32, R1 = 32, R2 = 1, NT = 128;
 };
 template <>
 struct RegShape<2048> {

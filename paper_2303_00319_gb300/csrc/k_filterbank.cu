@@ -398,9 +398,10 @@ __device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParam
   const float sum_e = sum_eo.x, sum_o = sum_eo.y;
   const float ixe = __fdividef(1.f, fast_sqrt(sum_e * sum_e + sum_o * sum_o) + kp.eps);
   const float me = sum_e * ixe, mo = sum_o * ixe;
-  float energy = 0.f;
+  // sum_s (E_s mE + O_s mO) = mE sum E + mO sum O: the projections once, on the sums
+  float energy = fmaf(sum_e, me, sum_o * mo);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) energy += e[s] * me + od[s] * mo - fabsf(e[s] * mo - od[s] * me);
+  for (int s = 0; s < NS; ++s) energy -= fabsf(e[s] * mo - od[s] * me);
   const float width = (sum_an * __fdividef(1.f, max_an + kp.eps) - 1.f) * kp.inv_ns1;
   const float wgt = __fdividef(1.f, 1.f + __expf((kp.cutoff - width) * kp.g));
   er = energy;

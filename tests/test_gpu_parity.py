@@ -85,6 +85,24 @@ def test_noise_threshold(small):
     np.testing.assert_allclose(t, small["oa"].maps["T"], rtol=1e-5)
 
 
+def test_noise_threshold_concentrated_amplitudes(pkg, dev):
+    """A grating's filter responses have one amplitude everywhere (|EO| = |G(k)| / 2 for a
+    one-sided filter), so every |EO_0,o| falls in one 12-bit bucket of the median's
+    selection and overflows its compaction: the last two digits are then selected on the
+    whole slice.  T_o against the oracle (absolute tolerance: orientations whose window
+    misses the grating have amplitudes at FP32 round-off)."""
+    h, w = 256, 320
+    y, x = np.mgrid[0:h, 0:w]
+    img = (0.5 + 0.4 * np.cos(2 * np.pi * (96 * x / w + 13 * y / h))).astype(np.float32)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=100), device=0)
+    f, = ctx.extract([torch.from_numpy(img).to(dev)], debug=True)
+    ctx.sync()
+    t = f.debug["noise_t"].cpu().numpy()
+    o = O.extract(img.astype(np.float64), O.Params(max_keypoints=100), keep_maps=True)
+    np.testing.assert_allclose(t, o.maps["T"], rtol=1e-5, atol=1e-5 * float(np.max(o.maps["T"])))
+    assert np.max(o.maps["T"]) > 0
+
+
 def test_pc_terms_and_moment(small):
     d = {k: v.cpu().numpy() for k, v in small["fa"].debug.items()}
     m = small["oa"].maps
