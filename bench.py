@@ -9,7 +9,9 @@ gamma speckle; at most 5000 keypoints per image).  Prints one JSON line on rank 
 
 --workload 2 times the uneven batch (64 pairs, sides 384..2048 step 128, <= 4000
 keypoints) and --workload 3 the 4096^2 scene (<= 20000 keypoints); the default line also
-carries an open-loop serving sweep (Poisson arrivals at 50..400 pairs/s).
+carries an open-loop serving sweep (Poisson arrivals at 50..400 pairs/s).  Besides the
+headline (one context, one stream) the line reports the same step as one replayed CUDA
+graph (graph_form) and split between two contexts on two streams (two_lane_form).
 
 Multi-GPU: independent replicas (the pairs shard with no exchange step); launched with
 torch.distributed.run, one rank per GPU, timing = max over ranks.
@@ -388,6 +390,44 @@ def run_ours(args):
                  "form": "one CUDA graph per batch (extract + match of every pair), replayed"}
         del g
 
+    # two-lane form: the batch split between two contexts on two streams, forked from and
+    # joined back to the timing stream every step, so that one lane's under-filled stages
+    # (top-K sort, median selection, re-rank) overlap the other lane's full-GPU kernels
+    lanes = None
+    if not args.no_lanes and B >= 2:
+        half = B // 2
+        ctx2 = pkg.Context(pkg.default_params(max_keypoints=max_kp, flags=pkg.FLAG_AUTOTUNE),
+                           device=local, hbm_budget=96 << 30)
+        s_a, s_b = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+        def step_lanes(imgs):
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            s_a.wait_event(fork)
+            s_b.wait_event(fork)
+            ctx.extract([imgs[i] for i in range(2 * half)], feats[:2 * half], stream=s_a)
+            ctx.match(feats[0:2 * half:2], feats[1:2 * half:2], matches[:half], stream=s_a)
+            ctx2.extract([imgs[i] for i in range(2 * half, 2 * B)], feats[2 * half:], stream=s_b)
+            ctx2.match(feats[2 * half::2], feats[2 * half + 1::2], matches[half:], stream=s_b)
+            stream.wait_stream(s_a)
+            stream.wait_stream(s_b)
+
+        for i in range(args.warmup):
+            step_lanes(devb[i % rot])
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            step_lanes(devb[i % rot])
+        e1.record(stream)
+        e1.synchronize()
+        lms = e0.elapsed_time(e1)
+        barrier()
+        lanes = {"value": whole_job_rate(world, B, args.steps, max_over_ranks(lms, dev)),
+                 "unit": "pairs/s", "ms_per_step": lms / args.steps,
+                 "form": f"two contexts on two streams, {half} + {B - half} pairs per step"}
+        ctx2.close()
+
     # plain form: one pair per call, no grouping, CUDA-core matcher
     plain = None
     if not args.no_plain and args.workload == 1:
@@ -528,6 +568,7 @@ def run_ours(args):
             "mpix_per_s": value * px_per_step / B / 1e6,
             "plain_form": plain,
             "graph_form": graph,
+            "two_lane_form": lanes,
             "serving": serving,
             "rift_baseline": rift,
             "corners_form": corners,
@@ -593,6 +634,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-rift", action="store_true", help="skip the RIFT-ring baseline")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay form")
+    ap.add_argument("--no-lanes", action="store_true", help="skip the two-stream form")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the open-loop serving run (0: skip)")
     ap.add_argument("--serve-rate", default="50,100,200,400",
