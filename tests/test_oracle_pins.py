@@ -372,6 +372,32 @@ def test_median_even_count():
     assert O.median_even_mean(x) == sorted(x)[500]
 
 
+def test_step_edge_phase_congruency_invariants():
+    """A bright vertical stripe on an odd-width circle (edges between columns 39 | 40 and
+    120 | 121, no Nyquist column): phase congruency lies in [0, 1], is the same on every
+    row, is zero for the orientations whose angular window misses the horizontal
+    frequency axis (60, 90, 120 degrees), mirrors under x -> 160 - x with orientation o
+    going to -o (the stripe maps to itself; global sign and conjugation leave PC
+    unchanged), sits on the edges only, and puts the maximum moment there."""
+    img = np.full((128, 161), 0.2)
+    img[:, 40:121] = 0.8
+    p = O.Params()
+    pc, _ = O.phase_congruency(O.responses(img, p), p)
+    M, m = O.moments(pc, p)
+    assert pc.min() >= 0.0 and pc.max() <= 1.0
+    assert np.array_equal(pc, np.broadcast_to(pc[:, :1, :], pc.shape))
+    for o in (2, 3, 4):
+        assert pc[o].max() < 1e-12
+    mir = pc[:, :, ::-1]
+    for o in range(6):
+        np.testing.assert_allclose(pc[o], mir[(6 - o) % 6], atol=1e-12)
+    # PC only next to the edges; the stripe's centre and the background far from it see none
+    assert pc[0, 64, 80] == 0.0 and pc[0, 64, 0] == 0.0
+    assert pc[0, 64, 39] > 0.3 and pc[0, 64, 40] > 0.3
+    assert set(np.argsort(M[64])[-4:].tolist()) == {39, 40, 120, 121}
+    assert np.all(M >= m)
+
+
 def test_moments_of_single_orientation():
     # PC only in orientation o: M = PC^2 (edge), m ~ 0 (no corner)
     pc = np.zeros((6, 1, 1))
