@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H
   }
 }
 
+constexpr int REG_NT = 256;   // threads per CTA of the register-tiled row kernels
+
 // ------------------------------------------------------- register-tiled forward DFT
 // Sum over the T threads of one transform group (T <= 32: shuffles inside the group's
 // lanes; T > 32: through shared memory, one slot per thread).
