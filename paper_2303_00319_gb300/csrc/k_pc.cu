@@ -44,10 +44,25 @@ __global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0
       if (pre == pre1) atomicAdd(&h[1][dig], 1u);
     }
   };
-  // 16-byte loads when the slice is 16-byte aligned (P % 4 == 0), scalar otherwise
+  // 16-byte loads when the slice is 16-byte aligned (P % 4 == 0), scalar otherwise; four
+  // loads per thread in flight before their values are counted
   if ((P & 3) == 0) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
-    for (long long i = beg / 4 + threadIdx.x; i < end / 4; i += blockDim.x) {
+    const long long e4 = end / 4;
+    long long i = beg / 4 + threadIdx.x;
+    for (; i + 3 * (long long)blockDim.x < e4; i += 4 * (long long)blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(s4 + i + u * (long long)blockDim.x);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        one(__float_as_uint(v[u].x));
+        one(__float_as_uint(v[u].y));
+        one(__float_as_uint(v[u].z));
+        one(__float_as_uint(v[u].w));
+      }
+    }
+    for (; i < e4; i += blockDim.x) {
       const float4 v = __ldg(s4 + i);
       one(__float_as_uint(v.x));
       one(__float_as_uint(v.y));
@@ -65,59 +80,71 @@ __global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0
   }
 }
 
-// One warp per target rank (warp 0: lower middle, warp 1: upper middle).
-__global__ void __launch_bounds__(64) median_select(long long P, int round, float noise_c,
-                                                    MedianWs ws) {
+// 256 threads: each sums its slice of the bins of both ranks' histograms, a block-wide
+// scan locates the bins holding the two target ranks.
+__global__ void __launch_bounds__(256) median_select(long long P, int round, float noise_c,
+                                                     MedianWs ws) {
+  __shared__ unsigned part[2][256];
+  __shared__ unsigned s_dig[2], s_rank[2];
   const int o = blockIdx.x, img = blockIdx.y;
-  const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
   unsigned* gh = ws.hist + ((size_t)img * NO + o) * 2 * MED_BINS;
   unsigned* st = ws.state + ((size_t)img * NO + o) * 4;
   const int nbins = (round == 2) ? 256 : MED_BINS;
   const int shift = (round == 2) ? 8 : 12;
-  const unsigned* hist = gh + ((round == 0) ? 0 : t) * MED_BINS;
-  unsigned prefix, rank;
-  if (round == 0) {
-    prefix = 0;
-    rank = (unsigned)(t == 0 ? (P - 1) / 2 : P / 2);
-  } else {
-    prefix = st[2 * t];
-    rank = st[2 * t + 1];
-  }
-  const int per = nbins / 32;
-  unsigned lsum = 0;
-  for (int i = 0; i < per; ++i) lsum += hist[lane * per + i];
-  unsigned incl = lsum;
-  for (int d = 1; d < 32; d <<= 1) {
-    unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += y;
-  }
-  unsigned excl = incl - lsum;
-  unsigned hit = __ballot_sync(0xffffffffu, excl <= rank && rank < incl);
-  int src = hit ? __ffs(hit) - 1 : 31;
-  unsigned dig = 0, newrank = 0;
-  if (lane == src) {
-    unsigned acc = excl;
-    int i = 0;
-    for (; i < per - 1; ++i) {
-      unsigned c = hist[lane * per + i];
-      if (rank < acc + c) break;
-      acc += c;
+  const int per = nbins / 256;
+  unsigned prefix[2], rank[2], loc[2];
+  for (int t = 0; t < 2; ++t) {
+    if (round == 0) {
+      prefix[t] = 0;
+      rank[t] = (unsigned)(t == 0 ? (P - 1) / 2 : P / 2);
+    } else {
+      prefix[t] = st[2 * t];
+      rank[t] = st[2 * t + 1];
     }
-    dig = lane * per + i;
-    newrank = rank - acc;
+    const unsigned* hist = gh + ((round == 0) ? 0 : t) * MED_BINS;
+    unsigned sum = 0;
+    for (int i = 0; i < per; ++i) sum += hist[tid * per + i];
+    loc[t] = sum;
+    part[t][tid] = sum;
   }
-  dig = __shfl_sync(0xffffffffu, dig, src);
-  newrank = __shfl_sync(0xffffffffu, newrank, src);
-  __syncthreads();   // every warp has read the histogram
-  if (lane == 0) {
-    st[2 * t] = (prefix << shift) | dig;
-    st[2 * t + 1] = newrank;
+  if (tid < 2) {
+    s_dig[tid] = nbins - 1;
+    s_rank[tid] = 0;
   }
-  for (int i = threadIdx.x; i < 2 * MED_BINS; i += blockDim.x) gh[i] = 0;   // ready for next round
+  __syncthreads();
+  for (int d = 1; d < 256; d <<= 1) {
+    const unsigned a0 = tid >= d ? part[0][tid - d] : 0u, a1 = tid >= d ? part[1][tid - d] : 0u;
+    __syncthreads();
+    part[0][tid] += a0;
+    part[1][tid] += a1;
+    __syncthreads();
+  }
+  for (int t = 0; t < 2; ++t) {
+    const unsigned incl = part[t][tid], excl = incl - loc[t];
+    if (excl <= rank[t] && rank[t] < incl) {
+      const unsigned* hist = gh + ((round == 0) ? 0 : t) * MED_BINS;
+      unsigned acc = excl;
+      int i = 0;
+      for (; i < per - 1; ++i) {
+        const unsigned c = hist[tid * per + i];
+        if (rank[t] < acc + c) break;
+        acc += c;
+      }
+      s_dig[t] = tid * per + i;
+      s_rank[t] = rank[t] - acc;
+    }
+  }
+  __syncthreads();   // every thread has read the histogram
+  if (tid < 2) {
+    st[2 * tid] = (prefix[tid] << shift) | s_dig[tid];
+    st[2 * tid + 1] = s_rank[tid];
+  }
+  for (int i = tid; i < 2 * MED_BINS; i += blockDim.x) gh[i] = 0;   // ready for next round
   if (round == 2) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-      float v0 = __uint_as_float(st[0]), v1 = __uint_as_float(st[2]);
+    if (tid == 0) {
+      const float v0 = __uint_as_float(st[0]), v1 = __uint_as_float(st[2]);
       ws.noise_t[img * NO + o] = 0.5f * (v0 + v1) * noise_c;
     }
   }
@@ -131,7 +158,7 @@ cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, cons
   if (chunks < 1) chunks = 1;
   for (int r = 0; r < 3; ++r) {
     median_hist<<<dim3(chunks, NO, nimg), 512, 0, st>>>(an0, P, r, ws);
-    median_select<<<dim3(NO, nimg), 64, 0, st>>>(P, r, kp.noise_c, ws);
+    median_select<<<dim3(NO, nimg), 256, 0, st>>>(P, r, kp.noise_c, ws);
   }
   return cudaGetLastError();
 }
