@@ -80,8 +80,11 @@ __global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0
   }
 }
 
-// 256 threads: each sums its slice of the bins of both ranks' histograms, a block-wide
-// scan locates the bins holding the two target ranks.
+// One CTA per (image, orientation) and round, for both middle ranks (lower = (P-1)/2,
+// upper = P/2): each of 256 threads sums its slice of the bins of both ranks' histograms,
+// a block-wide scan locates the bin holding each rank, and the state becomes (prefix with
+// that digit appended, rank within the bin).  The histograms are cleared for the next
+// round; after the last round T_o follows from the two middle values.
 __global__ void __launch_bounds__(256) median_select(long long P, int round, float noise_c,
                                                      MedianWs ws) {
   __shared__ unsigned part[2][256];
