@@ -372,6 +372,37 @@ def test_median_even_count():
     assert O.median_even_mean(x) == sorted(x)[500]
 
 
+def test_energy_polar_form_and_frequency_spread():
+    """The phase-congruency energy in its polar form: for scale components A_s e^(i phi_s)
+    with mean phase phibar = arg(sum_s A_s e^(i phi_s)), Er = sum_s A_s (cos(phi_s - phibar)
+    - |sin(phi_s - phibar)|) (eps -> 0).  Two equal components in quadrature give zero
+    energy, components in phase give sum A.  The frequency-spread width is 1 for equal
+    amplitudes on all scales and 0 for one scale alone, fixing the weight."""
+    p = O.Params(eps=1e-15)
+    rng = np.random.default_rng(5)
+    amp = rng.uniform(0.1, 2.0, (4, 64))
+    phi = rng.uniform(-math.pi, math.pi, (4, 64))
+    eo = (amp * np.exp(1j * phi))[:, None, None, :]          # [Ns][No=1][1][64]
+    er, q, an0, a_sum = O.pc_terms(eo, p)
+    phibar = np.angle((amp * np.exp(1j * phi)).sum(axis=0))
+    d = phi - phibar
+    polar = (amp * (np.cos(d) - np.abs(np.sin(d)))).sum(axis=0)
+    np.testing.assert_allclose(er[0, 0], polar, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(a_sum[0, 0], amp.sum(axis=0), rtol=1e-12)
+    np.testing.assert_allclose(an0[0, 0], amp[0], rtol=1e-12)
+    # quadrature pair (the other scales silent) and an in-phase set
+    quad = np.array([1.0, 1j, 0.0, 0.0])[:, None, None, None] * np.exp(0.7j)
+    assert abs(O.pc_terms(quad, p)[0][0, 0, 0]) < 1e-12
+    inph = np.array([0.3, 1.1, 0.6, 2.0])[:, None, None, None] * np.exp(-2.1j)
+    assert abs(O.pc_terms(inph, p)[0][0, 0, 0] - 4.0) < 1e-12
+    # spread weight: width 1 (equal amplitudes) and 0 (one scale), q = w / sum A
+    w = lambda width: 1.0 / (1.0 + math.exp((p.cutoff - width) * p.g))
+    eq = np.full((4, 1, 1, 1), 0.5 + 0.5j)
+    assert abs(O.pc_terms(eq, p)[1][0, 0, 0] - w(1.0) / (4 * abs(0.5 + 0.5j))) < 1e-12
+    one = np.array([0.0, 0.8, 0.0, 0.0])[:, None, None, None] + 0j
+    assert abs(O.pc_terms(one, p)[1][0, 0, 0] - w(0.0) / 0.8) < 1e-12
+
+
 def test_step_edge_phase_congruency_invariants():
     """A bright vertical stripe on an odd-width circle (edges between columns 39 | 40 and
     120 | 121, no Nyquist column): phase congruency lies in [0, 1], is the same on every
