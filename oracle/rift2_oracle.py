@@ -32,8 +32,11 @@ Pins (tests/test_oracle_*.py): FFT vs a direct DFT; filter properties (peak, ban
 low-pass half point, raised-cosine window values, partition of unity, one-sidedness);
 grating closed form for |EO| and MIM; 90-degree rotation invariant of MIM and of the
 recoded histograms; the paper's worked histogram example (§III); FAST on hand-built
-patterns and brute force; NN brute force.  Phase congruency and the moment map are pinned
-only by invariants and the grating closed form ("parity partially unpinned").
+patterns and brute force; NN brute force; the phase-congruency energy against its polar
+form with quadrature / in-phase special cases and the spread weight at widths 0 and 1;
+step-edge and single-orientation invariants of PC and the moments.  The paper prints no
+phase-congruency formula, so those pins hold PC and the moment map to the reading R2/R3,
+not to the paper ("parity partially unpinned").
 """
 from __future__ import annotations
 
