@@ -271,6 +271,25 @@ int rift2_profile_read(rift2_ctx* ctx, int n, double* ms, long long* count);
 long long rift2_launch_count(const rift2_ctx* ctx);
 
 /* ------------------------------------------------------------------------------
+ * Capacities and failure paths (no counterpart in the paper).
+ * ---------------------------------------------------------------------------- */
+
+/* The buffer capacities this context's calls require (the worst case of its parameters):
+ * rift2_features.cap_kp, .cap_desc and rift2_matches.cap.  A call given less returns
+ * RIFT2_E_CAPACITY before enqueuing anything; this reports the counts it needed.  Any
+ * pointer may be NULL.  Errors: RIFT2_E_INVAL (NULL context). */
+int rift2_required_capacity(const rift2_ctx* ctx, int* cap_kp, int* cap_desc, int* cap_match);
+
+/* Iteration limit of the FIRST bounded wait on each staged patch half in the descriptor
+ * kernel (default 2^24 polls of mbarrier.try_wait, far beyond a copy's latency).  When it
+ * runs out the kernel latches RIFT2_E_TIMEOUT in the status word, waits for its copies in
+ * flight with the full default limit (so none outlives the kernel) and returns; the
+ * descriptors of that call are then invalid and rift2_sync reports RIFT2_E_TIMEOUT.  0
+ * makes every such wait give up at once: a way to exercise the timeout path without a
+ * fault.  Errors: RIFT2_E_INVAL (NULL context, iters < 0). */
+int rift2_set_wait_limit(rift2_ctx* ctx, long long iters);
+
+/* ------------------------------------------------------------------------------
  * Stage entry points.  Each runs one stage of the pipeline on caller-supplied inputs
  * so that the stage can be checked against the oracle in isolation (an oracle near-tie
  * upstream then cannot cascade).  Same conventions as above.
@@ -310,9 +329,14 @@ int rift2_describe(rift2_ctx* ctx, int n, const unsigned char* mim, int height, 
  * exits.  A map needs ceil(H/2) * ceil(W/2) slots (any 1024 x 1024 map fits); larger
  * maps are refused with RIFT2_E_CAPACITY before anything is enqueued.
  *  - params: NULL for the defaults; out: kp_xy, kp_score, counts (cap_kp >= max_keypoints).
- *  - Runs on the calling thread's current device and the given stream.  The first call
- *    on a device looks up the array's device address; make that first call before any
- *    CUDA stream capture.
+ *  - Runs on the calling thread's current device and the given stream; `moment` and the
+ *    three output buffers must be device memory of that device (RIFT2_E_INVAL otherwise,
+ *    checked with cudaPointerGetAttributes before anything is enqueued).
+ *  - The first call on a device looks up the array's device address; make that first call
+ *    before any CUDA stream capture.  The address belongs to the device's primary context:
+ *    the library keeps the context's handle beside it and looks the address up again when
+ *    a later call finds another context current (e.g. after cudaDeviceReset); such a call
+ *    is again a first call and must not happen during a capture.
  *  - Every call shares the one array (it keeps the last call's contents; each call resets
  *    what must start at zero).  Calls whose work overlaps on the GPU (other streams, other
  *    host threads, concurrent graph launches) race on it: serialise them.

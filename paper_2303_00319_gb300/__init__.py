@@ -29,7 +29,8 @@ DESC_DIM = CELLS * CELLS * NO
 EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_extract",
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
-           "rift2_describe", "rift2_detect_static", "rift2_tuned_tile")
+           "rift2_describe", "rift2_detect_static", "rift2_tuned_tile",
+           "rift2_required_capacity", "rift2_set_wait_limit")
 STATIC_MAX_CANDIDATES = 262144
 STAGES = ("fft_fwd", "lg_cols", "lg_rows", "noise", "moment", "detect", "describe", "match")
 
@@ -92,6 +93,9 @@ def lib():
         L.rift2_launch_count.argtypes = [C.c_void_p]
         L.rift2_launch_count.restype = C.c_longlong
         L.rift2_tuned_tile.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.rift2_required_capacity.argtypes = [C.c_void_p, C.POINTER(C.c_int),
+                                              C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.rift2_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
         L.rift2_fft2.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                  C.c_void_p]
         L.rift2_detect.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
@@ -125,6 +129,17 @@ def default_params(**overrides) -> Params:
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _require(t, name: str, dtype, ndim: int):
+    """A dense CUDA tensor of the given dtype and rank: the C ABI reads it as a plain
+    row-major array, so a strided view would be read wrongly without an error."""
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or t.dim() != ndim:
+        raise ValueError(f"{name} must be a {ndim}-D {dtype} tensor, got {t.dim()}-D {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
 
 
 def _stream(stream):
@@ -265,6 +280,8 @@ class Context:
             feats = [self.alloc_features(tuple(im.shape) if debug else None) for im in images]
         arr = (Image * n)()
         for i, im in enumerate(images):
+            if not isinstance(im, torch.Tensor) or im.device.type != "cuda":
+                raise ValueError("images must be CUDA tensors")
             if im.dtype != torch.float32 or im.dim() != 2 or im.stride(1) != 1:
                 raise ValueError("images must be 2-D float32 with unit column stride")
             arr[i] = Image(im.data_ptr(), im.shape[0], im.shape[1], im.stride(0))
@@ -306,6 +323,18 @@ class Context:
     def launch_count(self) -> int:
         return int(lib().rift2_launch_count(self._h))
 
+    def required_capacity(self) -> dict:
+        """Buffer capacities this context's calls require (cap_kp, cap_desc, cap_match)."""
+        v = [C.c_int(), C.c_int(), C.c_int()]
+        _check(lib().rift2_required_capacity(self._h, *[C.byref(x) for x in v]),
+               "rift2_required_capacity")
+        return dict(cap_kp=v[0].value, cap_desc=v[1].value, cap_match=v[2].value)
+
+    def set_wait_limit(self, iters: int = 1 << 24):
+        """First-wait limit of the descriptor kernel's staged copies (0: give up at once,
+        which exercises the RIFT2_E_TIMEOUT path; the default restores normal waits)."""
+        _check(lib().rift2_set_wait_limit(self._h, int(iters)), "rift2_set_wait_limit")
+
     def tuned_tile(self, height: int, width: int) -> int:
         """Column tile the autotuner kept for this size (0: none tuned)."""
         return int(lib().rift2_tuned_tile(self._h, height, width))
@@ -313,6 +342,7 @@ class Context:
     # ---- stage entry points
     def fft2(self, img, stream=None):
         """img: float32 CUDA [n][H][W] contiguous -> complex64 [n][H][W]."""
+        _require(img, "img", torch.float32, 3)
         n, h, w = img.shape
         out = torch.empty((n, h, w), dtype=torch.complex64, device=img.device)
         _check(lib().rift2_fft2(self._h, n, _ptr(img), h, w, _ptr(out), _stream(stream)),
@@ -320,6 +350,8 @@ class Context:
         return out
 
     def detect(self, moment, feats=None, stream=None):
+        """moment: float32 CUDA [n][H][W] contiguous maximum-moment maps."""
+        _require(moment, "moment", torch.float32, 3)
         n, h, w = moment.shape
         if feats is None:
             feats = [self.alloc_features() for _ in range(n)]
@@ -331,6 +363,8 @@ class Context:
         return feats
 
     def describe(self, mim, feats, stream=None):
+        """mim: uint8 CUDA [n][H][W] contiguous maximum index maps (values 0..No-1)."""
+        _require(mim, "mim", torch.uint8, 3)
         n, h, w = mim.shape
         fc = (FeaturesC * n)()
         for i, f in enumerate(feats):
@@ -343,11 +377,15 @@ class Context:
 def detect_static(moment, feats: Features, params: Params | None = None, stream=None):
     """Keypoints of one moment map [H][W] (float32, CUDA) without any device allocation by
     the library (rift2_detect_static): for callers that must not allocate device memory.
-    `feats` supplies the output buffers.  Calls that overlap on the GPU share one static
-    scratch array and must be serialised."""
+    `feats` supplies the output buffers.  The call runs on the map's device (made current
+    for the call) and on `stream`, by default that device's current stream.  Calls that
+    overlap on the GPU share one static scratch array and must be serialised."""
+    _require(moment, "moment", torch.float32, 2)
     h, w = moment.shape
     fc, _ = feats.to_c()
     p = C.byref(params) if params is not None else None
-    _check(lib().rift2_detect_static(p, _ptr(moment), h, w, C.byref(fc), _stream(stream)),
-           "rift2_detect_static")
+    with torch.cuda.device(moment.device):
+        st = stream if stream is not None else torch.cuda.current_stream(moment.device)
+        _check(lib().rift2_detect_static(p, _ptr(moment), h, w, C.byref(fc), _stream(st)),
+               "rift2_detect_static")
     return feats

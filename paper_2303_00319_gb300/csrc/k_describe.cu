@@ -33,6 +33,8 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
+constexpr long long kWaitIters = 1ll << 24;   // try_wait polls before a wait gives up
+
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long max_iter) {
   for (long long it = 0; it < max_iter; ++it) {
     unsigned ok;
@@ -97,11 +99,14 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
     const int k = gw + (q >> 1) * gstride, hh = q & 1;
     const int px = kxy[2 * k] - HALF_PATCH;
     const int sh = px - (px & ~15);
-    if (!mbar_wait(bar0 + 8 * (q & 1), (q >> 1) & 1, 1ll << 24)) {
+    if (!mbar_wait(bar0 + 8 * (q & 1), (q >> 1) & 1, ws.wait_iters)) {
       if (lane == 0) atomicExch(ws.status, ST_TIMEOUT);
-      // the copies in flight may still land: give them a bounded chance before exiting
-      mbar_wait(bar0 + 8 * (q & 1), (q >> 1) & 1, 1ll << 24);
-      if (q + 1 < njobs) mbar_wait(bar0 + 8 * ((q + 1) & 1), ((q + 1) >> 1) & 1, 1ll << 24);
+      // the copies in flight may still land: wait for them with the full limit before
+      // exiting, so that no copy into this CTA's shared memory outlives the kernel.  The
+      // keypoints this warp leaves keep stale info words; desc_shifts reduces every shift
+      // modulo No, so the descriptor kernels stay in bounds on them.
+      mbar_wait(bar0 + 8 * (q & 1), (q >> 1) & 1, kWaitIters);
+      if (q + 1 < njobs) mbar_wait(bar0 + 8 * ((q + 1) & 1), ((q + 1) >> 1) & 1, kWaitIters);
       return;
     }
     const unsigned char* buf = buf0 + (q & 1) * HBUF;
@@ -196,8 +201,8 @@ __device__ __forceinline__ int desc_shifts(unsigned inf, int mode, int (&sh)[NO]
     sh[0] = 0;
     return 1;
   }
-  sh[0] = inf & 15u;
-  sh[1] = (inf >> 4) & 15u;
+  sh[0] = (int)((inf & 15u) % NO);
+  sh[1] = (int)(((inf >> 4) & 15u) % NO);
   return 1 + (int)((inf >> 8) & 1u);
 }
 

@@ -102,6 +102,7 @@ struct DescribeWs {
   unsigned* info;        // [nimg][max_kp]
   int* off;              // [nimg][max_kp]
   int* status;           // device status word
+  long long wait_iters;  // limit of the first wait on each staged patch half
 };
 int describe_box_rows();   // rows of the MIM tensor map's box (k_describe.cu)
 cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,

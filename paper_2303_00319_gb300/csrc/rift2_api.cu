@@ -55,6 +55,7 @@ struct rift2_ctx {
   void* ws = nullptr;
   size_t ws_size = 0;
   int* status = nullptr;
+  long long wait_iters = 1ll << 24;   // first-wait limit of the descriptor kernel's staging
   std::map<int, FftPlan> plans;
   std::map<std::pair<int, int>, unsigned char*> zero_cols;   // (H, W) -> [NO][W]
   std::map<std::pair<int, int>, int> col_tiles;              // (H, W) -> tuned column tile
@@ -511,7 +512,7 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
     rc = make_mim_map(c, &tm, mim, g, H, L.mim_pitch);
     if (rc) return rc;
     DescribeWs dsw{at<unsigned short>(ws, L.raw), at<unsigned>(ws, L.info), at<int>(ws, L.off),
-                   c->status};
+                   c->status, c->wait_iters};
     StageScope sc(c, RIFT2_STAGE_DESCRIBE, st, K_DESCRIBE);
     RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
   }
@@ -643,6 +644,20 @@ int rift2_profile_read(rift2_ctx* c, int n, double* ms, long long* count) {
 }
 
 long long rift2_launch_count(const rift2_ctx* c) { return c ? c->launches : -1; }
+
+int rift2_set_wait_limit(rift2_ctx* c, long long iters) {
+  if (!c || iters < 0) return RIFT2_E_INVAL;
+  c->wait_iters = iters;
+  return RIFT2_OK;
+}
+
+int rift2_required_capacity(const rift2_ctx* c, int* cap_kp, int* cap_desc, int* cap_match) {
+  if (!c) return RIFT2_E_INVAL;
+  if (cap_kp) *cap_kp = c->kp.kp_cap;
+  if (cap_desc) *cap_desc = desc_per_kp(c) * c->kp.kp_cap;
+  if (cap_match) *cap_match = desc_per_kp(c) * c->kp.kp_cap;
+  return RIFT2_OK;
+}
 
 int rift2_tuned_tile(const rift2_ctx* c, int height, int width) {
   if (!c) return RIFT2_E_INVAL;
@@ -830,7 +845,7 @@ int rift2_describe(rift2_ctx* c, int n, const unsigned char* mim, int H, int W,
     FeatPtrs fp = feat_ptrs(feats + i0, g);
     c->launches += K_DESCRIBE;
     DescribeWs dsw{at<unsigned short>(c->ws, L.raw), at<unsigned>(c->ws, L.info),
-                   at<int>(c->ws, L.off), c->status};
+                   at<int>(c->ws, L.off), c->status, c->wait_iters};
     RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
   }
   return RIFT2_OK;

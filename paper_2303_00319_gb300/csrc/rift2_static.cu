@@ -6,6 +6,8 @@
 // that plan every byte of device memory up front.  This entry point serves them: its only
 // scratch memory is a file-scope __device__ array of fixed size (every GPU that loads the
 // library holds it until the process exits), and it creates no context, plan or table.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -23,16 +25,38 @@ constexpr size_t kScratchBytes =
 
 __device__ __align__(256) unsigned char g_detect_scratch[kScratchBytes];
 
-// Device address of g_detect_scratch, looked up once per device with that device current.
-// (In host code the symbol's name is only a host-side stand-in, not a device address.)
+// Device address of g_detect_scratch, looked up with the device current.  (In host code
+// the symbol's name is only a host-side stand-in, not a device address.)  The address
+// belongs to the device's primary context: it is kept together with that context's
+// handle and looked up again when the current context is a different one (after a
+// device reset the module is loaded anew and the old address is stale).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
+CUcontext g_ctx[kMaxDevices] = {};
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+CtxGetCurrent g_ctx_get = nullptr;
 
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return RIFT2_E_INVAL;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_ctx_get) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault,
+                                         &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !fn) {
+      fprintf(stderr, "rift2_detect_static: cuCtxGetCurrent is unavailable\n");
+      return RIFT2_E_CUDA;
+    }
+    g_ctx_get = reinterpret_cast<CtxGetCurrent>(fn);
+  }
+  // Before the runtime's first context-using call on this thread no context may be
+  // current yet (cur == NULL); cudaGetSymbolAddress makes the primary context current,
+  // and the handle is read again after it.
+  CUcontext cur = nullptr;
+  if (g_ctx_get(&cur) != CUDA_SUCCESS) cur = nullptr;
+  if (!g_addr[dev] || !cur || cur != g_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_detect_scratch);
     if (e != cudaSuccess || !p) {
@@ -40,10 +64,22 @@ int scratch_address(int dev, void** out) {
               cudaGetErrorString(e));
       return RIFT2_E_CUDA;
     }
+    if (g_ctx_get(&cur) != CUDA_SUCCESS) cur = nullptr;
     g_addr[dev] = p;
+    g_ctx[dev] = cur;
   }
   *out = g_addr[dev];
   return RIFT2_OK;
+}
+
+// True iff p is device memory (or managed memory) that device `dev` owns.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -70,6 +106,13 @@ extern "C" int rift2_detect_static(const rift2_params* params, const float* mome
   if (out->cap_kp < p.max_keypoints) return RIFT2_E_CAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RIFT2_E_CUDA;
+  // every buffer must live on the current device: the kernels run there
+  if (!on_device(moment, dev) || !on_device(out->kp_xy, dev) || !on_device(out->kp_score, dev) ||
+      !on_device(out->counts, dev)) {
+    fprintf(stderr, "rift2_detect_static: the map and the outputs must be device memory of "
+                    "the current device (%d)\n", dev);
+    return RIFT2_E_INVAL;
+  }
   void* base = nullptr;
   int rc = scratch_address(dev, &base);
   if (rc) return rc;

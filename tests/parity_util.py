@@ -57,3 +57,51 @@ def compare_keypoints(gpu_xy, gpu_score, ora_xy, ora_score, uncertain, boundary_
             if abs(va - vb) >= tie_rel * max(va, vb):
                 inv += 1
     return {"bad": bad, "flips": len(flips), "inversions": inv, "n_gpu": len(g), "n_oracle": len(o)}
+
+
+def worst_above_floor(got, exp, floor_frac):
+    """(worst relative error, its flat index, how many elements exceed 1e-4): the figures a
+    failing map assertion reports."""
+    got = np.asarray(got, dtype=np.float64)
+    exp = np.asarray(exp, dtype=np.float64)
+    scale = np.max(np.abs(exp))
+    den = np.maximum(np.abs(exp), floor_frac * scale) if scale > 0 else np.ones_like(exp)
+    r = np.abs(got - exp) / den
+    i = int(np.argmax(r))
+    return float(r.flat[i]), i, int((r > 1e-4).sum())
+
+
+def assert_map(name, got, exp, floor_frac, bar=1e-4):
+    """Element-wise |got - exp| / max(|exp|, floor * max|exp|) < bar, reporting the worst."""
+    w, i, n = worst_above_floor(got, exp, floor_frac)
+    assert w < bar, f"{name}: worst rel err {w:.3e} at flat index {i} ({n} elements above {bar})"
+    return w
+
+
+def common_keypoint_descriptors(g, o, mim_mismatch, hp=48):
+    """Pairs (gpu rows, oracle rows) of descriptors of keypoints present in both lists whose
+    patch holds no MIM pixel that differs between the two maps (there the counts must be
+    identical).  g: host dict of the GPU features; o: oracle Features."""
+    gi = {tuple(map(int, p)): i for i, p in enumerate(g["xy"])}
+    out = []
+    for k, (x, y) in enumerate(np.asarray(o.xy).tolist()):
+        if (x, y) not in gi:
+            continue
+        if mim_mismatch[y - hp:y + hp, x - hp:x + hp].any():
+            continue
+        jo = np.flatnonzero(np.asarray(o.desc_kp) == k)
+        jg = np.flatnonzero(g["desc_kp"] == gi[(x, y)])
+        out.append((jg, jo))
+    return out
+
+
+def assert_nn_matches(m, nn, d1, d2, near, label=""):
+    """GPU matches against the oracle's exhaustive search on the same descriptors: indices
+    identical except at certified near ties, distances within 1e-5 relative."""
+    assert len(m["nn_desc"]) == len(nn), label
+    bad = ~((m["nn_desc"] == nn) | near)
+    assert not bad.any(), f"{label}: {int(bad.sum())} NN mismatches away from near ties"
+    np.testing.assert_allclose(m["d1"], d1, rtol=1e-5, atol=1e-9, err_msg=label)
+    fin = np.isfinite(d2)
+    np.testing.assert_allclose(m["d2"][fin], d2[fin], rtol=1e-5, atol=1e-9, err_msg=label)
+    return int(near.sum())

@@ -14,7 +14,8 @@ import pytest
 
 import oracle as O
 import synth
-from parity_util import compare_keypoints, rel_err
+from parity_util import (assert_map, assert_nn_matches, common_keypoint_descriptors,
+                         compare_keypoints, rel_err)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -104,16 +105,10 @@ def test_noise_threshold_concentrated_amplitudes(pkg, dev):
 
 
 def test_pc_terms_and_moment(small):
-    d = {k: v.cpu().numpy() for k, v in small["fa"].debug.items()}
-    m = small["oa"].maps
-    assert rel_err(d["an0"], m["An0"], 1e-2) < 1e-4
-    assert rel_err(d["q"], m["q"], 1e-3) < 1e-4
-    assert rel_err(d["er"], m["Er"], 5e-2) < 1e-4
-    assert rel_err(d["pc"], m["pc"], 1.0) < 1e-4      # PC in [0, 1]: against its scale
-    mo = m["M"]
-    # normalised units (what FAST compares): well inside the 1e-5 certification margin
-    assert np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min()) < 5e-6
-    assert rel_err(d["moment"], mo, 1e-2) < 1e-4
+    # both images: PC in [0, 1] against its scale; M also in FAST's normalised units, well
+    # inside the 1e-5 certification margin
+    _check_all_maps(small["fa"].debug, small["oa"], "256 A")
+    _check_all_maps(small["fb"].debug, small["ob"], "256 B")
 
 
 # --------------------------------------------------------------------- stages
@@ -302,26 +297,58 @@ def _e2e_check(f, o, ctx_p):
     return g, r
 
 
+def _check_descriptors_and_nn(ga, gb, fa_dbg, fb_dbg, oa, ob, m, min_checked, label):
+    """Descriptors of keypoints both lists share, whose patch has no MIM pixel that differs
+    from the oracle's, are identical; the GPU matches equal the oracle's exhaustive search
+    run on the GPU's own descriptors except at certified near ties."""
+    checked = 0
+    for g, dbg, o in ((ga, fa_dbg, oa), (gb, fb_dbg, ob)):
+        mis = dbg["mim"].cpu().numpy() != o.maps["mim"]
+        pairs = common_keypoint_descriptors(g, o, mis)
+        for jg, jo in pairs:
+            assert np.array_equal(g["desc"][jg].astype(np.int64), o.desc[jo]), label
+            assert np.array_equal(g["desc_dom"][jg], o.desc_dom[jo]), label
+        checked += len(pairs)
+    assert checked >= min_checked, (label, checked)
+    nn, d1, d2, near = O.match(ga["desc"].astype(np.int64), gb["desc"].astype(np.int64))
+    assert_nn_matches(m, nn, d1, d2, near, label)
+    assert np.array_equal(m["kp_a"], ga["desc_kp"][m["q_desc"]])
+    assert np.array_equal(m["kp_b"], gb["desc_kp"][m["nn_desc"]])
+    return checked
+
+
 def test_end_to_end_small_pair(small):
     ga, ra = _e2e_check(small["fa"], small["oa"], small["p"])
     gb, rb = _e2e_check(small["fb"], small["ob"], small["p"])
-    if ra["flips"] == 0 and rb["flips"] == 0:
-        # same keypoints: descriptors differ only where an uncertain MIM pixel is in a patch
-        for g, o, f in ((ga, small["oa"], small["fa"]), (gb, small["ob"], small["fb"])):
-            mim_gpu = f.debug["mim"].cpu().numpy()
-            if np.array_equal(mim_gpu, o.maps["mim"]):
-                assert np.array_equal(g["desc"].astype(np.int64), o.desc)
-        m = small["m"].host()
-        nn, d1, d2, near = O.match(small["oa"].desc, small["ob"].desc)
-        if np.array_equal(ga["desc"].astype(np.int64), small["oa"].desc) and \
-                np.array_equal(gb["desc"].astype(np.int64), small["ob"].desc):
-            assert np.all((m["nn_desc"] == nn) | near)
+    _check_descriptors_and_nn(ga, gb, small["fa"].debug, small["fb"].debug, small["oa"],
+                              small["ob"], small["m"].host(), 100, "256x256")
+
+
+def _check_all_maps(dbg, o, label):
+    """Every debug map of one image against the oracle (floors as in the module header)."""
+    d = {k: v.cpu().numpy() for k, v in dbg.items()}
+    m = o.maps
+    mis = d["mim"] != m["mim"]
+    assert np.all(m["mim_margin"][mis] < TIE), f"{label}: MIM {int(mis.sum())} mismatches"
+    assert_map(f"{label} A_o", d["amp"], m["A"], AMP_FLOOR)
+    assert_map(f"{label} |EO0|", d["an0"], m["An0"], 1e-2)
+    assert_map(f"{label} q", d["q"], m["q"], 1e-3)
+    assert_map(f"{label} Er", d["er"], m["Er"], 5e-2)
+    assert_map(f"{label} PC", d["pc"], m["pc"], 1.0)
+    np.testing.assert_allclose(d["noise_t"], m["T"], rtol=1e-5, err_msg=f"{label} T_o")
+    mo = m["M"]
+    dn = np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min())
+    assert dn < 5e-6, f"{label}: M in normalised units {dn:.3e}"
+    assert_map(f"{label} M", d["moment"], mo, 1e-2)
+    return int(mis.sum())
 
 
 @pytest.mark.slow
 def test_end_to_end_1024(pkg, dev):
     """Full-size workload (1024^2, <= 5000 keypoints) in the benchmark's launch grouping:
-    both images of a pair in one extract call; the oracle runs on image A."""
+    both images of a pair in one extract call, every map of both images against the
+    oracle, keypoints, descriptors of the shared keypoints, and the matches against the
+    oracle's exhaustive search on the GPU's descriptors."""
     pr = synth.config_pair(1)
     ctx = pkg.Context(pkg.default_params(), device=0)
     fa, fb = ctx.extract([torch.from_numpy(pr.a).to(dev), torch.from_numpy(pr.b).to(dev)],
@@ -329,32 +356,35 @@ def test_end_to_end_1024(pkg, dev):
     m = ctx.match([fa], [fb])[0]
     ctx.sync()
     oa = O.extract(pr.a.astype(np.float64), O.Params(), keep_maps=True)
-    d = {k: v.cpu().numpy() for k, v in fa.debug.items()}
-    mis = d["mim"] != oa.maps["mim"]
-    assert np.all(oa.maps["mim_margin"][mis] < TIE)
-    assert rel_err(d["amp"], oa.maps["A"], AMP_FLOOR) < 1e-4
-    np.testing.assert_allclose(d["noise_t"], oa.maps["T"], rtol=1e-5)
-    mo = oa.maps["M"]
-    assert np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min()) < 5e-6
-    ga, r = _e2e_check(fa, oa, None)
-    assert len(ga["xy"]) == 5000
-    # descriptors of keypoints common to both lists: equal where the patch has no MIM near tie
-    gi = {tuple(p): i for i, p in enumerate(ga["xy"].tolist())}
-    checked = 0
-    for k, (x, y) in enumerate(oa.xy.tolist()):
-        if (x, y) not in gi or checked >= 300:
-            continue
-        patch_mis = mis[y - 48:y + 48, x - 48:x + 48].any()
-        if patch_mis:
-            continue
-        jo = np.flatnonzero(oa.desc_kp == k)
-        jg = np.flatnonzero(ga["desc_kp"] == gi[(x, y)])
-        assert np.array_equal(ga["desc"][jg].astype(np.int64), oa.desc[jo])
-        checked += 1
-    assert checked >= 100
-    mh = m.host()
-    assert len(mh["nn_desc"]) == len(ga["desc"])
-    assert np.all((mh["nn_desc"] >= 0) & (mh["nn_desc"] < int(fb.counts.cpu()[1])))
+    ob = O.extract(pr.b.astype(np.float64), O.Params(), keep_maps=True)
+    _check_all_maps(fa.debug, oa, "1024 A")
+    _check_all_maps(fb.debug, ob, "1024 B")
+    ga, _ = _e2e_check(fa, oa, None)
+    gb, _ = _e2e_check(fb, ob, None)
+    assert len(ga["xy"]) == 5000 and len(gb["xy"]) == 5000
+    _check_descriptors_and_nn(ga, gb, fa.debug, fb.debug, oa, ob, m.host(), 1000, "1024")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("h,w", [(384, 640), (1408, 256)])
+def test_mixed_radix_maps_and_descriptors(pkg, dev, h, w):
+    """Sizes whose transforms run the shared-memory mixed-radix kernels (lg_cols_inverse,
+    lg_rows_reduce; 384 = 2^7 3, 640 = 2^7 5, 1408 = 2^7 11): every map, keypoints,
+    descriptors and matches of a pair against the oracle, as for the register path."""
+    pr = synth.make_pair(h, w, synth.pair_seed(2, h + w), angle_deg=None)
+    ctx = pkg.Context(pkg.default_params(max_keypoints=600), device=0)
+    fa, fb = ctx.extract([torch.from_numpy(pr.a).to(dev), torch.from_numpy(pr.b).to(dev)],
+                         debug=True)
+    m = ctx.match([fa], [fb])[0]
+    ctx.sync()
+    p = O.Params(max_keypoints=600)
+    oa = O.extract(pr.a.astype(np.float64), p, keep_maps=True)
+    ob = O.extract(pr.b.astype(np.float64), p, keep_maps=True)
+    _check_all_maps(fa.debug, oa, f"{h}x{w} A")
+    _check_all_maps(fb.debug, ob, f"{h}x{w} B")
+    ga, _ = _e2e_check(fa, oa, None)
+    gb, _ = _e2e_check(fb, ob, None)
+    _check_descriptors_and_nn(ga, gb, fa.debug, fb.debug, oa, ob, m.host(), 100, f"{h}x{w}")
 
 
 def test_edge_images(pkg, dev):
@@ -572,10 +602,8 @@ def test_rift_baseline_matching_and_ground_truth(pkg, dev, small):
     assert len(gb["desc"]) == 6 * len(gb["xy"]) and len(ga["desc"]) == len(ga["xy"])
     oa = O.extract(pr.a.astype(np.float64), p, mode="rift_template")
     ob = O.extract(pr.b.astype(np.float64), p, mode="rift_ring")
-    if np.array_equal(ga["desc"].astype(np.int64), oa.desc) and \
-            np.array_equal(gb["desc"].astype(np.int64), ob.desc):
-        nn, d1, d2, near = O.match(oa.desc, ob.desc)
-        assert np.all((gm["nn_desc"] == nn) | near)
+    nn, d1, d2, near = O.match(ga["desc"].astype(np.int64), gb["desc"].astype(np.int64))
+    assert_nn_matches(gm, nn, d1, d2, near, "RIFT ring")
     for gpu, orc in (((ga, gb, gm), (oa, ob)),
                      ((small["fa"].host(), small["fb"].host(), small["m"].host()),
                       (small["oa"], small["ob"]))):

@@ -372,6 +372,35 @@ def test_median_even_count():
     assert O.median_even_mean(x) == sorted(x)[500]
 
 
+@pytest.mark.parametrize("k", [1.0, 2.0])
+def test_noise_threshold_against_rayleigh_statistics(k):
+    """Noise model of reading R2 (§II-A names phase congruency with noise compensation):
+    the smallest-scale amplitude of pure noise is the modulus of a complex Gaussian, i.e.
+    Rayleigh(sigma).  With one scale the scale-sum factor is 1, so the threshold must equal
+    the noise energy's mean + k std, taken here from the SAMPLE moments of 1.2e6 moduli:
+    an estimate independent of the median route the oracle takes (median / sqrt(ln 4)
+    recovers sigma; mean sigma sqrt(pi/2), std sigma sqrt((4 - pi)/2)).  A wrong Rayleigh
+    constant, a dropped or mis-scaled k, or a median of the wrong quantity moves T by
+    several percent; the Monte-Carlo error here is about 0.1 %.  The scale-sum factor is
+    pinned on its own against the explicit series sum_{s < Ns} mult^-s."""
+    rng = np.random.default_rng(20230301)
+    sigma = 0.37
+    z = sigma * (rng.standard_normal(1_200_000) + 1j * rng.standard_normal(1_200_000))
+    mod = np.abs(z)
+    p1 = O.Params(n_scales=1, k=k)
+    # sigma from the median (the oracle's route) against the known sigma of the draw
+    assert abs(O.median_even_mean(mod) / math.sqrt(math.log(4.0)) - sigma) < 3e-3 * sigma
+    t1 = O.noise_threshold(mod, p1)
+    mc = mod.mean() + k * mod.std()
+    assert abs(t1 - mc) < 3e-3 * mc, (t1, mc)
+    # the scale-sum factor: T grows by the geometric series of the scale amplitudes
+    for ns, mult in ((4, 1.6), (3, 2.1), (6, 1.3)):
+        series = sum(mult ** -s for s in range(ns))
+        tn = O.noise_threshold(mod, O.Params(n_scales=ns, mult=mult, k=k))
+        t1m = O.noise_threshold(mod, O.Params(n_scales=1, mult=mult, k=k))
+        assert abs(tn / t1m - series) < 1e-12 * series
+
+
 def test_energy_polar_form_and_frequency_spread():
     """The phase-congruency energy in its polar form: for scale components A_s e^(i phi_s)
     with mean phase phibar = arg(sum_s A_s e^(i phi_s)), Er = sum_s A_s (cos(phi_s - phibar)

@@ -53,3 +53,43 @@ def test_static_detect_refuses_maps_beyond_its_scratch(pkg):
     with pytest.raises(pkg.Rift2Error) as e:
         pkg.detect_static(m, pkg.Features.alloc(5000, dev))
     assert e.value.code == pkg.E_CAPACITY
+
+
+def test_static_detect_allocates_no_device_memory(pkg):
+    """After a warm-up call (which loads the kernels), repeated calls on preallocated
+    outputs leave the device's free memory unchanged: nothing is allocated per call."""
+    dev = torch.device("cuda:0")
+    params = pkg.default_params(max_keypoints=2000)
+    m = torch.from_numpy(_map(768, 1024, 21)).to(dev)
+    feats = pkg.Features.alloc(2000, dev)
+    pkg.detect_static(m, feats, params)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    for _ in range(5):
+        pkg.detect_static(m, feats, params)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    assert int(feats.counts.cpu()[0]) > 100
+
+
+def test_static_detect_refuses_host_buffers(pkg):
+    """Through the C ABI directly (the Python wrapper refuses earlier): a host map or host
+    outputs are refused on the host with RIFT2_E_INVAL before anything is enqueued."""
+    import ctypes as C
+    dev = torch.device("cuda:0")
+    m_host = torch.from_numpy(_map(256, 256, 3))
+    m_dev = m_host.to(dev)
+    feats = pkg.Features.alloc(5000, dev)
+    fc, _ = feats.to_c()
+    L = pkg.lib()
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.rift2_detect_static(None, C.c_void_p(m_host.data_ptr()), 256, 256, C.byref(fc), st)
+    assert rc == pkg.E_INVAL
+    host_xy = torch.zeros((5000, 2), dtype=torch.int32)
+    fc.kp_xy = host_xy.data_ptr()
+    rc = L.rift2_detect_static(None, C.c_void_p(m_dev.data_ptr()), 256, 256, C.byref(fc), st)
+    assert rc == pkg.E_INVAL
+    with pytest.raises(ValueError):
+        pkg.detect_static(m_host, feats)
+    with pytest.raises(ValueError):   # a strided view is refused, not read as a dense map
+        pkg.detect_static(m_dev.t(), feats)
