@@ -77,6 +77,15 @@ enum {
  * the context; every tile computes bit-identical results.  Without the flag the default
  * tile is used.  rift2_tuned_tile reports the choice. */
 #define RIFT2_FLAG_AUTOTUNE 0x20
+/* Spatial orientation normalisation of the patch (a variant the paper does not have: §III
+ * normalises rotation through the dominant index alone, which leaves the 6x6 cell layout
+ * axis-aligned).  The dominant / secondary index comes from the MIM histogram over the
+ * disc of radius 48 around the keypoint; each descriptor's 96 x 96 grid is rotated by
+ * w pi / No (w its index), or that + 180 degrees when the centroid of the disc pixels with
+ * MIM == w lies behind the axis, in Q14 fixed point with rounding half away from zero;
+ * samples outside the image are not counted; counts are recoded by w (Eq. 2).  Not with
+ * RIFT2_FLAG_RIFT_TEMPLATE / RIFT2_FLAG_RIFT_RING (RIFT2_E_INVAL). */
+#define RIFT2_FLAG_SPATIAL_NORM 0x40
 
 /*
  * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
@@ -228,6 +237,31 @@ int rift2_extract(rift2_ctx* ctx, int n_images, const rift2_image* imgs,
  */
 int rift2_match(rift2_ctx* ctx, int n_pairs, const rift2_features* a,
                 const rift2_features* b, rift2_matches* out, void* stream);
+
+/*
+ * Ground-truth evaluation of putative correspondences (§IV: a correspondence is correct
+ * when the matched keypoint of image B lies within `tol` px (3 in the paper) of where the
+ * keypoint of image A lands under the known transform; the RMSE is taken over the correct
+ * ones and capped at `rmse_cap` (20); a pair succeeds with at least `min_correct` (10)
+ * correct ones).  Pair i: a[i], b[i] the features (kp_xy read on the device), m[i] its
+ * matches A -> B (m.count rows; rows whose kp_a or kp_b is -1 are not correspondences),
+ * affine: HOST array [n_pairs][6] of the transform of image A's pixel coordinates into
+ * image B's, (x', y') = (t0 x + t1 y + t2, t3 x + t4 y + t5).  out: DEVICE array of
+ * n_pairs structs, written asynchronously.  Residuals in FP64.  The transforms travel in
+ * the kernel's parameters: the host array may be reused once the call returns.
+ * Errors: RIFT2_E_INVAL (NULL pointers, n_pairs outside 1..32, tol <= 0), RIFT2_E_CUDA.
+ */
+typedef struct rift2_evaluation {
+  int n_matches;   /* rows that are correspondences */
+  int n_correct;   /* residual < tol */
+  int success;     /* n_correct >= min_correct */
+  int reserved;
+  double rmse;     /* over the correct rows, capped at rmse_cap (rmse_cap if none) */
+} rift2_evaluation;
+int rift2_evaluate(rift2_ctx* ctx, int n_pairs, const rift2_features* a,
+                   const rift2_features* b, const rift2_matches* m, const double* affine,
+                   double tol, double rmse_cap, int min_correct, rift2_evaluation* out,
+                   void* stream);
 
 /* Waits for `stream`, then returns and clears the device status word (RIFT2_OK or
  * RIFT2_E_TIMEOUT), or RIFT2_E_CUDA if the stream reported an error. */

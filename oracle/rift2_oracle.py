@@ -27,6 +27,10 @@ Where the paper is silent the module takes a reading, tagged [R1]..[R9]:
   R13 RIFT's corner keypoints (§II-A): FAST on the min-max normalised minimum moment with
      the edge detector's threshold, NMS and ordering, capped at max_keypoints; merged after
      the edge keypoints, pixels already in the edge list dropped.
+  R14 (a variant the paper does not have) spatial orientation normalisation of the patch:
+     dominant index from the disc |d| <= 48, a frame of angle w pi / No or that + 180 deg
+     chosen by the side of the centroid of the w-pixels, the 96x96 grid rotated into it in
+     Q14 fixed point with rounding half away from zero, out-of-image samples not counted.
 
 Pins (tests/test_oracle_*.py): FFT vs a direct DFT; filter properties (peak, bandwidth,
 low-pass half point, raised-cosine window values, partition of unity, one-sidedness);
@@ -191,6 +195,14 @@ def noise_threshold(an0, p: Params = DEFAULT) -> float:
     return tot * math.sqrt(math.pi / 2.0) + p.k * tot * math.sqrt((4.0 - math.pi) / 2.0)
 
 
+def mean_phase_energy(eo, p: Params = DEFAULT):
+    """X_o = |sum_s EO_{s,o}| + eps, the length of the summed response vector whose
+    direction is the mean phase [R2]."""
+    sum_e = eo.real.sum(axis=0)
+    sum_o = eo.imag.sum(axis=0)
+    return np.sqrt(sum_e ** 2 + sum_o ** 2) + p.eps
+
+
 def pc_terms(eo, p: Params = DEFAULT):
     """Per orientation, the terms of phase congruency before the noise threshold [R2]:
     Er_o = sum_s (E mE + O mO - |E mO - O mE|) with (mE, mO) the unit mean phase vector,
@@ -203,7 +215,7 @@ def pc_terms(eo, p: Params = DEFAULT):
     sum_o = od.sum(axis=0)
     sum_an = an.sum(axis=0)
     max_an = an.max(axis=0)
-    x_energy = np.sqrt(sum_e ** 2 + sum_o ** 2) + p.eps
+    x_energy = mean_phase_energy(eo, p)
     me = sum_e / x_energy
     mo = sum_o / x_energy
     er = (e * me + od * mo - np.abs(e * mo - od * me)).sum(axis=0)
@@ -405,7 +417,10 @@ def describe(mim, xy, p: Params = DEFAULT, mode: str = "rift2"):
     mode "rift_template" (§II-C, RIFT's baseline): one descriptor from the unshifted MIM.
     mode "rift_ring" (§II-C): the No descriptors of the convolution-sequence ring, the MIM
     with each layer w = 0..No-1 as the initial one, i.e. recoded by w.
+    mode "rift2_spatial" (a variant, reading R14): describe_spatial.
     Returns (desc int64 [n][216], desc_kp, desc_dom, per-keypoint (s, s2, has2, whole))."""
+    if mode == "rift2_spatial":
+        return describe_spatial(mim, xy, p)
     cells = cell_histograms(mim, xy, p)
     descs, dkp, ddom, info = [], [], [], []
     for kidx in range(len(xy)):
@@ -424,6 +439,118 @@ def describe(mim, xy, p: Params = DEFAULT, mode: str = "rift2"):
             descs.append(descriptor_from_cells(cells[kidx], w, p))
             dkp.append(kidx)
             ddom.append(w)
+    d = np.array(descs, dtype=np.int64).reshape(-1, p.desc_dim)
+    return d, np.array(dkp, dtype=np.int64), np.array(ddom, dtype=np.int64), info
+
+
+# ------------------------- spatial orientation normalisation (a variant, reading R14)
+# The paper normalises rotation through the dominant index alone (§III): the MIM values
+# are recoded, but the 6x6 cell layout stays axis-aligned, so the descriptor of a rotated
+# patch is the original one with its cells permuted (exactly so only for quarter turns).
+# Reading R14 adds the missing spatial step:
+#  * dominant index from the histogram over the disc |d| <= 48 around the keypoint (a
+#    rotation-symmetric region), pixels inside the image only; s, s2 and the secondary
+#    test as in Eq. 1 / R8;
+#  * an orientation index fixes an axis only up to 180 degrees: the frame for index w
+#    points along +a_w or -a_w, a_w = (cos th_w, -sin th_w) in array coordinates
+#    (th_w = w pi / No, y down), whichever side holds the centroid of the disc pixels
+#    whose MIM is w (exact integer sums; +a_w on a tie);
+#  * the patch grid d = (dx, dy), dx, dy in [-48, 47], is rotated by that frame's angle
+#    counter-clockwise (as displayed) with cos / sin in Q14 fixed point (rounded half away
+#    from zero) and each sample rounded half away from zero: sample = p + rnd(R d), so a
+#    quarter turn of the image maps every sample exactly;
+#  * samples outside the image are not counted; the counts are recoded by w (Eq. 2).
+ROT_Q = 14
+
+
+def _rnd_q(v):
+    """round(v / 2^ROT_Q) to the nearest integer, ties away from zero, on exact integers."""
+    v = np.asarray(v, dtype=np.int64)
+    return np.sign(v) * ((np.abs(v) + (1 << (ROT_Q - 1))) >> ROT_Q)
+
+
+def rotation_q14(w: int, p: Params = DEFAULT):
+    """(cos, sin) of th_w = w pi / No in Q14 fixed point, rounded half away from zero."""
+    th = w * math.pi / p.n_orient
+    def q(v):
+        a = abs(v) * (1 << ROT_Q)
+        return int(math.copysign(math.floor(a + 0.5), v)) if a > 0 else 0
+    return q(math.cos(th)), q(math.sin(th))
+
+
+def disc_offsets(p: Params = DEFAULT):
+    """Integer offsets d with |d|^2 <= half_patch^2, int64 [n][2] (dx, dy)."""
+    r = p.half_patch
+    dy, dx = np.mgrid[-r:r + 1, -r:r + 1]
+    keep = dx * dx + dy * dy <= r * r
+    return np.stack([dx[keep], dy[keep]], axis=1).astype(np.int64)
+
+
+def mim_at(mim, x, y, off):
+    """MIM values at (x, y) + off and whether each sample lies inside the image."""
+    h, w = mim.shape
+    qx, qy = x + off[:, 0], y + off[:, 1]
+    inside = (qx >= 0) & (qx < w) & (qy >= 0) & (qy < h)
+    vals = np.full(len(off), -1, dtype=np.int64)
+    vals[inside] = mim[qy[inside], qx[inside]]
+    return vals, inside
+
+
+def spatial_frame(mim, x, y, w: int, p: Params = DEFAULT):
+    """(cos, sin) in Q14 of the frame for index w at (x, y): th_w, or th_w + 180 degrees
+    when the centroid of the disc pixels with MIM == w lies on the -a_w side."""
+    c, sn = rotation_q14(w, p)
+    off = disc_offsets(p)
+    vals, _ = mim_at(mim, x, y, off)
+    sel = vals == w
+    sx, sy = int(off[sel, 0].sum()), int(off[sel, 1].sum())
+    proj = sx * c - sy * sn          # centroid . a_w, a_w = (c, -sn) in array coordinates
+    return (-c, -sn) if proj < 0 else (c, sn)
+
+
+def rotated_samples(x, y, c, sn, p: Params = DEFAULT):
+    """Sample pixels of the grid d in [-hp, hp)^2 rotated by the frame (c, sn):
+    (x + rnd(c dx + sn dy), y + rnd(-sn dx + c dy)), ordered cell by cell (cells row-major,
+    pixels row-major within a cell).  int64 [cells^2][cell^2][2]."""
+    hp, cs, nc = p.half_patch, p.cell_size, p.cells
+    out = np.zeros((nc * nc, cs * cs, 2), dtype=np.int64)
+    for i in range(nc):
+        for j in range(nc):
+            dy, dx = np.mgrid[-hp + i * cs:-hp + (i + 1) * cs, -hp + j * cs:-hp + (j + 1) * cs]
+            dx, dy = dx.ravel(), dy.ravel()
+            out[i * nc + j, :, 0] = x + _rnd_q(c * dx + sn * dy)
+            out[i * nc + j, :, 1] = y + _rnd_q(-sn * dx + c * dy)
+    return out
+
+
+def describe_spatial(mim, xy, p: Params = DEFAULT):
+    """Descriptors with the spatial orientation normalisation of reading R14: one per
+    keypoint from its dominant index (disc histogram) and a second one where the secondary
+    index qualifies (R8), each from the patch grid rotated into its index's frame and
+    recoded by that index (Eq. 2).  Returns (desc int64 [n][216], desc_kp, desc_dom,
+    per-keypoint (s, s2, has2, disc histogram))."""
+    h, w = mim.shape
+    no = p.n_orient
+    off = disc_offsets(p)
+    descs, dkp, ddom, info = [], [], [], []
+    for kidx, (x, y) in enumerate(np.asarray(xy).tolist()):
+        vals, inside = mim_at(mim, x, y, off)
+        whole = np.bincount(vals[inside], minlength=no)[:no]
+        s, s2, has2 = dominant_indices(whole, p)
+        info.append((s, s2, has2, whole))
+        for wi in ([s, s2] if has2 else [s]):
+            c, sn = spatial_frame(mim, x, y, wi, p)
+            smp = rotated_samples(x, y, c, sn, p)
+            d = np.zeros(p.desc_dim, dtype=np.int64)
+            for cell in range(p.cells * p.cells):
+                qx, qy = smp[cell, :, 0], smp[cell, :, 1]
+                ok = (qx >= 0) & (qx < w) & (qy >= 0) & (qy < h)
+                cnt = np.bincount(mim[qy[ok], qx[ok]].astype(np.int64), minlength=no)[:no]
+                for b in range(no):
+                    d[cell * no + int(recode(b, wi, p))] = cnt[b]
+            descs.append(d)
+            dkp.append(kidx)
+            ddom.append(wi)
     d = np.array(descs, dtype=np.int64).reshape(-1, p.desc_dim)
     return d, np.array(dkp, dtype=np.int64), np.array(ddom, dtype=np.int64), info
 
@@ -523,7 +650,8 @@ def extract(img, p: Params = DEFAULT, keep_maps: bool = False, mode: str = "rift
     if keep_maps:
         er, q, an0, _ = pc_terms(eo, p)
         maps = dict(A=a, mim=mim, mim_margin=mim_margin, pc=pc, T=t, M=m_max, m=m_min,
-                    Er=er, q=q, An0=an0, kp_uncertain=unc, kp_boundary_tie=btie, n_edge=n_edge)
+                    Er=er, q=q, An0=an0, X=mean_phase_energy(eo, p), kp_uncertain=unc,
+                    kp_boundary_tie=btie, n_edge=n_edge)
         if p.corners:
             maps.update(corner_xy=xy_c, corner_score=v_c, corner_uncertain=unc_c,
                         corner_boundary_tie=btie_c)

@@ -22,6 +22,7 @@ FLAG_RIFT_TEMPLATE = 0x4   # RIFT baseline: one descriptor per keypoint, unshift
 FLAG_RIFT_RING = 0x8       # RIFT baseline: the No descriptors of the convolution ring
 FLAG_CORNERS = 0x10        # RIFT's corner keypoints on the minimum moment, after the edge ones
 FLAG_AUTOTUNE = 0x20       # time the column tiles of a new image size once, keep the fastest
+FLAG_SPATIAL_NORM = 0x40   # variant: patch grid rotated into the dominant index's frame
 NS, NO, PATCH, CELLS = 4, 6, 96, 6
 DESC_DIM = CELLS * CELLS * NO
 
@@ -30,7 +31,7 @@ EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_ex
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
            "rift2_describe", "rift2_detect_static", "rift2_tuned_tile",
-           "rift2_required_capacity", "rift2_set_wait_limit")
+           "rift2_required_capacity", "rift2_set_wait_limit", "rift2_evaluate")
 STATIC_MAX_CANDIDATES = 262144
 STAGES = ("fft_fwd", "lg_cols", "lg_rows", "noise", "moment", "detect", "describe", "match")
 
@@ -67,6 +68,11 @@ class MatchesC(C.Structure):
                 ("d2", C.c_void_p), ("near_tie", C.c_void_p), ("count", C.c_void_p)]
 
 
+class Evaluation(C.Structure):
+    _fields_ = [("n_matches", C.c_int), ("n_correct", C.c_int), ("success", C.c_int),
+                ("reserved", C.c_int), ("rmse", C.c_double)]
+
+
 _LIB = None
 
 
@@ -96,6 +102,10 @@ def lib():
         L.rift2_required_capacity.argtypes = [C.c_void_p, C.POINTER(C.c_int),
                                               C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.rift2_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
+        L.rift2_evaluate.argtypes = [C.c_void_p, C.c_int, C.POINTER(FeaturesC),
+                                     C.POINTER(FeaturesC), C.POINTER(MatchesC),
+                                     C.POINTER(C.c_double), C.c_double, C.c_double, C.c_int,
+                                     C.c_void_p, C.c_void_p]
         L.rift2_fft2.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                  C.c_void_p]
         L.rift2_detect.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
@@ -304,6 +314,38 @@ class Context:
             cm[i] = out[i].to_c()
         _check(lib().rift2_match(self._h, n, ca, cb, cm, _stream(stream)), "rift2_match")
         return out
+
+    def evaluate(self, fa, fb, matches, affines, tol=3.0, rmse_cap=20.0, min_correct=10,
+                 out=None, stream=None):
+        """Ground truth of each pair's matches under its known transform (rift2_evaluate):
+        affines is a list of 6-tuples (t0..t5) mapping A's pixel coordinates into B's.
+        Returns a CUDA byte tensor holding the rift2_evaluation structs; evaluation_host()
+        reads it."""
+        n = len(fa)
+        if out is None:
+            out = torch.zeros(n * C.sizeof(Evaluation), dtype=torch.uint8,
+                              device=f"cuda:{self.device}")
+        ca, cb, cm = (FeaturesC * n)(), (FeaturesC * n)(), (MatchesC * n)()
+        for i in range(n):
+            ca[i], _ = fa[i].to_c()
+            cb[i], _ = fb[i].to_c()
+            cm[i] = matches[i].to_c()
+        tf = (C.c_double * (6 * n))(*[float(v) for t in affines for v in t])
+        _check(lib().rift2_evaluate(self._h, n, ca, cb, cm, tf, tol, rmse_cap, min_correct,
+                                    _ptr(out), _stream(stream)), "rift2_evaluate")
+        return out
+
+    @staticmethod
+    def evaluation_host(out) -> list:
+        """The rift2_evaluation structs of a Context.evaluate result as dicts."""
+        raw = bytes(out.cpu().numpy())
+        n = len(raw) // C.sizeof(Evaluation)
+        res = []
+        for i in range(n):
+            e = Evaluation.from_buffer_copy(raw, i * C.sizeof(Evaluation))
+            res.append(dict(matches=e.n_matches, correct=e.n_correct, success=bool(e.success),
+                            rmse=e.rmse))
+        return res
 
     def sync(self, stream=None):
         _check(lib().rift2_sync(self._h, _stream(stream)), "rift2_sync")

@@ -35,12 +35,15 @@ struct KParams {
   int max_kp;            // keypoints one detector pass keeps
   int kp_cap;            // keypoint list capacity per image (2 max_kp with corners)
   int ratio_pm;          // dominant ratio in per mille (integer comparison)
-  int desc_mode;         // DESC_RIFT2, DESC_RIFT_TEMPLATE or DESC_RIFT_RING
+  int desc_mode;         // DESC_RIFT2, DESC_RIFT_TEMPLATE, DESC_RIFT_RING or DESC_SPATIAL
+  int rot_c[NO], rot_s[NO];   // cos / sin of o pi / No in Q14, rounded half away from zero
 };
 
 // Descriptor modes: RIFT2's dominant index (one or two per keypoint), RIFT's template
 // (unshifted MIM, one per keypoint) and RIFT's reference ring (No per keypoint).
-constexpr int DESC_RIFT2 = 0, DESC_RIFT_TEMPLATE = 1, DESC_RIFT_RING = 2;
+// DESC_SPATIAL: RIFT2's descriptors on a patch grid rotated into the dominant index's frame
+// (a variant the paper does not have; see desc_spatial).
+constexpr int DESC_RIFT2 = 0, DESC_RIFT_TEMPLATE = 1, DESC_RIFT_RING = 2, DESC_SPATIAL = 3;
 
 // Per-launch-group pointers to the caller's buffers (passed by value).
 struct FeatPtrs {

@@ -190,6 +190,176 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
   }
 }
 
+// ------------------------------------------- spatial orientation normalisation (variant)
+// desc_spatial: one warp per keypoint (several in turn).  The window of MIM rows y-66..y+66
+// and 160 columns from (x-66) rounded down to 16 bytes is staged by one TMA box: it holds
+// the disc |d| <= 48 and every sample of the rotated grid (|rnd(R d)| <= 48 (cos 30 +
+// sin 30) < 66).  Out-of-image pixels are excluded by explicit bounds tests, never by the
+// copy's fill value.
+//  1. Disc histogram and centroid sums: each lane takes 16-pixel row segments, forms the
+//     three bit planes of their MIM values (as desc_hist does), masks them to the disc
+//     row and the image, and adds per bin the popcount, the sum of the pixels' dx (from
+//     popcounts against the four bit-weight masks of the pixel index) and dy x count.
+//  2. Dominant index s, secondary s2 and the ratio test (Eq. 1, §III) on the disc counts.
+//  3. Per descriptor index w: frame (cos, sin) of w pi / No in Q14, negated when the
+//     centroid of the w-pixels projects negatively on the axis (cos, -sin); the grid
+//     d = (dx, dy) in [-48, 47]^2 is sampled at p + (rnd(c dx + s dy), rnd(-s dx + c dy)),
+//     rnd rounding x / 2^14 half away from zero; a lane counts 8 samples of a cell in
+//     4-bit fields, the warp adds them with one redux per three bins.
+//  The raw (unrecoded) counts of grid w go to raw[k][d], d = 0 for s and 1 for s2.
+constexpr int SP_R = 66;
+constexpr int SP_BOX_W = 160;
+constexpr int SP_BOX_H = 2 * SP_R + 1;
+constexpr int SP_BUF = (SP_BOX_W * SP_BOX_H + 127) / 128 * 128;
+constexpr int SP_WARPS = 4;
+static_assert(SP_BOX_W >= 2 * SP_R + 1 + 15, "window holds the rounded-down x start");
+
+__device__ __forceinline__ int rnd_q14(int v) { return (v + 8192 - (v < 0 ? 1 : 0)) >> 14; }
+
+__global__ void __launch_bounds__(SP_WARPS * 32) desc_spatial(const __grid_constant__ CUtensorMap tmap,
+                                                              int H, int W, KParams kp,
+                                                              DescribeWs ws, FeatPtrs fp) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(dsm + SP_WARPS * SP_BUF);
+  const int img = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkp = fp.counts[img][0];
+  const int gw = blockIdx.x * SP_WARPS + warp, gstride = gridDim.x * SP_WARPS;
+  if (gw >= nkp) return;   // warp-uniform
+  unsigned char* buf = dsm + warp * SP_BUF;
+  const unsigned bar = smem_u32(&bars[warp]);
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int* kxy = fp.kp_xy[img];
+  const unsigned FULL = 0xffffffffu;
+  unsigned phase = 0;
+  for (int k = gw; k < nkp; k += gstride, phase ^= 1u) {
+    const int x = kxy[2 * k], y = kxy[2 * k + 1];
+    const int wx0 = (x - SP_R) & ~15, wy0 = y - SP_R;
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"(SP_BOX_W * SP_BOX_H)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(buf)),
+          "l"(&tmap), "r"(wx0), "r"(wy0), "r"(img), "r"(bar)
+          : "memory");
+    }
+    if (!mbar_wait(bar, phase, ws.wait_iters)) {
+      if (lane == 0) atomicExch(ws.status, ST_TIMEOUT);
+      mbar_wait(bar, phase, kWaitIters);   // the copy lands before the kernel exits
+      return;
+    }
+    // ---- 1. disc histogram and centroid sums (rows dy = -48..48, segments of 16 columns)
+    int cnt[NO], sx[NO], sy[NO];
+#pragma unroll
+    for (int b = 0; b < NO; ++b) cnt[b] = sx[b] = sy[b] = 0;
+    const int xoff = x - wx0;   // window column of the keypoint
+    for (int u = lane; u < 97 * (SP_BOX_W / 16); u += 32) {
+      const int ri = u / (SP_BOX_W / 16), sk = u - ri * (SP_BOX_W / 16);
+      const int dy = ri - HALF_PATCH;
+      if ((unsigned)(y + dy) >= (unsigned)H) continue;
+      const int r2 = HALF_PATCH * HALF_PATCH - dy * dy;
+      int rr = (int)sqrtf((float)r2);
+      while ((rr + 1) * (rr + 1) <= r2) ++rr;
+      while (rr * rr > r2) --rr;
+      const int lo = max(-rr, -x), hi = min(rr, W - 1 - x);
+      const int off = xoff - 16 * sk;          // pixel j of the segment is dx = j - off
+      const int jl = max(lo + off, 0), jh = min(hi + off, 15);
+      if (jl > jh) continue;
+      const uint4 v4 = *reinterpret_cast<const uint4*>(buf + (dy + SP_R) * SP_BOX_W + 16 * sk);
+      const unsigned wv[4] = {v4.x, v4.y, v4.z, v4.w};
+      unsigned p0 = 0, p1 = 0, p2 = 0, pv = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned idx = 0x03020100u + 0x04040404u * (unsigned)i;
+        const unsigned val = __vcmpgeu4(idx, 0x01010101u * (unsigned)jl) &
+                             __vcmpleu4(idx, 0x01010101u * (unsigned)jh) & 0x01010101u;
+        p0 |= (wv[i] & 0x01010101u) << i;
+        p1 |= ((wv[i] >> 1) & 0x01010101u) << i;
+        p2 |= ((wv[i] >> 2) & 0x01010101u) << i;
+        pv |= val << i;
+      }
+      // bit 8 j + i holds pixel 4 i + j: pixel-index bit b is set on these masks
+      const unsigned m[NO] = {~p2 & ~p1 & ~p0 & pv, ~p2 & ~p1 & p0 & pv, ~p2 & p1 & ~p0 & pv,
+                              ~p2 & p1 & p0 & pv,   p2 & ~p0 & pv,        p2 & p0 & pv};
+#pragma unroll
+      for (int b = 0; b < NO; ++b) {
+        const int n = __popc(m[b]);
+        const int sj = __popc(m[b] & 0x0F000F00u) + 2 * __popc(m[b] & 0x0F0F0000u) +
+                       4 * __popc(m[b] & 0x0A0A0A0Au) + 8 * __popc(m[b] & 0x0C0C0C0Cu);
+        cnt[b] += n;
+        sx[b] += sj - off * n;
+        sy[b] += dy * n;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NO; ++b) {
+      cnt[b] = __reduce_add_sync(FULL, cnt[b]);
+      sx[b] = __reduce_add_sync(FULL, sx[b]);
+      sy[b] = __reduce_add_sync(FULL, sy[b]);
+    }
+    // ---- 2. dominant and secondary index (lowest bin on ties), ratio test in integers
+    int s = 0;
+#pragma unroll
+    for (int b = 1; b < NO; ++b)
+      if (cnt[b] > cnt[s]) s = b;
+    int s2 = (s == 0) ? 1 : 0;
+#pragma unroll
+    for (int b = 0; b < NO; ++b)
+      if (b != s && cnt[b] > cnt[s2]) s2 = b;
+    const bool has2 = 1000ll * cnt[s2] >= (long long)kp.ratio_pm * cnt[s];
+    if (lane == 0)
+      ws.info[(size_t)img * kp.kp_cap + k] = (unsigned)s | ((unsigned)s2 << 4) | ((has2 ? 1u : 0u) << 8);
+    // ---- 3. the rotated grids
+    const bool interior = x >= SP_R && y >= SP_R && x + SP_R < W && y + SP_R < H;
+    unsigned short* raw = ws.raw + ((size_t)img * kp.kp_cap + k) * (2 * DESC_DIM);
+    for (int d = 0; d < (has2 ? 2 : 1); ++d) {
+      const int wi = d ? s2 : s;
+      int sxw = 0, syw = 0, c = 0, sn = 0;   // static indices only (no local copies)
+#pragma unroll
+      for (int b = 0; b < NO; ++b)
+        if (b == wi) { sxw = sx[b]; syw = sy[b]; c = kp.rot_c[b]; sn = kp.rot_s[b]; }
+      if ((long long)sxw * c - (long long)syw * sn < 0) { c = -c; sn = -sn; }
+      const int dx = -HALF_PATCH + (lane & 15);
+      const int dyl = -HALF_PATCH + (lane >> 4);
+      for (int cl = 0; cl < CELLS * CELLS; ++cl) {
+        const int ci = cl / CELLS, cj = cl - ci * CELLS;
+        const int ddx = dx + CELL * cj, ddy = dyl + CELL * ci;
+        int X = c * ddx + sn * ddy, Y = -sn * ddx + c * ddy;
+        unsigned acc = 0;
+#pragma unroll
+        for (int r = 0; r < CELL / 2; ++r) {
+          const int rx = rnd_q14(X), ry = rnd_q14(Y);
+          const bool ok = interior || ((unsigned)(x + rx) < (unsigned)W &&
+                                       (unsigned)(y + ry) < (unsigned)H);
+          if (ok) {
+            const unsigned mv = buf[(ry + SP_R) * SP_BOX_W + xoff + rx];
+            acc += 1u << (4 * mv);
+          }
+          X += 2 * sn;
+          Y += 2 * c;
+        }
+        // nibbles of bins 0..2 and 3..5 into 10-bit fields, summed over the warp
+        const unsigned e0 = (acc & 0xFu) | (((acc >> 4) & 0xFu) << 10) | (((acc >> 8) & 0xFu) << 20);
+        const unsigned e1 = ((acc >> 12) & 0xFu) | (((acc >> 16) & 0xFu) << 10) |
+                            (((acc >> 20) & 0xFu) << 20);
+        const unsigned t0 = __reduce_add_sync(FULL, e0), t1 = __reduce_add_sync(FULL, e1);
+        if (lane < NO) {
+          const unsigned t = lane < 3 ? t0 : t1;
+          raw[d * DESC_DIM + cl * NO + lane] = (unsigned short)((t >> (10 * (lane % 3))) & 1023u);
+        }
+      }
+    }
+    __syncwarp();   // every lane's reads of the window precede the next copy into it
+  }
+}
+
 // Descriptors of keypoint info `inf` under the mode: count, and the recoding shift of each.
 __device__ __forceinline__ int desc_shifts(unsigned inf, int mode, int (&sh)[NO]) {
   if (mode == DESC_RIFT_RING) {
@@ -265,8 +435,25 @@ __global__ void __launch_bounds__(256) desc_write(KParams kp, DescribeWs ws, Fea
   int sh[NO];
   const int nd = desc_shifts(ws.info[(size_t)img * kp.kp_cap + k], kp.desc_mode, sh);
   const int off = ws.off[(size_t)img * kp.kp_cap + k];
-  const unsigned short* raw = ws.raw + ((size_t)img * kp.kp_cap + k) * DESC_DIM;
   unsigned short* d0 = fp.desc[img] + (size_t)off * DESC_DIM;
+  if (kp.desc_mode == DESC_SPATIAL) {
+    // one raw count vector per descriptor (each from its own rotated grid), recoded by its
+    // index; its own norm
+    const unsigned short* rk = ws.raw + ((size_t)img * kp.kp_cap + k) * (2 * DESC_DIM);
+    for (int d = 0; d < nd; ++d) {
+      unsigned n2 = 0;
+      for (int e = lane; e < DESC_DIM; e += 32) {
+        const unsigned v = rk[d * DESC_DIM + e];
+        n2 += v * v;
+        const int c = e / NO, b = e - c * NO;
+        d0[(size_t)d * DESC_DIM + c * NO + (b - sh[d] + NO) % NO] = (unsigned short)v;
+      }
+      for (int dd = 16; dd > 0; dd >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, dd);
+      if (lane == 0) fp.desc_norm[img][off + d] = sqrtf((float)n2);
+    }
+    return;
+  }
+  const unsigned short* raw = ws.raw + ((size_t)img * kp.kp_cap + k) * DESC_DIM;
   unsigned n2 = 0;
   for (int e = lane; e < DESC_DIM; e += 32) {
     const unsigned v = raw[e];
@@ -278,15 +465,30 @@ __global__ void __launch_bounds__(256) desc_write(KParams kp, DescribeWs ws, Fea
   if (lane < nd) fp.desc_norm[img][off + lane] = sqrtf((float)n2);   // exact: n2 < 2^24
 }
 
-int describe_box_rows() { return HALF_ROWS; }
+void describe_box(int desc_mode, int* cols, int* rows) {
+  if (desc_mode == DESC_SPATIAL) {
+    *cols = SP_BOX_W;
+    *rows = SP_BOX_H;
+  } else {
+    *cols = BOX_W;
+    *rows = HALF_ROWS;
+  }
+}
 
 cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
                             const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
                             cudaStream_t st) {
-  size_t sm = (size_t)DH_WARPS * 2 * HBUF + DH_WARPS * 2 * sizeof(unsigned long long);
-  cudaFuncSetAttribute(desc_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int blocks = (kp.kp_cap + DH_WARPS * DH_KPW - 1) / (DH_WARPS * DH_KPW);
-  desc_hist<<<dim3(blocks, nimg), DH_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
+  if (kp.desc_mode == DESC_SPATIAL) {
+    const size_t sm = (size_t)SP_WARPS * SP_BUF + SP_WARPS * sizeof(unsigned long long);
+    cudaFuncSetAttribute(desc_spatial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int blocks = (kp.kp_cap + SP_WARPS * DH_KPW - 1) / (SP_WARPS * DH_KPW);
+    desc_spatial<<<dim3(blocks, nimg), SP_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
+  } else {
+    const size_t sm = (size_t)DH_WARPS * 2 * HBUF + DH_WARPS * 2 * sizeof(unsigned long long);
+    cudaFuncSetAttribute(desc_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int blocks = (kp.kp_cap + DH_WARPS * DH_KPW - 1) / (DH_WARPS * DH_KPW);
+    desc_hist<<<dim3(blocks, nimg), DH_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
+  }
   desc_scan<<<nimg, 1024, 0, st>>>(kp, ws, fp);
   desc_write<<<dim3((kp.kp_cap + 7) / 8, nimg), 256, 0, st>>>(kp, ws, fp);
   return cudaGetLastError();

@@ -104,7 +104,8 @@ struct DescribeWs {
   int* status;           // device status word
   long long wait_iters;  // limit of the first wait on each staged patch half
 };
-int describe_box_rows();   // rows of the MIM tensor map's box (k_describe.cu)
+// Box (columns, rows) of the MIM tensor map the descriptor kernel of `desc_mode` stages.
+void describe_box(int desc_mode, int* cols, int* rows);
 cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
                             const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
                             cudaStream_t st);
@@ -127,6 +128,19 @@ struct MatchPtrs {
   int* count[MAXB];
 };
 cudaError_t launch_match_simt(const MatchPtrs& mp, int npairs, int max_desc, cudaStream_t st);
+
+// k_evaluate.cu — ground-truth evaluation of correspondences under known transforms.
+struct EvalPtrs {
+  const int* xy_a[MAXB];
+  const int* xy_b[MAXB];
+  const int* kp_a[MAXB];
+  const int* kp_b[MAXB];
+  const int* count[MAXB];
+  double affine[MAXB * 6];     // per pair (x', y') = (t0 x + t1 y + t2, t3 x + t4 y + t5)
+  rift2_evaluation* out;       // device [npairs]
+};
+cudaError_t launch_evaluate(const EvalPtrs& ep, int npairs, double tol, double rmse_cap,
+                            int min_correct, cudaStream_t st);
 
 // k_match_tc.cu — tcgen05 BF16 distance GEMM fused with top-8 selection, exact re-rank.
 // `cap` (descriptor rows per pair) must be a multiple of 128.

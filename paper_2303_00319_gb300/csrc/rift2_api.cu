@@ -42,7 +42,13 @@ void derive_kparams(const rift2_params& p, KParams& k) {
   k.ratio_pm = (int)std::lround(p.second_ratio * 1000.0);
   k.desc_mode = (p.flags & RIFT2_FLAG_RIFT_RING)       ? DESC_RIFT_RING
                 : (p.flags & RIFT2_FLAG_RIFT_TEMPLATE) ? DESC_RIFT_TEMPLATE
+                : (p.flags & RIFT2_FLAG_SPATIAL_NORM)  ? DESC_SPATIAL
                                                        : DESC_RIFT2;
+  for (int o = 0; o < NO; ++o) {   // Q14, half away from zero (std::round)
+    const double a = o * M_PI / NO;
+    k.rot_c[o] = (int)std::round(std::cos(a) * 16384.0);
+    k.rot_s[o] = (int)std::round(std::sin(a) * 16384.0);
+  }
 }
 
 }  // namespace rift2
@@ -269,10 +275,13 @@ struct Layout {
 };
 
 // max_kp: keypoints one detector pass keeps; kp_cap: keypoint list capacity per image.
-Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners, bool debug) {
+Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners, bool debug,
+                      bool spatial) {
   Layout L{};
   const size_t P = (size_t)H * W;
-  L.mim_pitch = (int)align_up((size_t)(W > 112 ? W : 112), 16);
+  // at least one TMA box wide (112 bytes; 160 for the spatial variant's window)
+  const size_t box_w = spatial ? 160 : 112;
+  L.mim_pitch = (int)align_up((size_t)W > box_w ? (size_t)W : box_w, 16);
   L.cap_cand = ((H + 1) / 2) * ((W + 1) / 2);
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
@@ -297,7 +306,7 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   L.chist = take(multi ? (size_t)g * ((size_t)1 << TOPK_DIGIT_BITS) * 4 : 0);
   L.sel = take(multi ? (size_t)g * 4 * 4 : 0);
   L.comp = take(multi ? (size_t)g * topk_fast_cap(max_kp) * 8 : 0);
-  L.raw = take((size_t)g * kp_cap * DESC_DIM * 2);
+  L.raw = take((size_t)g * kp_cap * DESC_DIM * 2 * (spatial ? 2 : 1));
   L.info = take((size_t)g * kp_cap * 4);
   L.off = take((size_t)g * kp_cap * 4);
   const size_t none = (size_t)-1;
@@ -314,7 +323,8 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
 
 Layout ctx_layout(const rift2_ctx* c, int g, int H, int W, bool debug) {
   return extract_layout(g, H, W, c->kp.max_kp, c->kp.kp_cap,
-                        (c->p.flags & RIFT2_FLAG_CORNERS) != 0, debug);
+                        (c->p.flags & RIFT2_FLAG_CORNERS) != 0, debug,
+                        c->kp.desc_mode == DESC_SPATIAL);
 }
 
 template <typename T>
@@ -322,10 +332,14 @@ T* at(void* base, size_t off) {
   return off == (size_t)-1 ? nullptr : reinterpret_cast<T*>(static_cast<char*>(base) + off);
 }
 
+// The MIM as a [g][H][pitch] uint8 tensor for the descriptor kernel's TMA staging (box
+// shape: describe_box(), which depends on the descriptor mode).
 int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int g, int H, int pitch) {
   cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)H, (cuuint64_t)g};
   cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * H};
-  cuuint32_t box[3] = {RIFT2_PATCH + 16, (cuuint32_t)describe_box_rows(), 1};
+  int bw = 0, bh = 0;
+  describe_box(c->kp.desc_mode, &bw, &bh);
+  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, mim, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -571,6 +585,8 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
       !(p.lp_cutoff > 0) || p.lp_order < 1 || p.fast_arc < 1 || p.fast_arc > 16 ||
       p.max_keypoints < 1 || p.max_keypoints > 32768 || !(p.fast_threshold >= 0) ||
       ((p.flags & RIFT2_FLAG_RIFT_RING) && (p.flags & RIFT2_FLAG_RIFT_TEMPLATE)) ||
+      ((p.flags & RIFT2_FLAG_SPATIAL_NORM) &&
+       (p.flags & (RIFT2_FLAG_RIFT_RING | RIFT2_FLAG_RIFT_TEMPLATE))) ||
       !(p.second_ratio >= 0) || !(p.eps > 0))
     return RIFT2_E_INVAL;
   int ndev = 0;
@@ -768,6 +784,31 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
       RIFT2_CU(launch_match_tc(mp, g, cap, c->ws, &ta, &tb, nsplit, c->status, st));
     }
   }
+  return RIFT2_OK;
+}
+
+int rift2_evaluate(rift2_ctx* c, int n, const rift2_features* a, const rift2_features* b,
+                   const rift2_matches* m, const double* affine, double tol, double rmse_cap,
+                   int min_correct, rift2_evaluation* out, void* stream) {
+  if (!c || n < 1 || n > MAXB || !a || !b || !m || !affine || !out || !(tol > 0) ||
+      !(rmse_cap >= 0))
+    return RIFT2_E_INVAL;
+  EvalPtrs ep{};
+  for (int i = 0; i < n; ++i) {
+    if (!a[i].kp_xy || !b[i].kp_xy || !m[i].kp_a || !m[i].kp_b || !m[i].count)
+      return RIFT2_E_INVAL;
+    ep.xy_a[i] = a[i].kp_xy;
+    ep.xy_b[i] = b[i].kp_xy;
+    ep.kp_a[i] = m[i].kp_a;
+    ep.kp_b[i] = m[i].kp_b;
+    ep.count[i] = m[i].count;
+  }
+  for (int i = 0; i < 6 * n; ++i) ep.affine[i] = affine[i];   // passed by value
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ep.out = out;
+  c->launches += 1;
+  RIFT2_CU(launch_evaluate(ep, n, tol, rmse_cap, min_correct, st));
   return RIFT2_OK;
 }
 

@@ -126,6 +126,18 @@ def rotate_bilinear(img: np.ndarray, angle_deg: float) -> np.ndarray:
     return out
 
 
+def ground_truth_affine(angle_deg: float, shape) -> tuple:
+    """The known transform of a pair as (t0..t5), (x', y') = (t0 x + t1 y + t2,
+    t3 x + t4 y + t5): image B is image A sampled through the rotation by angle_deg about
+    ((W-1)/2, (H-1)/2) (rotate_bilinear), so a point p of A appears in B at
+    [[cos, sin], [-sin, cos]] (p - c) + c."""
+    h, w = shape
+    cy, cx = (h - 1) / 2.0, (w - 1) / 2.0
+    t = math.radians(angle_deg)
+    c, s = math.cos(t), math.sin(t)
+    return (c, s, cx - c * cx - s * cy, -s, c, cy + s * cx - c * cy)
+
+
 def make_pair(h: int, w: int, seed: int, angle_deg: float | None = None,
               n_blobs: int | None = None, n_segments: int | None = None) -> Pair:
     """One seeded pair. angle_deg=None draws the rotation uniformly from [0, 360)."""

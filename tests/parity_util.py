@@ -71,8 +71,19 @@ def worst_above_floor(got, exp, floor_frac):
     return float(r.flat[i]), i, int((r > 1e-4).sum())
 
 
-def assert_map(name, got, exp, floor_frac, bar=1e-4):
-    """Element-wise |got - exp| / max(|exp|, floor * max|exp|) < bar, reporting the worst."""
+def assert_map(name, got, exp, floor_frac, bar=1e-4, extra_den=None):
+    """Element-wise |got - exp| / max(|exp|, floor * max|exp|[, extra_den]) < bar, reporting
+    the worst element."""
+    if extra_den is not None:
+        got = np.asarray(got, dtype=np.float64)
+        exp = np.asarray(exp, dtype=np.float64)
+        scale = np.max(np.abs(exp))
+        den = np.maximum(np.maximum(np.abs(exp), floor_frac * scale), extra_den)
+        r = np.abs(got - exp) / den
+        i = int(np.argmax(r))
+        w, n = float(r.flat[i]), int((r > bar).sum())
+        assert w < bar, f"{name}: worst rel err {w:.3e} at flat index {i} ({n} elements above {bar})"
+        return w
     w, i, n = worst_above_floor(got, exp, floor_frac)
     assert w < bar, f"{name}: worst rel err {w:.3e} at flat index {i} ({n} elements above {bar})"
     return w

@@ -550,3 +550,125 @@ def test_merge_keypoints_brute_force():
         assert [tuple(q) for q in xy[ne:]] == [q for q, _ in exp]
         assert np.array_equal(v[ne:], np.array([w for _, w in exp]))
         assert len({tuple(q) for q in xy}) == len(xy)
+
+
+# ------------------------------------------- spatial orientation normalisation (R14)
+def _structured_mim(n, seed):
+    """A MIM with spatial structure (smoothed random orientation field, quantised) so that
+    dominant indices and centroids vary between keypoints; int values 0..5."""
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    k = np.fft.fftfreq(n)
+    lp = np.exp(-(k[:, None] ** 2 + k[None, :] ** 2) / (2 * 0.02 ** 2))
+    z = np.fft.ifft2(np.fft.fft2(f) * lp)
+    ang = np.angle(z) + math.pi                           # [0, 2 pi)
+    return (np.floor(ang / (2 * math.pi) * 6).astype(np.int64) % 6).astype(np.uint8)
+
+
+def _unambiguous(mim, x, y, p):
+    """Keypoints whose dominant / secondary choice and frame sides have no exact tie (ties
+    break by the lowest index, which a rotation of the values does not preserve)."""
+    off = O.disc_offsets(p)
+    vals, inside = O.mim_at(mim, x, y, off)
+    hist = np.bincount(vals[inside], minlength=6)[:6]
+    srt = np.sort(hist)[::-1]
+    if srt[0] == srt[1] or srt[1] == srt[2]:
+        return False
+    s, s2, has2 = O.dominant_indices(hist, p)
+    if 1000 * hist[s2] == 800 * hist[s]:
+        return False
+    for w in ([s, s2] if has2 else [s]):
+        c, sn = O.rotation_q14(w, p)
+        sel = vals == w
+        if int(off[sel, 0].sum()) * c - int(off[sel, 1].sum()) * sn == 0:
+            return False
+    return True
+
+
+def test_spatial_frame_zero_is_the_axis_aligned_descriptor():
+    """In frame 0 (dominant index 0, centroid on the +x side) with the whole patch inside
+    the image, the rotated grid is the R7 window itself: the R14 descriptor equals RIFT2's
+    descriptor recoded by 0, built here from explicit cell slices."""
+    p = O.Params()
+    rng = np.random.default_rng(17)
+    mim = rng.integers(1, 6, size=(200, 220)).astype(np.uint8)
+    mim[:, 110:] = np.where(rng.random((200, 110)) < 0.6, 0, mim[:, 110:])
+    x, y = 110, 100
+    d, dkp, ddom, info = O.describe_spatial(mim, np.array([[x, y]]), p)
+    assert info[0][0] == 0 and ddom[0] == 0
+    assert O.spatial_frame(mim, x, y, 0, p) == (1 << 14, 0)
+    patch = mim[y - 48:y + 48, x - 48:x + 48].astype(np.int64)
+    exp = np.concatenate([np.bincount(patch[16 * i:16 * i + 16, 16 * j:16 * j + 16].ravel(),
+                                      minlength=6) for i in range(6) for j in range(6)])
+    assert np.array_equal(d[0], exp)
+    # Q14 table: exact values at 0 and 90 degrees, symmetric rounding elsewhere
+    assert O.rotation_q14(0) == (16384, 0) and O.rotation_q14(3) == (0, 16384)
+    assert O.rotation_q14(1) == (round(16384 * math.sqrt(3) / 2), 8192)
+
+
+@pytest.mark.parametrize("turns", [1, 2, 3])
+def test_spatial_descriptor_invariant_under_quarter_turns(turns):
+    """R14 makes the descriptor itself rotation invariant, not only up to a permutation of
+    its cells (as RIFT2's index recoding alone is, §III): on an odd-size MIM turned by
+    turns x 90 degrees (the values shifting by 3 turns mod 6, as the filter bank's
+    orientations do) every keypoint without an exact tie has identical descriptors,
+    including keypoints whose rotated grid leaves the image."""
+    p = O.Params()
+    n = 151
+    mim = _structured_mim(n, 5)
+    mim_r = ((np.rot90(mim, turns).astype(np.int64) + 3 * turns) % 6).astype(np.uint8)
+    rng = np.random.default_rng(9)
+    pts = rng.integers(48, n - 48, size=(60, 2))
+    checked = 0
+    for x, y in pts.tolist():
+        # np.rot90 (k=1): pixel (x, y) moves to (y, n-1-x)
+        xr, yr = x, y
+        for _ in range(turns):
+            xr, yr = yr, n - 1 - xr
+        if not (_unambiguous(mim, x, y, p) and 48 <= xr < n - 48 and 48 <= yr < n - 48):
+            continue
+        d, _, dom, _ = O.describe_spatial(mim, np.array([[x, y]]), p)
+        dr, _, dom_r, _ = O.describe_spatial(mim_r, np.array([[xr, yr]]), p)
+        assert np.array_equal((dom + 3 * turns) % 6, dom_r)
+        assert np.array_equal(d, dr), (x, y)
+        checked += 1
+    assert checked >= 30
+    # RIFT2's recoding alone leaves the cells permuted: its descriptors differ here
+    x, y = 75, 75
+    a = O.describe(mim, np.array([[x, y]]), p)[0]
+    b = O.describe(mim_r, np.array([[x if turns == 2 else y, n - 1 - x if turns == 1 else
+                                     (n - 1 - x if turns == 2 else x)]]), p)[0]
+    assert not np.array_equal(a[:1], b[:1])
+
+
+def test_spatial_normalisation_follows_the_rotation_direction():
+    """The grid turns the way the filter bank's orientation index does (counter-clockwise
+    as displayed, pinned by the grating tests): for a scene and its copy turned by 30
+    degrees (bilinear, so only approximately equal), R14 descriptors of corresponding
+    keypoints are far closer than with the grid turned the other way."""
+    from synth import rotate_bilinear, scene
+    p = O.Params()
+    n = 161
+    img = scene(n, n, np.random.Generator(np.random.PCG64(31)), n_blobs=25, n_segments=12)
+    rot = rotate_bilinear(img, 30.0)
+    mim = O.max_index_map(O.amplitude_sums(O.responses(img)))[0]
+    mim_r = O.max_index_map(O.amplitude_sums(O.responses(rot)))[0]
+    c = (n - 1) / 2
+    th = math.radians(30.0)
+    dists = {"ccw": [], "cw": []}
+    rng = np.random.default_rng(4)
+    for x, y in rng.integers(60, n - 60, size=(40, 2)).tolist():
+        # where (x, y) of img lands in rot: rotate_bilinear samples img at R^-1 (q - c) + c
+        dx, dy = x - c, y - c
+        xr = int(round(math.cos(th) * dx + math.sin(th) * dy + c))
+        yr = int(round(-math.sin(th) * dx + math.cos(th) * dy + c))
+        if not (48 <= xr < n - 48 and 48 <= yr < n - 48):
+            continue
+        d0 = O.describe_spatial(mim, np.array([[x, y]]), p)[0][0].astype(float)
+        d1 = O.describe_spatial(mim_r, np.array([[xr, yr]]), p)[0][0].astype(float)
+        dists["ccw"].append(np.linalg.norm(d0 - d1))
+        # the other turning sense: the same construction on the mirrored scene
+        m0 = O.describe_spatial(mim[:, ::-1], np.array([[n - 1 - x, y]]), p)[0][0].astype(float)
+        dists["cw"].append(np.linalg.norm(m0 - d1))
+    assert len(dists["ccw"]) >= 15
+    assert np.median(dists["ccw"]) < 0.6 * np.median(dists["cw"]), dists
