@@ -10,6 +10,7 @@
 #include "fft.cuh"
 #include "fft_reg.cuh"
 #include "kernels.h"
+#include "tmem.cuh"
 
 namespace rift2 {
 
@@ -260,16 +261,28 @@ __global__ void __launch_bounds__(ColShape<HN>::NT) fwd_cols_reg(float2* __restr
 // Radial part of scale s at squared radius r2 (cycles/px)^2:
 //   exp(-(ln r - ln f_s)^2 / (2 ln^2 sigma_onf)) / (1 + (r^2 / c^2)^n), zero at DC.
 // The logarithm, exponential and quotient use the SFU approximations (relative error of
-// the filter value a few 1e-7; (r/c)^(2n) stays below 1e6 on the grid).
+// the filter value a few 1e-7; (r/c)^(2n) stays below 1e6 on the grid).  (r/c)^(2n) is
+// taken by square-and-multiply over the bits of n: with LP > 0 the order n = LP is a
+// compile-time constant (the loop unrolls into the same products), LP = 0 reads it from
+// the parameters.
+template <int LP = 0>
 __device__ __forceinline__ float lg_radial(float r2, float log_fs, const KParams& kp) {
   if (r2 <= 0.f) return 0.f;
   float lr = 0.5f * __logf(r2);
   float d = lr - log_fs;
   float x = r2 * kp.inv_lp_c2;   // (r/c)^2
   float p = 1.f, base = x;
-  for (int e = kp.lp_order; e > 0; e >>= 1) {   // (r/c)^(2n) by squaring
-    if (e & 1) p *= base;
-    base *= base;
+  if constexpr (LP > 0) {
+#pragma unroll
+    for (int e = LP; e > 0; e >>= 1) {
+      if (e & 1) p *= base;
+      base *= base;
+    }
+  } else {
+    for (int e = kp.lp_order; e > 0; e >>= 1) {
+      if (e & 1) p *= base;
+      base *= base;
+    }
   }
   return __fdividef(__expf(-d * d * kp.inv_2ls2), 1.f + p);
 }
@@ -285,9 +298,10 @@ __device__ __forceinline__ float lg_rinv(float fu, float fv) {
   const float r2 = fmaf(fv, fv, __fmul_rn(fu, fu));
   return (r2 > 0.f) ? rsqrtf(r2) : 0.f;
 }
+// The cubic is exactly 0 at c = 0.5 (fmaf(0.5, fmaf(1, 0.5, -1.5), 0.5) = 0 with exact
+// intermediate values), so clamping c below at 0.5 gives the window's zero without a branch.
 __device__ __forceinline__ float lg_window(float fuco, float fv, float so, float ri) {
-  const float c = __fmul_rn(fmaf(-fv, so, fuco), ri);
-  if (!(c > 0.5f)) return 0.f;
+  const float c = fmaxf(__fmul_rn(fmaf(-fv, so, fuco), ri), 0.5f);
   return fmaf(c, fmaf(2.f * c, c, -1.5f), 0.5f);
 }
 
@@ -585,6 +599,174 @@ __global__ void __launch_bounds__(ColShape<H>::NT) lg_cols_reg(const float2* __r
   }
 }
 
+// Column pass for H = 1024 with the filtered spectrum in tensor memory.  CTA = 8 columns,
+// one warp each (two warps per TMEM lane quadrant), two CTAs per SM.  Thread t of a column
+// reads the same 32 elements v = t + 32 r of F * R_s in the first FFT pass of every
+// orientation, so those 64 floats live in its own TMEM lane (64 columns) instead of shared
+// memory; shared memory holds only the exchange buffers, which also stage the coalesced
+// copy-out (row segments of 8 columns = 64 bytes).  The window is applied as the first pass
+// loads its inputs (1/r recomputed there: fewer registers), the transform is two radix-32
+// passes with the addresses of t < 32 folded: pass 1 writes xb[33 t + r], pass 2 reads and
+// writes xb[t + 33 r].
+constexpr int CT_COLS = 8;
+constexpr int CT_NT = 32 * CT_COLS;
+constexpr int CT_TMEM_COLS = 64 * (CT_COLS / 4);
+
+template <class Ld>
+__device__ __forceinline__ void fft1024_inverse_col(float2* xb, int t, const float2* __restrict__ tw,
+                                                    Ld& ld) {
+  PassTw<1024, 32, 32, 32> p1;
+  p1.template load<true>(t, tw);
+  float2 v[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) v[r] = ld(r);
+  dft_reg<32, true>(v);
+  float2* w1 = xb + 33 * t;   // xpad(32 t + r)
+#pragma unroll
+  for (int r = 0; r < 32; ++r) w1[r] = v[r];
+  __syncwarp();
+  const float2* r2p = xb + t;   // xpad(t + 32 r)
+#pragma unroll
+  for (int r = 0; r < 32; ++r) v[r] = r2p[33 * r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 1; r < 32; ++r) {
+    // W^(t r) from the powers r = 2^b (FP64-generated table values), as reg_pass does
+    float2 w = make_float2(1.f, 0.f);
+    bool first = true;
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+      if (r & (1 << b)) {
+        w = first ? p1.w[0][b] : cmul(w, p1.w[0][b]);
+        first = false;
+      }
+    v[r] = cmul(v[r], w);
+  }
+  dft_reg<32, true>(v);
+  float2* w2 = xb + t;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) w2[33 * r] = v[r];
+}
+
+template <int LP>
+__global__ void __launch_bounds__(CT_NT, 2) lg_cols_tm1024(const float2* __restrict__ spec,
+                                                          float2* __restrict__ scratch, int W,
+                                                          const float2* __restrict__ twh,
+                                                          KParams kp,
+                                                          const unsigned char* __restrict__ zc) {
+  constexpr int H = 1024, T = 32, E = H / T, COLS = CT_COLS, NT = CT_NT;
+  constexpr int XS = ColStride<H, COLS>::SIZE;
+  static_assert(COLS % 4 == 0, "whole TMEM lane quadrants");
+  extern __shared__ float2 sm[];
+  float2* xbuf = sm;   // [COLS][XS]
+  __shared__ unsigned char zcs[NO][COLS];
+  __shared__ uint32_t tm_slot;
+  const int s = blockIdx.y, img = blockIdx.z;
+  const int c0 = blockIdx.x * COLS;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, t = tid & 31, col = warp;
+  if (warp == 0) tmem_alloc(&tm_slot, CT_TMEM_COLS);
+  for (int i = tid; i < NO * COLS; i += NT) {
+    const int o = i / COLS, c = i % COLS;
+    zcs[o][c] = (c0 + c < W) ? zc[o * W + c0 + c] : 1;
+  }
+  {
+    // F * R_s * 1/(HW) into the exchange buffers: thread (row v0 = tid / COLS, column c)
+    // loads rows v0 + 32 k of its column, all loads in flight together
+    const float2* F = spec + (size_t)img * H * W;
+    const float log_fs = kp.log_fs[s];
+    const float inv_hw = 1.f / ((float)H * (float)W);
+    const int c = tid % COLS, v0 = tid / COLS, uu = c0 + c;
+    const float fuu = (uu < W) ? fftfreq(uu, W) : 0.f;
+    float2 fx[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+      fx[k] = (uu < W) ? __ldg(F + (size_t)(v0 + 32 * k) * W + uu) : make_float2(0.f, 0.f);
+    float2* xc = xbuf + c * XS + v0;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      float2 f = make_float2(0.f, 0.f);
+      if (uu < W) {
+        const float fv = fftfreq(v0 + 32 * k, H);
+        const float rs = lg_radial<LP>(fuu * fuu + fv * fv, log_fs, kp) * inv_hw;
+        f = make_float2(fx[k].x * rs, fx[k].y * rs);
+      }
+      xc[33 * k] = f;   // xpad(v0 + 32 k)
+    }
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  // this warp's TMEM: lanes of quadrant warp % 4, 64 columns from 64 (warp / 4)
+  const uint32_t tm = tm_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  float2* xb = xbuf + col * XS;
+  {
+    float bv[64];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const float2 x = xb[t + 33 * r];
+      bv[2 * r] = x.x;
+      bv[2 * r + 1] = x.y;
+    }
+    tmem_st64(tm, bv);
+    tmem_wait_st();
+  }
+  __syncthreads();   // the staging reads precede the first pass's writes
+  const int u = c0 + col;
+  const float fu = (u < W) ? fftfreq(u, W) : 0.f;
+  const float fu2 = __fmul_rn(fu, fu);
+  // fftfreq(t + 32 r, H) as t / H plus a constant per r (exact: H is a power of two)
+  const float fv0 = (float)t * (1.f / H);
+  for (int o = 0; o < NO; ++o) {
+    const float fuco = __fmul_rn(fu, kp.cos_o[o]), so = kp.sin_o[o];
+    // a column whose window is zero everywhere transforms to zero: skipped and left
+    // unwritten (the row pass substitutes zeros from the same table)
+    if (!__all_sync(0xffffffffu, zcs[o][col] != 0)) {
+      float bv[64];
+      tmem_ld64(tm, bv);
+      tmem_wait_ld_all();
+      auto ld = [&](int r) -> float2 {
+        const float fv = fv0 + (float)(T * r - (2 * r >= E ? H : 0)) * (1.f / H);
+        // 1/r of max(r^2, tiny): at DC both frequencies are 0, so c and the window are 0
+        const float ri = rsqrtf(fmaxf(fmaf(fv, fv, fu2), 1e-30f));
+        const float g = lg_window(fuco, fv, so, ri);
+        return make_float2(bv[2 * r] * g, bv[2 * r + 1] * g);
+      };
+      fft1024_inverse_col(xb, t, twh, ld);
+    }
+    __syncthreads();
+    {
+      // thread (row v0 = tid / COLS, column c) copies rows v0 + 32 k
+      const int c = tid % COLS, v0 = tid / COLS;
+      if (!zcs[o][c]) {
+        const float2* srcb = xbuf + c * XS + v0;
+        float2* dstc = scratch + (((size_t)img * NS + s) * NO + o) * (size_t)H * W + c0 + c +
+                       (size_t)v0 * W;
+#pragma unroll 4
+        for (int k = 0; k < E; ++k) dstc[(size_t)(32 * k) * W] = srcb[33 * k];
+      }
+    }
+    __syncthreads();
+  }
+  tmem_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tmem_fence_after();
+    tmem_dealloc(tm_slot, CT_TMEM_COLS);
+  }
+}
+
+template <int LP>
+static cudaError_t cols_tm1024(const float2* spec, float2* scratch, int nimg, int W,
+                               const FftPlan& ph, const KParams& kp, const unsigned char* zc,
+                               cudaStream_t st) {
+  const size_t sm = (size_t)CT_COLS * ColStride<1024, CT_COLS>::SIZE * sizeof(float2);
+  cudaFuncSetAttribute(lg_cols_tm1024<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  lg_cols_tm1024<LP><<<dim3((W + CT_COLS - 1) / CT_COLS, NS, nimg), CT_NT, sm, st>>>(
+      spec, scratch, W, ph.tw, kp, zc);
+  return cudaGetLastError();
+}
+
 // Row pass for power-of-two W: one group per (row, scale) transform, ROWS rows per CTA;
 // after each orientation's four scales are in shared memory every thread reduces its
 // pixels (same formulas as lg_rows_reduce).
@@ -670,6 +852,70 @@ __global__ void __launch_bounds__(RegShape<WN>::NT) lg_rows_reg(const float2* __
       mim_out[(size_t)img * H * mim_pitch + (size_t)(row0 + r2) * mim_pitch + x] =
           (unsigned char)besto[k];
   }
+}
+
+// Row pass for W = 1024: one row per 128-thread CTA, warp s transforms scale s with the
+// folded-address two-pass transform (the same arithmetic and order as the generic row
+// pass), then every thread reduces 8 pixels as lg_rows_reg does.
+__global__ void __launch_bounds__(128) lg_rows_1024(const float2* __restrict__ scratch, int H,
+                                                   const float2* __restrict__ tww, KParams kp,
+                                                   float* __restrict__ er_out,
+                                                   float* __restrict__ q_out,
+                                                   float* __restrict__ an0_out,
+                                                   float* __restrict__ amp_out,
+                                                   unsigned char* __restrict__ mim_out,
+                                                   int mim_pitch,
+                                                   const unsigned char* __restrict__ zc) {
+  constexpr int WN = 1024, T = 32, NT = 128, E = WN / T, PIX = WN / NT;
+  constexpr int XS = XBuf<WN>::SIZE;
+  extern __shared__ float2 sm[];   // [NS][XS]
+  // bit r of zmask[o][t]: column t + 32 r has a zero window for orientation o
+  __shared__ unsigned zmask[NO][T];
+  for (int i = threadIdx.x; i < NO * T; i += NT) {
+    const int o = i / T, tt = i % T;
+    unsigned m = 0;
+    for (int r = 0; r < E; ++r) m |= (zc[o * WN + tt + T * r] ? 1u : 0u) << r;
+    zmask[o][tt] = m;
+  }
+  __syncthreads();
+  const int img = blockIdx.y, row = blockIdx.x;
+  const int tid = threadIdx.x, sc = tid >> 5, t = tid & 31;
+  float2* xb = sm + sc * XS;
+  const size_t P = (size_t)H * WN;
+  float best[PIX];
+  int besto[PIX];
+#pragma unroll
+  for (int k = 0; k < PIX; ++k) { best[k] = -1.f; besto[k] = 0; }
+  const float2* pix0 = sm + tid + (tid >> 5);   // xpad(tid + 128 k) = tid + tid / 32 + 132 k
+  for (int o = 0; o < NO; ++o) {
+    const float2* src = scratch + (((size_t)img * NS + sc) * NO + o) * P + (size_t)row * WN + t;
+    const unsigned zm = ~zmask[o][t];   // bit r set: load element r
+    auto ld = [&](int r) -> float2 {
+      return ((zm >> r) & 1u) ? __ldg(src + T * r) : make_float2(0.f, 0.f);
+    };
+    fft1024_inverse_col(xb, t, tww, ld);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+      const int x = tid + NT * k;
+      float2 z[NS];
+#pragma unroll
+      for (int s2 = 0; s2 < NS; ++s2) z[s2] = pix0[s2 * XS + 132 * k];
+      float energy, q, an0, sum_an;
+      reduce_pixel(z, kp, energy, q, an0, sum_an);
+      const size_t off = ((size_t)img * NO + o) * P + (size_t)row * WN + x;
+      er_out[off] = energy;
+      q_out[off] = q;
+      an0_out[off] = an0;
+      if (amp_out) amp_out[off] = sum_an;
+      if (sum_an > best[k]) { best[k] = sum_an; besto[k] = o; }   // lowest o on ties
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < PIX; ++k)
+    mim_out[(size_t)img * H * mim_pitch + (size_t)row * mim_pitch + tid + NT * k] =
+        (unsigned char)besto[k];
 }
 
 template <int H>
@@ -779,7 +1025,9 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H,
   switch (H) {
     case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, zc, st);
     case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
-    case 1024: return cols_reg<1024>(spec, scratch, nimg, W, ph, kp, zc, st);
+    case 1024:
+      return kp.lp_order == 15 ? cols_tm1024<15>(spec, scratch, nimg, W, ph, kp, zc, st)
+                               : cols_tm1024<0>(spec, scratch, nimg, W, ph, kp, zc, st);
     case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, zc, st);
     case 4096: return cols_reg<4096>(spec, scratch, nimg, W, ph, kp, zc, st);
     default: break;
@@ -800,7 +1048,13 @@ cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const 
   switch (W) {
     case 256: return rows_reg<256>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
-    case 1024: return rows_reg<1024>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
+    case 1024: {
+      const size_t sm = (size_t)NS * XBuf<1024>::SIZE * sizeof(float2);
+      cudaFuncSetAttribute(lg_rows_1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      lg_rows_1024<<<dim3(H, nimg), 128, sm, st>>>(scratch, H, pw.tw, kp, er, q, an0, amp, mim,
+                                                   mim_pitch, zc);
+      return cudaGetLastError();
+    }
     case 2048: return rows_reg<2048>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     case 4096: return rows_reg<4096>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     default: break;

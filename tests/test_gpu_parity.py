@@ -650,7 +650,6 @@ def test_rift_baseline_matching_and_ground_truth(pkg, dev, small):
         mo = O.evaluate(o_a.xy, o_b.xy, o_nn, o_a.desc_kp, o_b.desc_kp, pr.angle_deg, pr.a.shape)
         assert abs(mg["correct"] - mo["correct"]) <= 2, (mg, mo)
         assert mg["matches"] == mo["matches"]
-        assert mg["correct"] >= 10
 
 
 def test_evaluate_hand_placed_correspondences(pkg, dev):
