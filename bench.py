@@ -328,8 +328,13 @@ def run_ours(args):
     # steps' copies lie inside the timed region
     copy_stream = torch.cuda.Stream(device=dev)
     dbuf = [[torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host[0]] for _ in range(2)]
+    # every pair's correspondences (q_desc, nn_desc, kp_a, kp_b, d1, d2 as 32-bit words,
+    # near_tie bytes, the row count) and both images' keypoints (x, y, score, n_kp, n_desc)
     ncap = matches[0].nn_desc.shape[0]
-    out_h = [torch.empty(2 * ncap + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
+    kcap = feats[0].kp_xy.shape[0]
+    out_h = [torch.empty(6 * ncap + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
+    tie_h = [torch.empty(ncap, dtype=torch.uint8).pin_memory() for _ in range(B)]
+    kp_h = [torch.empty(3 * kcap + 2, dtype=torch.int32).pin_memory() for _ in range(2 * B)]
     ev_copied = [torch.cuda.Event() for _ in range(args.steps)]
     ev_done = [torch.cuda.Event() for _ in range(args.steps)]
     barrier()
@@ -348,9 +353,15 @@ def run_ours(args):
         step(buf)
         for b in range(B):
             m = matches[b]
-            out_h[b][:ncap].copy_(m.nn_desc, non_blocking=True)
-            out_h[b][ncap:2 * ncap].copy_(m.d1.view(torch.int32), non_blocking=True)
-            out_h[b][2 * ncap:].copy_(m.count, non_blocking=True)
+            for k, tsr in enumerate((m.q_desc, m.nn_desc, m.kp_a, m.kp_b, m.d1.view(torch.int32),
+                                     m.d2.view(torch.int32))):
+                out_h[b][k * ncap:(k + 1) * ncap].copy_(tsr, non_blocking=True)
+            out_h[b][6 * ncap:].copy_(m.count, non_blocking=True)
+            tie_h[b].copy_(m.near_tie, non_blocking=True)
+        for j, f in enumerate(feats):
+            kp_h[j][:2 * kcap].copy_(f.kp_xy.view(-1), non_blocking=True)
+            kp_h[j][2 * kcap:3 * kcap].copy_(f.kp_score.view(torch.int32), non_blocking=True)
+            kp_h[j][3 * kcap:].copy_(f.counts, non_blocking=True)
         ev_done[i].record(stream)
     e1.record(stream)
     e1.synchronize()
@@ -358,7 +369,7 @@ def run_ours(args):
     barrier()
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(sum(e2e_ms), dev))
     h2d = int(sum(t.numel() for t in host[0]) * 4)
-    d2h = int(B * (2 * ncap + 1) * 4)
+    d2h = int(B * ((6 * ncap + 1) * 4 + ncap) + 2 * B * (3 * kcap + 2) * 4)
 
     # graph form: the step's launches (extract + match of the whole batch, every size
     # group) captured once into a CUDA graph and replayed; the context's plans, tables and
@@ -428,11 +439,10 @@ def run_ours(args):
                  "form": f"two contexts on two streams, {half} + {B - half} pairs per step"}
         ctx2.close()
 
-    # plain form: one pair per call, no grouping, CUDA-core matcher
-    plain = None
-    if not args.no_plain and args.workload == 1:
-        pctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP,
-                                              flags=pkg.FLAG_PLAIN_MATCH | pkg.FLAG_NO_GROUPING),
+    # plain forms: one pair per call, no launch grouping; with the CUDA-core matcher and
+    # with the tensor-core one (the latter isolates the gain from batching)
+    def plain_form(flags, label):
+        pctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP, flags=flags),
                            device=local, hbm_budget=16 << 30)
         pf = [pctx.alloc_features() for _ in range(2)]
         pm = [pctx.alloc_matches()]
@@ -448,11 +458,18 @@ def run_ours(args):
             if i >= 2:
                 lat.append(e0.elapsed_time(e1))
         lat.sort()
-        plain = {"value": 1000.0 / statistics.mean(lat), "unit": "pairs/s",
-                 "latency_ms_p50": lat[len(lat) // 2],
-                 "latency_ms_p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
-                 "form": "one pair per call, no launch grouping, CUDA-core matcher"}
         pctx.close()
+        return {"value": 1000.0 / statistics.mean(lat), "unit": "pairs/s",
+                "latency_ms_p50": lat[len(lat) // 2],
+                "latency_ms_p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                "form": label}
+
+    plain = plain_tc = None
+    if not args.no_plain and args.workload == 1:
+        plain = plain_form(pkg.FLAG_PLAIN_MATCH | pkg.FLAG_NO_GROUPING,
+                           "one pair per call, no launch grouping, CUDA-core matcher")
+        plain_tc = plain_form(pkg.FLAG_NO_GROUPING,
+                              "one pair per call, no launch grouping, tensor-core matcher")
 
     # roofline of the dominant HBM-bound stage
     peak, peak_kind = load_peaks()
@@ -476,7 +493,8 @@ def run_ours(args):
                     "peak_kind": tkind, "unit": "TFLOP/s",
                     "frac": gemm_flop / match_s / 1e12 / tpeak,
                     "flop_per_step": gemm_flop, "descriptors": [na, nb],
-                    "note": "whole match stage (BF16 prep, tcgen05 GEMM + top-8, exact re-rank)"}
+                    "note": "whole match stage (BF16 prep, tcgen05 GEMM + top-4 screen per column "
+                            "half, certified exact re-rank, exhaustive pass for uncertified queries)"}
 
     # RIFT's own rotation handling on the same batches (§II-C): template descriptors for A,
     # the six-member convolution ring for B, matching A against all ring members
@@ -567,6 +585,7 @@ def run_ours(args):
                              " and each step streams ~0.3 KB of workspace per pixel, > L2"},
             "mpix_per_s": value * px_per_step / B / 1e6,
             "plain_form": plain,
+            "plain_form_tensor_matcher": plain_tc,
             "graph_form": graph,
             "two_lane_form": lanes,
             "serving": serving,
@@ -581,7 +600,9 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "form": "pinned host images in on a copy stream (step i+1's copy overlaps "
-                            "step i's kernels), matches out every step",
+                            "step i's kernels); every step copies out each pair's full "
+                            "correspondences (q_desc, nn_desc, kp_a, kp_b, d1, d2, near_tie, count) "
+                            "and both images' keypoints (xy, score, counts)",
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,

@@ -73,13 +73,23 @@ def _add_segment(img, rng):
     x1 = min(w, int(math.ceil(max(px, qx) + half + 2)))
     if y0 >= y1 or x0 >= x1:
         return
-    yy = np.arange(y0, y1, dtype=np.float64)[:, None]
-    xx = np.arange(x0, x1, dtype=np.float64)[None, :]
     dx, dy = qx - px, qy - py
     l2 = dx * dx + dy * dy
-    t = np.clip(((xx - px) * dx + (yy - py) * dy) / l2, 0.0, 1.0)
-    dist = np.hypot(xx - (px + t * dx), yy - (py + t * dy))
-    img[y0:y1, x0:x1] += amp * np.clip(1.0 - dist / half, 0.0, 1.0)
+    # tiles of the bounding box whose centre lies farther than half + the tile's half
+    # diagonal from the segment hold no pixel within `half` of it: they would add 0
+    tile = 64
+    for ty in range(y0, y1, tile):
+        for tx in range(x0, x1, tile):
+            ty1, tx1 = min(y1, ty + tile), min(x1, tx + tile)
+            mx, my = 0.5 * (tx + tx1 - 1), 0.5 * (ty + ty1 - 1)
+            tc = min(1.0, max(0.0, ((mx - px) * dx + (my - py) * dy) / l2))
+            if math.hypot(mx - (px + tc * dx), my - (py + tc * dy)) > half + 0.75 * tile:
+                continue
+            yy = np.arange(ty, ty1, dtype=np.float64)[:, None]
+            xx = np.arange(tx, tx1, dtype=np.float64)[None, :]
+            t = np.clip(((xx - px) * dx + (yy - py) * dy) / l2, 0.0, 1.0)
+            dist = np.hypot(xx - (px + t * dx), yy - (py + t * dy))
+            img[ty:ty1, tx:tx1] += amp * np.clip(1.0 - dist / half, 0.0, 1.0)
 
 
 def scene(h: int, w: int, rng: np.random.Generator, n_blobs: int | None = None,
@@ -105,24 +115,30 @@ def rotate_bilinear(img: np.ndarray, angle_deg: float) -> np.ndarray:
     cy, cx = (h - 1) / 2.0, (w - 1) / 2.0
     a = math.radians(angle_deg)
     ca, sa = math.cos(a), math.sin(a)
-    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
     # destination (x, y) samples the source at R^-1 (x - c) + c; screen y points down,
     # so a counter-clockwise on-screen rotation uses +sin in the y row.
-    dx, dy = xx - cx, yy - cy
-    sx = ca * dx - sa * dy + cx
-    sy = sa * dx + ca * dy + cy
-    x0 = np.floor(sx).astype(np.int64)
-    y0 = np.floor(sy).astype(np.int64)
-    fx = sx - x0
-    fy = sy - y0
+    dx = np.arange(w, dtype=np.float64)[None, :] - cx
+    flat = img.ravel()
     out = np.zeros_like(img)
-    for oy in (0, 1):
-        for ox in (0, 1):
-            xi = x0 + ox
-            yi = y0 + oy
-            wgt = (fx if ox else 1 - fx) * (fy if oy else 1 - fy)
-            ok = (xi >= 0) & (xi < w) & (yi >= 0) & (yi < h)
-            out[ok] += wgt[ok] * img[yi[ok], xi[ok]]
+    band = 128   # destination rows per band: the band's source samples stay cache-local
+    for r0 in range(0, h, band):
+        dy = np.arange(r0, min(h, r0 + band), dtype=np.float64)[:, None] - cy
+        sx = ca * dx - sa * dy + cx
+        sy = sa * dx + ca * dy + cy
+        x0 = np.floor(sx).astype(np.int64)
+        y0 = np.floor(sy).astype(np.int64)
+        fx = sx - x0
+        fy = sy - y0
+        acc = out[r0:r0 + band]
+        # the four taps in a fixed order; a tap outside the source adds exactly 0
+        for oy in (0, 1):
+            for ox in (0, 1):
+                xi = x0 + ox
+                yi = y0 + oy
+                wgt = (fx if ox else 1 - fx) * (fy if oy else 1 - fy)
+                ok = (xi >= 0) & (xi < w) & (yi >= 0) & (yi < h)
+                val = flat[np.where(ok, yi * w + xi, 0)]
+                acc += np.where(ok, wgt * val, 0.0)
     return out
 
 
