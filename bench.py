@@ -223,6 +223,161 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------- parity of the sampled pair
+def _worst(got, exp, floor, extra=None):
+    got = np.asarray(got, dtype=np.float64)
+    exp = np.asarray(exp, dtype=np.float64)
+    scale = float(np.max(np.abs(exp)))
+    if scale == 0:
+        return float(np.max(np.abs(got)))
+    den = np.maximum(np.abs(exp), floor * scale)
+    if extra is not None:
+        den = np.maximum(den, extra)
+    return float(np.max(np.abs(got - exp) / den))
+
+
+def parity_summary(pkg, dev, pair, oa, ob, of_match):
+    """Every output of the GPU path on one pair against the FP64 oracle's: worst element-wise
+    relative error of each float map above its floor, integer outputs that differ and how
+    many of those the oracle certifies as near ties (relative top-two margin < 1e-5)."""
+    import torch
+    ctx = pkg.Context(pkg.default_params(max_keypoints=MAX_KP), device=dev.index)
+    fa, fb = ctx.extract([torch.from_numpy(pair.a).to(dev), torch.from_numpy(pair.b).to(dev)],
+                         debug=True)
+    m = ctx.match([fa], [fb])[0]
+    ctx.sync()
+    out = {"pair": "1024x1024 pair of the generator (seed 20231001), images A and B"}
+    maps = {}
+    mim_bad = mim_diff = near_px = 0
+    kp_only = kp_cert = 0
+    hosts = []
+    for f, o in ((fa, oa), (fb, ob)):
+        d = {k: v.cpu().numpy() for k, v in f.debug.items()}
+        mo = o.maps
+        amax = float(np.max(mo["A"]))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            cq = np.where(mo["A"] > 0, mo["q"] * 2.5e-3 * amax / mo["A"], 0.0)
+        ce = mo["A"] / (4.0 * mo["X"]) * 1e-2 * amax
+        vals = {"A_o": _worst(d["amp"], mo["A"], 2.5e-3), "|EO0|": _worst(d["an0"], mo["An0"], 1e-2),
+                "q": _worst(d["q"], mo["q"], 1e-3, cq), "Er": _worst(d["er"], mo["Er"], 5e-2, ce),
+                "PC": _worst(d["pc"], mo["pc"], 1.0), "M": _worst(d["moment"], mo["M"], 1e-2),
+                "T_o": float(np.max(np.abs(d["noise_t"] - mo["T"]) / np.abs(mo["T"]))),
+                "M_normalised_abs": float(np.max(np.abs(d["moment"] - mo["M"])) /
+                                          (mo["M"].max() - mo["M"].min()))}
+        for k, v in vals.items():
+            maps[k] = max(maps.get(k, 0.0), v)
+        mis = d["mim"] != mo["mim"]
+        mim_diff += int(mis.sum())
+        mim_bad += int((mis & (mo["mim_margin"] >= 1e-5)).sum())
+        near_px += int((mo["mim_margin"] < 1e-5).sum())
+        g = f.host()
+        hosts.append(g)
+        gs = {tuple(map(int, q)) for q in g["xy"]}
+        osx = {tuple(map(int, q)) for q in o.xy}
+        for q in gs ^ osx:
+            kp_only += 1
+            kp_cert += int(bool(mo["kp_uncertain"][q[1], q[0]]))
+    out["max_rel_err"] = maps
+    out["tolerance"] = "1e-4 relative above each floor (A_o 2.5e-3, |EO0| 1e-2, q 1e-3 with A's floor, Er 5e-2 with its A/X conditioning, PC 1.0, M 1e-2); T_o 1e-5; M 5e-6 in FAST's normalised units"
+    out["mim"] = {"pixels_differing": mim_diff, "of_which_not_near_ties": mim_bad,
+                  "oracle_near_tie_pixels": near_px}
+    out["keypoints"] = {"in_one_list_only": kp_only, "of_which_certified": kp_cert,
+                        "per_image": [len(h["xy"]) for h in hosts]}
+    # descriptors of keypoints both lists share whose patch has no differing MIM pixel
+    checked = bad = 0
+    for g, f, o in ((hosts[0], fa, oa), (hosts[1], fb, ob)):
+        mis = f.debug["mim"].cpu().numpy() != o.maps["mim"]
+        gi = {tuple(map(int, q)): i for i, q in enumerate(g["xy"])}
+        for k, (x, y) in enumerate(np.asarray(o.xy).tolist()):
+            if (x, y) not in gi or mis[y - 48:y + 48, x - 48:x + 48].any():
+                continue
+            jo = np.flatnonzero(o.desc_kp == k)
+            jg = np.flatnonzero(g["desc_kp"] == gi[(x, y)])
+            checked += 1
+            bad += int(not np.array_equal(g["desc"][jg].astype(np.int64), o.desc[jo]))
+    out["descriptors"] = {"keypoints_compared": checked, "differing": bad}
+    nn, d1, d2, near = of_match(hosts[0]["desc"].astype(np.int64), hosts[1]["desc"].astype(np.int64))
+    mh = m.host()
+    diff = mh["nn_desc"] != nn
+    fin = np.isfinite(d1) & (d1 > 0)
+    out["matches"] = {"rows": int(len(nn)), "nn_differing": int(diff.sum()),
+                      "of_which_not_near_ties": int((diff & ~near).sum()),
+                      "oracle_near_ties": int(near.sum()),
+                      "d1_max_rel_err": float(np.max(np.abs(mh["d1"][fin] - d1[fin]) / d1[fin]))
+                      if fin.any() else 0.0,
+                      "reference": "the oracle's exhaustive search on the GPU's descriptors"}
+    ctx.close()
+    return out
+
+
+# ------------------------------------------------- summaries of the other workloads
+def _make_pair_job(args):
+    import synth
+    h, w, seed = args
+    kw = dict(n_blobs=400, n_segments=200) if (h, w) == (1024, 1024) else {}
+    pr = synth.make_pair(h, w, seed, angle_deg=None, **kw)
+    return pr.a, pr.b
+
+
+def make_pairs(jobs):
+    """Synthetic pairs generated on the host cores (a spawn pool: safe after CUDA init)."""
+    import multiprocessing as mp
+    n = min(len(jobs), os.cpu_count() or 1)
+    if n <= 1:
+        return [_make_pair_job(j) for j in jobs]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(_make_pair_job, jobs, chunksize=1)
+
+
+def workload_summary(pkg, dev, wl_id, steps=4, warmup=3):
+    """pairs/s of a workload other than the headline one, timed the same way (inputs
+    resident, CUDA events on the launching stream), with the kernel launches per step."""
+    import torch
+    wl = WORKLOADS[wl_id]
+    B = wl["pairs"]
+    sizes = wl["sizes"](B, 0)
+    pairs = make_pairs([(h, w, synth_seed(wl_id, b)) for b, (h, w) in enumerate(sizes)])
+    imgs = []
+    for a, b in pairs:
+        imgs += [torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)]
+    ctx = pkg.Context(pkg.default_params(max_keypoints=wl["max_kp"], flags=pkg.FLAG_AUTOTUNE),
+                      device=dev.index, hbm_budget=96 << 30)
+    feats = [ctx.alloc_features() for _ in range(2 * B)]
+    matches = [ctx.alloc_matches() for _ in range(B)]
+    st = torch.cuda.current_stream()
+
+    def step():
+        ctx.extract(imgs, feats, stream=st)
+        ctx.match(feats[0::2], feats[1::2], matches, stream=st)
+
+    for _ in range(warmup):
+        step()
+    ctx.sync()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    px = sum(2 * h * w for h, w in sizes)
+    ctx.sync()
+    out = {"workload": wl["desc"], "metric": wl["metric"], "pairs_per_step": B,
+           "value": B / (ms / 1000.0), "unit": "pairs/s", "ms_per_step": ms,
+           "mpix_per_s": px / 1e6 / (ms / 1000.0),
+           "launches_per_step": (ctx.launch_count() - l0) // steps, "steps": steps,
+           "warmup": warmup}
+    ctx.close()
+    return out
+
+
+def synth_seed(wl_id, b):
+    import synth
+    return synth.pair_seed(wl_id, b)
+
+
 # ------------------------------------------------------------- multi-rank timing
 def max_over_ranks(ms: float, device=None) -> float:
     """The slowest rank's time: every rank's value, MAX-reduced (no-op on one process)."""
@@ -566,12 +721,25 @@ def run_ours(args):
     if args.serve_requests > 0 and args.workload == 1:
         serving = run_serving(args, local)
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == 1:
-        tcpu = oracle_pair_seconds(H, MAX_KP, synth.pair_seed(1, 0))
+        import oracle
+        pr = synth.config_pair(1)
+        op = oracle.Params(max_keypoints=MAX_KP)
+        t0 = time.perf_counter()
+        oa = oracle.extract(pr.a.astype(np.float64), op, keep_maps=True)
+        ob = oracle.extract(pr.b.astype(np.float64), op, keep_maps=True)
+        oracle.match(oa.desc, ob.desc)
+        tcpu = time.perf_counter() - t0
         cpu = {"value": 1.0 / tcpu, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one 1024x1024 pair (2 FP64 oracle extracts + brute-force match); "
-                         "numpy FFT runs on one core, the matching matmul on the BLAS threads"}
+               "sample": "one 1024x1024 pair (2 FP64 oracle extracts keeping their maps + "
+                         "brute-force match); numpy FFT runs on one core, the matching matmul "
+                         "on the BLAS threads"}
+        parity = parity_summary(pkg, dev, pr, oa, ob, oracle.match)
+
+    others = None
+    if rank == 0 and world == 1 and args.workload == 1 and not args.no_other_workloads:
+        others = {"workload2": workload_summary(pkg, dev, 2), "workload3": workload_summary(pkg, dev, 3)}
 
     if rank == 0:
         line = {
@@ -598,6 +766,8 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "match_tensor": match_tensor,
             "cpu_baseline": cpu,
+            "parity": parity,
+            "other_workloads": others,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "form": "pinned host images in on a copy stream (step i+1's copy overlaps "
                             "step i's kernels); every step copies out each pair's full "
@@ -621,24 +791,30 @@ def run_serving(args, device: int):
     import synth
     from paper_2303_00319_gb300 import serve
     sizes = synth.serving_sizes(args.serve_pool, seed=synth.pair_seed(4, 0))
-    pool = [synth.make_pair(h, w, synth.pair_seed(4, i + 1), angle_deg=None)
-            for i, (h, w) in enumerate(sizes)]
+    pool = make_pairs([(h, w, synth.pair_seed(4, i + 1)) for i, (h, w) in enumerate(sizes)])
     srv = serve.Server(device=device, max_keypoints=MAX_KP, max_batch_pairs=8,
-                       hbm_budget=120 << 30, lanes=2)
-    warm = [serve.PairRequest(-1 - i, p.a, p.b) for i, p in enumerate(pool)]
+                       hbm_budget=120 << 30, lanes=2, keep_resident=True)
+    warm = [serve.PairRequest(-1 - i, a, b) for i, (a, b) in enumerate(pool)]
     for r in warm:
         srv.submit(r)
-    srv.drain()                           # plans, tables and workspaces for every size
+    srv.drain()                           # plans, tables, workspaces and pools for every size
+    for r in warm:
+        srv.release(r.rid)
+    pools0 = srv.pool_stats()
     runs = []
     for k, rate in enumerate(float(x) for x in str(args.serve_rate).split(",")):
-        reqs = [serve.PairRequest(i, pool[i % len(pool)].a, pool[i % len(pool)].b)
-                for i in range(args.serve_requests)]
+        reqs = [serve.PairRequest(i, *pool[i % len(pool)]) for i in range(args.serve_requests)]
         runs.append(serve.run_open_loop(srv, reqs, rate=rate, seed=7 + k))
+    grown = {k: v - pools0[k] for k, v in srv.pool_stats().items()}
     srv.close()
     return {"workload": (f"{len(pool)} distinct pairs cycled, sides log-uniform 256..4096 "
                          f"(13-smooth, width <= 3584), mean "
-                         f"{np.mean([p.a.size for p in pool]) / 1e6:.2f} MPix per image, "
-                         "<= 5000 keypoints, HBM admission budget 120 GB"),
+                         f"{np.mean([a.size for a, _ in pool]) / 1e6:.2f} MPix per image, "
+                         "<= 5000 keypoints, HBM admission budget 120 GB (the library's "
+                         "workspace figure per batch), each request's features, matches, "
+                         "spectra and MIMs device-resident until the client releases them "
+                         "on completion"),
+            "buffers_created_during_the_runs": grown,
             "rates": runs}
 
 
@@ -660,7 +836,9 @@ def main():
                     help="requests of the open-loop serving run (0: skip)")
     ap.add_argument("--serve-rate", default="50,100,200,400",
                     help="offered pairs/s, comma-separated for a sweep")
-    ap.add_argument("--serve-pool", type=int, default=8, help="distinct pairs generated")
+    ap.add_argument("--serve-pool", type=int, default=32, help="distinct pairs generated")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the uneven-batch and 4096^2 summaries of the default line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

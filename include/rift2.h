@@ -137,6 +137,9 @@ typedef struct rift2_image {
  *   moment [H][W]      maximum moment M (edge map FAST runs on)             (§II-A)
  *   mim    [H][W]      uint8 maximum index map, values 0..No-1              (§II-B)
  *   noise_t [No]       noise thresholds T_o
+ *   spectrum [H][W]    complex (re, im float32) forward DFT F of the image (§II-B)
+ * amp and pc need workspace of their own (NO * H * W * 4 bytes each per image of the launch
+ * group); the others are copies of what the pipeline keeps anyway.
  */
 typedef struct rift2_debug_maps {
   float* amp;
@@ -147,6 +150,7 @@ typedef struct rift2_debug_maps {
   float* moment;
   unsigned char* mim;
   float* noise_t;
+  float* spectrum;
 } rift2_debug_maps;
 
 /*
@@ -303,6 +307,15 @@ int rift2_profile_read(rift2_ctx* ctx, int n, double* ms, long long* count);
 
 /* Kernels enqueued by this context since it was created. */
 long long rift2_launch_count(const rift2_ctx* ctx);
+
+/* Device workspace the context needs for rift2_extract of n_images images of the given
+ * sizes (host arrays; grouped as rift2_extract groups them, no debug maps) followed by
+ * rift2_match of n_pairs pairs: the largest launch group's layout or the matcher's (the
+ * workspace is one buffer reused by every group and by the matcher).  For admission
+ * control by a serving loop; no counterpart in the paper.  *bytes is written.
+ * Errors: RIFT2_E_INVAL. */
+int rift2_workspace_bytes(const rift2_ctx* ctx, int n_images, const int* heights,
+                          const int* widths, int n_pairs, size_t* bytes);
 
 /* ------------------------------------------------------------------------------
  * Capacities and failure paths (no counterpart in the paper).

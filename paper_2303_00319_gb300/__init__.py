@@ -31,7 +31,8 @@ EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_ex
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
            "rift2_describe", "rift2_detect_static", "rift2_tuned_tile",
-           "rift2_required_capacity", "rift2_set_wait_limit", "rift2_evaluate")
+           "rift2_required_capacity", "rift2_set_wait_limit", "rift2_evaluate",
+           "rift2_workspace_bytes")
 STATIC_MAX_CANDIDATES = 262144
 STAGES = ("fft_fwd", "lg_cols", "lg_rows", "noise", "moment", "detect", "describe", "match")
 
@@ -52,7 +53,7 @@ class Image(C.Structure):
 
 class DebugMaps(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("amp", "er", "q", "an0", "pc", "moment", "mim",
-                                          "noise_t")]
+                                          "noise_t", "spectrum")]
 
 
 class FeaturesC(C.Structure):
@@ -102,6 +103,8 @@ def lib():
         L.rift2_required_capacity.argtypes = [C.c_void_p, C.POINTER(C.c_int),
                                               C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.rift2_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
+        L.rift2_workspace_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                            C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_size_t)]
         L.rift2_evaluate.argtypes = [C.c_void_p, C.c_int, C.POINTER(FeaturesC),
                                      C.POINTER(FeaturesC), C.POINTER(MatchesC),
                                      C.POINTER(C.c_double), C.c_double, C.c_double, C.c_int,
@@ -189,6 +192,16 @@ class Features:
             f.debug["mim"] = torch.zeros((h, w), dtype=torch.uint8, device=dev)
             f.debug["noise_t"] = torch.zeros(NO, dtype=torch.float32, device=dev)
         return f
+
+    def keep_maps(self, shape, names=("mim", "spectrum")):
+        """Attach device buffers that the next extraction fills with the named maps (a
+        subset of the debug maps; "spectrum" is complex64 [H][W], "mim" uint8 [H][W])."""
+        h, w = shape
+        dev = self.kp_xy.device
+        shapes = {"mim": ((h, w), torch.uint8), "spectrum": ((h, w), torch.complex64),
+                  "moment": ((h, w), torch.float32), "noise_t": ((NO,), torch.float32)}
+        self.debug = {n: torch.empty(shapes[n][0], dtype=shapes[n][1], device=dev) for n in names}
+        return self
 
     def to_c(self):
         c = FeaturesC(self.kp_xy.shape[0], self.desc.shape[0], _ptr(self.kp_xy).value,
@@ -371,6 +384,17 @@ class Context:
         _check(lib().rift2_required_capacity(self._h, *[C.byref(x) for x in v]),
                "rift2_required_capacity")
         return dict(cap_kp=v[0].value, cap_desc=v[1].value, cap_match=v[2].value)
+
+    def workspace_bytes(self, sizes, n_pairs: int = 0) -> int:
+        """Workspace bytes an extract of images of `sizes` [(H, W), ...] followed by a match
+        of n_pairs pairs needs in this context (rift2_workspace_bytes)."""
+        n = len(sizes)
+        hs = (C.c_int * max(n, 1))(*[int(h) for h, _ in sizes])
+        ws = (C.c_int * max(n, 1))(*[int(w) for _, w in sizes])
+        out = C.c_size_t()
+        _check(lib().rift2_workspace_bytes(self._h, n, hs, ws, int(n_pairs), C.byref(out)),
+               "rift2_workspace_bytes")
+        return int(out.value)
 
     def set_wait_limit(self, iters: int = 1 << 24):
         """First-wait limit of the descriptor kernel's staged copies (0: give up at once,

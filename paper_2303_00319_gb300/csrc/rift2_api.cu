@@ -275,7 +275,7 @@ struct Layout {
 };
 
 // max_kp: keypoints one detector pass keeps; kp_cap: keypoint list capacity per image.
-Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners, bool debug,
+Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners, int debug,
                       bool spatial) {
   Layout L{};
   const size_t P = (size_t)H * W;
@@ -290,8 +290,8 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   L.er = take((size_t)g * NO * P * 4);
   L.q = take((size_t)g * NO * P * 4);
   L.an0 = take((size_t)g * NO * P * 4);
-  L.amp = debug ? take((size_t)g * NO * P * 4) : (size_t)-1;
-  L.pc = debug ? take((size_t)g * NO * P * 4) : (size_t)-1;
+  L.amp = (debug & 1) ? take((size_t)g * NO * P * 4) : (size_t)-1;
+  L.pc = (debug & 2) ? take((size_t)g * NO * P * 4) : (size_t)-1;
   L.moment = take((size_t)g * P * 4);
   L.mim = take((size_t)g * H * L.mim_pitch);
   L.mhist = take((size_t)g * NO * 2 * 4096 * 4);
@@ -321,7 +321,7 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   return L;
 }
 
-Layout ctx_layout(const rift2_ctx* c, int g, int H, int W, bool debug) {
+Layout ctx_layout(const rift2_ctx* c, int g, int H, int W, int debug) {
   return extract_layout(g, H, W, c->kp.max_kp, c->kp.kp_cap,
                         (c->p.flags & RIFT2_FLAG_CORNERS) != 0, debug,
                         c->kp.desc_mode == DESC_SPATIAL);
@@ -412,6 +412,7 @@ int copy_debug(const rift2_features* f, int n, void* ws, const Layout& L, int H,
     RIFT2_CU(cp(d->pc, L.pc, NO * P * 4));
     RIFT2_CU(cp(d->moment, L.moment, P * 4));
     RIFT2_CU(cp(d->noise_t, L.noise, NO * 4));
+    RIFT2_CU(cp(d->spectrum, L.spec, P * sizeof(float2)));
     if (d->mim)
       RIFT2_CU(cudaMemcpy2DAsync(d->mim, W, static_cast<char*>(ws) + L.mim + (size_t)i * H * L.mim_pitch,
                                  L.mim_pitch, W, H, cudaMemcpyDeviceToDevice, st));
@@ -419,10 +420,18 @@ int copy_debug(const rift2_features* f, int n, void* ws, const Layout& L, int H,
   return RIFT2_OK;
 }
 
-bool wants_debug(const rift2_features* f, int n) {
-  for (int i = 0; i < n; ++i)
-    if (f[i].debug) return true;
-  return false;
+// Which optional outputs a launch group needs: bit 0 the amplitude sums, bit 1 PC (both
+// need workspace of their own), bit 2 any other debug copy (no extra workspace).
+int wants_debug(const rift2_features* f, int n) {
+  int w = 0;
+  for (int i = 0; i < n; ++i) {
+    const rift2_debug_maps* d = f[i].debug;
+    if (!d) continue;
+    if (d->amp) w |= 1;
+    if (d->pc) w |= 2;
+    w |= 4;
+  }
+  return w;
 }
 
 // One launch group: g images of the same size.
@@ -438,7 +447,7 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   unsigned char* zc = nullptr;
   rc = get_zero_cols(c, H, W, st, &zc);
   if (rc) return rc;
-  const bool dbg = wants_debug(out, g);
+  const int dbg = wants_debug(out, g);
   Layout L = ctx_layout(c, g, H, W, dbg);
   rc = ensure_ws(c, L.total);
   if (rc) return rc;
@@ -661,6 +670,31 @@ int rift2_profile_read(rift2_ctx* c, int n, double* ms, long long* count) {
 
 long long rift2_launch_count(const rift2_ctx* c) { return c ? c->launches : -1; }
 
+int rift2_workspace_bytes(const rift2_ctx* c, int n, const int* heights, const int* widths,
+                          int n_pairs, size_t* bytes) {
+  if (!c || n < 0 || n_pairs < 0 || !bytes || (n > 0 && (!heights || !widths))) return RIFT2_E_INVAL;
+  size_t need = 0;
+  const bool group = !(c->p.flags & RIFT2_FLAG_NO_GROUPING);
+  int i = 0;
+  while (i < n) {   // the grouping rift2_extract applies
+    int j = i + 1;
+    while (group && j < n && j - i < MAXB && heights[j] == heights[i] && widths[j] == widths[i]) ++j;
+    int g = j - i;
+    while (g > 1 && ctx_layout(c, g, heights[i], widths[i], 0).total > c->budget) g = (g + 1) / 2;
+    const size_t t = ctx_layout(c, g, heights[i], widths[i], 0).total;
+    if (t > need) need = t;
+    i += g;
+  }
+  if (n_pairs > 0 && !(c->p.flags & RIFT2_FLAG_PLAIN_MATCH)) {
+    const int gp = (c->p.flags & RIFT2_FLAG_NO_GROUPING) ? 1 : (n_pairs < MAXB ? n_pairs : MAXB);
+    const int cap = (desc_per_kp(c) * c->kp.kp_cap + 127) / 128 * 128;
+    const size_t t = match_tc_ws_bytes(gp, cap, match_tc_nsplit(gp, cap));
+    if (t > need) need = t;
+  }
+  *bytes = need;
+  return RIFT2_OK;
+}
+
 int rift2_set_wait_limit(rift2_ctx* c, long long iters) {
   if (!c || iters < 0) return RIFT2_E_INVAL;
   c->wait_iters = iters;
@@ -845,7 +879,7 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
   const long long P = (long long)H * W;
   for (int i0 = 0; i0 < n; i0 += MAXB) {
     int g = n - i0 < MAXB ? n - i0 : MAXB;
-    Layout L = ctx_layout(c, g, H, W, false);
+    Layout L = ctx_layout(c, g, H, W, 0);
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
     unsigned* minmax = at<unsigned>(c->ws, L.minmax);
@@ -874,7 +908,7 @@ int rift2_describe(rift2_ctx* c, int n, const unsigned char* mim, int H, int W,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i0 = 0; i0 < n; i0 += MAXB) {
     int g = n - i0 < MAXB ? n - i0 : MAXB;
-    Layout L = ctx_layout(c, g, H, W, false);
+    Layout L = ctx_layout(c, g, H, W, 0);
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
     unsigned char* wm = at<unsigned char>(c->ws, L.mim);
