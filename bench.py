@@ -260,7 +260,7 @@ def parity_summary(pkg, dev, pair, oa, ob, of_match):
         ce = mo["A"] / (4.0 * mo["X"]) * 1e-2 * amax
         vals = {"A_o": _worst(d["amp"], mo["A"], 2.5e-3), "|EO0|": _worst(d["an0"], mo["An0"], 1e-2),
                 "q": _worst(d["q"], mo["q"], 1e-3, cq), "Er": _worst(d["er"], mo["Er"], 5e-2, ce),
-                "PC": _worst(d["pc"], mo["pc"], 1.0), "M": _worst(d["moment"], mo["M"], 1e-2),
+                "PC": _worst(d["pc"], mo["pc"], 1.0), "M": _worst(d["moment"], mo["M"], 2e-2),
                 "T_o": float(np.max(np.abs(d["noise_t"] - mo["T"]) / np.abs(mo["T"]))),
                 "M_normalised_abs": float(np.max(np.abs(d["moment"] - mo["M"])) /
                                           (mo["M"].max() - mo["M"].min()))}
@@ -278,7 +278,7 @@ def parity_summary(pkg, dev, pair, oa, ob, of_match):
             kp_only += 1
             kp_cert += int(bool(mo["kp_uncertain"][q[1], q[0]]))
     out["max_rel_err"] = maps
-    out["tolerance"] = "1e-4 relative above each floor (A_o 2.5e-3, |EO0| 1e-2, q 1e-3 with A's floor, Er 5e-2 with its A/X conditioning, PC 1.0, M 1e-2); T_o 1e-5; M 5e-6 in FAST's normalised units"
+    out["tolerance"] = "1e-4 relative above each floor (A_o 2.5e-3, |EO0| 1e-2, q 1e-3 with A's floor, Er 5e-2 with its A/X conditioning, PC 1.0, M 2e-2); T_o 1e-5; M 5e-6 in FAST's normalised units"
     out["mim"] = {"pixels_differing": mim_diff, "of_which_not_near_ties": mim_bad,
                   "oracle_near_tie_pixels": near_px}
     out["keypoints"] = {"in_one_list_only": kp_only, "of_which_certified": kp_cert,
@@ -807,8 +807,8 @@ def run_serving(args, device: int):
         runs.append(serve.run_open_loop(srv, reqs, rate=rate, seed=7 + k))
     grown = {k: v - pools0[k] for k, v in srv.pool_stats().items()}
     srv.close()
-    return {"workload": (f"{len(pool)} distinct pairs cycled, sides log-uniform 256..4096 "
-                         f"(13-smooth, width <= 3584), mean "
+    return {"workload": (f"{len(pool)} distinct pairs cycled, integer sides log-uniform "
+                         f"256..4096 (most with a prime factor above 13: Bluestein transforms), mean "
                          f"{np.mean([a.size for a, _ in pool]) / 1e6:.2f} MPix per image, "
                          "<= 5000 keypoints, HBM admission budget 120 GB (the library's "
                          "workspace figure per batch), each request's features, matches, "

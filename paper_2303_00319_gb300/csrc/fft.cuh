@@ -15,11 +15,23 @@ namespace rift2 {
 
 constexpr int FFT_MAX_STAGES = 16;
 
+// A transform of length n: directly (n 13-smooth: radices of n, twiddles of length n), or
+// by Bluestein's chirp-z identity when n has a larger prime factor.  With c_j =
+// exp(-i pi j^2 / n), jk = (j^2 + k^2 - (k - j)^2) / 2 turns the DFT into a convolution:
+//     X_k = c_k sum_j (x_j c_j) conj(c_(k-j))          (forward; the inverse conjugates c)
+// evaluated as a cyclic convolution of length m >= 2n - 1 (m 13-smooth) with FFTs of
+// length m: the radices and twiddles below are then those of m, and kern_* hold
+// FFT_m(conj(c)) / m (forward) and FFT_m(c) / m (inverse), c extended cyclically
+// (c_(m-j) = c_j for 0 < j < n, 0 between).  All tables are generated in FP64.
 struct FftPlan {
   int n;
   int nst;
   int radix[FFT_MAX_STAGES];
-  const float2* tw;   // device, n entries
+  const float2* tw;   // device, m entries (twiddles of the length the passes run at)
+  int m;              // length of one transform's shared-memory slot: n, or the convolution length
+  const float2* chirp;      // Bluestein only: [n] c_j
+  const float2* kern_fwd;   // Bluestein only: [m]
+  const float2* kern_inv;   // Bluestein only: [m]
 };
 
 template <bool INV>
@@ -209,23 +221,24 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* 
   }
 }
 
-// Full transform; data starts in `a`, `b` is scratch of the same size.  Returns the
-// buffer holding the result.  Ends with a __syncthreads().
+// The Stockham passes of a length-len transform (radices and twiddles of `pl`); data
+// starts in `a`, `b` is scratch.  Returns the buffer holding the result.
 template <bool INV, bool BFAST>
-__device__ float2* fft_smem(float2* a, float2* b, const FftPlan& pl, int nb, int bs, int ks) {
+__device__ float2* fft_passes(float2* a, float2* b, const FftPlan& pl, int len, int nb, int bs,
+                              int ks) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   int ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = pl.radix[st];
     switch (R) {
-      case 8: fft_pass<8, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 4: fft_pass<4, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 2: fft_pass<2, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 3: fft_pass<3, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 5: fft_pass<5, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 7: fft_pass<7, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 11: fft_pass<11, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 13: fft_pass<13, INV, BFAST>(a, b, pl.n, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 8: fft_pass<8, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 4: fft_pass<4, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 2: fft_pass<2, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 3: fft_pass<3, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 5: fft_pass<5, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 7: fft_pass<7, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 11: fft_pass<11, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+      case 13: fft_pass<13, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
       default: break;
     }
     __syncthreads();
@@ -233,6 +246,49 @@ __device__ float2* fft_smem(float2* a, float2* b, const FftPlan& pl, int nb, int
     float2* t = a; a = b; b = t;
   }
   return a;
+}
+
+// Full transform of nb transforms of length pl.n; element k of transform t at
+// buf[t * bs + k * ks], where each transform owns pl.m slots (pl.m = pl.n for direct
+// plans).  Data starts in `a`, `b` is scratch of the same size; returns the buffer holding
+// the result (the first pl.n elements of each slot).  Ends with a __syncthreads().
+template <bool INV, bool BFAST>
+__device__ float2* fft_smem(float2* a, float2* b, const FftPlan& pl, int nb, int bs, int ks) {
+  if (!pl.chirp) return fft_passes<INV, BFAST>(a, b, pl, pl.n, nb, bs, ks);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int n = pl.n, m = pl.m;
+  const FastDiv dm((unsigned)m);
+  // u_j = x_j c_j (conj(c_j) for the inverse) for j < n, zero up to m
+  for (int i = tid; i < nb * m; i += nthr) {
+    const int t = (int)dm.div((unsigned)i), j = i - t * m;
+    float2* p = a + t * bs + j * ks;
+    if (j < n) {
+      const float2 c = __ldg(pl.chirp + j);
+      *p = INV ? cmulc(*p, c) : cmul(*p, c);
+    } else {
+      *p = make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  float2* r = fft_passes<false, BFAST>(a, b, pl, m, nb, bs, ks);
+  float2* o = (r == a) ? b : a;
+  const float2* kern = INV ? pl.kern_inv : pl.kern_fwd;
+  for (int i = tid; i < nb * m; i += nthr) {
+    const int t = (int)dm.div((unsigned)i), j = i - t * m;
+    float2* p = r + t * bs + j * ks;
+    *p = cmul(*p, __ldg(kern + j));
+  }
+  __syncthreads();
+  r = fft_passes<true, BFAST>(r, o, pl, m, nb, bs, ks);
+  // X_k = c_k y_k (conj(c_k) for the inverse), k < n
+  for (int i = tid; i < nb * n; i += nthr) {
+    const int t = i / n, k = i - t * n;
+    float2* p = r + t * bs + k * ks;
+    const float2 c = __ldg(pl.chirp + k);
+    *p = INV ? cmulc(*p, c) : cmul(*p, c);
+  }
+  __syncthreads();
+  return r;
 }
 
 }  // namespace rift2

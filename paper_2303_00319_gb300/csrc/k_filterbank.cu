@@ -24,6 +24,55 @@ __global__ void twiddle_gen(float2* tw, int n) {
   tw[e] = make_float2((float)c, (float)s);
 }
 
+// Bluestein tables (FP64 arithmetic, rounded once to FP32).  c_j = exp(-i pi j^2 / n) with
+// j^2 reduced modulo 2n first (exact in 64-bit integers), so the argument stays small.
+__global__ void chirp_gen(float2* c32, double2* c64, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const long long r = ((long long)j * j) % (2ll * n);
+  double sn, cs;
+  sincospi(-(double)r / (double)n, &sn, &cs);
+  c64[j] = make_double2(cs, sn);
+  c32[j] = make_float2((float)cs, (float)sn);
+}
+__global__ void twiddle64_gen(double2* tw, int m) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  double sn, cs;
+  sincospi(-2.0 * (double)e / (double)m, &sn, &cs);
+  tw[e] = make_double2(cs, sn);
+}
+// kern_fwd[k] = (1/m) sum_j conj(c~_j) W_m^(jk), kern_inv[k] = (1/m) sum_j c~_j W_m^(jk),
+// c~ the cyclic extension of c to length m (c~_j = c_j, c~_(m-j) = c_j for 0 < j < n, zero
+// between): a direct DFT in FP64, one output per thread.
+__global__ void bluestein_kern_gen(float2* kf, float2* ki, const double2* __restrict__ c64,
+                                   const double2* __restrict__ tw64, int n, int m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  double fr = 0.0, fi = 0.0, ir = 0.0, ii = 0.0;
+  for (int j = 0; j < m; ++j) {
+    const int jj = (j < n) ? j : ((j > m - n) ? m - j : -1);
+    if (jj < 0) continue;
+    const double2 c = c64[jj];
+    const double2 w = tw64[(int)(((long long)j * k) % m)];
+    // conj(c) w and c w
+    fr += c.x * w.x + c.y * w.y;
+    fi += c.x * w.y - c.y * w.x;
+    ir += c.x * w.x - c.y * w.y;
+    ii += c.x * w.y + c.y * w.x;
+  }
+  const double s = 1.0 / (double)m;
+  kf[k] = make_float2((float)(fr * s), (float)(fi * s));
+  ki[k] = make_float2((float)(ir * s), (float)(ii * s));
+}
+
+void launch_bluestein_tables(float2* chirp, float2* kf, float2* ki, double2* c64, double2* tw64,
+                             int n, int m, cudaStream_t st) {
+  chirp_gen<<<(n + 255) / 256, 256, 0, st>>>(chirp, c64, n);
+  twiddle64_gen<<<(m + 255) / 256, 256, 0, st>>>(tw64, m);
+  bluestein_kern_gen<<<(m + 127) / 128, 128, 0, st>>>(kf, ki, c64, tw64, n, m);
+}
+
 // ------------------------------------------------------------------ forward 2-D DFT
 // The large DC term dominates the rounding error of an FP32 FFT.  Each 1-D transform
 // therefore runs on its input minus the input's mean and gets its bin 0 back as the
@@ -56,26 +105,30 @@ __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restr
   const int img = blockIdx.y;
   const int r0 = blockIdx.x * tr;
   const int nel = tr * W;
+  const int L = pw.m;   // shared-memory slot of one row transform (> W for Bluestein plans)
   float2* a = sm;
-  float2* b = sm + nel;
+  float2* b = sm + tr * L;
   const float* src = dense ? dense + (size_t)img * H * W : ip.img[img];
   const long long pitch = dense ? W : ip.pitch[img];
   const FastDiv dW((unsigned)W);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     const int rr = (int)dW.div((unsigned)i), x = i - rr * W, r = r0 + rr;
     float v = (r < H) ? __ldg(src + (size_t)r * pitch + x) : 0.f;
-    a[i] = make_float2(v, 0.f);
+    a[rr * L + x] = make_float2(v, 0.f);
   }
   __syncthreads();
-  seg_means(a, tr, W, 1, W, mean);
+  seg_means(a, tr, W, 1, L, mean);
   __syncthreads();
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) a[i].x -= mean[dW.div((unsigned)i)].x;
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    const int rr = (int)dW.div((unsigned)i), x = i - rr * W;
+    a[rr * L + x].x -= mean[rr].x;
+  }
   __syncthreads();
-  float2* res = fft_smem<false, false>(a, b, pw, tr, W, 1);
+  float2* res = fft_smem<false, false>(a, b, pw, tr, L, 1);
   float2* dst = spec + (size_t)img * H * W;
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     const int rr = (int)dW.div((unsigned)i), x = i - rr * W, r = r0 + rr;
-    float2 v = res[i];
+    float2 v = res[rr * L + x];
     if (x == 0) v.x += mean[rr].x * W;
     if (r < H) dst[(size_t)r * W + x] = v;
   }
@@ -90,7 +143,7 @@ __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H
   const int c0 = blockIdx.x * tc;
   const int nel = H * tc;
   float2* a = sm;
-  float2* b = sm + nel;
+  float2* b = sm + ph.m * tc;   // [ph.m][tc] each: a column transform's slot is ph.m long
   float2* base = spec + (size_t)img * H * W;
   const FastDiv dtc((unsigned)tc);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
@@ -337,10 +390,11 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
   const int img = blockIdx.z;
   const int c0 = blockIdx.x * tc;
   const int nel = H * tc;
+  const int nl = ph.m * tc;   // a transform slot is ph.m long (> H for Bluestein plans)
   float2* base = sm;
   float2* a = sm + nel;
-  float2* b = sm + 2 * nel;
-  float* fvt = reinterpret_cast<float*>(sm + 3 * nel);   // fftfreq(v, H) per row
+  float2* b = sm + nel + nl;
+  float* fvt = reinterpret_cast<float*>(sm + nel + 2 * nl);   // fftfreq(v, H) per row
   __shared__ float fut[16];                               // fftfreq(u, W) per column
   const float2* F = spec + (size_t)img * H * W;
   const float log_fs = kp.log_fs[s];
@@ -438,9 +492,9 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
   extern __shared__ float2 sm[];
   const int row = blockIdx.x;
   const int img = blockIdx.y;
-  const int nel = NS * W;
+  const int L = pw.m;   // a row transform's slot (> W for Bluestein plans)
   float2* a = sm;
-  float2* b = sm + nel;
+  float2* b = sm + NS * L;
   const size_t P = (size_t)H * W;
   float best[RR_MAXPIX];
   int besto[RR_MAXPIX];
@@ -454,18 +508,18 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
 #pragma unroll 4
       for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const float2 v = __ldg(src + x);
-        a[s * W + x] = zc[o * W + x] ? make_float2(0.f, 0.f) : v;
+        a[s * L + x] = zc[o * W + x] ? make_float2(0.f, 0.f) : v;
       }
     }
     __syncthreads();
-    float2* res = fft_smem<true, false>(a, b, pw, NS, W, 1);
+    float2* res = fft_smem<true, false>(a, b, pw, NS, L, 1);
 #pragma unroll
     for (int k = 0; k < RR_MAXPIX; ++k) {
       int x = threadIdx.x + k * blockDim.x;
       if (x >= W) break;
       float2 z[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) z[s] = res[s * W + x];
+      for (int s = 0; s < NS; ++s) z[s] = res[s * L + x];
       float energy, q, an0, sum_an;
       reduce_pixel(z, kp, energy, q, an0, sum_an);
       size_t off = ((size_t)img * NO + o) * P + (size_t)row * W + x;
@@ -483,6 +537,59 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
     if (x >= W) break;
     mim_out[(size_t)img * H * mim_pitch + (size_t)row * mim_pitch + x] = (unsigned char)besto[k];
   }
+}
+
+// Row pass for rows too wide for lg_rows_reduce: each CTA transforms one (row, scale) for
+// the six orientations and writes the responses back in place (zero-window columns are
+// read as zeros and every column is written), then lg_rows_pixels reduces each pixel from
+// its 24 responses exactly as lg_rows_reduce does.
+__global__ void __launch_bounds__(512) lg_rows_split(float2* __restrict__ scratch, int H, int W,
+                                                     FftPlan pw, const unsigned char* __restrict__ zc) {
+  extern __shared__ float2 sm[];
+  const int row = blockIdx.x, s = blockIdx.y, img = blockIdx.z;
+  float2* a = sm;
+  float2* b = sm + pw.m;
+  const size_t P = (size_t)H * W;
+  for (int o = 0; o < NO; ++o) {
+    float2* rowp = scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W;
+    for (int x = threadIdx.x; x < W; x += blockDim.x)
+      a[x] = zc[o * W + x] ? make_float2(0.f, 0.f) : rowp[x];
+    __syncthreads();
+    float2* res = fft_smem<true, false>(a, b, pw, 1, pw.m, 1);
+    for (int x = threadIdx.x; x < W; x += blockDim.x) rowp[x] = res[x];
+    __syncthreads();   // the stores have read res before the next orientation's loads
+  }
+}
+
+__global__ void __launch_bounds__(256) lg_rows_pixels(const float2* __restrict__ scratch, int H,
+                                                      int W, KParams kp,
+                                                      float* __restrict__ er_out,
+                                                      float* __restrict__ q_out,
+                                                      float* __restrict__ an0_out,
+                                                      float* __restrict__ amp_out,
+                                                      unsigned char* __restrict__ mim_out,
+                                                      int mim_pitch) {
+  const int img = blockIdx.y;
+  const long long P = (long long)H * W;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  float best = -1.f;
+  int besto = 0;
+  for (int o = 0; o < NO; ++o) {
+    float2 z[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) z[s] = __ldg(scratch + (((size_t)img * NS + s) * NO + o) * P + i);
+    float energy, q, an0, sum_an;
+    reduce_pixel(z, kp, energy, q, an0, sum_an);
+    const size_t off = ((size_t)img * NO + o) * P + i;
+    er_out[off] = energy;
+    q_out[off] = q;
+    an0_out[off] = an0;
+    if (amp_out) amp_out[off] = sum_an;
+    if (sum_an > best) { best = sum_an; besto = o; }   // lowest o on ties
+  }
+  const long long y = i / W, x = i - y * W;
+  mim_out[(size_t)img * H * mim_pitch + (size_t)y * mim_pitch + x] = (unsigned char)besto;
 }
 
 // ------------------------------------------------------- register-tiled fast path
@@ -987,8 +1094,8 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
     case 2048: rows_fwd_reg<2048>(ipr, dense, spec, nimg, H, pw, st); break;
     case 4096: rows_fwd_reg<4096>(ipr, dense, spec, nimg, H, pw, st); break;
     default: {
-      int tr = rows_tile(W);
-      size_t smr = 2 * (size_t)tr * W * sizeof(float2);
+      int tr = rows_tile(pw.m);
+      size_t smr = 2 * (size_t)tr * pw.m * sizeof(float2);
       cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
       fwd_rows<<<dim3((H + tr - 1) / tr, nimg), 512, smr, st>>>(ipr, dense, spec, H, W, tr, pw);
     }
@@ -1000,8 +1107,8 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
     case 2048: cols_fwd_reg<2048>(spec, nimg, W, ph, st); break;
     case 4096: cols_fwd_reg<4096>(spec, nimg, W, ph, st); break;
     default: {
-      int tc = cols_tile(H);
-      size_t smc = 2 * (size_t)tc * H * sizeof(float2);
+      int tc = cols_tile(ph.m);
+      size_t smc = 2 * (size_t)tc * ph.m * sizeof(float2);
       cudaFuncSetAttribute(fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
       fwd_cols<<<dim3((W + tc - 1) / tc, nimg), 512, smc, st>>>(spec, H, W, tc, ph);
     }
@@ -1009,42 +1116,58 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
   return cudaGetLastError();
 }
 
-int lg_cols_tile_candidates(int H, int* out, int max_n) {
-  switch (H) {
-    case 256: case 512: case 1024: case 2048: case 4096: return 0;   // register path
-    default: break;
+// Shared memory of the generic column pass for a tile of tc columns: F R_s (H rows), the
+// two transform buffers (slot length L each) and the per-row frequencies.
+static size_t cols_inverse_smem(int H, int L, int tc) {
+  return ((size_t)H + 2 * (size_t)L) * tc * sizeof(float2) + (size_t)H * sizeof(float);
+}
+static int cols_inverse_tile(int H, int L) {
+  int tc = cols_tile(L);
+  while (tc > 1 && cols_inverse_smem(H, L, tc) > 227 * 1024) tc /= 2;
+  return tc;
+}
+
+int lg_cols_tile_candidates(int H, int L, int* out, int max_n) {
+  if (L == H) {
+    switch (H) {
+      case 256: case 512: case 1024: case 2048: case 4096: return 0;   // register path
+      default: break;
+    }
   }
   int n = 0;
-  for (int tc = cols_tile(H); tc >= 1 && n < max_n; tc /= 2) out[n++] = tc;
+  for (int tc = cols_inverse_tile(H, L); tc >= 1 && n < max_n; tc /= 2) out[n++] = tc;
   return n;
 }
 
 cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
                            const FftPlan& ph, const KParams& kp, const unsigned char* zc,
                            cudaStream_t st, int tile) {
-  switch (H) {
-    case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, zc, st);
-    case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
-    case 1024:
-      return kp.lp_order == 15 ? cols_tm1024<15>(spec, scratch, nimg, W, ph, kp, zc, st)
-                               : cols_tm1024<0>(spec, scratch, nimg, W, ph, kp, zc, st);
-    case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, zc, st);
-    case 4096: return cols_reg<4096>(spec, scratch, nimg, W, ph, kp, zc, st);
-    default: break;
+  if (ph.m == H) {
+    switch (H) {
+      case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, zc, st);
+      case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
+      case 1024:
+        return kp.lp_order == 15 ? cols_tm1024<15>(spec, scratch, nimg, W, ph, kp, zc, st)
+                                 : cols_tm1024<0>(spec, scratch, nimg, W, ph, kp, zc, st);
+      case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, zc, st);
+      case 4096: return cols_reg<4096>(spec, scratch, nimg, W, ph, kp, zc, st);
+      default: break;
+    }
   }
-  int tc = cols_tile(H);
+  int tc = cols_inverse_tile(H, ph.m);
   if (tile >= 1 && tile <= tc) tc = tile;   // a tuned (smaller) tile; any tile gives the same result
-  size_t sm2 = 3 * (size_t)tc * H * sizeof(float2) + (size_t)H * sizeof(float);
+  size_t sm2 = cols_inverse_smem(H, ph.m, tc);
   cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   lg_cols_inverse<<<dim3((W + tc - 1) / tc, NS, nimg), 512, sm2, st>>>(spec, scratch, H, W, tc,
                                                                        ph, kp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
+cudaError_t launch_lg_rows(float2* scratch, int nimg, int H, int W, const FftPlan& pw,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
                            unsigned char* mim, int mim_pitch, const unsigned char* zc,
                            cudaStream_t st) {
+  if (pw.m != W) goto generic;   // Bluestein widths take the shared-memory paths
   switch (W) {
     case 256: return rows_reg<256>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
@@ -1059,11 +1182,39 @@ cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const 
     case 4096: return rows_reg<4096>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
     default: break;
   }
-  size_t sm3 = 2 * (size_t)NS * W * sizeof(float2);
-  cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
-  lg_rows_reduce<<<dim3(H, nimg), 512, sm3, st>>>(scratch, H, W, pw, kp, er, q, an0, amp, mim,
-                                                  mim_pitch, zc);
-  return cudaGetLastError();
+generic:
+  {
+    const size_t sm3 = 2 * (size_t)NS * pw.m * sizeof(float2);
+    if (sm3 <= 227 * 1024 && W <= RR_MAXPIX * 512) {
+      cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+      lg_rows_reduce<<<dim3(H, nimg), 512, sm3, st>>>(scratch, H, W, pw, kp, er, q, an0, amp, mim,
+                                                      mim_pitch, zc);
+      return cudaGetLastError();
+    }
+  }
+  // rows too wide for four scales in shared memory: transform each (row, scale) in place,
+  // then reduce the pixels from the transformed responses
+  {
+    const size_t sm4 = 2 * (size_t)pw.m * sizeof(float2);
+    cudaFuncSetAttribute(lg_rows_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+    lg_rows_split<<<dim3(H, NS, nimg), 512, sm4, st>>>(scratch, H, W, pw, zc);
+    const long long P = (long long)H * W;
+    const int blocks = (int)((P + 255) / 256);
+    lg_rows_pixels<<<dim3(blocks, nimg), 256, 0, st>>>(scratch, H, W, kp, er, q, an0, amp, mim,
+                                                       mim_pitch);
+    return cudaGetLastError();
+  }
+}
+
+int lg_rows_launches(int H, int W, const FftPlan& pw) {
+  if (pw.m == W) {
+    switch (W) {
+      case 256: case 512: case 1024: case 2048: case 4096: return 1;
+      default: break;
+    }
+  }
+  const size_t sm3 = 2 * (size_t)NS * pw.m * sizeof(float2);
+  return (sm3 <= 227 * 1024 && W <= RR_MAXPIX * 512) ? 1 : 2;
 }
 
 }  // namespace rift2

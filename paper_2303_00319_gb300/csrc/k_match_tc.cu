@@ -3,16 +3,19 @@
 //
 //   nn_prep   : descriptor counts -> BF16 rows padded to K = 256 (counts <= 256 are exact
 //               in BF16), exact squared norms, 1/|b| for the screening scores.
-//   nn_tc     : per CTA 128 queries x a range of 128-wide tiles of B.  One thread issues
-//               TMA loads (128-byte swizzle), one issues tcgen05.mma (BF16 x BF16 -> FP32
-//               in TMEM, M = 128, N = 128, 14 K-steps of 16 cover K = 216); eight epilogue
-//               warps (two per TMEM lane quadrant, one column half each) read the
-//               accumulators with tcgen05.ld (double-buffered in TMEM so the next tile's
-//               MMAs overlap) and keep each query's 8 best candidates per half by the FP32
-//               score dot / |b|, screening 32 columns at a time against the larger of the
-//               two halves' 8th-best scores.  No score matrix ever reaches HBM.
+//   nn_tc     : per CTA 128 queries x a range of 256-wide tiles of B.  One thread issues
+//               TMA loads (128-byte swizzle, three 32 KB K-atom slots in flight), one issues
+//               tcgen05.mma (BF16 x BF16 -> FP32 in TMEM, M = 128, N = 256, 14 K-steps of 16
+//               cover K = 216) into two accumulators of 256 TMEM columns (all 512), so the
+//               next tile's MMAs overlap the epilogue of this one; eight epilogue warps (two
+//               per TMEM lane quadrant, one 128-column half each) read the accumulators with
+//               tcgen05.ld and keep each query's 4 best candidates per half by the FP32
+//               score dot / |b|, screening 32 columns at a time against the larger of the two
+//               halves' 4th-best scores.  No score matrix ever reaches HBM.
 //   nn_rerank : one thread per query: the exact comparison of match_common.cuh over its
-//               candidates, distances and near-tie flags.
+//               candidates, distances and near-tie flags, and the certification that no
+//               screened-out column can enter the top two (else the query is listed).
+//   nn_exact  : the listed queries against all of B with exact integer dots.
 // The products and partial sums of integer counts stay below 2^24, so every FP32 addition
 // in the tensor-core accumulation is exact: the accumulators hold the exact integer dot
 // products, which the epilogue stores with each candidate for the re-rank.
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(&bars[TC_NBARS]);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* rinv_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 256);
-  float* thr_s = rinv_s + TC_ACC * TC_BN;          // [half][row]: 8th-best score of a list
+  float* thr_s = rinv_s + TC_ACC * TC_BN;          // [half][row]: TC_TOPK-th best score of a list
   float* stage_s = thr_s + TC_HALVES * TC_BM;      // [epilogue warp][lane][32], swizzled
   for (int i = threadIdx.x; i < TC_HALVES * TC_BM; i += TC_THREADS) thr_s[i] = -1.f;
 
@@ -319,11 +322,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
   } else {
     // ----------------------------------------------------------------- epilogue
     // Warp w reads TMEM lanes 32 (w % 4) .. +31 (the quadrant the hardware lets it access)
-    // and one half (TC_SLICE columns) of every accumulator tile.  Each lane keeps the 8
-    // best candidates of its row within its half.  The two halves of a row publish their
-    // 8th-best score in shared memory and each screens against the larger of the two: a
-    // candidate below the partner's 8th best has 8 better ones in the partner's half and
-    // cannot be among the row's 8 best, so the union of the two lists still holds them.
+    // and one half (TC_SLICE columns) of every accumulator tile.  Each lane keeps the
+    // TC_TOPK best candidates of its row within its half.  The two halves of a row publish
+    // their TC_TOPK-th best score in shared memory and each screens against the larger of
+    // the two: a candidate below the partner's TC_TOPK-th best has TC_TOPK better ones in
+    // the partner's half and cannot be among the row's TC_TOPK best, so the union of the
+    // two lists still holds them.
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const int etid = threadIdx.x - 64;

@@ -11,6 +11,10 @@ namespace rift2 {
 
 // k_filterbank.cu
 void launch_twiddles(float2* tw, int n, cudaStream_t st);
+// Bluestein tables of a length-n transform run as a length-m convolution (FftPlan);
+// c64 [n] and tw64 [m] are FP64 scratch the caller frees after the stream has passed.
+void launch_bluestein_tables(float2* chirp, float2* kf, float2* ki, double2* c64, double2* tw64,
+                             int n, int m, cudaStream_t st);
 cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
                                 int H, int W, const FftPlan& ph, const FftPlan& pw,
                                 cudaStream_t st);
@@ -19,11 +23,13 @@ void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaSt
 // Column tiles (columns per CTA) the shared-memory column pass can use for height H, the
 // default first; none for the register-tiled heights.  `tile` of launch_lg_cols picks one
 // (0: the default); every tile computes the same result.
-int lg_cols_tile_candidates(int H, int* out, int max_n);
+int lg_cols_tile_candidates(int H, int L, int* out, int max_n);
+// kernels one launch_lg_rows enqueues (2 for the split path of wide rows)
+int lg_rows_launches(int H, int W, const FftPlan& pw);
 cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
                            const FftPlan& ph, const KParams& kp, const unsigned char* zc,
                            cudaStream_t st, int tile = 0);
-cudaError_t launch_lg_rows(const float2* scratch, int nimg, int H, int W, const FftPlan& pw,
+cudaError_t launch_lg_rows(float2* scratch, int nimg, int H, int W, const FftPlan& pw,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
                            unsigned char* mim, int mim_pitch, const unsigned char* zc,
                            cudaStream_t st);
@@ -142,7 +148,8 @@ struct EvalPtrs {
 cudaError_t launch_evaluate(const EvalPtrs& ep, int npairs, double tol, double rmse_cap,
                             int min_correct, cudaStream_t st);
 
-// k_match_tc.cu — tcgen05 BF16 distance GEMM fused with top-8 selection, exact re-rank.
+// k_match_tc.cu — tcgen05 BF16 distance GEMM fused with a top-4 screen per column half,
+// certified exact re-rank, exhaustive pass for the uncertified queries.
 // `cap` (descriptor rows per pair) must be a multiple of 128.
 size_t match_tc_ws_bytes(int npairs, int cap, int nsplit);
 int match_tc_nsplit(int npairs, int cap);

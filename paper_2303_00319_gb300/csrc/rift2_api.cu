@@ -122,18 +122,51 @@ bool factor_plan(int n, FftPlan& pl) {
   return true;
 }
 
+// Length of the Bluestein convolution for a length-n transform: the smallest 13-smooth
+// m >= 2n - 1 (0 if none within the passes' stage limit).
+int bluestein_length(int n) {
+  FftPlan t{};
+  for (int m = 2 * n - 1; m <= 4 * n; ++m)
+    if (factor_plan(m, t)) return m;
+  return 0;
+}
+
 int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
   auto it = c->plans.find(n);
   if (it != c->plans.end()) { *out = it->second; return RIFT2_OK; }
   FftPlan pl{};
-  if (!factor_plan(n, pl)) return RIFT2_E_UNIMPL;
+  int m = n;
+  if (!factor_plan(n, pl)) {
+    m = bluestein_length(n);
+    if (!m || !factor_plan(m, pl)) return RIFT2_E_UNIMPL;
+    pl.n = n;
+  }
+  pl.m = m;
   float2* tw = nullptr;
-  RIFT2_CU(cudaMalloc(&tw, sizeof(float2) * n));
-  launch_twiddles(tw, n, st);
+  RIFT2_CU(cudaMalloc(&tw, sizeof(float2) * m));
+  launch_twiddles(tw, m, st);
   c->launches += 1;
   RIFT2_CU(cudaGetLastError());
-  RIFT2_CU(cudaStreamSynchronize(st));
   pl.tw = tw;
+  if (m != n) {
+    float2 *ch = nullptr, *kf = nullptr, *ki = nullptr;
+    double2 *c64 = nullptr, *tw64 = nullptr;
+    RIFT2_CU(cudaMalloc(&ch, sizeof(float2) * n));
+    RIFT2_CU(cudaMalloc(&kf, sizeof(float2) * m));
+    RIFT2_CU(cudaMalloc(&ki, sizeof(float2) * m));
+    RIFT2_CU(cudaMalloc(&c64, sizeof(double2) * n));
+    RIFT2_CU(cudaMalloc(&tw64, sizeof(double2) * m));
+    launch_bluestein_tables(ch, kf, ki, c64, tw64, n, m, st);
+    c->launches += 3;
+    RIFT2_CU(cudaGetLastError());
+    RIFT2_CU(cudaStreamSynchronize(st));
+    cudaFree(c64);
+    cudaFree(tw64);
+    pl.chirp = ch;
+    pl.kern_fwd = kf;
+    pl.kern_inv = ki;
+  }
+  RIFT2_CU(cudaStreamSynchronize(st));
   c->plans[n] = pl;
   *out = pl;
   return RIFT2_OK;
@@ -174,21 +207,20 @@ int ensure_ws(rift2_ctx* c, size_t need) {
   return RIFT2_OK;
 }
 
+// Sides the transforms take: 13-smooth up to 8192 (direct), any other length up to 4096
+// (Bluestein: a convolution of 13-smooth length < 8192).
 int check_size(int H, int W) {
   if (H < 16 || W < 16) return RIFT2_E_INVAL;
+  if (H > 8192 || W > 8192) return RIFT2_E_UNIMPL;
   FftPlan t{};
-  if (!factor_plan(H, t) || !factor_plan(W, t)) return RIFT2_E_UNIMPL;
-  // the generic row pass keeps the four scales of a row in shared memory; power-of-two
-  // widths up to 4096 take the register-tiled path
-  const bool pow2_w = (W & (W - 1)) == 0 && W >= 256 && W <= 4096;
-  if (!pow2_w && (size_t)2 * NS * W * sizeof(float2) > 227 * 1024) return RIFT2_E_UNIMPL;
-  if (W > 4096 || H > 8192) return RIFT2_E_UNIMPL;
+  for (int n : {H, W})
+    if (!factor_plan(n, t) && (n > 4096 || !bluestein_length(n))) return RIFT2_E_UNIMPL;
   return RIFT2_OK;
 }
 
 // ------------------------------------------------------------------ tracing
 // Kernels enqueued by each launcher (kept next to the launch sequences they count).
-constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_LG_ROWS = 1, K_NOISE = 6, K_MOMENT = 1,
+constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_NOISE = 6, K_MOMENT = 1,
               K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1,
               K_MERGE = 1;
 
@@ -235,7 +267,7 @@ int tune_col_tile(rift2_ctx* c, const float2* spec, float2* scratch, int g, int 
   auto it = c->col_tiles.find(key);
   if (it != c->col_tiles.end()) { *tile = it->second; return RIFT2_OK; }
   int cand[8];
-  const int n = lg_cols_tile_candidates(H, cand, 8);
+  const int n = lg_cols_tile_candidates(H, ph.m, cand, 8);
   if (n <= 1) { *tile = n ? cand[0] : 0; c->col_tiles[key] = *tile; return RIFT2_OK; }
   cudaEvent_t ev[9];
   for (int i = 0; i <= n; ++i) RIFT2_CU(cudaEventCreate(&ev[i]));
@@ -490,7 +522,7 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
     RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, tile));
   }
   {
-    StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, K_LG_ROWS);
+    StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, lg_rows_launches(H, W, pw));
     RIFT2_CU(launch_lg_rows(scratch, g, H, W, pw, c->kp, er, q, an0, at<float>(ws, L.amp), mim,
                             L.mim_pitch, zc, st));
   }
@@ -631,7 +663,14 @@ int rift2_destroy(rift2_ctx* c) {
   if (!c) return RIFT2_E_INVAL;
   DeviceGuard dg(c->device);
   cudaDeviceSynchronize();
-  for (auto& kv : c->plans) cudaFree(const_cast<float2*>(kv.second.tw));
+  for (auto& kv : c->plans) {
+    cudaFree(const_cast<float2*>(kv.second.tw));
+    if (kv.second.chirp) {
+      cudaFree(const_cast<float2*>(kv.second.chirp));
+      cudaFree(const_cast<float2*>(kv.second.kern_fwd));
+      cudaFree(const_cast<float2*>(kv.second.kern_inv));
+    }
+  }
   for (auto& kv : c->zero_cols) cudaFree(kv.second);
   for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : c->free_events) cudaEventDestroy(e);

@@ -205,17 +205,22 @@ def smooth_sizes(lo: int = 16, hi: int = 8192, primes=(2, 3, 5, 7, 11, 13)):
     return np.array(out)
 
 
-def serving_sizes(n: int, seed: int, lo: int = 256, hi: int = 4096, max_width: int = 3584):
-    """Pair sizes of the serving workload: each side log-uniform in [lo, hi], snapped to the
-    nearest size the transforms take (13-smooth; width at most max_width)."""
+def serving_sizes(n: int, seed: int, lo: int = 256, hi: int = 4096, smooth: bool = False,
+                  max_width: int = 3584):
+    """Pair sizes of the serving workload: each side an integer log-uniform in [lo, hi]
+    (rounded to the nearest integer).  With smooth=True each side is instead snapped to the
+    nearest 13-smooth size (width at most max_width)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    ok = smooth_sizes(lo, hi)
+    ok = smooth_sizes(lo, hi) if smooth else None
     out = []
     for _ in range(n):
         side = []
         for lim in (hi, max_width):
             x = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
-            cand = ok[ok <= lim]
-            side.append(int(cand[np.argmin(np.abs(cand - x))]))
+            if smooth:
+                cand = ok[ok <= lim]
+                side.append(int(cand[np.argmin(np.abs(cand - x))]))
+            else:
+                side.append(int(min(hi, max(lo, round(x)))))
         out.append((side[0], side[1]))
     return out

@@ -60,7 +60,11 @@ def small(pkg, dev):
 
 # --------------------------------------------------------------------------- FFT
 @pytest.mark.parametrize("h,w", [(16, 16), (256, 256), (1024, 1024), (48, 80), (105, 63),
-                                 (384, 640), (224, 448), (1408, 176), (1664, 208), (2048, 1920)])
+                                 (384, 640), (224, 448), (1408, 176), (1664, 208), (2048, 1920),
+                                 # Bluestein lengths (a prime factor above 13): primes, 17,
+                                 # the largest side, and wide smooth rows beyond the register path
+                                 (257, 263), (17, 34), (1021, 97), (4093, 24), (40, 4091),
+                                 (64, 6144)])
 def test_fft2_matches_numpy(pkg, dev, h, w):
     ctx = pkg.Context(pkg.default_params(), device=0)
     x = np.random.default_rng(h * 7 + w).random((2, h, w)).astype(np.float32)
@@ -367,7 +371,10 @@ def _check_all_maps(dbg, o, label):
     def m_norm():
         assert dn < 5e-6, f"{label}: M in normalised units {dn:.3e}"
     check(m_norm)
-    check(lambda: assert_map(f"{label} M", d["moment"], mo, 1e-2))
+    # M is quadratic in PC: its relative error is twice PC's at leading order, so its floor
+    # is twice the floor 1e-2 that PC's own bar implies; what the detector thresholds is M
+    # in normalised units, checked above against the certification margin
+    check(lambda: assert_map(f"{label} M", d["moment"], mo, 2e-2))
     assert not errs, "; ".join(errs)
     return int(mis.sum())
 
@@ -395,11 +402,16 @@ def test_end_to_end_1024(pkg, dev):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("h,w", [(384, 640), (1408, 256)])
+@pytest.mark.parametrize("h,w", [(384, 640), (1408, 256),
+                                 # Bluestein sides: both prime; and rows too wide for the fused
+                                 # row pass (split path): 6144 = 2^11 3, prime 2053
+                                 (257, 263), (150, 6144), (160, 2053)])
 def test_mixed_radix_maps_and_descriptors(pkg, dev, h, w):
-    """Sizes whose transforms run the shared-memory mixed-radix kernels (lg_cols_inverse,
-    lg_rows_reduce; 384 = 2^7 3, 640 = 2^7 5, 1408 = 2^7 11): every map, keypoints,
-    descriptors and matches of a pair against the oracle, as for the register path."""
+    """Sizes whose transforms run the shared-memory kernels (lg_cols_inverse, lg_rows_reduce;
+    384 = 2^7 3, 640 = 2^7 5, 1408 = 2^7 11), Bluestein's chirp-z form for sides with a
+    prime factor above 13, and the split row pass for rows too wide for four scales in
+    shared memory: every map, keypoints, descriptors and matches of a pair against the
+    oracle, as for the register path."""
     pr = synth.make_pair(h, w, synth.pair_seed(2, h + w), angle_deg=None)
     ctx = pkg.Context(pkg.default_params(max_keypoints=600), device=0)
     fa, fb = ctx.extract([torch.from_numpy(pr.a).to(dev), torch.from_numpy(pr.b).to(dev)],
@@ -429,9 +441,12 @@ def test_edge_images(pkg, dev):
     assert f[1].counts.cpu().tolist() == [0, 0]
     o = O.extract(r.cpu().numpy().astype(np.float64), O.Params(max_keypoints=100), keep_maps=True)
     g, _ = _e2e_check(f[2], o, None)
-    # unsupported size (prime factor 17) is refused, not computed wrongly
-    with pytest.raises(pkg.Rift2Error):
-        ctx.extract([torch.rand((136, 128), device=dev)])
+    # sides the transforms do not take are refused, not computed wrongly: a length with a
+    # prime factor above 13 beyond 4096, and any side beyond 8192
+    for shape in ((4099, 128), (128, 8200)):
+        with pytest.raises(pkg.Rift2Error) as e:
+            ctx.extract([torch.rand(shape, device=dev)])
+        assert e.value.code == pkg.E_UNIMPL
 
 
 @pytest.mark.parametrize("na,nb", [(3000, 4500), (129, 127), (1, 300), (640, 1)])
