@@ -482,49 +482,79 @@ def run_ours(args):
     # two device input buffers), runs extract + match, and copies its matches out; all K
     # steps' copies lie inside the timed region
     copy_stream = torch.cuda.Stream(device=dev)
-    dbuf = [[torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host[0]] for _ in range(2)]
-    # every pair's correspondences (q_desc, nn_desc, kp_a, kp_b, d1, d2 as 32-bit words,
-    # near_tie bytes, the row count) and both images' keypoints (x, y, score, n_kp, n_desc)
+    # inputs: each batch as one pinned host tensor and two device tensors [2B][H][W] (one
+    # H2D copy per step); outputs: every pair's correspondences (q_desc, nn_desc, kp_a, kp_b,
+    # d1, d2, near_tie, count) and both images' keypoints (xy, score, counts) as views into
+    # one device arena (one D2H copy per step), descriptors in their own buffers
     ncap = matches[0].nn_desc.shape[0]
     kcap = feats[0].kp_xy.shape[0]
-    out_h = [torch.empty(6 * ncap + 1, dtype=torch.int32).pin_memory() for _ in range(B)]
-    tie_h = [torch.empty(ncap, dtype=torch.uint8).pin_memory() for _ in range(B)]
-    kp_h = [torch.empty(3 * kcap + 2, dtype=torch.int32).pin_memory() for _ in range(2 * B)]
+    al = lambda n: (n + 15) // 16 * 16  # noqa: E731  (64-byte aligned sub-arrays)
+    per_pair = 6 * al(ncap) + al((ncap + 3) // 4) + 16
+    per_img = al(2 * kcap) + al(kcap) + 16
+    arena = torch.zeros(B * per_pair + 2 * B * per_img, dtype=torch.int32, device=dev)
+    e2e_feats, e2e_matches = [], []
+    for b in range(B):
+        o = b * per_pair
+        m = ctx.alloc_matches()
+        views = []
+        for k in range(6):
+            views.append(arena[o + k * al(ncap):o + k * al(ncap) + ncap])
+        o6 = o + 6 * al(ncap)
+        tie = arena[o6:o6 + (ncap + 3) // 4].view(torch.uint8)[:ncap]
+        cnt = arena[o6 + al((ncap + 3) // 4):o6 + al((ncap + 3) // 4) + 1]
+        e2e_matches.append(pkg.Matches(views[0], views[1], views[2], views[3],
+                                       views[4].view(torch.float32), views[5].view(torch.float32),
+                                       tie, cnt))
+    for j in range(2 * B):
+        o = B * per_pair + j * per_img
+        f = ctx.alloc_features()
+        f.kp_xy = arena[o:o + 2 * kcap].view(kcap, 2)
+        f.kp_score = arena[o + al(2 * kcap):o + al(2 * kcap) + kcap].view(torch.float32)
+        f.counts = arena[o + al(2 * kcap) + al(kcap):o + al(2 * kcap) + al(kcap) + 2]
+        e2e_feats.append(f)
+    # each batch flattened into one buffer (sizes may differ), images as views into it
+    offs = [0]
+    for t in host[0]:
+        offs.append(offs[-1] + t.numel())
+    host_flat = [torch.cat([t.reshape(-1) for t in batch]).pin_memory() for batch in host]
+    dflat = [torch.empty_like(host_flat[0], device=dev) for _ in range(2)]
+    shapes = [tuple(t.shape) for t in host[0]]
+    views = lambda flat: [flat[offs[k]:offs[k + 1]].view(shapes[k]) for k in range(2 * B)]  # noqa: E731
+    arena_h = [torch.empty(arena.shape, dtype=torch.int32).pin_memory() for _ in range(2)]
     ev_copied = [torch.cuda.Event() for _ in range(args.steps)]
     ev_done = [torch.cuda.Event() for _ in range(args.steps)]
+
+    def e2e_step(imgs):
+        ctx.extract(imgs, e2e_feats, stream=stream)
+        ctx.match(e2e_feats[0::2], e2e_feats[1::2], e2e_matches, stream=stream)
+
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     copy_stream.wait_stream(stream)
     for i in range(args.steps):
-        buf = dbuf[i % 2]
+        buf = dflat[i % 2]
         with torch.cuda.stream(copy_stream):
             if i >= 2:
                 copy_stream.wait_event(ev_done[i - 2])   # this buffer's previous step is done
-            for d, h in zip(buf, host[i % rot]):
-                d.copy_(h, non_blocking=True)
+            buf.copy_(host_flat[i % rot], non_blocking=True)
             ev_copied[i].record(copy_stream)
         stream.wait_event(ev_copied[i])
-        step(buf)
-        for b in range(B):
-            m = matches[b]
-            for k, tsr in enumerate((m.q_desc, m.nn_desc, m.kp_a, m.kp_b, m.d1.view(torch.int32),
-                                     m.d2.view(torch.int32))):
-                out_h[b][k * ncap:(k + 1) * ncap].copy_(tsr, non_blocking=True)
-            out_h[b][6 * ncap:].copy_(m.count, non_blocking=True)
-            tie_h[b].copy_(m.near_tie, non_blocking=True)
-        for j, f in enumerate(feats):
-            kp_h[j][:2 * kcap].copy_(f.kp_xy.view(-1), non_blocking=True)
-            kp_h[j][2 * kcap:3 * kcap].copy_(f.kp_score.view(torch.int32), non_blocking=True)
-            kp_h[j][3 * kcap:].copy_(f.counts, non_blocking=True)
+        e2e_step(views(buf))
+        arena_h[i % 2].copy_(arena, non_blocking=True)
         ev_done[i].record(stream)
     e1.record(stream)
     e1.synchronize()
     e2e_ms = [e0.elapsed_time(e1)]
     barrier()
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(sum(e2e_ms), dev))
-    h2d = int(sum(t.numel() for t in host[0]) * 4)
-    d2h = int(B * ((6 * ncap + 1) * 4 + ncap) + 2 * B * (3 * kcap + 2) * 4)
+    h2d = int(host_flat[0].numel() * 4)
+    d2h = int(arena.numel() * 4)
+    # the last step's copied-back correspondences equal those of the device-resident steps
+    # on the same batch (the timed loop's last step ran batch (steps - 1) % rot as well)
+    last = arena_h[(args.steps - 1) % 2]
+    n0 = int(matches[0].count.item())
+    e2e_same = bool(torch.equal(last[al(ncap):al(ncap) + n0], matches[0].nn_desc[:n0].cpu()))
 
     # graph form: the step's launches (extract + match of the whole batch, every size
     # group) captured once into a CUDA graph and replayed; the context's plans, tables and
@@ -769,11 +799,12 @@ def run_ours(args):
             "parity": parity,
             "other_workloads": others,
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-                    "form": "pinned host images in on a copy stream (step i+1's copy overlaps "
-                            "step i's kernels); every step copies out each pair's full "
-                            "correspondences (q_desc, nn_desc, kp_a, kp_b, d1, d2, near_tie, count) "
-                            "and both images' keypoints (xy, score, counts)",
-                    "d2h_bytes_per_step": d2h},
+                    "form": "pinned host images in (one copy per step, on a copy stream: step "
+                            "i+1's copy overlaps step i's kernels); every step copies out each "
+                            "pair's full correspondences (q_desc, nn_desc, kp_a, kp_b, d1, d2, "
+                            "near_tie, count) and both images' keypoints (xy, score, counts), "
+                            "packed in one device arena (one copy per step)",
+                    "d2h_bytes_per_step": d2h, "results_equal_device_resident_steps": e2e_same},
             "gpu_launches": launches,
             "clocks": clk,
             "wall_s_timed": wall,
