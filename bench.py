@@ -423,14 +423,14 @@ def run_ours(args):
     # inputs: `rot` batches of B pairs, distinct per rank; pinned host copies for e2e
     host = []
     sizes = wl["sizes"](B, rank)
+    jobs = [(sizes[b][0], sizes[b][1], synth.pair_seed(args.workload, 100000 * rank + r * B + b))
+            for r in range(rot) for b in range(B)]
+    made = make_pairs(jobs)   # on the host cores, in parallel
     for r in range(rot):
         batch = []
         for b in range(B):
-            h, w = sizes[b]
-            kw = dict(n_blobs=400, n_segments=200) if (h, w) == (1024, 1024) else {}
-            pr = synth.make_pair(h, w, synth.pair_seed(args.workload, 100000 * rank + r * B + b),
-                                 angle_deg=None, **kw)
-            batch += [torch.from_numpy(pr.a).pin_memory(), torch.from_numpy(pr.b).pin_memory()]
+            a, bb = made[r * B + b]
+            batch += [torch.from_numpy(a).pin_memory(), torch.from_numpy(bb).pin_memory()]
         host.append(batch)
     devb = [[t.to(dev) for t in batch] for batch in host]
     feats = [ctx.alloc_features() for _ in range(2 * B)]
