@@ -35,7 +35,11 @@ __device__ constexpr int kCircleDy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1
 // A run of >= arc cyclically contiguous set bits in the 16-bit circle mask (1 <= arc <= 16).
 // acc holds the AND of r >> 0 .. h-1 (bit i set: bits i .. i+h-1 of r all set); doubling h
 // and one final shift by arc - h (<= h) extend it to arc.
+// ARC > 0: the arc length as a compile-time constant (the loop unrolls into a fixed
+// sequence of shifts); ARC = 0 reads it from `arc`.
+template <int ARC = 0>
 __device__ __forceinline__ bool has_arc(unsigned m16, int arc) {
+  if constexpr (ARC > 0) arc = ARC;
   if (__popc(m16) < arc) return false;
   const unsigned r = m16 | (m16 << 16);   // cyclic: any run of length <= 16 appears linearly
   unsigned acc = r;
@@ -48,6 +52,7 @@ __device__ __forceinline__ bool has_arc(unsigned m16, int arc) {
   return acc != 0;
 }
 
+template <int ARC>
 __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment, int H, int W,
                                                 KParams kp, DetectWs ws) {
   __shared__ float mn[FSY][FSX];
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
         nb += (q > p + t) ? 1 : 0;
         nd += (q < p - t) ? 1 : 0;
       }
-      if (max(nb, nd) >= (kp.fast_arc >> 2)) {
+      if (max(nb, nd) >= ((ARC > 0 ? ARC : kp.fast_arc) >> 2)) {
         unsigned bright = 0, dark = 0;
         float vb = 0.f, vd = 0.f;
 #pragma unroll
@@ -96,7 +101,8 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
           if (q > p + t) { bright |= 1u << k; vb += q - p - t; }
           if (q < p - t) { dark |= 1u << k; vd += p - q - t; }
         }
-        if (has_arc(bright, kp.fast_arc) || has_arc(dark, kp.fast_arc)) score = fmaxf(vb, vd);
+        if (has_arc<ARC>(bright, kp.fast_arc) || has_arc<ARC>(dark, kp.fast_arc))
+          score = fmaxf(vb, vd);
       }
     }
     vs[ly][lx] = score;
@@ -577,7 +583,8 @@ cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KPa
     cudaError_t e = cudaMemsetAsync(ws.cand_hist, 0, ((size_t)nimg << TOPK_DIGIT_BITS) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
   }
-  fast_nms<<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
+  if (kp.fast_arc == 9) fast_nms<9><<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
+  else fast_nms<0><<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
   if (ws.cand_hist) {
     topk_select<<<nimg, 1024, 0, st>>>(kp, ws);
     topk_gather<<<dim3(16, nimg), 256, 0, st>>>(kp, ws);

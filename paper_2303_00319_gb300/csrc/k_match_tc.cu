@@ -163,19 +163,12 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
 }
 
 // --------------------------------------------------------------------------- prep
-// B's rows are ordered by squared norm before the GEMM (a bucket sort: buckets of 1024 in
-// |b|^2 <= 36 * 256^2), so that the 32 columns an epilogue chunk screens have nearly equal
-// 1/|b|: one product of the chunk's largest raw dot and its largest 1/|b| then bounds every
-// score of the chunk, and most chunks are rejected before any per-column multiply.
-constexpr int TC_NBUCKET = 4096, TC_BUCKET_SHIFT = 10;
-static_assert((36 * 256 * 256) >> TC_BUCKET_SHIFT < TC_NBUCKET, "bucket range");
-
-// grid (rows / 8, 2 sides, pairs); warp per descriptor row.  Side A: BF16 rows, squared
-// norms.  Side B: squared norms and their bucket histogram (rows are written sorted later).
+// grid (rows / 8, 2 sides, pairs); warp per descriptor row.
 __global__ void __launch_bounds__(256) nn_prep(MatchPtrs mp, __nv_bfloat16* __restrict__ abf,
+                                               __nv_bfloat16* __restrict__ bbf,
+                                               float* __restrict__ rinv_b,
                                                int* __restrict__ n2_a, int* __restrict__ n2_b,
-                                               int* __restrict__ bhist, int cap,
-                                               int* __restrict__ n_unsure) {
+                                               int cap, int* __restrict__ n_unsure) {
   const int pr = blockIdx.z, side = blockIdx.y;
   if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) *n_unsure = 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,6 +176,7 @@ __global__ void __launch_bounds__(256) nn_prep(MatchPtrs mp, __nv_bfloat16* __re
   const int n = side ? mp.counts_b[pr][1] : mp.counts_a[pr][1];
   if (row >= n) return;
   const unsigned short* src = (side ? mp.desc_b[pr] : mp.desc_a[pr]) + (size_t)row * DESC_DIM;
+  __nv_bfloat16* dst = (side ? bbf : abf) + ((size_t)pr * cap + row) * TC_KP;
   unsigned n2 = 0;
   __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
@@ -192,98 +186,23 @@ __global__ void __launch_bounds__(256) nn_prep(MatchPtrs mp, __nv_bfloat16* __re
     n2 += c * c;
     v[i] = __float2bfloat16_rn((float)c);   // counts <= 256: exact
   }
-  if (!side) {
-    __nv_bfloat16* dst = abf + ((size_t)pr * cap + row) * TC_KP;
-    *reinterpret_cast<uint4*>(dst + lane * 8) = *reinterpret_cast<const uint4*>(v);
-  }
+  *reinterpret_cast<uint4*>(dst + lane * 8) = *reinterpret_cast<const uint4*>(v);
   for (int d = 16; d > 0; d >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, d);
   if (lane == 0) {
     if (side) {
       n2_b[(size_t)pr * cap + row] = (int)n2;
-      atomicAdd(bhist + (size_t)pr * TC_NBUCKET + (n2 >> TC_BUCKET_SHIFT), 1);
+      rinv_b[(size_t)pr * cap + row] = 1.f / sqrtf((float)n2);
     } else {
       n2_a[(size_t)pr * cap + row] = (int)n2;
     }
   }
 }
 
-// One CTA per pair: exclusive scan of the bucket histogram into the buckets' first slots.
-__global__ void __launch_bounds__(1024) nn_bucket_scan(int* __restrict__ bhist) {
-  __shared__ int part[1024];
-  int* h = bhist + (size_t)blockIdx.x * TC_NBUCKET;
-  constexpr int PER = TC_NBUCKET / 1024;
-  int loc[PER], sum = 0;
-#pragma unroll
-  for (int i = 0; i < PER; ++i) { loc[i] = h[threadIdx.x * PER + i]; sum += loc[i]; }
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    const int a = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
-    __syncthreads();
-    part[threadIdx.x] += a;
-    __syncthreads();
-  }
-  int run = part[threadIdx.x] - sum;
-#pragma unroll
-  for (int i = 0; i < PER; ++i) { h[threadIdx.x * PER + i] = run; run += loc[i]; }
-}
-
-// Row j of B goes to the next free slot of its bucket: perm[slot] = j.
-__global__ void __launch_bounds__(256) nn_bucket_scatter(MatchPtrs mp, const int* __restrict__ n2_b,
-                                                         int* __restrict__ bhist,
-                                                         int* __restrict__ perm, int cap) {
-  const int pr = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= mp.counts_b[pr][1]) return;
-  const int n2 = n2_b[(size_t)pr * cap + j];
-  const int slot = atomicAdd(bhist + (size_t)pr * TC_NBUCKET + (n2 >> TC_BUCKET_SHIFT), 1);
-  perm[(size_t)pr * cap + slot] = j;
-}
-
-// Warp per sorted slot: the BF16 row of B's descriptor perm[slot] and its 1/|b|.
-__global__ void __launch_bounds__(256) nn_gather_b(MatchPtrs mp, const int* __restrict__ n2_b,
-                                                   const int* __restrict__ perm,
-                                                   __nv_bfloat16* __restrict__ bbf,
-                                                   float* __restrict__ rinv_s, int cap) {
-  const int pr = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = blockIdx.x * 8 + warp;
-  if (slot >= mp.counts_b[pr][1]) return;
-  const int j = perm[(size_t)pr * cap + slot];
-  const unsigned short* src = mp.desc_b[pr] + (size_t)j * DESC_DIM;
-  __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int k = lane * 8 + i;
-    v[i] = __float2bfloat16_rn((float)((k < DESC_DIM) ? src[k] : 0u));
-  }
-  __nv_bfloat16* dst = bbf + ((size_t)pr * cap + slot) * TC_KP;
-  *reinterpret_cast<uint4*>(dst + lane * 8) = *reinterpret_cast<const uint4*>(v);
-  if (lane == 0) rinv_s[(size_t)pr * cap + slot] = 1.f / sqrtf((float)n2_b[(size_t)pr * cap + j]);
-}
-
-// Largest 1/|b| of each chunk of 32 sorted slots (slots beyond n_B count as 0).
-__global__ void __launch_bounds__(256) nn_chunk_max(MatchPtrs mp, const float* __restrict__ rinv_s,
-                                                    float* __restrict__ rmax, int cap) {
-  const int pr = blockIdx.y;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nch = cap / 32 + 8;   // chunks a tile range can touch (tiles of TC_BN past cap)
-  if (c >= nch) return;
-  const int nB = mp.counts_b[pr][1];
-  float m = 0.f;
-  for (int k = 0; k < 32; ++k) {
-    const int slot = 32 * c + k;
-    if (slot < nB) m = fmaxf(m, rinv_s[(size_t)pr * cap + slot]);
-  }
-  rmax[(size_t)pr * nch + c] = m;
-}
-
 // ------------------------------------------------------------------------- GEMM
 struct TcArgs {
   const int* counts_a[MAXB];
   const int* counts_b[MAXB];
-  const float* rinv_b;   // [pairs][cap], B's sorted slot order
-  const float* rmax;     // [pairs][cap / 32 + 8]: largest 1/|b| of each 32-slot chunk
+  const float* rinv_b;   // [pairs][cap]
   int2* cand;            // [pairs][nsplit * TC_HALVES][cap][TOPK] (index, dot bits)
   int cap, nsplit;
   int* status;
@@ -424,7 +343,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
     float4* stg = reinterpret_cast<float4*>(stage_s + ((warp - 2) * 32 + lane) * 32);
     const int swz = lane & 7;
     const float* rinv = args.rinv_b + (size_t)pr * args.cap;
-    const float* rmx = args.rmax + (size_t)pr * (args.cap / 32 + 8);
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     // 1/|b| of the next tile, prefetched one tile ahead into registers, staged in smem
     float rnext = (nt > 0 && etid < TC_BN) ? __ldg(rinv + t0 * TC_BN + etid) : 0.f;
@@ -460,17 +378,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) nn_tc(const __grid_constant__ C
         for (int c = 0; c < 2; ++c) {
           const int j0 = (t0 + i) * TC_BN + half * TC_SLICE + rd * 64 + c * 32;
           const float* rs = rinv_s + acc * TC_BN + half * TC_SLICE + rd * 64 + c * 32;
-          // chunk bound: every score dot_j / |b_j| of the chunk is at most (largest dot) x
-          // (largest 1/|b|), and rounding is monotonic, so when that product does not beat
-          // the threshold no column of the chunk would enter the list (B is sorted by norm,
-          // which keeps the bound tight)
-          {
-            float raw[32];
-#pragma unroll
-            for (int k = 0; k < 32; ++k) raw[k] = __uint_as_float(r[c][k]);
-            if (__fmul_rn(max32(raw), __ldg(rmx + (j0 >> 5))) <= fmaxf(sc[TC_TOPK - 1], *pa_thr))
-              continue;
-          }
           float sv[32];
 #pragma unroll
           for (int e4 = 0; e4 < 8; ++e4) {
@@ -575,8 +482,7 @@ __device__ __forceinline__ void write_match(const MatchPtrs& mp, int pr, int q, 
 __global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int2* __restrict__ cand,
                                                  const int* __restrict__ n2_a,
                                                  const int* __restrict__ n2_b,
-                                                 const float* __restrict__ rinv_b,
-                                                 const int* __restrict__ perm, int cap,
+                                                 const float* __restrict__ rinv_b, int cap,
                                                  int nsplit, int* __restrict__ unsure,
                                                  int* __restrict__ n_unsure) {
   const int pr = blockIdx.y;
@@ -596,17 +502,13 @@ __global__ void __launch_bounds__(256) nn_rerank(MatchPtrs mp, const int2* __res
       e[2 * k] = make_int2(v.x, v.y);
       e[2 * k + 1] = make_int2(v.z, v.w);
     }
-    // candidates carry B's sorted slots: map them to descriptor indices, which decide ties
-    int jo[TC_TOPK];
     float n2[TC_TOPK];
 #pragma unroll
-    for (int k = 0; k < TC_TOPK; ++k) {
-      jo[k] = (e[k].x >= 0 && e[k].x < nB) ? __ldg(perm + (size_t)pr * cap + e[k].x) : -1;
-      n2[k] = jo[k] >= 0 ? (float)__ldg(n2_b + (size_t)pr * cap + jo[k]) : 0.f;
-    }
+    for (int k = 0; k < TC_TOPK; ++k)
+      n2[k] = (e[k].x >= 0 && e[k].x < nB) ? (float)__ldg(n2_b + (size_t)pr * cap + e[k].x) : 0.f;
 #pragma unroll
     for (int k = 0; k < TC_TOPK; ++k)
-      if (jo[k] >= 0) push2(c1, c2, Cand{__int_as_float(e[k].y), n2[k], jo[k]});
+      if (e[k].x >= 0 && e[k].x < nB) push2(c1, c2, Cand{__int_as_float(e[k].y), n2[k], e[k].x});
     const int2 last = e[TC_TOPK - 1];
     if (last.x >= 0 && last.x < nB)
       s_cut = fmaxf(s_cut, __fmul_rn(__int_as_float(last.y), __ldg(rinv_b + (size_t)pr * cap + last.x)));
@@ -665,8 +567,7 @@ __global__ void __launch_bounds__(NN_EXACT_THREADS) nn_exact(MatchPtrs mp,
 size_t match_tc_ws_bytes(int npairs, int cap, int nsplit) {
   size_t bf = (size_t)npairs * cap * TC_KP * 2;
   size_t per = (size_t)npairs * cap * 4;
-  return 2 * bf + 5 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8 + 4096 +
-         (size_t)npairs * TC_NBUCKET * 4 + (size_t)npairs * (cap / 32 + 8) * 4 + 256;
+  return 2 * bf + 4 * per + (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8 + 4096;
 }
 
 int match_tc_nsplit(int npairs, int cap) {
@@ -694,26 +595,13 @@ cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
   int2* cand = reinterpret_cast<int2*>(p);
   p += (size_t)npairs * nsplit * TC_HALVES * cap * TC_TOPK * 8;
   int* n_unsure = reinterpret_cast<int*>(p);
-  p += 4096;
-  int* perm = reinterpret_cast<int*>(p);
-  p += (size_t)npairs * cap * 4;
-  int* bhist = reinterpret_cast<int*>(p);
-  p += (size_t)npairs * TC_NBUCKET * 4;
-  float* rmax = reinterpret_cast<float*>(p);
-  const int nch = cap / 32 + 8;
-  cudaMemsetAsync(bhist, 0, (size_t)npairs * TC_NBUCKET * 4, st);
-  nn_prep<<<dim3((cap + 7) / 8, 2, npairs), 256, 0, st>>>(mp, abf, n2a, n2b, bhist, cap, n_unsure);
-  nn_bucket_scan<<<npairs, 1024, 0, st>>>(bhist);
-  nn_bucket_scatter<<<dim3((cap + 255) / 256, npairs), 256, 0, st>>>(mp, n2b, bhist, perm, cap);
-  nn_gather_b<<<dim3((cap + 7) / 8, npairs), 256, 0, st>>>(mp, n2b, perm, bbf, rinv, cap);
-  nn_chunk_max<<<dim3((nch + 255) / 256, npairs), 256, 0, st>>>(mp, rinv, rmax, cap);
+  nn_prep<<<dim3((cap + 7) / 8, 2, npairs), 256, 0, st>>>(mp, abf, bbf, rinv, n2a, n2b, cap, n_unsure);
   TcArgs ta{};
   for (int i = 0; i < npairs; ++i) {
     ta.counts_a[i] = mp.counts_a[i] + 1;
     ta.counts_b[i] = mp.counts_b[i] + 1;
   }
   ta.rinv_b = rinv;
-  ta.rmax = rmax;
   ta.cand = cand;
   ta.cap = cap;
   ta.nsplit = nsplit;
@@ -721,8 +609,8 @@ cudaError_t launch_match_tc(const MatchPtrs& mp, int npairs, int cap, void* ws,
   const size_t sm = TC_SMEM;
   cudaFuncSetAttribute(nn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   nn_tc<<<dim3((cap + TC_BM - 1) / TC_BM, nsplit, npairs), TC_THREADS, sm, st>>>(*tmA, *tmB, ta);
-  nn_rerank<<<dim3((cap + 255) / 256, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, rinv, perm, cap,
-                                                             nsplit, unsure, n_unsure);
+  nn_rerank<<<dim3((cap + 255) / 256, npairs), 256, 0, st>>>(mp, cand, n2a, n2b, rinv, cap, nsplit,
+                                                             unsure, n_unsure);
   nn_exact<<<152, NN_EXACT_THREADS, 0, st>>>(mp, n2a, n2b, cap, unsure, n_unsure);
   return cudaGetLastError();
 }

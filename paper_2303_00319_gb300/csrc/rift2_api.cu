@@ -221,7 +221,7 @@ int check_size(int H, int W) {
 // ------------------------------------------------------------------ tracing
 // Kernels enqueued by each launcher (kept next to the launch sequences they count).
 constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_NOISE = 6, K_MOMENT = 1,
-              K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 8, K_INIT = 1,
+              K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1,
               K_MERGE = 1;
 
 cudaEvent_t take_event(rift2_ctx* c) {
