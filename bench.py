@@ -340,36 +340,54 @@ def workload_summary(pkg, dev, wl_id, steps=4, warmup=3):
     imgs = []
     for a, b in pairs:
         imgs += [torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)]
-    ctx = pkg.Context(pkg.default_params(max_keypoints=wl["max_kp"], flags=pkg.FLAG_AUTOTUNE),
-                      device=dev.index, hbm_budget=96 << 30)
-    feats = [ctx.alloc_features() for _ in range(2 * B)]
-    matches = [ctx.alloc_matches() for _ in range(B)]
+    px = sum(2 * h * w for h, w in sizes)
     st = torch.cuda.current_stream()
 
-    def step():
-        ctx.extract(imgs, feats, stream=st)
-        ctx.match(feats[0::2], feats[1::2], matches, stream=st)
+    def timed(flags, stages=False):
+        ctx = pkg.Context(pkg.default_params(max_keypoints=wl["max_kp"], flags=flags),
+                          device=dev.index, hbm_budget=96 << 30)
+        feats = [ctx.alloc_features() for _ in range(2 * B)]
+        matches = [ctx.alloc_matches() for _ in range(B)]
 
-    for _ in range(warmup):
-        step()
-    ctx.sync()
-    torch.cuda.synchronize()
-    l0 = ctx.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(steps):
-        step()
-    e1.record(st)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    px = sum(2 * h * w for h, w in sizes)
-    ctx.sync()
-    out = {"workload": wl["desc"], "metric": wl["metric"], "pairs_per_step": B,
-           "value": B / (ms / 1000.0), "unit": "pairs/s", "ms_per_step": ms,
-           "mpix_per_s": px / 1e6 / (ms / 1000.0),
-           "launches_per_step": (ctx.launch_count() - l0) // steps, "steps": steps,
-           "warmup": warmup}
-    ctx.close()
+        def step():
+            ctx.extract(imgs, feats, stream=st)
+            ctx.match(feats[0::2], feats[1::2], matches, stream=st)
+
+        for _ in range(warmup):
+            step()
+        ctx.sync()
+        torch.cuda.synchronize()
+        l0 = ctx.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            step()
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ctx.sync()
+        res = {"value": B / (ms / 1000.0), "unit": "pairs/s", "ms_per_step": ms,
+               "mpix_per_s": px / 1e6 / (ms / 1000.0),
+               "launches_per_step": (ctx.launch_count() - l0) // steps}
+        if stages:   # one more step with per-stage events (after the timed ones)
+            ctx.set_profiling(True)
+            step()
+            ctx.sync()
+            res["stage_ms_per_step"] = {k: round(v[0], 4) for k, v in ctx.profile_read().items()}
+            ctx.set_profiling(False)
+        ctx.close()
+        return res
+
+    out = {"workload": wl["desc"], "metric": wl["metric"], "pairs_per_step": B}
+    out.update(timed(pkg.FLAG_AUTOTUNE, stages=True))
+    out.update({"steps": steps, "warmup": warmup})
+    if len({tuple(x) for x in sizes}) > 1:
+        # the same batch with launch groups of one image size each (RIFT2_FLAG_SIZE_GROUPS)
+        sg = timed(pkg.FLAG_AUTOTUNE | pkg.FLAG_SIZE_GROUPS)
+        out["size_groups_form"] = {"value": sg["value"], "unit": "pairs/s",
+                                   "ms_per_step": sg["ms_per_step"],
+                                   "launches_per_step": sg["launches_per_step"],
+                                   "form": "launch groups of one image size each"}
     return out
 
 

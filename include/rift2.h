@@ -86,6 +86,11 @@ enum {
  * samples outside the image are not counted; counts are recoded by w (Eq. 2).  Not with
  * RIFT2_FLAG_RIFT_TEMPLATE / RIFT2_FLAG_RIFT_RING (RIFT2_E_INVAL). */
 #define RIFT2_FLAG_SPATIAL_NORM 0x40
+/* Launch groups of one image size only (consecutive images of equal size share launches,
+ * in call order).  Without it rift2_extract orders the call's images by size and lets up
+ * to RIFT2_MAX_BATCH images of any sizes share one launch per stage; each image's results
+ * are bit-identical either way. */
+#define RIFT2_FLAG_SIZE_GROUPS 0x80
 
 /*
  * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
@@ -223,10 +228,13 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
  * log-Gabor bank in the frequency domain -> MIM and phase congruency -> maximum
  * moment -> FAST + NMS + top-K -> dominant-index-recoded 6x6xNo descriptors.
  * imgs[i] (host array of n_images structs; data on the device) -> out[i] (host array).
- * Each side must be >= 16 with prime factors in {2, 3, 5, 7, 11, 13} and width <= 3584
- * (the row pass keeps the four scales of a row in shared memory); images smaller than
- * patch + 6 on a side produce zero keypoints.  Images of equal size are grouped into
- * shared launches unless RIFT2_FLAG_NO_GROUPING is set.
+ * Each side must be >= 16, and either 13-smooth (prime factors in {2, 3, 5, 7, 11, 13})
+ * up to 8192 or any length up to 4096 (Bluestein transforms); images smaller than patch
+ * + 6 on a side produce zero keypoints.  Launch groups: up to RIFT2_MAX_BATCH images of
+ * any sizes share one launch per stage (the images taken in order of size; one launch per
+ * run of equal size for the register-tiled transforms of power-of-two sides), split
+ * further while a group's workspace exceeds the HBM budget; RIFT2_FLAG_SIZE_GROUPS keeps
+ * one size per group, RIFT2_FLAG_NO_GROUPING one image.
  * Errors: RIFT2_E_INVAL, RIFT2_E_UNIMPL (size), RIFT2_E_CAPACITY, RIFT2_E_NOMEM,
  * RIFT2_E_CUDA.
  */

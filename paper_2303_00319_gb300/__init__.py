@@ -23,6 +23,7 @@ FLAG_RIFT_RING = 0x8       # RIFT baseline: the No descriptors of the convolutio
 FLAG_CORNERS = 0x10        # RIFT's corner keypoints on the minimum moment, after the edge ones
 FLAG_AUTOTUNE = 0x20       # time the column tiles of a new image size once, keep the fastest
 FLAG_SPATIAL_NORM = 0x40   # variant: patch grid rotated into the dominant index's frame
+FLAG_SIZE_GROUPS = 0x80    # launch groups of one image size only (mixed sizes share launches without it)
 NS, NO, PATCH, CELLS = 4, 6, 96, 6
 DESC_DIM = CELLS * CELLS * NO
 

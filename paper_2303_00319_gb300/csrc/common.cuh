@@ -61,6 +61,21 @@ struct ImgPtrs {
   long long pitch[MAXB];
 };
 
+// The images of one launch group, which may differ in size (passed by value to the
+// kernels of every stage; image i of the group is blockIdx.y or .z == i, and CTAs past
+// the extent of a smaller image return at once).  Per-pixel workspace planes are packed
+// image after image: image i's pixels start at pixel poff[i] of a plane, so a buffer of k
+// planes per pixel holds image i from k * poff[i] on; its MIM rows start at row mrow[i]
+// of the MIM buffer.  The extraction pads each image's pixel count to a multiple of 64,
+// so every plane of every image starts 256-byte aligned.
+struct Group {
+  int n;
+  int H[MAXB], W[MAXB];
+  int mrow[MAXB];
+  long long poff[MAXB];
+  __host__ __device__ long long P(int i) const { return (long long)H[i] * W[i]; }
+};
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

@@ -5,15 +5,53 @@
 //     v_r = in[j + r n/R] * W_{ns R}^{k r},   v = DFT_R(v),
 //     out[(j / ns) ns R + k + r ns] = v_r,
 // and leaves the result in natural order after the last pass.  Twiddles come from one
-// table per length, tw[e] = exp(-2 pi i e / n), generated in double precision; the odd
-// radices' own roots are compile-time constants.
+// table per length, tw[e] = exp(-2 pi i e / n), generated in double precision, gathered
+// once per plan into a per-pass table (FftPasses::ptw); the odd radices' own roots are
+// compile-time constants.
 #pragma once
 
 #include "common.cuh"
 
 namespace rift2 {
 
-constexpr int FFT_MAX_STAGES = 16;
+constexpr int FFT_MAX_STAGES = 12;   // 13-smooth lengths below 8192 need at most 9 passes
+
+// Unsigned division by a run-time divisor d >= 1 for dividends below 2^31: the
+// multiply-shift method (Granlund and Montgomery), q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  unsigned m = 1, s = 0, d = 1;
+  FastDiv() = default;
+  __host__ __device__ explicit FastDiv(unsigned dv) : d(dv) {
+    s = 0;
+    while ((1u << s) < dv) ++s;
+    m = (unsigned)(((1ull << 32) * ((1ull << s) - dv)) / dv + 1);
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> s; }
+};
+
+// One Stockham pass of a length-L transform as the shared-memory kernels run it.
+struct FftPass {
+  int R;        // radix
+  int ns;       // product of the radices of the passes before this one
+  FastDiv q;    // L / R: butterflies per transform
+  FastDiv k;    // ns
+  int tw;       // offset of the pass's twiddles in FftPasses::ptw, laid out [ns][R - 1]
+};
+
+// The device copy of a plan the shared-memory kernels read (made once per length): the
+// passes at the transform length L (n, or the Bluestein convolution length) with their
+// divisors precomputed on the host, and every pass's twiddles W_(ns R)^(k r), k < ns,
+// 1 <= r < R, gathered from the FP64-generated length-L table.
+struct FftPasses {
+  int n, L, nst;
+  FftPass p[FFT_MAX_STAGES];
+  FastDiv dL, dn;
+  const float2* ptw;
+  const float2* chirp;      // Bluestein only: [n] c_j (NULL for a direct transform)
+  const float2* kern_fwd;   // Bluestein only: [L]
+  const float2* kern_inv;   // Bluestein only: [L]
+};
 
 // A transform of length n: directly (n 13-smooth: radices of n, twiddles of length n), or
 // by Bluestein's chirp-z identity when n has a larger prime factor.  With c_j =
@@ -32,6 +70,18 @@ struct FftPlan {
   const float2* chirp;      // Bluestein only: [n] c_j
   const float2* kern_fwd;   // Bluestein only: [m]
   const float2* kern_inv;   // Bluestein only: [m]
+  const FftPasses* dev;     // device: the shared-memory kernels' copy
+};
+
+// Per-image transform data of one shared-memory-path launch over a Group: the device plan
+// of the transformed side, the tile (rows or columns per CTA) with its divisor, and the
+// zero-window column table of the image's size ([NO][W]: 1 where orientation o's angular
+// window is zero on the whole column).
+struct FftGroup {
+  const FftPasses* pass[MAXB];
+  int tile[MAXB];
+  FastDiv dtile[MAXB];
+  const unsigned char* zc[MAXB];
 };
 
 template <bool INV>
@@ -149,19 +199,6 @@ __device__ __forceinline__ void dft_odd(float2* v) {
   v[0] = sum;
 }
 
-// Unsigned division by a run-time divisor d >= 1 for dividends below 2^31: the
-// multiply-shift method (Granlund and Montgomery), q = (umulhi(n, m) + n) >> s with
-// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1.
-struct FastDiv {
-  unsigned m, s, d;
-  __host__ __device__ explicit FastDiv(unsigned dv) : d(dv) {
-    s = 0;
-    while ((1u << s) < dv) ++s;
-    m = (unsigned)(((1ull << 32) * ((1ull << s) - dv)) / dv + 1);
-  }
-  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> s; }
-};
-
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2* v) {
   if constexpr (R == 2) dft2<INV>(v);
@@ -171,47 +208,30 @@ __device__ __forceinline__ void dft_r(float2* v) {
 }
 
 // One Stockham pass over nb transforms; element k of transform b at buf[b*bs + k*ks].
-// BFAST: consecutive threads take consecutive transforms (column tiles, ks > 1);
-// otherwise consecutive butterflies of one transform (rows, ks == 1).
+// BFAST: consecutive threads take consecutive transforms (column tiles, ks > 1; dnb is the
+// divisor nb); otherwise consecutive butterflies of one transform (rows, ks == 1).
 template <int R, bool INV, bool BFAST>
 __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* __restrict__ out,
-                                         int n, int ns, int nb, int bs, int ks,
-                                         const float2* __restrict__ tw, int tid, int nthr) {
-  const int m = n / R;
-  const int tstep = n / (ns * R);
+                                         const FftPass& ps, const float2* __restrict__ ptw,
+                                         const FastDiv& dnb, int nb, int bs, int ks, int tid,
+                                         int nthr) {
+  const int m = (int)ps.q.d;   // butterflies per transform
+  const int ns = ps.ns;
   const int total = nb * m;
-  const FastDiv dnb((unsigned)nb), dm((unsigned)m), dns((unsigned)ns);
+  const float2* __restrict__ pw = ptw + ps.tw;
   for (int idx = tid; idx < total; idx += nthr) {
     int b, j;
     if (BFAST) { j = (int)dnb.div((unsigned)idx); b = idx - j * nb; }
-    else       { b = (int)dm.div((unsigned)idx); j = idx - b * m; }
-    const int k = j - (int)dns.div((unsigned)j) * ns;
+    else       { b = (int)ps.q.div((unsigned)idx); j = idx - b * m; }
+    const int k = j - (int)ps.k.div((unsigned)j) * ns;
     const float2* src = in + b * bs;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * ks];
     if (ns > 1) {
-      if constexpr ((R & (R - 1)) == 0) {
-        // powers of two: the table gives W^(k 2^q tstep); other r are products of those
-        float2 wp[3];
+      const float2* w = pw + k * (R - 1);
 #pragma unroll
-        for (int q = 0; (1 << q) < R; ++q) wp[q] = twiddle<INV>(tw, k * (1 << q) * tstep);
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = make_float2(1.f, 0.f);
-          bool first = true;
-#pragma unroll
-          for (int q = 0; (1 << q) < R; ++q)
-            if (r & (1 << q)) {
-              w = first ? wp[q] : cmul(w, wp[q]);
-              first = false;
-            }
-          v[r] = cmul(v[r], w);
-        }
-      } else {
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(tw, k * r * tstep));
-      }
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(w, r - 1));
     }
     dft_r<R, INV>(v);
     float2* dst = out + b * bs;
@@ -221,46 +241,44 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* 
   }
 }
 
-// The Stockham passes of a length-len transform (radices and twiddles of `pl`); data
-// starts in `a`, `b` is scratch.  Returns the buffer holding the result.
+// The Stockham passes of the plan's length-L transform; data starts in `a`, `b` is
+// scratch.  Returns the buffer holding the result.
 template <bool INV, bool BFAST>
-__device__ float2* fft_passes(float2* a, float2* b, const FftPlan& pl, int len, int nb, int bs,
-                              int ks) {
+__device__ float2* fft_passes(float2* a, float2* b, const FftPasses& pl, const FastDiv& dnb,
+                              int nb, int bs, int ks) {
   const int tid = threadIdx.x, nthr = blockDim.x;
-  int ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
-    const int R = pl.radix[st];
-    switch (R) {
-      case 8: fft_pass<8, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 4: fft_pass<4, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 2: fft_pass<2, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 3: fft_pass<3, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 5: fft_pass<5, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 7: fft_pass<7, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 11: fft_pass<11, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
-      case 13: fft_pass<13, INV, BFAST>(a, b, len, ns, nb, bs, ks, pl.tw, tid, nthr); break;
+    const FftPass& ps = pl.p[st];
+    switch (ps.R) {
+      case 8: fft_pass<8, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 4: fft_pass<4, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 2: fft_pass<2, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 3: fft_pass<3, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 5: fft_pass<5, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 7: fft_pass<7, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 11: fft_pass<11, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 13: fft_pass<13, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
       default: break;
     }
     __syncthreads();
-    ns *= R;
     float2* t = a; a = b; b = t;
   }
   return a;
 }
 
 // Full transform of nb transforms of length pl.n; element k of transform t at
-// buf[t * bs + k * ks], where each transform owns pl.m slots (pl.m = pl.n for direct
+// buf[t * bs + k * ks], where each transform owns pl.L slots (pl.L = pl.n for direct
 // plans).  Data starts in `a`, `b` is scratch of the same size; returns the buffer holding
 // the result (the first pl.n elements of each slot).  Ends with a __syncthreads().
 template <bool INV, bool BFAST>
-__device__ float2* fft_smem(float2* a, float2* b, const FftPlan& pl, int nb, int bs, int ks) {
-  if (!pl.chirp) return fft_passes<INV, BFAST>(a, b, pl, pl.n, nb, bs, ks);
+__device__ float2* fft_smem(float2* a, float2* b, const FftPasses& pl, const FastDiv& dnb,
+                            int nb, int bs, int ks) {
+  if (!pl.chirp) return fft_passes<INV, BFAST>(a, b, pl, dnb, nb, bs, ks);
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int n = pl.n, m = pl.m;
-  const FastDiv dm((unsigned)m);
+  const int n = pl.n, m = pl.L;
   // u_j = x_j c_j (conj(c_j) for the inverse) for j < n, zero up to m
   for (int i = tid; i < nb * m; i += nthr) {
-    const int t = (int)dm.div((unsigned)i), j = i - t * m;
+    const int t = (int)pl.dL.div((unsigned)i), j = i - t * m;
     float2* p = a + t * bs + j * ks;
     if (j < n) {
       const float2 c = __ldg(pl.chirp + j);
@@ -270,19 +288,19 @@ __device__ float2* fft_smem(float2* a, float2* b, const FftPlan& pl, int nb, int
     }
   }
   __syncthreads();
-  float2* r = fft_passes<false, BFAST>(a, b, pl, m, nb, bs, ks);
+  float2* r = fft_passes<false, BFAST>(a, b, pl, dnb, nb, bs, ks);
   float2* o = (r == a) ? b : a;
   const float2* kern = INV ? pl.kern_inv : pl.kern_fwd;
   for (int i = tid; i < nb * m; i += nthr) {
-    const int t = (int)dm.div((unsigned)i), j = i - t * m;
+    const int t = (int)pl.dL.div((unsigned)i), j = i - t * m;
     float2* p = r + t * bs + j * ks;
     *p = cmul(*p, __ldg(kern + j));
   }
   __syncthreads();
-  r = fft_passes<true, BFAST>(r, o, pl, m, nb, bs, ks);
+  r = fft_passes<true, BFAST>(r, o, pl, dnb, nb, bs, ks);
   // X_k = c_k y_k (conj(c_k) for the inverse), k < n
   for (int i = tid; i < nb * n; i += nthr) {
-    const int t = i / n, k = i - t * n;
+    const int t = (int)pl.dn.div((unsigned)i), k = i - t * n;
     float2* p = r + t * bs + k * ks;
     const float2 c = __ldg(pl.chirp + k);
     *p = INV ? cmulc(*p, c) : cmul(*p, c);

@@ -53,13 +53,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long lon
 // index).  Every keypoint is two jobs, the upper and lower half of its patch; a job's
 // 112 x 48 box is staged while the previous job is counted (two buffers per warp).
 __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant__ CUtensorMap tmap,
-                                                           int H, int W, KParams kp,
-                                                           DescribeWs ws, FeatPtrs fp) {
+                                                           const __grid_constant__ Group gr,
+                                                           KParams kp, DescribeWs ws,
+                                                           FeatPtrs fp) {
   // [DH_WARPS][2 half-patch buffers][DH_WARPS][2 mbarriers]; no static shared memory, so
   // the dynamic block starts at the (16-byte aligned) base the TMA destination needs.
   extern __shared__ __align__(128) unsigned char dsm[];
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(dsm + DH_WARPS * 2 * HBUF);
   const int img = blockIdx.y;
+  const int row0 = gr.mrow[img];   // the image's first row in the stacked MIM
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkp = fp.counts[img][0];
   const int gw = blockIdx.x * DH_WARPS + warp, gstride = gridDim.x * DH_WARPS;
@@ -85,10 +87,10 @@ __global__ void __launch_bounds__(DH_WARPS * 32) desc_hist(const __grid_constant
                  "r"(BOX_W * HALF_ROWS)
                  : "memory");
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(buf0 + (q & 1) * HBUF)),
-        "l"(&tmap), "r"((x - HALF_PATCH) & ~15), "r"(y - HALF_PATCH + (q & 1) * HALF_ROWS),
-        "r"(img), "r"(b)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(buf0 + (q & 1) * HBUF)),
+        "l"(&tmap), "r"((x - HALF_PATCH) & ~15),
+        "r"(row0 + y - HALF_PATCH + (q & 1) * HALF_ROWS), "r"(b)
         : "memory");
   };
   if (lane == 0) issue(0);
@@ -217,11 +219,14 @@ static_assert(SP_BOX_W >= 2 * SP_R + 1 + 15, "window holds the rounded-down x st
 __device__ __forceinline__ int rnd_q14(int v) { return (v + 8192 - (v < 0 ? 1 : 0)) >> 14; }
 
 __global__ void __launch_bounds__(SP_WARPS * 32) desc_spatial(const __grid_constant__ CUtensorMap tmap,
-                                                              int H, int W, KParams kp,
-                                                              DescribeWs ws, FeatPtrs fp) {
+                                                              const __grid_constant__ Group gr,
+                                                              KParams kp, DescribeWs ws,
+                                                              FeatPtrs fp) {
   extern __shared__ __align__(128) unsigned char dsm[];
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(dsm + SP_WARPS * SP_BUF);
   const int img = blockIdx.y;
+  const int H = gr.H[img], W = gr.W[img];
+  const int row0 = gr.mrow[img];   // the image's first row in the stacked MIM
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkp = fp.counts[img][0];
   const int gw = blockIdx.x * SP_WARPS + warp, gstride = gridDim.x * SP_WARPS;
@@ -245,9 +250,9 @@ __global__ void __launch_bounds__(SP_WARPS * 32) desc_spatial(const __grid_const
                    "r"(SP_BOX_W * SP_BOX_H)
                    : "memory");
       asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-          " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(buf)),
-          "l"(&tmap), "r"(wx0), "r"(wy0), "r"(img), "r"(bar)
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(buf)),
+          "l"(&tmap), "r"(wx0), "r"(row0 + wy0), "r"(bar)
           : "memory");
     }
     if (!mbar_wait(bar, phase, ws.wait_iters)) {
@@ -475,19 +480,19 @@ void describe_box(int desc_mode, int* cols, int* rows) {
   }
 }
 
-cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
-                            const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
-                            cudaStream_t st) {
+cudaError_t launch_describe(const CUtensorMap* mim_map, const Group& gr, const KParams& kp,
+                            DescribeWs ws, const FeatPtrs& fp, cudaStream_t st) {
+  const int nimg = gr.n;
   if (kp.desc_mode == DESC_SPATIAL) {
     const size_t sm = (size_t)SP_WARPS * SP_BUF + SP_WARPS * sizeof(unsigned long long);
     cudaFuncSetAttribute(desc_spatial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int blocks = (kp.kp_cap + SP_WARPS * DH_KPW - 1) / (SP_WARPS * DH_KPW);
-    desc_spatial<<<dim3(blocks, nimg), SP_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
+    desc_spatial<<<dim3(blocks, nimg), SP_WARPS * 32, sm, st>>>(*mim_map, gr, kp, ws, fp);
   } else {
     const size_t sm = (size_t)DH_WARPS * 2 * HBUF + DH_WARPS * 2 * sizeof(unsigned long long);
     cudaFuncSetAttribute(desc_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int blocks = (kp.kp_cap + DH_WARPS * DH_KPW - 1) / (DH_WARPS * DH_KPW);
-    desc_hist<<<dim3(blocks, nimg), DH_WARPS * 32, sm, st>>>(*mim_map, H, W, kp, ws, fp);
+    desc_hist<<<dim3(blocks, nimg), DH_WARPS * 32, sm, st>>>(*mim_map, gr, kp, ws, fp);
   }
   desc_scan<<<nimg, 1024, 0, st>>>(kp, ws, fp);
   desc_write<<<dim3((kp.kp_cap + 7) / 8, nimg), 256, 0, st>>>(kp, ws, fp);

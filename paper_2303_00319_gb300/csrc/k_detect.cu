@@ -53,11 +53,13 @@ __device__ __forceinline__ bool has_arc(unsigned m16, int arc) {
 }
 
 template <int ARC>
-__global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment, int H, int W,
-                                                KParams kp, DetectWs ws) {
+__global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment,
+                                                const __grid_constant__ Group gr, KParams kp,
+                                                DetectWs ws) {
   __shared__ float mn[FSY][FSX];
   __shared__ float vs[VSY][VSX];
   const int img = blockIdx.z;
+  const int H = gr.H[img], W = gr.W[img];
   const int tx0 = blockIdx.x * FTX, ty0 = blockIdx.y * FTY;
   const int ylo = HALF_PATCH, yhi = H - HALF_PATCH, xlo = HALF_PATCH, xhi = W - HALF_PATCH;
   // tiles with no candidate pixel in or next to them do nothing
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(256) fast_nms(const float* __restrict__ moment
   const float hi = __uint_as_float(ws.minmax[2 * img + 1]);
   if (!(hi > lo)) return;   // constant map: no keypoints
   const float rinv = 1.f / (hi - lo);
-  const float* M = moment + (size_t)img * H * W;
+  const float* M = moment + gr.poff[img];
   for (int i = threadIdx.x; i < FSX * FSY; i += blockDim.x) {
     int y = ty0 - FH + i / FSX, x = tx0 - FH + i % FSX;
     float v = 0.f;
@@ -344,11 +346,13 @@ __global__ void __launch_bounds__(256) topk_gather(KParams kp, DetectWs ws) {
   }
 }
 
-__global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws, FeatPtrs fp) {
+__global__ void __launch_bounds__(1024) topk_sort(const __grid_constant__ Group gr, KParams kp,
+                                                  DetectWs ws, FeatPtrs fp) {
   extern __shared__ unsigned long long skeys[];
   __shared__ unsigned hist[256];
   __shared__ unsigned s_sel[4];
   const int img = blockIdx.x;
+  const unsigned W = (unsigned)gr.W[img];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned long long* cand = ws.cand + (size_t)img * ws.cap_cand;
   unsigned n = ws.cand_count[img];
@@ -450,8 +454,8 @@ __global__ void __launch_bounds__(1024) topk_sort(int W, KParams kp, DetectWs ws
   for (unsigned r = threadIdx.x; r < nout; r += blockDim.x) {
     unsigned long long k = keys[r];
     unsigned idx = (unsigned)k;
-    xy[2 * r] = (int)(idx % (unsigned)W);
-    xy[2 * r + 1] = (int)(idx / (unsigned)W);
+    xy[2 * r] = (int)(idx % W);
+    xy[2 * r + 1] = (int)(idx / W);
     sc[r] = __uint_as_float(~(unsigned)(k >> 32));
   }
   if (threadIdx.x == 0) {
@@ -493,17 +497,20 @@ __global__ void minmax_kernel(const float* __restrict__ m, long long P, unsigned
 // CTA per image marks the edge keypoints' pixels in a bitmap, then compacts the corner
 // list (already in (score desc, index asc) order) without the marked pixels, block-wide
 // scans keeping the order.
-__global__ void __launch_bounds__(1024) merge_corners(int H, int W, KParams kp, FeatPtrs fp,
+__global__ void __launch_bounds__(1024) merge_corners(const __grid_constant__ Group gr, KParams kp,
+                                                      FeatPtrs fp,
                                                       const int* __restrict__ cxy,
                                                       const float* __restrict__ csc,
                                                       const int* __restrict__ ccnt,
-                                                      unsigned* __restrict__ bits) {
+                                                      unsigned* __restrict__ bits,
+                                                      long long bits_stride) {
   __shared__ unsigned wsum[32];
   __shared__ int s_base;
   const int img = blockIdx.x;
+  const int H = gr.H[img], W = gr.W[img];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const size_t nw = ((size_t)H * W + 31) / 32;
-  unsigned* bm = bits + (size_t)img * nw;
+  unsigned* bm = bits + (size_t)img * bits_stride;
   for (size_t i = threadIdx.x; i < nw; i += blockDim.x) bm[i] = 0u;
   __syncthreads();
   int* xy = fp.kp_xy[img];
@@ -557,10 +564,10 @@ __global__ void __launch_bounds__(1024) merge_corners(int H, int W, KParams kp, 
   if (threadIdx.x == 0) fp.counts[img][0] = s_base;
 }
 
-cudaError_t launch_merge_corners(int nimg, int H, int W, const KParams& kp, const FeatPtrs& fp,
+cudaError_t launch_merge_corners(const Group& gr, const KParams& kp, const FeatPtrs& fp,
                                  const int* cxy, const float* csc, const int* ccnt,
-                                 unsigned* bits, cudaStream_t st) {
-  merge_corners<<<nimg, 1024, 0, st>>>(H, W, kp, fp, cxy, csc, ccnt, bits);
+                                 unsigned* bits, long long bits_stride, cudaStream_t st) {
+  merge_corners<<<gr.n, 1024, 0, st>>>(gr, kp, fp, cxy, csc, ccnt, bits, bits_stride);
   return cudaGetLastError();
 }
 
@@ -572,28 +579,33 @@ void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStr
   minmax_kernel<<<dim3(256, g), 256, 0, st>>>(m, P, minmax);
 }
 
-cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
-                          DetectWs ws, const FeatPtrs& fp, cudaStream_t st) {
-  dim3 grid((W + FTX - 1) / FTX, (H + FTY - 1) / FTY, nimg);
-  if (!ws.cand_hist || !ws.sel || !ws.comp || !topk_multi(kp.max_kp, H, W)) {
+cudaError_t launch_detect(const float* moment, const Group& gr, const KParams& kp, DetectWs ws,
+                          const FeatPtrs& fp, cudaStream_t st) {
+  int hmax = 1, wmax = 1;
+  for (int i = 0; i < gr.n; ++i) {
+    hmax = gr.H[i] > hmax ? gr.H[i] : hmax;
+    wmax = gr.W[i] > wmax ? gr.W[i] : wmax;
+  }
+  dim3 grid((wmax + FTX - 1) / FTX, (hmax + FTY - 1) / FTY, gr.n);
+  if (!ws.cand_hist || !ws.sel || !ws.comp || !topk_multi_group(kp.max_kp, gr)) {
     ws.cand_hist = nullptr;   // single-CTA refinement only
     ws.sel = nullptr;
     ws.comp = nullptr;
   } else {
-    cudaError_t e = cudaMemsetAsync(ws.cand_hist, 0, ((size_t)nimg << TOPK_DIGIT_BITS) * sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(ws.cand_hist, 0, ((size_t)gr.n << TOPK_DIGIT_BITS) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
   }
-  if (kp.fast_arc == 9) fast_nms<9><<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
-  else fast_nms<0><<<grid, 256, 0, st>>>(moment, H, W, kp, ws);
+  if (kp.fast_arc == 9) fast_nms<9><<<grid, 256, 0, st>>>(moment, gr, kp, ws);
+  else fast_nms<0><<<grid, 256, 0, st>>>(moment, gr, kp, ws);
   if (ws.cand_hist) {
-    topk_select<<<nimg, 1024, 0, st>>>(kp, ws);
-    topk_gather<<<dim3(16, nimg), 256, 0, st>>>(kp, ws);
+    topk_select<<<gr.n, 1024, 0, st>>>(kp, ws);
+    topk_gather<<<dim3(16, gr.n), 256, 0, st>>>(kp, ws);
   }
   const int kc = topk_sort_cap(kp.max_kp);
   const int skeys = kc <= SORT_CAP ? kc : (kp.max_kp <= TOPK_SMEM_ANY_CAP ? TOPK_SMEM_ANY_CAP : 0);
   size_t sm = (size_t)skeys * sizeof(unsigned long long);
   cudaFuncSetAttribute(topk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  topk_sort<<<nimg, 1024, sm, st>>>(W, kp, ws, fp);
+  topk_sort<<<gr.n, 1024, sm, st>>>(gr, kp, ws, fp);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,20 @@ __global__ void twiddle_gen(float2* tw, int n) {
   tw[e] = make_float2((float)c, (float)s);
 }
 
+// Per-pass twiddles of a Stockham plan: pass st (radix R, ns) holds W_(ns R)^(k r) =
+// tw[k r L / (ns R)] for k < ns, 1 <= r < R at ptw[off_st + k (R - 1) + r - 1] (a gather
+// from the FP64-generated length-L table, so the values are the table's own).
+__global__ void pass_twiddle_gather(float2* __restrict__ ptw, const float2* __restrict__ tw,
+                                    int L, PassDims pd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pd.total) return;
+  int st = 0;
+  while (st + 1 < pd.nst && i >= pd.off[st + 1]) ++st;
+  const int e = i - pd.off[st], R = pd.R[st], ns = pd.ns[st];
+  const int k = e / (R - 1), r = e - k * (R - 1) + 1;
+  ptw[i] = tw[(long long)k * r * (L / (ns * R))];
+}
+
 // Bluestein tables (FP64 arithmetic, rounded once to FP32).  c_j = exp(-i pi j^2 / n) with
 // j^2 reduced modulo 2n first (exact in 64-bit integers), so the argument stays small.
 __global__ void chirp_gen(float2* c32, double2* c64, int n) {
@@ -96,19 +110,25 @@ __device__ __forceinline__ void seg_means(const float2* a, int nseg, int len, in
   }
 }
 
-// Rows of real images: tile of `tr` rows, complex FFT with zero imaginary part.
-__global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restrict__ dense,
-                                                float2* __restrict__ spec, int H, int W, int tr,
-                                                FftPlan pw) {
+// Rows of real images: tile of `tr` rows (fg.tile of the image), complex FFT with zero
+// imaginary part.  Image blockIdx.y of the group; dense (if not NULL) holds the images
+// packed like the spectrum.
+__global__ void __launch_bounds__(512, 1) fwd_rows(ImgPtrs ip, const float* __restrict__ dense,
+                                                float2* __restrict__ spec,
+                                                const __grid_constant__ Group gr,
+                                                const __grid_constant__ FftGroup fg) {
   extern __shared__ float2 sm[];
   __shared__ float2 mean[256];
   const int img = blockIdx.y;
+  const int H = gr.H[img], W = gr.W[img], tr = fg.tile[img];
+  const FftPasses& pw = *fg.pass[img];
   const int r0 = blockIdx.x * tr;
+  if (r0 >= H) return;
   const int nel = tr * W;
-  const int L = pw.m;   // shared-memory slot of one row transform (> W for Bluestein plans)
+  const int L = pw.L;   // shared-memory slot of one row transform (> W for Bluestein plans)
   float2* a = sm;
   float2* b = sm + tr * L;
-  const float* src = dense ? dense + (size_t)img * H * W : ip.img[img];
+  const float* src = dense ? dense + gr.poff[img] : ip.img[img];
   const long long pitch = dense ? W : ip.pitch[img];
   const FastDiv dW((unsigned)W);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
@@ -124,8 +144,8 @@ __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restr
     a[rr * L + x].x -= mean[rr].x;
   }
   __syncthreads();
-  float2* res = fft_smem<false, false>(a, b, pw, tr, L, 1);
-  float2* dst = spec + (size_t)img * H * W;
+  float2* res = fft_smem<false, false>(a, b, pw, fg.dtile[img], tr, L, 1);
+  float2* dst = spec + gr.poff[img];
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     const int rr = (int)dW.div((unsigned)i), x = i - rr * W, r = r0 + rr;
     float2 v = res[rr * L + x];
@@ -134,18 +154,22 @@ __global__ void __launch_bounds__(512) fwd_rows(ImgPtrs ip, const float* __restr
   }
 }
 
-// Columns, in place on spec [H][W]: tile of `tc` columns.
-__global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H, int W, int tc,
-                                                FftPlan ph) {
+// Columns, in place on spec [H][W]: tile of `tc` columns (fg.tile of the image).
+__global__ void __launch_bounds__(512, 1) fwd_cols(float2* __restrict__ spec,
+                                                const __grid_constant__ Group gr,
+                                                const __grid_constant__ FftGroup fg) {
   extern __shared__ float2 sm[];
   __shared__ float2 mean[64];
   const int img = blockIdx.y;
+  const int H = gr.H[img], W = gr.W[img], tc = fg.tile[img];
+  const FftPasses& ph = *fg.pass[img];
   const int c0 = blockIdx.x * tc;
+  if (c0 >= W) return;
   const int nel = H * tc;
   float2* a = sm;
-  float2* b = sm + ph.m * tc;   // [ph.m][tc] each: a column transform's slot is ph.m long
-  float2* base = spec + (size_t)img * H * W;
-  const FastDiv dtc((unsigned)tc);
+  float2* b = sm + ph.L * tc;   // [ph.L][tc] each: a column transform's slot is ph.L long
+  float2* base = spec + gr.poff[img];
+  const FastDiv& dtc = fg.dtile[img];
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
     a[i] = (c0 + c < W) ? base[(size_t)v * W + c0 + c] : make_float2(0.f, 0.f);
@@ -159,7 +183,7 @@ __global__ void __launch_bounds__(512) fwd_cols(float2* __restrict__ spec, int H
     a[i].y -= m.y;
   }
   __syncthreads();
-  float2* res = fft_smem<false, true>(a, b, ph, tc, 1, tc);
+  float2* res = fft_smem<false, true>(a, b, ph, dtc, tc, 1, tc);
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
     float2 r = res[i];
@@ -382,24 +406,30 @@ void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaSt
 
 // Column pass of the inverse for the six orientations of scale blockIdx.y.
 // smem: base (F * R_s), a, b each [H][tc].
-__global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict__ spec,
-                                                       float2* __restrict__ scratch, int H, int W,
-                                                       int tc, FftPlan ph, KParams kp) {
+__global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restrict__ spec,
+                                                       float2* __restrict__ scratch,
+                                                       const __grid_constant__ Group gr,
+                                                       const __grid_constant__ FftGroup fg,
+                                                       KParams kp) {
   extern __shared__ float2 sm[];
   const int s = blockIdx.y;
   const int img = blockIdx.z;
+  const int H = gr.H[img], W = gr.W[img], tc = fg.tile[img];
+  const FftPasses& ph = *fg.pass[img];
   const int c0 = blockIdx.x * tc;
+  if (c0 >= W) return;
+  const size_t P = (size_t)H * W;
   const int nel = H * tc;
-  const int nl = ph.m * tc;   // a transform slot is ph.m long (> H for Bluestein plans)
+  const int nl = ph.L * tc;   // a transform slot is ph.L long (> H for Bluestein plans)
   float2* base = sm;
   float2* a = sm + nel;
   float2* b = sm + nel + nl;
   float* fvt = reinterpret_cast<float*>(sm + nel + 2 * nl);   // fftfreq(v, H) per row
   __shared__ float fut[16];                               // fftfreq(u, W) per column
-  const float2* F = spec + (size_t)img * H * W;
+  const float2* F = spec + gr.poff[img];
   const float log_fs = kp.log_fs[s];
   const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
-  const FastDiv dtc((unsigned)tc);
+  const FastDiv& dtc = fg.dtile[img];
   for (int v = threadIdx.x; v < H; v += blockDim.x) fvt[v] = fftfreq(v, H);
   if (threadIdx.x < tc) fut[threadIdx.x] = fftfreq(c0 + threadIdx.x, W);
   __syncthreads();
@@ -428,8 +458,8 @@ __global__ void __launch_bounds__(512) lg_cols_inverse(const float2* __restrict_
       a[i] = make_float2(x.x * g, x.y * g);
     }
     __syncthreads();
-    float2* res = fft_smem<true, true>(a, b, ph, tc, 1, tc);
-    float2* dst = scratch + (((size_t)img * NS + s) * NO + o) * H * W;
+    float2* res = fft_smem<true, true>(a, b, ph, dtc, tc, 1, tc);
+    float2* dst = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P;
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
       const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
       if (c0 + c < W) dst[(size_t)v * W + c0 + c] = res[i];
@@ -480,22 +510,28 @@ __device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParam
 // for each orientation the four scales are transformed together.
 constexpr int RR_MAXPIX = 8;   // pixels per thread: W <= 8 * blockDim.x
 
-__global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restrict__ scratch, int H,
-                                                      int W, FftPlan pw, KParams kp,
+__global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restrict__ scratch,
+                                                      const __grid_constant__ Group gr,
+                                                      const __grid_constant__ FftGroup fg,
+                                                      KParams kp,
                                                       float* __restrict__ er_out,
                                                       float* __restrict__ q_out,
                                                       float* __restrict__ an0_out,
                                                       float* __restrict__ amp_out,
                                                       unsigned char* __restrict__ mim_out,
-                                                      int mim_pitch,
-                                                      const unsigned char* __restrict__ zc) {
+                                                      int mim_pitch) {
   extern __shared__ float2 sm[];
   const int row = blockIdx.x;
   const int img = blockIdx.y;
-  const int L = pw.m;   // a row transform's slot (> W for Bluestein plans)
+  const int H = gr.H[img], W = gr.W[img];
+  if (row >= H) return;
+  const FftPasses& pw = *fg.pass[img];
+  const unsigned char* __restrict__ zc = fg.zc[img];
+  const int L = pw.L;   // a row transform's slot (> W for Bluestein plans)
   float2* a = sm;
   float2* b = sm + NS * L;
   const size_t P = (size_t)H * W;
+  const size_t pb = (size_t)gr.poff[img];
   float best[RR_MAXPIX];
   int besto[RR_MAXPIX];
 #pragma unroll
@@ -503,7 +539,7 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
 
   for (int o = 0; o < NO; ++o) {
     for (int s = 0; s < NS; ++s) {
-      const float2* src = scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W;
+      const float2* src = scratch + NS * NO * pb + ((size_t)s * NO + o) * P + (size_t)row * W;
       // unconditional loads (a zero-window column's data is not used), several in flight
 #pragma unroll 4
       for (int x = threadIdx.x; x < W; x += blockDim.x) {
@@ -512,7 +548,7 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
       }
     }
     __syncthreads();
-    float2* res = fft_smem<true, false>(a, b, pw, NS, L, 1);
+    float2* res = fft_smem<true, false>(a, b, pw, fg.dtile[img], NS, L, 1);
 #pragma unroll
     for (int k = 0; k < RR_MAXPIX; ++k) {
       int x = threadIdx.x + k * blockDim.x;
@@ -522,7 +558,7 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
       for (int s = 0; s < NS; ++s) z[s] = res[s * L + x];
       float energy, q, an0, sum_an;
       reduce_pixel(z, kp, energy, q, an0, sum_an);
-      size_t off = ((size_t)img * NO + o) * P + (size_t)row * W + x;
+      size_t off = NO * pb + o * P + (size_t)row * W + x;
       er_out[off] = energy;
       q_out[off] = q;
       an0_out[off] = an0;
@@ -535,7 +571,7 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
   for (int k = 0; k < RR_MAXPIX; ++k) {
     int x = threadIdx.x + k * blockDim.x;
     if (x >= W) break;
-    mim_out[(size_t)img * H * mim_pitch + (size_t)row * mim_pitch + x] = (unsigned char)besto[k];
+    mim_out[((size_t)gr.mrow[img] + row) * mim_pitch + x] = (unsigned char)besto[k];
   }
 }
 
@@ -543,26 +579,33 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
 // the six orientations and writes the responses back in place (zero-window columns are
 // read as zeros and every column is written), then lg_rows_pixels reduces each pixel from
 // its 24 responses exactly as lg_rows_reduce does.
-__global__ void __launch_bounds__(512) lg_rows_split(float2* __restrict__ scratch, int H, int W,
-                                                     FftPlan pw, const unsigned char* __restrict__ zc) {
+__global__ void __launch_bounds__(512) lg_rows_split(float2* __restrict__ scratch,
+                                                     const __grid_constant__ Group gr,
+                                                     const __grid_constant__ FftGroup fg) {
   extern __shared__ float2 sm[];
   const int row = blockIdx.x, s = blockIdx.y, img = blockIdx.z;
+  const int H = gr.H[img], W = gr.W[img];
+  if (row >= H) return;
+  const FftPasses& pw = *fg.pass[img];
+  const unsigned char* __restrict__ zc = fg.zc[img];
   float2* a = sm;
-  float2* b = sm + pw.m;
+  float2* b = sm + pw.L;
   const size_t P = (size_t)H * W;
   for (int o = 0; o < NO; ++o) {
-    float2* rowp = scratch + (((size_t)img * NS + s) * NO + o) * P + (size_t)row * W;
+    float2* rowp = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P +
+                   (size_t)row * W;
     for (int x = threadIdx.x; x < W; x += blockDim.x)
       a[x] = zc[o * W + x] ? make_float2(0.f, 0.f) : rowp[x];
     __syncthreads();
-    float2* res = fft_smem<true, false>(a, b, pw, 1, pw.m, 1);
+    float2* res = fft_smem<true, false>(a, b, pw, fg.dtile[img], 1, pw.L, 1);
     for (int x = threadIdx.x; x < W; x += blockDim.x) rowp[x] = res[x];
     __syncthreads();   // the stores have read res before the next orientation's loads
   }
 }
 
-__global__ void __launch_bounds__(256) lg_rows_pixels(const float2* __restrict__ scratch, int H,
-                                                      int W, KParams kp,
+__global__ void __launch_bounds__(256) lg_rows_pixels(const float2* __restrict__ scratch,
+                                                      const __grid_constant__ Group gr,
+                                                      KParams kp,
                                                       float* __restrict__ er_out,
                                                       float* __restrict__ q_out,
                                                       float* __restrict__ an0_out,
@@ -570,18 +613,20 @@ __global__ void __launch_bounds__(256) lg_rows_pixels(const float2* __restrict__
                                                       unsigned char* __restrict__ mim_out,
                                                       int mim_pitch) {
   const int img = blockIdx.y;
-  const long long P = (long long)H * W;
+  const int W = gr.W[img];
+  const long long P = gr.P(img);
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
+  const size_t pb = (size_t)gr.poff[img];
   float best = -1.f;
   int besto = 0;
   for (int o = 0; o < NO; ++o) {
     float2 z[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) z[s] = __ldg(scratch + (((size_t)img * NS + s) * NO + o) * P + i);
+    for (int s = 0; s < NS; ++s) z[s] = __ldg(scratch + NS * NO * pb + ((size_t)s * NO + o) * P + i);
     float energy, q, an0, sum_an;
     reduce_pixel(z, kp, energy, q, an0, sum_an);
-    const size_t off = ((size_t)img * NO + o) * P + i;
+    const size_t off = NO * pb + o * P + i;
     er_out[off] = energy;
     q_out[off] = q;
     an0_out[off] = an0;
@@ -589,7 +634,7 @@ __global__ void __launch_bounds__(256) lg_rows_pixels(const float2* __restrict__
     if (sum_an > best) { best = sum_an; besto = o; }   // lowest o on ties
   }
   const long long y = i / W, x = i - y * W;
-  mim_out[(size_t)img * H * mim_pitch + (size_t)y * mim_pitch + x] = (unsigned char)besto;
+  mim_out[((size_t)gr.mrow[img] + y) * mim_pitch + x] = (unsigned char)besto;
 }
 
 // ------------------------------------------------------- register-tiled fast path
@@ -1057,6 +1102,12 @@ void launch_twiddles(float2* tw, int n, cudaStream_t st) {
   twiddle_gen<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
 }
 
+void launch_pass_twiddles(float2* ptw, const float2* tw, int L, const PassDims& pd,
+                          cudaStream_t st) {
+  if (pd.total > 0)
+    pass_twiddle_gather<<<(pd.total + 255) / 256, 256, 0, st>>>(ptw, tw, L, pd);
+}
+
 static int rows_tile(int W) { return W >= 4096 ? 1 : (4096 / W > 256 ? 256 : 4096 / W); }
 static int cols_tile(int H) {
   int tc = 8192 / H;
@@ -1082,37 +1133,135 @@ static void cols_fwd_reg(float2* spec, int nimg, int W, const FftPlan& ph, cudaS
   fwd_cols_reg<HN><<<dim3((W + COLS - 1) / COLS, nimg), NT, sm, st>>>(spec, W, ph.tw);
 }
 
-cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
-                                int H, int W, const FftPlan& ph, const FftPlan& pw,
-                                cudaStream_t st) {
+// ------------------------------------------------------------------ group launchers
+// A launch group is walked in runs of consecutive images of one size.  A run whose
+// transformed side has a register-tiled kernel (a power-of-two side, direct transform)
+// gets that kernel on the run's slice of the packed buffers (the run's images lie H W
+// pixels apart there, as those kernels expect); every other image joins one shared-memory
+// launch over the images of all sizes, in which each CTA reads its image's size, plan and
+// tile from the group tables.
+namespace {
+
+bool reg_side(int n, const FftPlan& p) {
+  if (p.m != n) return false;
+  switch (n) {
+    case 256: case 512: case 1024: case 2048: case 4096: return true;
+    default: return false;
+  }
+}
+
+template <class F>
+void for_runs(const Group& gr, F&& f) {
+  int i = 0;
+  while (i < gr.n) {
+    int j = i + 1;
+    while (j < gr.n && gr.H[j] == gr.H[i] && gr.W[j] == gr.W[i]) ++j;
+    f(i, j - i);
+    i = j;
+  }
+}
+
+// Appends image i of gr to the shared-memory launch's tables.
+void sub_add(Group& sub, FftGroup& sf, const Group& gr, int i, const FftPlan& pl, int tile,
+             const unsigned char* zc) {
+  const int k = sub.n++;
+  sub.H[k] = gr.H[i];
+  sub.W[k] = gr.W[i];
+  sub.poff[k] = gr.poff[i];
+  sub.mrow[k] = gr.mrow[i];
+  sf.pass[k] = pl.dev;
+  sf.tile[k] = tile;
+  sf.dtile[k] = FastDiv((unsigned)(tile > 0 ? tile : 1));
+  sf.zc[k] = zc;
+}
+
+template <class T>
+inline T max_of(T a, T b) { return a > b ? a : b; }
+
+}  // namespace
+
+cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec,
+                                const Group& gr, const FbImage* fi, cudaStream_t st,
+                                int* launches) {
   ImgPtrs none{};
   const ImgPtrs& ipr = ip ? *ip : none;
-  switch (W) {
-    case 256: rows_fwd_reg<256>(ipr, dense, spec, nimg, H, pw, st); break;
-    case 512: rows_fwd_reg<512>(ipr, dense, spec, nimg, H, pw, st); break;
-    case 1024: rows_fwd_reg<1024>(ipr, dense, spec, nimg, H, pw, st); break;
-    case 2048: rows_fwd_reg<2048>(ipr, dense, spec, nimg, H, pw, st); break;
-    case 4096: rows_fwd_reg<4096>(ipr, dense, spec, nimg, H, pw, st); break;
-    default: {
-      int tr = rows_tile(pw.m);
-      size_t smr = 2 * (size_t)tr * pw.m * sizeof(float2);
+  int nl = 0;
+  // rows of the real images
+  {
+    Group sub{};
+    FftGroup sf{};
+    ImgPtrs sip{};
+    int grid_x = 0;
+    size_t smr = 0;
+    for_runs(gr, [&](int i0, int cnt) {
+      const int H = gr.H[i0], W = gr.W[i0];
+      const FftPlan& pw = fi[i0].pw;
+      if (reg_side(W, pw)) {
+        ImgPtrs rp{};
+        for (int k = 0; k < cnt; ++k) {
+          rp.img[k] = ipr.img[i0 + k];
+          rp.pitch[k] = ipr.pitch[i0 + k];
+        }
+        const float* d = dense ? dense + gr.poff[i0] : nullptr;
+        float2* sp = spec + gr.poff[i0];
+        switch (W) {
+          case 256: rows_fwd_reg<256>(rp, d, sp, cnt, H, pw, st); break;
+          case 512: rows_fwd_reg<512>(rp, d, sp, cnt, H, pw, st); break;
+          case 1024: rows_fwd_reg<1024>(rp, d, sp, cnt, H, pw, st); break;
+          case 2048: rows_fwd_reg<2048>(rp, d, sp, cnt, H, pw, st); break;
+          default: rows_fwd_reg<4096>(rp, d, sp, cnt, H, pw, st); break;
+        }
+        ++nl;
+        return;
+      }
+      const int tr = rows_tile(pw.m);
+      for (int k = 0; k < cnt; ++k) {
+        sip.img[sub.n] = ipr.img[i0 + k];
+        sip.pitch[sub.n] = ipr.pitch[i0 + k];
+        sub_add(sub, sf, gr, i0 + k, pw, tr, nullptr);
+      }
+      grid_x = max_of(grid_x, (H + tr - 1) / tr);
+      smr = max_of(smr, 2 * (size_t)tr * pw.m * sizeof(float2));
+    });
+    if (sub.n) {
       cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-      fwd_rows<<<dim3((H + tr - 1) / tr, nimg), 512, smr, st>>>(ipr, dense, spec, H, W, tr, pw);
+      fwd_rows<<<dim3(grid_x, sub.n), 512, smr, st>>>(sip, dense, spec, sub, sf);
+      ++nl;
     }
   }
-  switch (H) {
-    case 256: cols_fwd_reg<256>(spec, nimg, W, ph, st); break;
-    case 512: cols_fwd_reg<512>(spec, nimg, W, ph, st); break;
-    case 1024: cols_fwd_reg<1024>(spec, nimg, W, ph, st); break;
-    case 2048: cols_fwd_reg<2048>(spec, nimg, W, ph, st); break;
-    case 4096: cols_fwd_reg<4096>(spec, nimg, W, ph, st); break;
-    default: {
-      int tc = cols_tile(ph.m);
-      size_t smc = 2 * (size_t)tc * ph.m * sizeof(float2);
+  // columns, in place
+  {
+    Group sub{};
+    FftGroup sf{};
+    int grid_x = 0;
+    size_t smc = 0;
+    for_runs(gr, [&](int i0, int cnt) {
+      const int H = gr.H[i0], W = gr.W[i0];
+      const FftPlan& ph = fi[i0].ph;
+      if (reg_side(H, ph)) {
+        float2* sp = spec + gr.poff[i0];
+        switch (H) {
+          case 256: cols_fwd_reg<256>(sp, cnt, W, ph, st); break;
+          case 512: cols_fwd_reg<512>(sp, cnt, W, ph, st); break;
+          case 1024: cols_fwd_reg<1024>(sp, cnt, W, ph, st); break;
+          case 2048: cols_fwd_reg<2048>(sp, cnt, W, ph, st); break;
+          default: cols_fwd_reg<4096>(sp, cnt, W, ph, st); break;
+        }
+        ++nl;
+        return;
+      }
+      const int tc = cols_tile(ph.m);
+      for (int k = 0; k < cnt; ++k) sub_add(sub, sf, gr, i0 + k, ph, tc, nullptr);
+      grid_x = max_of(grid_x, (W + tc - 1) / tc);
+      smc = max_of(smc, 2 * (size_t)tc * ph.m * sizeof(float2));
+    });
+    if (sub.n) {
       cudaFuncSetAttribute(fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-      fwd_cols<<<dim3((W + tc - 1) / tc, nimg), 512, smc, st>>>(spec, H, W, tc, ph);
+      fwd_cols<<<dim3(grid_x, sub.n), 512, smc, st>>>(spec, sub, sf);
+      ++nl;
     }
   }
+  if (launches) *launches = nl;
   return cudaGetLastError();
 }
 
@@ -1139,82 +1288,125 @@ int lg_cols_tile_candidates(int H, int L, int* out, int max_n) {
   return n;
 }
 
-cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
-                           const FftPlan& ph, const KParams& kp, const unsigned char* zc,
-                           cudaStream_t st, int tile) {
-  if (ph.m == H) {
-    switch (H) {
-      case 256: return cols_reg<256>(spec, scratch, nimg, W, ph, kp, zc, st);
-      case 512: return cols_reg<512>(spec, scratch, nimg, W, ph, kp, zc, st);
-      case 1024:
-        return kp.lp_order == 15 ? cols_tm1024<15>(spec, scratch, nimg, W, ph, kp, zc, st)
-                                 : cols_tm1024<0>(spec, scratch, nimg, W, ph, kp, zc, st);
-      case 2048: return cols_reg<2048>(spec, scratch, nimg, W, ph, kp, zc, st);
-      case 4096: return cols_reg<4096>(spec, scratch, nimg, W, ph, kp, zc, st);
-      default: break;
+cudaError_t launch_lg_cols(const float2* spec, float2* scratch, const Group& gr,
+                           const FbImage* fi, const KParams& kp, cudaStream_t st, int* launches) {
+  int nl = 0;
+  Group sub{};
+  FftGroup sf{};
+  int grid_x = 0;
+  size_t smx = 0;
+  cudaError_t err = cudaSuccess;
+  for_runs(gr, [&](int i0, int cnt) {
+    const int H = gr.H[i0], W = gr.W[i0];
+    const FftPlan& ph = fi[i0].ph;
+    if (reg_side(H, ph)) {
+      const float2* sp = spec + gr.poff[i0];
+      float2* sc = scratch + (size_t)NS * NO * gr.poff[i0];
+      const unsigned char* zc = fi[i0].zc;
+      cudaError_t e;
+      switch (H) {
+        case 256: e = cols_reg<256>(sp, sc, cnt, W, ph, kp, zc, st); break;
+        case 512: e = cols_reg<512>(sp, sc, cnt, W, ph, kp, zc, st); break;
+        case 1024:
+          e = kp.lp_order == 15 ? cols_tm1024<15>(sp, sc, cnt, W, ph, kp, zc, st)
+                                : cols_tm1024<0>(sp, sc, cnt, W, ph, kp, zc, st);
+          break;
+        case 2048: e = cols_reg<2048>(sp, sc, cnt, W, ph, kp, zc, st); break;
+        default: e = cols_reg<4096>(sp, sc, cnt, W, ph, kp, zc, st); break;
+      }
+      if (e != cudaSuccess) err = e;
+      ++nl;
+      return;
     }
+    int tc = cols_inverse_tile(H, ph.m);
+    const int tuned = fi[i0].col_tile;
+    if (tuned >= 1 && tuned <= tc) tc = tuned;   // a tuned (smaller) tile; same result
+    for (int k = 0; k < cnt; ++k) sub_add(sub, sf, gr, i0 + k, ph, tc, nullptr);
+    grid_x = max_of(grid_x, (W + tc - 1) / tc);
+    smx = max_of(smx, cols_inverse_smem(H, ph.m, tc));
+  });
+  if (err != cudaSuccess) return err;
+  if (sub.n) {
+    cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+    lg_cols_inverse<<<dim3(grid_x, NS, sub.n), 512, smx, st>>>(spec, scratch, sub, sf, kp);
+    ++nl;
   }
-  int tc = cols_inverse_tile(H, ph.m);
-  if (tile >= 1 && tile <= tc) tc = tile;   // a tuned (smaller) tile; any tile gives the same result
-  size_t sm2 = cols_inverse_smem(H, ph.m, tc);
-  cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-  lg_cols_inverse<<<dim3((W + tc - 1) / tc, NS, nimg), 512, sm2, st>>>(spec, scratch, H, W, tc,
-                                                                       ph, kp);
+  if (launches) *launches = nl;
   return cudaGetLastError();
 }
 
-cudaError_t launch_lg_rows(float2* scratch, int nimg, int H, int W, const FftPlan& pw,
+cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
-                           unsigned char* mim, int mim_pitch, const unsigned char* zc,
-                           cudaStream_t st) {
-  if (pw.m != W) goto generic;   // Bluestein widths take the shared-memory paths
-  switch (W) {
-    case 256: return rows_reg<256>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
-    case 512: return rows_reg<512>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
-    case 1024: {
-      const size_t sm = (size_t)NS * XBuf<1024>::SIZE * sizeof(float2);
-      cudaFuncSetAttribute(lg_rows_1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      lg_rows_1024<<<dim3(H, nimg), 128, sm, st>>>(scratch, H, pw.tw, kp, er, q, an0, amp, mim,
-                                                   mim_pitch, zc);
-      return cudaGetLastError();
+                           unsigned char* mim, int mim_pitch, cudaStream_t st, int* launches) {
+  int nl = 0;
+  Group red{}, spl{};
+  FftGroup rf{}, sf{};
+  int red_rows = 0, spl_rows = 0;
+  long long spl_px = 0;
+  size_t red_sm = 0, spl_sm = 0;
+  cudaError_t err = cudaSuccess;
+  for_runs(gr, [&](int i0, int cnt) {
+    const int H = gr.H[i0], W = gr.W[i0];
+    const FftPlan& pw = fi[i0].pw;
+    const unsigned char* zc = fi[i0].zc;
+    if (reg_side(W, pw)) {
+      const size_t pb = (size_t)gr.poff[i0];
+      const float2* sc = scratch + NS * NO * pb;
+      float* e_ = er + NO * pb;
+      float* q_ = q + NO * pb;
+      float* a0 = an0 + NO * pb;
+      float* am = amp ? amp + NO * pb : nullptr;
+      unsigned char* mm = mim + (size_t)gr.mrow[i0] * mim_pitch;
+      cudaError_t e;
+      switch (W) {
+        case 256: e = rows_reg<256>(sc, cnt, H, pw, kp, e_, q_, a0, am, mm, mim_pitch, zc, st); break;
+        case 512: e = rows_reg<512>(sc, cnt, H, pw, kp, e_, q_, a0, am, mm, mim_pitch, zc, st); break;
+        case 1024: {
+          const size_t sm = (size_t)NS * XBuf<1024>::SIZE * sizeof(float2);
+          cudaFuncSetAttribute(lg_rows_1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+          lg_rows_1024<<<dim3(H, cnt), 128, sm, st>>>(sc, H, pw.tw, kp, e_, q_, a0, am, mm,
+                                                      mim_pitch, zc);
+          e = cudaGetLastError();
+          break;
+        }
+        case 2048: e = rows_reg<2048>(sc, cnt, H, pw, kp, e_, q_, a0, am, mm, mim_pitch, zc, st); break;
+        default: e = rows_reg<4096>(sc, cnt, H, pw, kp, e_, q_, a0, am, mm, mim_pitch, zc, st); break;
+      }
+      if (e != cudaSuccess) err = e;
+      ++nl;
+      return;
     }
-    case 2048: return rows_reg<2048>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
-    case 4096: return rows_reg<4096>(scratch, nimg, H, pw, kp, er, q, an0, amp, mim, mim_pitch, zc, st);
-    default: break;
-  }
-generic:
-  {
     const size_t sm3 = 2 * (size_t)NS * pw.m * sizeof(float2);
     if (sm3 <= 227 * 1024 && W <= RR_MAXPIX * 512) {
-      cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
-      lg_rows_reduce<<<dim3(H, nimg), 512, sm3, st>>>(scratch, H, W, pw, kp, er, q, an0, amp, mim,
-                                                      mim_pitch, zc);
-      return cudaGetLastError();
+      for (int k = 0; k < cnt; ++k) sub_add(red, rf, gr, i0 + k, pw, 0, zc);
+      red_rows = max_of(red_rows, H);
+      red_sm = max_of(red_sm, sm3);
+    } else {
+      // rows too wide for four scales in shared memory: transform each (row, scale) in
+      // place, then reduce the pixels from the transformed responses
+      for (int k = 0; k < cnt; ++k) sub_add(spl, sf, gr, i0 + k, pw, 0, zc);
+      spl_rows = max_of(spl_rows, H);
+      spl_px = max_of(spl_px, (long long)H * W);
+      spl_sm = max_of(spl_sm, 2 * (size_t)pw.m * sizeof(float2));
     }
+  });
+  if (err != cudaSuccess) return err;
+  if (red.n) {
+    cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_sm);
+    lg_rows_reduce<<<dim3(red_rows, red.n), 512, red_sm, st>>>(scratch, red, rf, kp, er, q, an0,
+                                                               amp, mim, mim_pitch);
+    ++nl;
   }
-  // rows too wide for four scales in shared memory: transform each (row, scale) in place,
-  // then reduce the pixels from the transformed responses
-  {
-    const size_t sm4 = 2 * (size_t)pw.m * sizeof(float2);
-    cudaFuncSetAttribute(lg_rows_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
-    lg_rows_split<<<dim3(H, NS, nimg), 512, sm4, st>>>(scratch, H, W, pw, zc);
-    const long long P = (long long)H * W;
-    const int blocks = (int)((P + 255) / 256);
-    lg_rows_pixels<<<dim3(blocks, nimg), 256, 0, st>>>(scratch, H, W, kp, er, q, an0, amp, mim,
-                                                       mim_pitch);
-    return cudaGetLastError();
+  if (spl.n) {
+    cudaFuncSetAttribute(lg_rows_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spl_sm);
+    lg_rows_split<<<dim3(spl_rows, NS, spl.n), 512, spl_sm, st>>>(scratch, spl, sf);
+    const int blocks = (int)((spl_px + 255) / 256);
+    lg_rows_pixels<<<dim3(blocks, spl.n), 256, 0, st>>>(scratch, spl, kp, er, q, an0, amp, mim,
+                                                        mim_pitch);
+    nl += 2;
   }
-}
-
-int lg_rows_launches(int H, int W, const FftPlan& pw) {
-  if (pw.m == W) {
-    switch (W) {
-      case 256: case 512: case 1024: case 2048: case 4096: return 1;
-      default: break;
-    }
-  }
-  const size_t sm3 = 2 * (size_t)NS * pw.m * sizeof(float2);
-  return (sm3 <= 227 * 1024 && W <= RR_MAXPIX * 512) ? 1 : 2;
+  if (launches) *launches = nl;
+  return cudaGetLastError();
 }
 
 }  // namespace rift2

@@ -21,16 +21,18 @@ __device__ __forceinline__ void med_digit(unsigned bits, int round, unsigned& pr
   else { pre = bits >> 8; dig = bits & 0xFFu; }
 }
 
-__global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0, long long P,
-                                                   int round, MedianWs ws) {
+__global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0,
+                                                   const __grid_constant__ Group gr, int round,
+                                                   MedianWs ws) {
   __shared__ unsigned h[2][MED_BINS];
   const int nslot = (round == 0) ? 1 : 2;   // round 0: both ranks share one histogram
   const int o = blockIdx.y, img = blockIdx.z;
+  const long long P = gr.P(img);
   for (int i = threadIdx.x; i < nslot * MED_BINS; i += blockDim.x) (&h[0][0])[i] = 0;
   const unsigned* st = ws.state + ((size_t)img * NO + o) * 4;
   const unsigned pre0 = st[0], pre1 = st[2];
   __syncthreads();
-  const float* src = an0 + ((size_t)img * NO + o) * P;
+  const float* src = an0 + (size_t)NO * gr.poff[img] + (size_t)o * P;
   const long long chunk = ((P + gridDim.x - 1) / gridDim.x + 3) & ~3ll;
   const long long beg = blockIdx.x * chunk;
   const long long end = min(P, beg + chunk);
@@ -85,11 +87,12 @@ __global__ void __launch_bounds__(512) median_hist(const float* __restrict__ an0
 // a block-wide scan locates the bin holding each rank, and the state becomes (prefix with
 // that digit appended, rank within the bin).  The histograms are cleared for the next
 // round; after the last round T_o follows from the two middle values.
-__global__ void __launch_bounds__(256) median_select(long long P, int round, float noise_c,
-                                                     MedianWs ws) {
+__global__ void __launch_bounds__(256) median_select(const __grid_constant__ Group gr, int round,
+                                                     float noise_c, MedianWs ws) {
   __shared__ unsigned part[2][256];
   __shared__ unsigned s_dig[2], s_rank[2];
   const int o = blockIdx.x, img = blockIdx.y;
+  const long long P = gr.P(img);
   const int tid = threadIdx.x;
   unsigned* gh = ws.hist + ((size_t)img * NO + o) * 2 * MED_BINS;
   unsigned* st = ws.state + ((size_t)img * NO + o) * 4;
@@ -153,15 +156,18 @@ __global__ void __launch_bounds__(256) median_select(long long P, int round, flo
   }
 }
 
-cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, const KParams& kp,
+cudaError_t launch_noise_threshold(const float* an0, const Group& gr, const KParams& kp,
                                    MedianWs ws, cudaStream_t st) {
-  // ~64K values per CTA: the histogram set-up and flush stay small next to the scan
-  int chunks = (int)((P + 65535) / 65536);
+  // ~64K values per CTA of the largest image (a smaller image's CTAs take smaller
+  // slices): the histogram set-up and flush stay small next to the scan
+  long long pmax = 1;
+  for (int i = 0; i < gr.n; ++i) pmax = gr.P(i) > pmax ? gr.P(i) : pmax;
+  int chunks = (int)((pmax + 65535) / 65536);
   if (chunks > 64) chunks = 64;
   if (chunks < 1) chunks = 1;
   for (int r = 0; r < 3; ++r) {
-    median_hist<<<dim3(chunks, NO, nimg), 512, 0, st>>>(an0, P, r, ws);
-    median_select<<<dim3(NO, nimg), 256, 0, st>>>(P, r, kp.noise_c, ws);
+    median_hist<<<dim3(chunks, NO, gr.n), 512, 0, st>>>(an0, gr, r, ws);
+    median_select<<<dim3(NO, gr.n), 256, 0, st>>>(gr, r, kp.noise_c, ws);
   }
   return cudaGetLastError();
 }
@@ -193,18 +199,21 @@ __device__ __forceinline__ float moment_px(const float (&qv)[NO], const float (&
 
 __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
                                                  const float* __restrict__ q,
-                                                 const float* __restrict__ noise_t, long long P,
+                                                 const float* __restrict__ noise_t,
+                                                 const __grid_constant__ Group gr,
                                                  KParams kp, float* __restrict__ moment,
                                                  unsigned* __restrict__ minmax,
                                                  float* __restrict__ pc_out,
                                                  float* __restrict__ mcorner,
                                                  unsigned* __restrict__ minmax_c) {
   const int img = blockIdx.y;
+  const long long P = gr.P(img);
+  const size_t pb = (size_t)gr.poff[img];
   float tn[NO];
 #pragma unroll
   for (int o = 0; o < NO; ++o) tn[o] = __ldg(noise_t + img * NO + o);
   float lo = 3.0e38f, hi = 0.f, loc = 3.0e38f, hic = 0.f;
-  const size_t ib = (size_t)img * NO * P;
+  const size_t ib = NO * pb;
   if ((P & 3) == 0) {
     // four pixels per thread and step: twelve 16-byte loads in flight
     const long long P4 = P >> 2;
@@ -235,9 +244,9 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
         lo = fminf(lo, mv[c]);
         hi = fmaxf(hi, mv[c]);
       }
-      reinterpret_cast<float4*>(moment + (size_t)img * P)[i] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+      reinterpret_cast<float4*>(moment + pb)[i] = make_float4(mv[0], mv[1], mv[2], mv[3]);
       if (mcorner)
-        reinterpret_cast<float4*>(mcorner + (size_t)img * P)[i] = make_float4(mcv[0], mcv[1], mcv[2], mcv[3]);
+        reinterpret_cast<float4*>(mcorner + pb)[i] = make_float4(mcv[0], mcv[1], mcv[2], mcv[3]);
     }
   } else {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
@@ -250,14 +259,14 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
       }
       float mc;
       const float m = moment_px(qv, ev, tn, kp, pc, mc);
-      if (mcorner) mcorner[(size_t)img * P + i] = mc;
+      if (mcorner) mcorner[pb + i] = mc;
       loc = fminf(loc, mc);
       hic = fmaxf(hic, mc);
       if (pc_out) {
 #pragma unroll
         for (int o = 0; o < NO; ++o) pc_out[ib + (size_t)o * P + i] = pc[o];
       }
-      moment[(size_t)img * P + i] = m;
+      moment[pb + i] = m;
       lo = fminf(lo, m);
       hi = fmaxf(hi, m);
     }
@@ -289,13 +298,15 @@ __global__ void __launch_bounds__(256) pc_moment(const float* __restrict__ er,
   }
 }
 
-cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t, int nimg,
-                             long long P, const KParams& kp, float* moment, unsigned* minmax,
+cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t,
+                             const Group& gr, const KParams& kp, float* moment, unsigned* minmax,
                              float* pc_out, float* mcorner, unsigned* minmax_c, cudaStream_t st) {
-  long long blocks = (P / 4 + 255) / 256;
+  long long pmax = 1;
+  for (int i = 0; i < gr.n; ++i) pmax = gr.P(i) > pmax ? gr.P(i) : pmax;
+  long long blocks = (pmax / 4 + 255) / 256;
   if (blocks < 1) blocks = 1;
   if (blocks > 1216) blocks = 1216;   // 8 per SM on 152 SMs; grid-stride beyond
-  pc_moment<<<dim3((unsigned)blocks, nimg), 256, 0, st>>>(er, q, noise_t, P, kp, moment, minmax,
+  pc_moment<<<dim3((unsigned)blocks, gr.n), 256, 0, st>>>(er, q, noise_t, gr, kp, moment, minmax,
                                                           pc_out, mcorner, minmax_c);
   return cudaGetLastError();
 }

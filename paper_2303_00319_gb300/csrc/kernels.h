@@ -11,28 +11,42 @@ namespace rift2 {
 
 // k_filterbank.cu
 void launch_twiddles(float2* tw, int n, cudaStream_t st);
+// The passes of a plan as pass_twiddle_gather reads them: pass st has radix R[st], ns[st]
+// and its twiddles from off[st] on; total = sum of ns (R - 1) = L - 1.
+struct PassDims {
+  int nst, total;
+  int R[FFT_MAX_STAGES], ns[FFT_MAX_STAGES], off[FFT_MAX_STAGES];
+};
+void launch_pass_twiddles(float2* ptw, const float2* tw, int L, const PassDims& pd,
+                          cudaStream_t st);
 // Bluestein tables of a length-n transform run as a length-m convolution (FftPlan);
 // c64 [n] and tw64 [m] are FP64 scratch the caller frees after the stream has passed.
 void launch_bluestein_tables(float2* chirp, float2* kf, float2* ki, double2* c64, double2* tw64,
                              int n, int m, cudaStream_t st);
-cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec, int nimg,
-                                int H, int W, const FftPlan& ph, const FftPlan& pw,
-                                cudaStream_t st);
-// zc [NO][W]: 1 where orientation o's angular window is zero on the whole column u.
+// Per-image inputs of the filter-bank launchers: the plans of the image's height and
+// width, its zero-window column table (zc [NO][W]: 1 where orientation o's angular window
+// is zero on the whole column u) and its column tile (0: the default).
+struct FbImage {
+  FftPlan ph, pw;
+  const unsigned char* zc;
+  int col_tile;
+};
+// Each launcher walks the group in runs of one size (register-tiled kernels per run where
+// the side allows, one shared-memory launch for the rest) and reports the kernels it
+// enqueued in *launches.  Buffers are packed as the Group describes.
+cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* spec,
+                                const Group& gr, const FbImage* fi, cudaStream_t st,
+                                int* launches);
 void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaStream_t st);
 // Column tiles (columns per CTA) the shared-memory column pass can use for height H, the
-// default first; none for the register-tiled heights.  `tile` of launch_lg_cols picks one
-// (0: the default); every tile computes the same result.
+// default first; none for the register-tiled heights.  FbImage::col_tile picks one; every
+// tile computes the same result.
 int lg_cols_tile_candidates(int H, int L, int* out, int max_n);
-// kernels one launch_lg_rows enqueues (2 for the split path of wide rows)
-int lg_rows_launches(int H, int W, const FftPlan& pw);
-cudaError_t launch_lg_cols(const float2* spec, float2* scratch, int nimg, int H, int W,
-                           const FftPlan& ph, const KParams& kp, const unsigned char* zc,
-                           cudaStream_t st, int tile = 0);
-cudaError_t launch_lg_rows(float2* scratch, int nimg, int H, int W, const FftPlan& pw,
+cudaError_t launch_lg_cols(const float2* spec, float2* scratch, const Group& gr,
+                           const FbImage* fi, const KParams& kp, cudaStream_t st, int* launches);
+cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
-                           unsigned char* mim, int mim_pitch, const unsigned char* zc,
-                           cudaStream_t st);
+                           unsigned char* mim, int mim_pitch, cudaStream_t st, int* launches);
 
 // k_pc.cu — exact median of |EO_0,o| (radix select), noise thresholds, PC, moments.
 struct MedianWs {
@@ -40,12 +54,12 @@ struct MedianWs {
   unsigned* state;   // [nimg][NO][2][2]  (prefix, rank)
   float* noise_t;    // [nimg][NO]
 };
-cudaError_t launch_noise_threshold(const float* an0, int nimg, long long P, const KParams& kp,
+cudaError_t launch_noise_threshold(const float* an0, const Group& gr, const KParams& kp,
                                    MedianWs ws, cudaStream_t st);
 // mcorner / minmax_c (both NULL unless corners are wanted): the minimum moment without its
 // -eps/2 offset (>= 0, the same FAST input up to the min-max normalisation) and its min / max.
-cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t, int nimg,
-                             long long P, const KParams& kp, float* moment, unsigned* minmax,
+cudaError_t launch_pc_moment(const float* er, const float* q, const float* noise_t,
+                             const Group& gr, const KParams& kp, float* moment, unsigned* minmax,
                              float* pc_out, float* mcorner, unsigned* minmax_c, cudaStream_t st);
 
 // k_detect.cu — FAST + NMS on the normalised moment map, then top-K.
@@ -81,19 +95,26 @@ __host__ __device__ inline int topk_fast_cap(int max_kp) {
 inline bool topk_multi(int max_kp, int H, int W) {
   return topk_fast_cap(max_kp) > 0 && (long long)H * W > (1ll << 22);
 }
+// A group takes the multi-CTA selection for all its images when one of them needs it (the
+// selected keypoints are the same either way).
+inline bool topk_multi_group(int max_kp, const Group& gr) {
+  for (int i = 0; i < gr.n; ++i)
+    if (topk_multi(max_kp, gr.H[i], gr.W[i])) return true;
+  return false;
+}
 inline bool topk_needs_sortbuf(int max_kp) {
   return topk_sort_cap(max_kp) > TOPK_SMEM_CAP && max_kp > TOPK_SMEM_ANY_CAP;
 }
-cudaError_t launch_detect(const float* moment, int nimg, int H, int W, const KParams& kp,
-                          DetectWs ws, const FeatPtrs& fp, cudaStream_t st);
+cudaError_t launch_detect(const float* moment, const Group& gr, const KParams& kp, DetectWs ws,
+                          const FeatPtrs& fp, cudaStream_t st);
 // min = +inf bits, max = 0, candidate counts = 0 for g images
 void launch_init_detect(unsigned* minmax, unsigned* ccount, int g, cudaStream_t st);
 // Appends each image's corner keypoints (cxy / csc / ccnt[2 i], max_kp per image) after its
 // edge keypoints in fp, leaving out pixels already among the edge keypoints (order kept);
-// bits: scratch of ceil(H W / 32) words per image.
-cudaError_t launch_merge_corners(int nimg, int H, int W, const KParams& kp, const FeatPtrs& fp,
+// bits: scratch of bits_stride >= ceil(H W / 32) words per image.
+cudaError_t launch_merge_corners(const Group& gr, const KParams& kp, const FeatPtrs& fp,
                                  const int* cxy, const float* csc, const int* ccnt,
-                                 unsigned* bits, cudaStream_t st);
+                                 unsigned* bits, long long bits_stride, cudaStream_t st);
 // image-wide min / max of g non-negative maps [g][P] (ordered-int atomics)
 void launch_minmax(const float* m, int g, long long P, unsigned* minmax, cudaStream_t st);
 // worst-case number of NMS survivors of an H x W map (one per 2 x 2 block)
@@ -112,9 +133,9 @@ struct DescribeWs {
 };
 // Box (columns, rows) of the MIM tensor map the descriptor kernel of `desc_mode` stages.
 void describe_box(int desc_mode, int* cols, int* rows);
-cudaError_t launch_describe(const CUtensorMap* mim_map, int nimg, int H, int W,
-                            const KParams& kp, DescribeWs ws, const FeatPtrs& fp,
-                            cudaStream_t st);
+// mim_map: 2-D tensor map over the group's MIMs stacked row after row (Group::mrow).
+cudaError_t launch_describe(const CUtensorMap* mim_map, const Group& gr, const KParams& kp,
+                            DescribeWs ws, const FeatPtrs& fp, cudaStream_t st);
 
 // k_match.cu — brute-force nearest neighbour.
 struct MatchPtrs {

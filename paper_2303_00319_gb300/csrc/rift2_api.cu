@@ -2,6 +2,7 @@
 // the launch sequences of rift2_extract / rift2_match and the stage entry points.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -63,6 +64,7 @@ struct rift2_ctx {
   int* status = nullptr;
   long long wait_iters = 1ll << 24;   // first-wait limit of the descriptor kernel's staging
   std::map<int, FftPlan> plans;
+  std::vector<float2*> pass_tw;   // per-pass twiddle tables of the plans (freed at destroy)
   std::map<std::pair<int, int>, unsigned char*> zero_cols;   // (H, W) -> [NO][W]
   std::map<std::pair<int, int>, int> col_tiles;              // (H, W) -> tuned column tile
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -166,6 +168,46 @@ int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
     pl.kern_fwd = kf;
     pl.kern_inv = ki;
   }
+  // the shared-memory kernels' device copy: passes with precomputed divisors, per-pass
+  // twiddles gathered from tw
+  FftPasses pp{};
+  PassDims pd{};
+  pp.n = n;
+  pp.L = m;
+  pp.nst = pl.nst;
+  pd.nst = pl.nst;
+  int ns = 1, off = 0;
+  for (int st2 = 0; st2 < pl.nst; ++st2) {
+    const int R = pl.radix[st2];
+    FftPass& ps = pp.p[st2];
+    ps.R = R;
+    ps.ns = ns;
+    ps.q = FastDiv((unsigned)(m / R));
+    ps.k = FastDiv((unsigned)ns);
+    ps.tw = off;
+    pd.R[st2] = R;
+    pd.ns[st2] = ns;
+    pd.off[st2] = off;
+    off += ns * (R - 1);
+    ns *= R;
+  }
+  pd.total = off;
+  pp.dL = FastDiv((unsigned)m);
+  pp.dn = FastDiv((unsigned)n);
+  pp.chirp = pl.chirp;
+  pp.kern_fwd = pl.kern_fwd;
+  pp.kern_inv = pl.kern_inv;
+  float2* ptw = nullptr;
+  RIFT2_CU(cudaMalloc(&ptw, sizeof(float2) * (off > 0 ? off : 1)));
+  launch_pass_twiddles(ptw, tw, m, pd, st);
+  c->launches += 1;
+  RIFT2_CU(cudaGetLastError());
+  pp.ptw = ptw;
+  FftPasses* dev = nullptr;
+  RIFT2_CU(cudaMalloc(&dev, sizeof(FftPasses)));
+  RIFT2_CU(cudaMemcpyAsync(dev, &pp, sizeof(FftPasses), cudaMemcpyHostToDevice, st));
+  pl.dev = dev;
+  c->pass_tw.push_back(ptw);
   RIFT2_CU(cudaStreamSynchronize(st));
   c->plans[n] = pl;
   *out = pl;
@@ -258,35 +300,45 @@ struct StageScope {
 
 // ------------------------------------------------------------------ autotuning
 // First extraction of a size with a shared-memory column pass: run that pass once per
-// candidate tile on the call's own spectrum (two timed repetitions each, events on the
-// stream, one synchronisation), keep the fastest.  The outputs of every candidate are
-// identical, so the scratch the last run leaves is as good as any.
-int tune_col_tile(rift2_ctx* c, const float2* spec, float2* scratch, int g, int H, int W,
-                  const FftPlan& ph, const unsigned char* zc, cudaStream_t st, int* tile) {
+// candidate tile on image i of the group (its own spectrum; two timed repetitions each,
+// events on the stream, one synchronisation), keep the fastest.  The outputs of every
+// candidate are identical, so the scratch the last run leaves is as good as any.
+int tune_col_tile(rift2_ctx* c, const float2* spec, float2* scratch, const Group& gr, int i,
+                  const FbImage& fim, cudaStream_t st, int* tile) {
+  const int H = gr.H[i], W = gr.W[i];
   const auto key = std::make_pair(H, W);
   auto it = c->col_tiles.find(key);
   if (it != c->col_tiles.end()) { *tile = it->second; return RIFT2_OK; }
   int cand[8];
-  const int n = lg_cols_tile_candidates(H, ph.m, cand, 8);
+  const int n = lg_cols_tile_candidates(H, fim.ph.m, cand, 8);
   if (n <= 1) { *tile = n ? cand[0] : 0; c->col_tiles[key] = *tile; return RIFT2_OK; }
+  Group one{};
+  one.n = 1;
+  one.H[0] = H;
+  one.W[0] = W;
+  one.poff[0] = gr.poff[i];
+  one.mrow[0] = gr.mrow[i];
+  FbImage f = fim;
   cudaEvent_t ev[9];
-  for (int i = 0; i <= n; ++i) RIFT2_CU(cudaEventCreate(&ev[i]));
-  RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, cand[0]));   // warm-up
+  for (int k = 0; k <= n; ++k) RIFT2_CU(cudaEventCreate(&ev[k]));
+  f.col_tile = cand[0];
+  RIFT2_CU(launch_lg_cols(spec, scratch, one, &f, c->kp, st, nullptr));   // warm-up
   c->launches += 1 + 2 * n;
   RIFT2_CU(cudaEventRecord(ev[0], st));
-  for (int i = 0; i < n; ++i) {
-    for (int r = 0; r < 2; ++r) RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, cand[i]));
-    RIFT2_CU(cudaEventRecord(ev[i + 1], st));
+  for (int k = 0; k < n; ++k) {
+    f.col_tile = cand[k];
+    for (int r = 0; r < 2; ++r) RIFT2_CU(launch_lg_cols(spec, scratch, one, &f, c->kp, st, nullptr));
+    RIFT2_CU(cudaEventRecord(ev[k + 1], st));
   }
   RIFT2_CU(cudaEventSynchronize(ev[n]));
   int best = cand[0];
   float best_ms = 1e30f;
-  for (int i = 0; i < n; ++i) {
+  for (int k = 0; k < n; ++k) {
     float ms = 0.f;
-    RIFT2_CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-    if (ms < best_ms) { best_ms = ms; best = cand[i]; }
+    RIFT2_CU(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+    if (ms < best_ms) { best_ms = ms; best = cand[k]; }
   }
-  for (int i = 0; i <= n; ++i) cudaEventDestroy(ev[i]);
+  for (int k = 0; k <= n; ++k) cudaEventDestroy(ev[k]);
   c->col_tiles[key] = best;
   *tile = best;
   return RIFT2_OK;
@@ -295,7 +347,9 @@ int tune_col_tile(rift2_ctx* c, const float2* spec, float2* scratch, int g, int 
 // ------------------------------------------------------------------ workspace layout
 // Kernels one launch_detect issues: FAST + sort, plus the multi-CTA selection's two
 // kernels when it runs for this keypoint budget and map size.
-static int detect_launches(int max_kp, int H, int W) { return topk_multi(max_kp, H, W) ? 4 : 2; }
+static int detect_launches(int max_kp, const Group& gr) {
+  return topk_multi_group(max_kp, gr) ? 4 : 2;
+}
 
 struct Layout {
   size_t spec, scratch, er, q, an0, amp, pc, moment, mim, mhist, mstate, noise, minmax, ccount,
@@ -303,29 +357,83 @@ struct Layout {
   // corner keypoints (RIFT2_FLAG_CORNERS): minimum-moment map, its min / max, candidate
   // count, the corner list before the merge, and the bitmap of edge-keypoint pixels
   size_t mcorner, minmax_c, ccount_c, cxy, csc, ccnt, bits;
-  int mim_pitch, cap_cand;
+  int mim_pitch, mim_rows, cap_cand;
+  long long bits_words;   // words of the edge-keypoint bitmap per image
 };
 
+// Pixels of an image in the packed per-pixel planes: a multiple of 64, so that every
+// plane of every image starts 256-byte aligned.
+inline long long padded_px(int H, int W) { return ((long long)H * W + 63) / 64 * 64; }
+
+// The packed layout of n images (Group): pixel offsets from padded counts, MIM rows
+// stacked.  *ptot / *rows: pixels of one plane and MIM rows of the whole group.
+Group make_group(int n, const int* H, const int* W, long long* ptot, int* rows) {
+  Group gr{};
+  gr.n = n;
+  long long p = 0;
+  int r = 0;
+  for (int i = 0; i < n; ++i) {
+    gr.H[i] = H[i];
+    gr.W[i] = W[i];
+    gr.poff[i] = p;
+    gr.mrow[i] = r;
+    p += padded_px(H[i], W[i]);
+    r += H[i];
+  }
+  if (ptot) *ptot = p;
+  if (rows) *rows = r;
+  return gr;
+}
+
+// g images of one size whose pixels lie `stride` apart (a caller's dense [g][H][W] array:
+// stride H W; the packed workspace: padded_px).
+Group uniform_group(int g, int H, int W, long long stride) {
+  Group gr{};
+  gr.n = g;
+  for (int i = 0; i < g; ++i) {
+    gr.H[i] = H;
+    gr.W[i] = W;
+    gr.poff[i] = i * stride;
+    gr.mrow[i] = i * H;
+  }
+  return gr;
+}
+
 // max_kp: keypoints one detector pass keeps; kp_cap: keypoint list capacity per image.
-Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners, int debug,
+Layout extract_layout(const Group& gr, int max_kp, int kp_cap, bool corners, int debug,
                       bool spatial) {
   Layout L{};
-  const size_t P = (size_t)H * W;
+  const int g = gr.n;
+  size_t P = 0;      // pixels of one packed plane
+  int rows = 0, wmax = 0;
+  long long cc = 1, bw = 1;
+  for (int i = 0; i < g; ++i) {
+    P += (size_t)padded_px(gr.H[i], gr.W[i]);
+    rows += gr.H[i];
+    wmax = gr.W[i] > wmax ? gr.W[i] : wmax;
+    const long long c = detect_cap_candidates(gr.H[i], gr.W[i]);
+    cc = c > cc ? c : cc;
+    const long long w = (gr.P(i) + 31) / 32;
+    bw = w > bw ? w : bw;
+  }
   // at least one TMA box wide (112 bytes; 160 for the spatial variant's window)
   const size_t box_w = spatial ? 160 : 112;
-  L.mim_pitch = (int)align_up((size_t)W > box_w ? (size_t)W : box_w, 16);
-  L.cap_cand = ((H + 1) / 2) * ((W + 1) / 2);
+  L.mim_pitch = (int)align_up((size_t)wmax > box_w ? (size_t)wmax : box_w, 16);
+  L.cap_cand = (int)cc;
+  L.bits_words = bw;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
-  L.spec = take((size_t)g * P * sizeof(float2));
-  L.scratch = take((size_t)g * NS * NO * P * sizeof(float2));
-  L.er = take((size_t)g * NO * P * 4);
-  L.q = take((size_t)g * NO * P * 4);
-  L.an0 = take((size_t)g * NO * P * 4);
-  L.amp = (debug & 1) ? take((size_t)g * NO * P * 4) : (size_t)-1;
-  L.pc = (debug & 2) ? take((size_t)g * NO * P * 4) : (size_t)-1;
-  L.moment = take((size_t)g * P * 4);
-  L.mim = take((size_t)g * H * L.mim_pitch);
+  L.spec = take(P * sizeof(float2));
+  L.scratch = take((size_t)NS * NO * P * sizeof(float2));
+  L.er = take((size_t)NO * P * 4);
+  L.q = take((size_t)NO * P * 4);
+  L.an0 = take((size_t)NO * P * 4);
+  L.amp = (debug & 1) ? take((size_t)NO * P * 4) : (size_t)-1;
+  L.pc = (debug & 2) ? take((size_t)NO * P * 4) : (size_t)-1;
+  L.moment = take(P * 4);
+  // rows of the stacked MIMs, at least one TMA box high (the tensor map covers them all)
+  L.mim_rows = rows > 160 ? rows : 160;
+  L.mim = take((size_t)L.mim_rows * L.mim_pitch);
   L.mhist = take((size_t)g * NO * 2 * 4096 * 4);
   L.mstate = take((size_t)g * NO * 4 * 4);
   L.noise = take((size_t)g * NO * 4);
@@ -334,7 +442,7 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   L.cand = take((size_t)g * L.cap_cand * 8);
   const int kc = topk_sort_cap(max_kp);
   L.sortbuf = take(topk_needs_sortbuf(max_kp) ? (size_t)g * kc * 8 : 0);
-  const bool multi = topk_multi(max_kp, H, W);
+  const bool multi = topk_multi_group(max_kp, gr);
   L.chist = take(multi ? (size_t)g * ((size_t)1 << TOPK_DIGIT_BITS) * 4 : 0);
   L.sel = take(multi ? (size_t)g * 4 * 4 : 0);
   L.comp = take(multi ? (size_t)g * topk_fast_cap(max_kp) * 8 : 0);
@@ -342,21 +450,20 @@ Layout extract_layout(int g, int H, int W, int max_kp, int kp_cap, bool corners,
   L.info = take((size_t)g * kp_cap * 4);
   L.off = take((size_t)g * kp_cap * 4);
   const size_t none = (size_t)-1;
-  L.mcorner = corners ? take((size_t)g * P * 4) : none;
+  L.mcorner = corners ? take(P * 4) : none;
   L.minmax_c = corners ? take((size_t)g * 2 * 4) : none;
   L.ccount_c = corners ? take((size_t)g * 4) : none;
   L.cxy = corners ? take((size_t)g * max_kp * 2 * 4) : none;
   L.csc = corners ? take((size_t)g * max_kp * 4) : none;
   L.ccnt = corners ? take((size_t)g * 2 * 4) : none;
-  L.bits = corners ? take((size_t)g * ((P + 31) / 32) * 4) : none;
+  L.bits = corners ? take((size_t)g * L.bits_words * 4) : none;
   L.total = o;
   return L;
 }
 
-Layout ctx_layout(const rift2_ctx* c, int g, int H, int W, int debug) {
-  return extract_layout(g, H, W, c->kp.max_kp, c->kp.kp_cap,
-                        (c->p.flags & RIFT2_FLAG_CORNERS) != 0, debug,
-                        c->kp.desc_mode == DESC_SPATIAL);
+Layout ctx_layout(const rift2_ctx* c, const Group& gr, int debug) {
+  return extract_layout(gr, c->kp.max_kp, c->kp.kp_cap, (c->p.flags & RIFT2_FLAG_CORNERS) != 0,
+                        debug, c->kp.desc_mode == DESC_SPATIAL);
 }
 
 template <typename T>
@@ -366,14 +473,18 @@ T* at(void* base, size_t off) {
 
 // The MIM as a [g][H][pitch] uint8 tensor for the descriptor kernel's TMA staging (box
 // shape: describe_box(), which depends on the descriptor mode).
-int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int g, int H, int pitch) {
-  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)H, (cuuint64_t)g};
-  cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * H};
+// The MIMs of a group stacked row after row ([rows][pitch] uint8) as one 2-D tensor map
+// for the descriptor kernel's TMA staging (box shape: describe_box(), which depends on
+// the descriptor mode).  A box reaching past an image's rows reads a neighbour's rows or
+// the fill value; the descriptor kernels only count pixels inside their own image.
+int make_mim_map(rift2_ctx* c, CUtensorMap* tm, unsigned char* mim, int rows, int pitch) {
+  cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch};
   int bw = 0, bh = 0;
   describe_box(c->kp.desc_mode, &bw, &bh);
-  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, mim, dims, strides, box, es,
+  cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, mim, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -426,28 +537,31 @@ FeatPtrs feat_ptrs(const rift2_features* f, int n) {
   return fp;
 }
 
-int copy_debug(const rift2_features* f, int n, void* ws, const Layout& L, int H, int W,
+int copy_debug(const rift2_features* f, const Group& gr, void* ws, const Layout& L,
                cudaStream_t st) {
-  const size_t P = (size_t)H * W;
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < gr.n; ++i) {
     const rift2_debug_maps* d = f[i].debug;
     if (!d) continue;
-    auto cp = [&](void* dst, size_t off, size_t bytes_per_img) -> cudaError_t {
+    const size_t P = (size_t)gr.P(i), pb = (size_t)gr.poff[i];
+    auto cp = [&](void* dst, size_t off, size_t planes, size_t esize) -> cudaError_t {
       if (!dst || off == (size_t)-1) return cudaSuccess;
-      return cudaMemcpyAsync(dst, static_cast<char*>(ws) + off + i * bytes_per_img, bytes_per_img,
-                             cudaMemcpyDeviceToDevice, st);
+      return cudaMemcpyAsync(dst, static_cast<char*>(ws) + off + planes * pb * esize,
+                             planes * P * esize, cudaMemcpyDeviceToDevice, st);
     };
-    RIFT2_CU(cp(d->amp, L.amp, NO * P * 4));
-    RIFT2_CU(cp(d->er, L.er, NO * P * 4));
-    RIFT2_CU(cp(d->q, L.q, NO * P * 4));
-    RIFT2_CU(cp(d->an0, L.an0, NO * P * 4));
-    RIFT2_CU(cp(d->pc, L.pc, NO * P * 4));
-    RIFT2_CU(cp(d->moment, L.moment, P * 4));
-    RIFT2_CU(cp(d->noise_t, L.noise, NO * 4));
-    RIFT2_CU(cp(d->spectrum, L.spec, P * sizeof(float2)));
+    RIFT2_CU(cp(d->amp, L.amp, NO, 4));
+    RIFT2_CU(cp(d->er, L.er, NO, 4));
+    RIFT2_CU(cp(d->q, L.q, NO, 4));
+    RIFT2_CU(cp(d->an0, L.an0, NO, 4));
+    RIFT2_CU(cp(d->pc, L.pc, NO, 4));
+    RIFT2_CU(cp(d->moment, L.moment, 1, 4));
+    RIFT2_CU(cp(d->spectrum, L.spec, 1, sizeof(float2)));
+    if (d->noise_t)
+      RIFT2_CU(cudaMemcpyAsync(d->noise_t, static_cast<char*>(ws) + L.noise + (size_t)i * NO * 4,
+                               NO * 4, cudaMemcpyDeviceToDevice, st));
     if (d->mim)
-      RIFT2_CU(cudaMemcpy2DAsync(d->mim, W, static_cast<char*>(ws) + L.mim + (size_t)i * H * L.mim_pitch,
-                                 L.mim_pitch, W, H, cudaMemcpyDeviceToDevice, st));
+      RIFT2_CU(cudaMemcpy2DAsync(d->mim, gr.W[i],
+                                 static_cast<char*>(ws) + L.mim + (size_t)gr.mrow[i] * L.mim_pitch,
+                                 L.mim_pitch, gr.W[i], gr.H[i], cudaMemcpyDeviceToDevice, st));
   }
   return RIFT2_OK;
 }
@@ -466,22 +580,39 @@ int wants_debug(const rift2_features* f, int n) {
   return w;
 }
 
-// One launch group: g images of the same size.
+// The group of images imgs[0..g) (any sizes) in the packed layout.
+Group image_group(int g, const rift2_image* imgs) {
+  int H[MAXB], W[MAXB];
+  for (int i = 0; i < g; ++i) {
+    H[i] = imgs[i].height;
+    W[i] = imgs[i].width;
+  }
+  return make_group(g, H, W, nullptr, nullptr);
+}
+
+// One launch group: g <= MAXB images of any sizes, one launch per stage (plus one per run of
+// a register-tiled size in the transform stages).
 int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* out,
                   cudaStream_t st) {
-  const int H = imgs[0].height, W = imgs[0].width;
-  const long long P = (long long)H * W;
-  FftPlan ph{}, pw{};
-  int rc = get_plan(c, H, st, &ph);
-  if (rc) return rc;
-  rc = get_plan(c, W, st, &pw);
-  if (rc) return rc;
-  unsigned char* zc = nullptr;
-  rc = get_zero_cols(c, H, W, st, &zc);
-  if (rc) return rc;
+  const Group gr = image_group(g, imgs);
+  FbImage fi[MAXB];
+  for (int i = 0; i < g; ++i) {
+    const int H = gr.H[i], W = gr.W[i];
+    fi[i] = FbImage{};
+    int rc = get_plan(c, H, st, &fi[i].ph);
+    if (rc) return rc;
+    rc = get_plan(c, W, st, &fi[i].pw);
+    if (rc) return rc;
+    unsigned char* zc = nullptr;
+    rc = get_zero_cols(c, H, W, st, &zc);
+    if (rc) return rc;
+    fi[i].zc = zc;
+    auto it = c->col_tiles.find(std::make_pair(H, W));
+    fi[i].col_tile = it == c->col_tiles.end() ? 0 : it->second;
+  }
   const int dbg = wants_debug(out, g);
-  Layout L = ctx_layout(c, g, H, W, dbg);
-  rc = ensure_ws(c, L.total);
+  Layout L = ctx_layout(c, gr, dbg);
+  int rc = ensure_ws(c, L.total);
   if (rc) return rc;
   void* ws = c->ws;
   ImgPtrs ip{};
@@ -503,47 +634,56 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
   }
   RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * 2 * 4096 * 4, st));
   float2* spec = at<float2>(ws, L.spec);
+  int nl = 0;
   {
-    StageScope sc(c, RIFT2_STAGE_FFT_FWD, st, K_FFT_FWD);
-    RIFT2_CU(launch_fft2_forward(&ip, nullptr, spec, g, H, W, ph, pw, st));
+    StageScope sc(c, RIFT2_STAGE_FFT_FWD, st, 0);
+    RIFT2_CU(launch_fft2_forward(&ip, nullptr, spec, gr, fi, st, &nl));
+    c->launches += nl;
   }
   float* er = at<float>(ws, L.er);
   float* q = at<float>(ws, L.q);
   float* an0 = at<float>(ws, L.an0);
   unsigned char* mim = at<unsigned char>(ws, L.mim);
   float2* scratch = at<float2>(ws, L.scratch);
-  int tile = 0;
   if (c->p.flags & RIFT2_FLAG_AUTOTUNE) {
-    rc = tune_col_tile(c, spec, scratch, g, H, W, ph, zc, st, &tile);
-    if (rc) return rc;
+    for (int i = 0; i < g; ++i) {   // each size once, on its first image
+      if (i > 0 && gr.H[i] == gr.H[i - 1] && gr.W[i] == gr.W[i - 1]) {
+        fi[i].col_tile = fi[i - 1].col_tile;
+        continue;
+      }
+      rc = tune_col_tile(c, spec, scratch, gr, i, fi[i], st, &fi[i].col_tile);
+      if (rc) return rc;
+    }
   }
   {
-    StageScope sc(c, RIFT2_STAGE_LG_COLS, st, K_LG_COLS);
-    RIFT2_CU(launch_lg_cols(spec, scratch, g, H, W, ph, c->kp, zc, st, tile));
+    StageScope sc(c, RIFT2_STAGE_LG_COLS, st, 0);
+    RIFT2_CU(launch_lg_cols(spec, scratch, gr, fi, c->kp, st, &nl));
+    c->launches += nl;
   }
   {
-    StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, lg_rows_launches(H, W, pw));
-    RIFT2_CU(launch_lg_rows(scratch, g, H, W, pw, c->kp, er, q, an0, at<float>(ws, L.amp), mim,
-                            L.mim_pitch, zc, st));
+    StageScope sc(c, RIFT2_STAGE_LG_ROWS, st, 0);
+    RIFT2_CU(launch_lg_rows(scratch, gr, fi, c->kp, er, q, an0, at<float>(ws, L.amp), mim,
+                            L.mim_pitch, st, &nl));
+    c->launches += nl;
   }
   MedianWs mw{at<unsigned>(ws, L.mhist), at<unsigned>(ws, L.mstate), at<float>(ws, L.noise)};
   {
     StageScope sc(c, RIFT2_STAGE_NOISE, st, K_NOISE);
-    RIFT2_CU(launch_noise_threshold(an0, g, P, c->kp, mw, st));
+    RIFT2_CU(launch_noise_threshold(an0, gr, c->kp, mw, st));
   }
   float* moment = at<float>(ws, L.moment);
   {
     StageScope sc(c, RIFT2_STAGE_MOMENT, st, K_MOMENT);
-    RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, g, P, c->kp, moment, minmax, at<float>(ws, L.pc),
+    RIFT2_CU(launch_pc_moment(er, q, mw.noise_t, gr, c->kp, moment, minmax, at<float>(ws, L.pc),
                               corners ? at<float>(ws, L.mcorner) : nullptr, minmax_c, st));
   }
   DetectWs dw{minmax, at<unsigned long long>(ws, L.cand), ccount, L.cap_cand,
               at<unsigned long long>(ws, L.sortbuf), at<unsigned>(ws, L.chist),
               at<unsigned>(ws, L.sel), at<unsigned long long>(ws, L.comp)};
   {
-    const int kd = detect_launches(c->kp.max_kp, H, W);
+    const int kd = detect_launches(c->kp.max_kp, gr);
     StageScope sc(c, RIFT2_STAGE_DETECT, st, corners ? 2 * kd + K_MERGE : kd);
-    RIFT2_CU(launch_detect(moment, g, H, W, c->kp, dw, fp, st));
+    RIFT2_CU(launch_detect(moment, gr, c->kp, dw, fp, st));
     if (corners) {
       // corner keypoints on the minimum moment into the side list, then appended
       FeatPtrs fc{};
@@ -558,20 +698,65 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
       DetectWs dwc{minmax_c, at<unsigned long long>(ws, L.cand), ccount_c, L.cap_cand,
                    at<unsigned long long>(ws, L.sortbuf), at<unsigned>(ws, L.chist),
                    at<unsigned>(ws, L.sel), at<unsigned long long>(ws, L.comp)};
-      RIFT2_CU(launch_detect(at<float>(ws, L.mcorner), g, H, W, c->kp, dwc, fc, st));
-      RIFT2_CU(launch_merge_corners(g, H, W, c->kp, fp, cxy, csc, ccnt, at<unsigned>(ws, L.bits), st));
+      RIFT2_CU(launch_detect(at<float>(ws, L.mcorner), gr, c->kp, dwc, fc, st));
+      RIFT2_CU(launch_merge_corners(gr, c->kp, fp, cxy, csc, ccnt, at<unsigned>(ws, L.bits),
+                                    L.bits_words, st));
     }
   }
-  if (H >= RIFT2_PATCH && W >= RIFT2_PATCH) {
+  // images smaller than the patch keep no keypoint (fast_nms has no candidate pixel there;
+  // topk_sort wrote their descriptor count 0)
+  bool any_patch = false;
+  for (int i = 0; i < g; ++i) any_patch |= gr.H[i] >= RIFT2_PATCH && gr.W[i] >= RIFT2_PATCH;
+  if (any_patch) {
     CUtensorMap tm;
-    rc = make_mim_map(c, &tm, mim, g, H, L.mim_pitch);
+    rc = make_mim_map(c, &tm, mim, L.mim_rows, L.mim_pitch);
     if (rc) return rc;
     DescribeWs dsw{at<unsigned short>(ws, L.raw), at<unsigned>(ws, L.info), at<int>(ws, L.off),
                    c->status, c->wait_iters};
     StageScope sc(c, RIFT2_STAGE_DESCRIBE, st, K_DESCRIBE);
-    RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
+    RIFT2_CU(launch_describe(&tm, gr, c->kp, dsw, fp, st));
   }
-  return copy_debug(out, g, ws, L, H, W, st);
+  return copy_debug(out, gr, ws, L, st);
+}
+
+// The launch groups rift2_extract forms (rift2_workspace_bytes applies the same): with
+// RIFT2_FLAG_NO_GROUPING one image each; with RIFT2_FLAG_SIZE_GROUPS runs of consecutive
+// images of one size; otherwise all images in order of size (height, then width; equal
+// sizes keep their order) cut into groups of up to MAXB images.  A group whose workspace
+// exceeds the budget is halved until it fits or holds one image.  dbg[i]: the optional
+// outputs image i wants (wants_debug bits; NULL: none).
+void plan_groups(const rift2_ctx* c, int n, const int* H, const int* W, const int* dbg,
+                 std::vector<int>& order, std::vector<int>& sizes) {
+  order.resize(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  const int fl = c->p.flags;
+  const bool none = (fl & RIFT2_FLAG_NO_GROUPING) != 0, same = (fl & RIFT2_FLAG_SIZE_GROUPS) != 0;
+  if (!none && !same)
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return H[x] != H[y] ? H[x] < H[y] : W[x] < W[y];
+    });
+  sizes.clear();
+  int i = 0;
+  while (i < n) {
+    int j = i + 1;
+    if (!none)
+      while (j < n && j - i < MAXB &&
+             (!same || (H[order[j]] == H[order[i]] && W[order[j]] == W[order[i]])))
+        ++j;
+    auto total = [&](int g) {
+      int hh[MAXB], ww[MAXB], d = 0;
+      for (int k = 0; k < g; ++k) {
+        hh[k] = H[order[i + k]];
+        ww[k] = W[order[i + k]];
+        if (dbg) d |= dbg[order[i + k]];
+      }
+      return ctx_layout(c, make_group(g, hh, ww, nullptr, nullptr), d).total;
+    };
+    int g = j - i;
+    while (g > 1 && total(g) > c->budget) g = (g + 1) / 2;
+    sizes.push_back(g);
+    i += g;
+  }
 }
 
 }  // namespace
@@ -670,7 +855,9 @@ int rift2_destroy(rift2_ctx* c) {
       cudaFree(const_cast<float2*>(kv.second.kern_fwd));
       cudaFree(const_cast<float2*>(kv.second.kern_inv));
     }
+    cudaFree(const_cast<FftPasses*>(kv.second.dev));
   }
+  for (float2* p : c->pass_tw) cudaFree(p);
   for (auto& kv : c->zero_cols) cudaFree(kv.second);
   for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : c->free_events) cudaEventDestroy(e);
@@ -713,14 +900,16 @@ int rift2_workspace_bytes(const rift2_ctx* c, int n, const int* heights, const i
                           int n_pairs, size_t* bytes) {
   if (!c || n < 0 || n_pairs < 0 || !bytes || (n > 0 && (!heights || !widths))) return RIFT2_E_INVAL;
   size_t need = 0;
-  const bool group = !(c->p.flags & RIFT2_FLAG_NO_GROUPING);
+  std::vector<int> order, sizes;
+  plan_groups(c, n, heights, widths, nullptr, order, sizes);   // the groups rift2_extract forms
   int i = 0;
-  while (i < n) {   // the grouping rift2_extract applies
-    int j = i + 1;
-    while (group && j < n && j - i < MAXB && heights[j] == heights[i] && widths[j] == widths[i]) ++j;
-    int g = j - i;
-    while (g > 1 && ctx_layout(c, g, heights[i], widths[i], 0).total > c->budget) g = (g + 1) / 2;
-    const size_t t = ctx_layout(c, g, heights[i], widths[i], 0).total;
+  for (int g : sizes) {
+    int hh[MAXB], ww[MAXB];
+    for (int k = 0; k < g; ++k) {
+      hh[k] = heights[order[i + k]];
+      ww[k] = widths[order[i + k]];
+    }
+    const size_t t = ctx_layout(c, make_group(g, hh, ww, nullptr, nullptr), 0).total;
     if (t > need) need = t;
     i += g;
   }
@@ -781,19 +970,22 @@ int rift2_extract(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* 
   }
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const bool group = !(c->p.flags & RIFT2_FLAG_NO_GROUPING);
+  std::vector<int> hh(n), ww(n), dbg(n), order, sizes;
+  for (int i = 0; i < n; ++i) {
+    hh[i] = imgs[i].height;
+    ww[i] = imgs[i].width;
+    dbg[i] = wants_debug(out + i, 1);
+  }
+  plan_groups(c, n, hh.data(), ww.data(), dbg.data(), order, sizes);
   int i = 0;
-  while (i < n) {
-    int j = i + 1;
-    while (group && j < n && j - i < MAXB && imgs[j].height == imgs[i].height &&
-           imgs[j].width == imgs[i].width)
-      ++j;
-    // shrink the group until its workspace fits the budget
-    int g = j - i;
-    while (g > 1 && ctx_layout(c, g, imgs[i].height, imgs[i].width, wants_debug(out + i, g)).total >
-                        c->budget)
-      g = (g + 1) / 2;
-    int rc = extract_group(c, g, imgs + i, out + i, st);
+  for (int g : sizes) {
+    rift2_image gi[MAXB];
+    rift2_features go[MAXB];
+    for (int k = 0; k < g; ++k) {
+      gi[k] = imgs[order[i + k]];
+      go[k] = out[order[i + k]];
+    }
+    int rc = extract_group(c, g, gi, go, st);
     if (rc) return rc;
     i += g;
   }
@@ -891,17 +1083,21 @@ int rift2_fft2(rift2_ctx* c, int n, const float* img, int H, int W, float* out, 
   if (rc) return rc;
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  FftPlan ph{}, pw{};
-  rc = get_plan(c, H, st, &ph);
+  FbImage f{};
+  rc = get_plan(c, H, st, &f.ph);
   if (rc) return rc;
-  rc = get_plan(c, W, st, &pw);
+  rc = get_plan(c, W, st, &f.pw);
   if (rc) return rc;
-  for (int i0 = 0; i0 < n; i0 += 65535) {
-    int g = n - i0 < 65535 ? n - i0 : 65535;
-    c->launches += K_FFT_FWD;
-    RIFT2_CU(launch_fft2_forward(nullptr, img + (size_t)i0 * H * W,
-                                 reinterpret_cast<float2*>(out) + (size_t)i0 * H * W, g, H, W, ph,
-                                 pw, st));
+  FbImage fi[MAXB];
+  for (int k = 0; k < MAXB; ++k) fi[k] = f;
+  const long long P = (long long)H * W;
+  for (int i0 = 0; i0 < n; i0 += MAXB) {
+    const int g = n - i0 < MAXB ? n - i0 : MAXB;
+    Group gr = uniform_group(g, H, W, P);   // the caller's dense [n][H][W] layout
+    int nl = 0;
+    RIFT2_CU(launch_fft2_forward(nullptr, img + (size_t)i0 * P,
+                                 reinterpret_cast<float2*>(out) + (size_t)i0 * P, gr, fi, st, &nl));
+    c->launches += nl;
   }
   return RIFT2_OK;
 }
@@ -918,12 +1114,13 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
   const long long P = (long long)H * W;
   for (int i0 = 0; i0 < n; i0 += MAXB) {
     int g = n - i0 < MAXB ? n - i0 : MAXB;
-    Layout L = ctx_layout(c, g, H, W, 0);
+    const Group gr = uniform_group(g, H, W, P);   // the caller's dense [n][H][W] maps
+    Layout L = ctx_layout(c, gr, 0);
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
     unsigned* minmax = at<unsigned>(c->ws, L.minmax);
     unsigned* ccount = at<unsigned>(c->ws, L.ccount);
-    c->launches += K_INIT + 1 + detect_launches(c->kp.max_kp, H, W);
+    c->launches += K_INIT + 1 + detect_launches(c->kp.max_kp, gr);
     launch_init_detect(minmax, ccount, g, st);
     const float* m = moment + (size_t)i0 * P;
     launch_minmax(m, g, P, minmax, st);
@@ -931,7 +1128,7 @@ int rift2_detect(rift2_ctx* c, int n, const float* moment, int H, int W, rift2_f
     DetectWs dw{minmax, at<unsigned long long>(c->ws, L.cand), ccount, L.cap_cand,
                 at<unsigned long long>(c->ws, L.sortbuf), at<unsigned>(c->ws, L.chist),
                 at<unsigned>(c->ws, L.sel), at<unsigned long long>(c->ws, L.comp)};
-    RIFT2_CU(launch_detect(m, g, H, W, c->kp, dw, fp, st));
+    RIFT2_CU(launch_detect(m, gr, c->kp, dw, fp, st));
   }
   return RIFT2_OK;
 }
@@ -947,20 +1144,21 @@ int rift2_describe(rift2_ctx* c, int n, const unsigned char* mim, int H, int W,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i0 = 0; i0 < n; i0 += MAXB) {
     int g = n - i0 < MAXB ? n - i0 : MAXB;
-    Layout L = ctx_layout(c, g, H, W, 0);
+    const Group gr = uniform_group(g, H, W, padded_px(H, W));
+    Layout L = ctx_layout(c, gr, 0);
     int rc = ensure_ws(c, L.total);
     if (rc) return rc;
     unsigned char* wm = at<unsigned char>(c->ws, L.mim);
     RIFT2_CU(cudaMemcpy2DAsync(wm, L.mim_pitch, mim + (size_t)i0 * H * W, W, W, (size_t)g * H,
                                cudaMemcpyDeviceToDevice, st));
     CUtensorMap tm;
-    rc = make_mim_map(c, &tm, wm, g, H, L.mim_pitch);
+    rc = make_mim_map(c, &tm, wm, L.mim_rows, L.mim_pitch);
     if (rc) return rc;
     FeatPtrs fp = feat_ptrs(feats + i0, g);
     c->launches += K_DESCRIBE;
     DescribeWs dsw{at<unsigned short>(c->ws, L.raw), at<unsigned>(c->ws, L.info),
                    at<int>(c->ws, L.off), c->status, c->wait_iters};
-    RIFT2_CU(launch_describe(&tm, g, H, W, c->kp, dsw, fp, st));
+    RIFT2_CU(launch_describe(&tm, gr, c->kp, dsw, fp, st));
   }
   return RIFT2_OK;
 }

@@ -131,6 +131,10 @@ extern "C" int rift2_detect_static(const rift2_params* params, const float* mome
   fp.kp_score[0] = out->kp_score;
   fp.counts[0] = out->counts;
   DetectWs dw{minmax, cand, ccount, RIFT2_STATIC_MAX_CANDIDATES, nullptr};
-  if (launch_detect(moment, 1, height, width, kp, dw, fp, st) != cudaSuccess) return RIFT2_E_CUDA;
+  Group gr{};
+  gr.n = 1;
+  gr.H[0] = height;
+  gr.W[0] = width;
+  if (launch_detect(moment, gr, kp, dw, fp, st) != cudaSuccess) return RIFT2_E_CUDA;
   return RIFT2_OK;
 }

@@ -1,8 +1,9 @@
 """Continuous-batching request loop over the RIFT2 C ABI.
 
 Requests are image pairs of any supported size.  They are admitted in arrival order as
-device memory and batch slots free up, grouped into shared launches (the library groups
-equal-size images inside one extract call), and run on one of several lanes; each lane
+device memory and batch slots free up, batched into shared launches (one extract call
+per batch, in which the library runs images of any sizes in one launch per stage), and run
+on one of several lanes; each lane
 is a context (own workspace) with its own CUDA stream, so a batch that is admitted while
 another one is on the GPU overlaps with it on the device.  Per request the loop records
 arrival, admission, launch and completion times (host clock; completion is when the
@@ -180,7 +181,7 @@ class Server:
             if self.keep_resident and self.resident_bytes + res + need_res > self.resident_budget:
                 break                     # back-pressure until the caller releases state
             trial = sizes + [r.a.shape, r.b.shape]
-            order = tuple(sorted(trial))  # the launch sorts its images by size
+            order = tuple(sorted(trial))  # the library orders a call's images by size too
             if self._workspace(lane.ctx, order, len(batch) + 1) > self.per_lane_budget:
                 if batch:
                     break
@@ -209,9 +210,6 @@ class Server:
         for r in batch:
             r.admitted = now
         ctx = lane.ctx
-        # images sorted by size inside the launch so that equal sizes share launch groups
-        order = sorted(range(2 * len(batch)),
-                       key=lambda j: (batch[j // 2].a.shape if j % 2 == 0 else batch[j // 2].b.shape))
         with torch.cuda.stream(lane.stream):
             imgs, inputs = [None] * (2 * len(batch)), []
             for j in range(2 * len(batch)):
@@ -230,7 +228,7 @@ class Server:
             matches = [self._matches.take(0) for _ in batch]
             for r in batch:
                 r.launched = time.perf_counter()
-            ctx.extract([imgs[j] for j in order], [feats[j] for j in order], stream=lane.stream)
+            ctx.extract(imgs, feats, stream=lane.stream)
             ctx.match(feats[0::2], feats[1::2], matches, stream=lane.stream)
             outs = []
             ncap, kcap = matches[0].nn_desc.shape[0], feats[0].kp_xy.shape[0]
