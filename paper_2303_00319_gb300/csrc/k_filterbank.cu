@@ -405,7 +405,8 @@ void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaSt
 }
 
 // Column pass of the inverse for the six orientations of scale blockIdx.y.
-// smem: base (F * R_s), a, b each [H][tc].
+// smem: base (F * R_s), a, b each [H][tc].  A tile whose columns all have a zero angular
+// window for an orientation (fg.zc) writes nothing for it.
 __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restrict__ spec,
                                                        float2* __restrict__ scratch,
                                                        const __grid_constant__ Group gr,
@@ -444,8 +445,13 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
     }
     base[i] = f;
   }
+  const unsigned char* __restrict__ zc = fg.zc[img];
   for (int o = 0; o < NO; ++o) {
-    __syncthreads();
+    // a tile whose columns all have a zero window for o has nothing to transform or
+    // store: the row pass reads those columns as zeros from the same table
+    const int t = threadIdx.x;
+    const bool zt = t >= tc || c0 + t >= W || (zc && zc[o * W + c0 + t]);
+    if (__syncthreads_and(zt)) continue;
     const float co = kp.cos_o[o], so = kp.sin_o[o];
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
       const int v = (int)dtc.div((unsigned)i), c = i - v * tc, u = c0 + c;
@@ -540,11 +546,12 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
   for (int o = 0; o < NO; ++o) {
     for (int s = 0; s < NS; ++s) {
       const float2* src = scratch + NS * NO * pb + ((size_t)s * NO + o) * P + (size_t)row * W;
-      // unconditional loads (a zero-window column's data is not used), several in flight
+      // zero-window columns are not read (the column pass may not have written them)
 #pragma unroll 4
       for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const float2 v = __ldg(src + x);
-        a[s * L + x] = zc[o * W + x] ? make_float2(0.f, 0.f) : v;
+        float2 v = make_float2(0.f, 0.f);
+        if (!zc[o * W + x]) v = __ldg(src + x);
+        a[s * L + x] = v;
       }
     }
     __syncthreads();
@@ -1321,7 +1328,7 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, const Group& gr,
     int tc = cols_inverse_tile(H, ph.m);
     const int tuned = fi[i0].col_tile;
     if (tuned >= 1 && tuned <= tc) tc = tuned;   // a tuned (smaller) tile; same result
-    for (int k = 0; k < cnt; ++k) sub_add(sub, sf, gr, i0 + k, ph, tc, nullptr);
+    for (int k = 0; k < cnt; ++k) sub_add(sub, sf, gr, i0 + k, ph, tc, fi[i0].zc);
     grid_x = max_of(grid_x, (W + tc - 1) / tc);
     smx = max_of(smx, cols_inverse_smem(H, ph.m, tc));
   });
@@ -1339,11 +1346,13 @@ cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
                            unsigned char* mim, int mim_pitch, cudaStream_t st, int* launches) {
   int nl = 0;
-  Group red{}, spl{};
-  FftGroup rf{}, sf{};
-  int red_rows = 0, spl_rows = 0;
+  // red[0]: rows whose shared memory lets two CTAs share an SM, red[1]: the others (one
+  // launch each, so that a wide image does not set the occupancy of the narrow ones)
+  Group red[2] = {}, spl{};
+  FftGroup rf[2] = {}, sf{};
+  int red_rows[2] = {0, 0}, spl_rows = 0;
   long long spl_px = 0;
-  size_t red_sm = 0, spl_sm = 0;
+  size_t red_sm[2] = {0, 0}, spl_sm = 0;
   cudaError_t err = cudaSuccess;
   for_runs(gr, [&](int i0, int cnt) {
     const int H = gr.H[i0], W = gr.W[i0];
@@ -1378,9 +1387,10 @@ cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
     }
     const size_t sm3 = 2 * (size_t)NS * pw.m * sizeof(float2);
     if (sm3 <= 227 * 1024 && W <= RR_MAXPIX * 512) {
-      for (int k = 0; k < cnt; ++k) sub_add(red, rf, gr, i0 + k, pw, 0, zc);
-      red_rows = max_of(red_rows, H);
-      red_sm = max_of(red_sm, sm3);
+      const int cl = sm3 <= 113 * 1024 ? 0 : 1;
+      for (int k = 0; k < cnt; ++k) sub_add(red[cl], rf[cl], gr, i0 + k, pw, 0, zc);
+      red_rows[cl] = max_of(red_rows[cl], H);
+      red_sm[cl] = max_of(red_sm[cl], sm3);
     } else {
       // rows too wide for four scales in shared memory: transform each (row, scale) in
       // place, then reduce the pixels from the transformed responses
@@ -1391,10 +1401,11 @@ cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
     }
   });
   if (err != cudaSuccess) return err;
-  if (red.n) {
-    cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_sm);
-    lg_rows_reduce<<<dim3(red_rows, red.n), 512, red_sm, st>>>(scratch, red, rf, kp, er, q, an0,
-                                                               amp, mim, mim_pitch);
+  for (int cl = 0; cl < 2; ++cl) {
+    if (!red[cl].n) continue;
+    cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_sm[cl]);
+    lg_rows_reduce<<<dim3(red_rows[cl], red[cl].n), 512, red_sm[cl], st>>>(
+        scratch, red[cl], rf[cl], kp, er, q, an0, amp, mim, mim_pitch);
     ++nl;
   }
   if (spl.n) {
