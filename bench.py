@@ -765,9 +765,11 @@ def run_ours(args):
                    "form": "edge keypoints (maximum moment) + corner keypoints (minimum moment)"}
         cc.close()
 
-    serving = None
+    serving = serving1024 = None
     if args.serve_requests > 0 and args.workload == 1:
         serving = run_serving(args, local)
+    if args.serve1024_requests > 0 and args.workload == 1 and args.serve_requests > 0:
+        serving1024 = run_serving_1024(args, local)
 
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == 1:
@@ -805,6 +807,7 @@ def run_ours(args):
             "graph_form": graph,
             "two_lane_form": lanes,
             "serving": serving,
+            "serving_1024": serving1024,
             "rift_baseline": rift,
             "corners_form": corners,
             "stage_ms_per_step": stage_ms,
@@ -867,6 +870,36 @@ def run_serving(args, device: int):
             "rates": runs}
 
 
+def run_serving_1024(args, device: int):
+    """The served form at 1024^2 (the plain forms' size): open-loop Poisson arrivals of
+    1024^2 pairs (8 distinct pairs cycled, held in pinned host memory as a client would
+    hand them over) through the same continuous-batching loop, at offered rates around and
+    above what the plain single-pair forms sustain."""
+    import torch
+
+    import synth
+    from paper_2303_00319_gb300 import serve
+    pool = make_pairs([(H, W, synth.pair_seed(6, i)) for i in range(8)])
+    pool = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in pool]
+    srv = serve.Server(device=device, max_keypoints=MAX_KP, max_batch_pairs=8,
+                       hbm_budget=120 << 30, lanes=2, keep_resident=True)
+    warm = [serve.PairRequest(-1 - i, a, b) for i, (a, b) in enumerate(pool * 4)]
+    for r in warm:
+        srv.submit(r)
+    srv.drain()
+    for r in warm:
+        srv.release(r.rid)
+    runs = []
+    for k, rate in enumerate(float(x) for x in str(args.serve1024_rate).split(",")):
+        reqs = [serve.PairRequest(i, *pool[i % len(pool)]) for i in range(args.serve1024_requests)]
+        runs.append(serve.run_open_loop(srv, reqs, rate=rate, seed=17 + k))
+    srv.close()
+    return {"workload": "1024x1024 pairs (8 distinct, cycled; pinned host images), <= 5000 "
+                        "keypoints, up to 8 pairs per batch, two lanes, state resident until "
+                        "the client releases it on completion",
+            "rates": runs}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -886,6 +919,10 @@ def main():
     ap.add_argument("--serve-rate", default="50,100,200,400",
                     help="offered pairs/s, comma-separated for a sweep")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct pairs generated")
+    ap.add_argument("--serve1024-requests", type=int, default=600,
+                    help="requests per rate of the 1024^2 serving run (0: skip)")
+    ap.add_argument("--serve1024-rate", default="500,1000,2000,4000",
+                    help="offered pairs/s of the 1024^2 serving run")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the uneven-batch and 4096^2 summaries of the default line")
     args = ap.parse_args()

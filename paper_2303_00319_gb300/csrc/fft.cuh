@@ -241,6 +241,88 @@ __device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* 
   }
 }
 
+// The same pass with its input and output as functors: src(t, e) returns element e of
+// transform t, dst(t, e, v) stores it.  The first pass of a transform can read its input
+// from wherever it lives (a window applied on the fly, global memory) and the last pass
+// can write its output there, without a staging round trip through shared memory.
+template <int R, bool INV, bool BFAST, class Src, class Dst>
+__device__ __forceinline__ void fft_pass_io(Src&& src, Dst&& dst, const FftPass& ps,
+                                            const float2* __restrict__ ptw, const FastDiv& dnb,
+                                            int nb, int tid, int nthr) {
+  const int m = (int)ps.q.d;
+  const int ns = ps.ns;
+  const int total = nb * m;
+  const float2* __restrict__ pw = ptw + ps.tw;
+  for (int idx = tid; idx < total; idx += nthr) {
+    int b, j;
+    if (BFAST) { j = (int)dnb.div((unsigned)idx); b = idx - j * nb; }
+    else       { b = (int)ps.q.div((unsigned)idx); j = idx - b * m; }
+    const int k = j - (int)ps.k.div((unsigned)j) * ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src(b, j + r * m);
+    if (ns > 1) {
+      const float2* w = pw + k * (R - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(w, r - 1));
+    }
+    dft_r<R, INV>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst(b, base + r * ns, v[r]);
+  }
+}
+
+template <bool INV, bool BFAST, class Src, class Dst>
+__device__ __forceinline__ void fft_pass_io_r(int R, Src&& src, Dst&& dst, const FftPass& ps,
+                                              const float2* __restrict__ ptw,
+                                              const FastDiv& dnb, int nb, int tid, int nthr) {
+  switch (R) {
+    case 8: fft_pass_io<8, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 4: fft_pass_io<4, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 2: fft_pass_io<2, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 3: fft_pass_io<3, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 5: fft_pass_io<5, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 7: fft_pass_io<7, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 11: fft_pass_io<11, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 13: fft_pass_io<13, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    default: break;
+  }
+}
+
+// A direct (non-Bluestein) transform of nb transforms whose first pass reads src and whose
+// last pass writes dst (functors as fft_pass_io); the passes between use the shared-memory
+// buffers a and b (element e of transform t at t * bs + e * ks).  With last_smem the last
+// pass writes to shared memory instead, and the buffer holding the result is returned
+// (dst unused).  Ends with a __syncthreads().
+template <bool INV, bool BFAST, class Src, class Dst>
+__device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
+                                 const FftPasses& pl, const FastDiv& dnb, int nb, int bs,
+                                 int ks) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  auto lds = [&](float2* buf) {
+    return [buf, bs, ks](int t, int e) { return buf[t * bs + e * ks]; };
+  };
+  auto sts = [&](float2* buf) {
+    return [buf, bs, ks](int t, int e, float2 v) { buf[t * bs + e * ks] = v; };
+  };
+  const int last = pl.nst - 1;
+  for (int st = 0; st <= last; ++st) {
+    const FftPass& ps = pl.p[st];
+    if (st == last && !last_smem) {
+      if (st == 0) fft_pass_io_r<INV, BFAST>(ps.R, src, dst, ps, pl.ptw, dnb, nb, tid, nthr);
+      else fft_pass_io_r<INV, BFAST>(ps.R, lds(a), dst, ps, pl.ptw, dnb, nb, tid, nthr);
+    } else if (st == 0) {
+      fft_pass_io_r<INV, BFAST>(ps.R, src, sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
+    } else {
+      fft_pass_io_r<INV, BFAST>(ps.R, lds(a), sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
+    }
+    __syncthreads();
+    if (st < last || last_smem) { float2* t = a; a = b; b = t; }
+  }
+  return a;
+}
+
 // The Stockham passes of the plan's length-L transform; data starts in `a`, `b` is
 // scratch.  Returns the buffer holding the result.
 template <bool INV, bool BFAST>

@@ -453,6 +453,23 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
     const bool zt = t >= tc || c0 + t >= W || (zc && zc[o * W + c0 + t]);
     if (__syncthreads_and(zt)) continue;
     const float co = kp.cos_o[o], so = kp.sin_o[o];
+    float2* dst = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P;
+    if (!ph.chirp) {
+      // direct transform: the first pass reads F R_s and applies the window, the last
+      // pass writes the responses to HBM
+      auto src = [&](int t, int e) -> float2 {
+        if (c0 + t >= W) return make_float2(0.f, 0.f);
+        const float fu = fut[t], fv = fvt[e];
+        const float g = lg_window(__fmul_rn(fu, co), fv, so, lg_rinv(fu, fv));
+        const float2 x = base[e * tc + t];
+        return make_float2(x.x * g, x.y * g);
+      };
+      auto out = [&](int t, int e, float2 v) {
+        if (c0 + t < W) dst[(size_t)e * W + c0 + t] = v;
+      };
+      fft_direct_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+      continue;
+    }
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
       const int v = (int)dtc.div((unsigned)i), c = i - v * tc, u = c0 + c;
       float g = 0.f;
@@ -465,7 +482,6 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
     }
     __syncthreads();
     float2* res = fft_smem<true, true>(a, b, ph, dtc, tc, 1, tc);
-    float2* dst = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P;
     for (int i = threadIdx.x; i < nel; i += blockDim.x) {
       const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
       if (c0 + c < W) dst[(size_t)v * W + c0 + c] = res[i];
@@ -543,19 +559,31 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
 #pragma unroll
   for (int k = 0; k < RR_MAXPIX; ++k) { best[k] = -1.f; besto[k] = 0; }
 
+  const float2* rows = scratch + NS * NO * pb + (size_t)row * W;
   for (int o = 0; o < NO; ++o) {
-    for (int s = 0; s < NS; ++s) {
-      const float2* src = scratch + NS * NO * pb + ((size_t)s * NO + o) * P + (size_t)row * W;
-      // zero-window columns are not read (the column pass may not have written them)
+    float2* res;
+    if (!pw.chirp) {
+      // direct transform: the first pass loads the four scales' rows from HBM (zero-window
+      // columns are not read: the column pass may not have written them)
+      auto src = [&](int t, int e) -> float2 {
+        if (zc[o * W + e]) return make_float2(0.f, 0.f);
+        return __ldg(rows + ((size_t)t * NO + o) * P + e);
+      };
+      res = fft_direct_io<true, false>(src, [](int, int, float2) {}, true, a, b, pw,
+                                       fg.dtile[img], NS, L, 1);
+    } else {
+      for (int s = 0; s < NS; ++s) {
+        const float2* src = rows + ((size_t)s * NO + o) * P;
 #pragma unroll 4
-      for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        float2 v = make_float2(0.f, 0.f);
-        if (!zc[o * W + x]) v = __ldg(src + x);
-        a[s * L + x] = v;
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+          float2 v = make_float2(0.f, 0.f);
+          if (!zc[o * W + x]) v = __ldg(src + x);
+          a[s * L + x] = v;
+        }
       }
+      __syncthreads();
+      res = fft_smem<true, false>(a, b, pw, fg.dtile[img], NS, L, 1);
     }
-    __syncthreads();
-    float2* res = fft_smem<true, false>(a, b, pw, fg.dtile[img], NS, L, 1);
 #pragma unroll
     for (int k = 0; k < RR_MAXPIX; ++k) {
       int x = threadIdx.x + k * blockDim.x;

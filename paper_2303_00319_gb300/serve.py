@@ -39,7 +39,7 @@ from . import FLAG_AUTOTUNE, Context, default_params
 @dataclass
 class PairRequest:
     rid: int
-    a: np.ndarray            # float32 [H][W] in [0, 1]
+    a: np.ndarray            # float32 [H][W] in [0, 1] (or a pinned host tensor: no staging copy)
     b: np.ndarray
     arrival: float = 0.0     # seconds, host clock
     admitted: float = math.nan
@@ -49,7 +49,7 @@ class PairRequest:
 
     @property
     def pixels(self) -> int:
-        return int(self.a.size + self.b.size)
+        return int(np.prod(self.a.shape) + np.prod(self.b.shape))
 
 
 @dataclass
@@ -216,10 +216,14 @@ class Server:
                 r = batch[j // 2]
                 x = r.a if j % 2 == 0 else r.b
                 hw = tuple(x.shape)
-                ph = self._pinned_in.take(hw)
-                ph.numpy()[...] = x
                 d = self._dev_in.take(hw)
-                d.copy_(ph, non_blocking=True)
+                if isinstance(x, torch.Tensor) and x.is_pinned():
+                    ph = None                 # already in pinned host memory
+                    d.copy_(x, non_blocking=True)
+                else:
+                    ph = self._pinned_in.take(hw)
+                    ph.numpy()[...] = x
+                    d.copy_(ph, non_blocking=True)
                 imgs[j] = d
                 inputs.append((hw, ph, d))
             feats = [self._feats.take(0) for _ in imgs]
@@ -276,7 +280,8 @@ class Server:
                 self._matches.give(0, matches[i])
             self.finished.append(r)
         for hw, ph, d in lane.inputs:
-            self._pinned_in.give(hw, ph)
+            if ph is not None:
+                self._pinned_in.give(hw, ph)
             self._dev_in.give(hw, d)
         lane.batch, lane.event, lane.outputs, lane.inputs, lane.state = [], None, [], [], []
         return True
