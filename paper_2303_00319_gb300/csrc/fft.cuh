@@ -323,6 +323,41 @@ __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a
   return a;
 }
 
+// A Bluestein transform (pl.chirp != NULL) of nb transforms of length pl.n as two
+// length-L pass sequences: the forward sequence's first pass reads src(t, j) times c_j
+// (conj(c_j) for the inverse) for j < n and zeros beyond; the kernel product rides on the
+// first pass of the inverse sequence, whose last pass hands dst(t, k, X_k) the outputs
+// k < n times c_k (conj(c_k) for the inverse).  With last_smem the outputs stay in shared
+// memory WITHOUT that last chirp product (the caller applies it as it reads them) and the
+// buffer holding them is returned.  Ends with a __syncthreads().
+template <bool INV, bool BFAST, class Src, class Dst>
+__device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
+                                    const FftPasses& pl, const FastDiv& dnb, int nb, int bs,
+                                    int ks) {
+  const int n = pl.n;
+  const float2* __restrict__ chirp = pl.chirp;
+  auto s1 = [&](int t, int j) -> float2 {
+    if (j >= n) return make_float2(0.f, 0.f);
+    const float2 c = __ldg(chirp + j);
+    const float2 x = src(t, j);
+    return INV ? cmulc(x, c) : cmul(x, c);
+  };
+  float2* r1 = fft_direct_io<false, BFAST>(s1, [](int, int, float2) {}, true, a, b, pl, dnb, nb,
+                                           bs, ks);
+  float2* o = (r1 == a) ? b : a;
+  const float2* __restrict__ kern = INV ? pl.kern_inv : pl.kern_fwd;
+  auto s2 = [r1, kern, bs, ks](int t, int j) -> float2 {
+    return cmul(r1[t * bs + j * ks], __ldg(kern + j));
+  };
+  auto d2 = [&](int t, int k, float2 v) {
+    if (k < n) {
+      const float2 c = __ldg(chirp + k);
+      dst(t, k, INV ? cmulc(v, c) : cmul(v, c));
+    }
+  };
+  return fft_direct_io<true, BFAST>(s2, d2, last_smem, r1, o, pl, dnb, nb, bs, ks);
+}
+
 // The Stockham passes of the plan's length-L transform; data starts in `a`, `b` is
 // scratch.  Returns the buffer holding the result.
 template <bool INV, bool BFAST>

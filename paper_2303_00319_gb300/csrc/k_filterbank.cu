@@ -454,38 +454,21 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
     if (__syncthreads_and(zt)) continue;
     const float co = kp.cos_o[o], so = kp.sin_o[o];
     float2* dst = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P;
-    if (!ph.chirp) {
-      // direct transform: the first pass reads F R_s and applies the window, the last
-      // pass writes the responses to HBM
-      auto src = [&](int t, int e) -> float2 {
-        if (c0 + t >= W) return make_float2(0.f, 0.f);
-        const float fu = fut[t], fv = fvt[e];
-        const float g = lg_window(__fmul_rn(fu, co), fv, so, lg_rinv(fu, fv));
-        const float2 x = base[e * tc + t];
-        return make_float2(x.x * g, x.y * g);
-      };
-      auto out = [&](int t, int e, float2 v) {
-        if (c0 + t < W) dst[(size_t)e * W + c0 + t] = v;
-      };
-      fft_direct_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
-      continue;
-    }
-    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-      const int v = (int)dtc.div((unsigned)i), c = i - v * tc, u = c0 + c;
-      float g = 0.f;
-      if (u < W) {
-        const float fu = fut[c], fv = fvt[v];
-        g = lg_window(__fmul_rn(fu, co), fv, so, lg_rinv(fu, fv));
-      }
-      float2 x = base[i];
-      a[i] = make_float2(x.x * g, x.y * g);
-    }
-    __syncthreads();
-    float2* res = fft_smem<true, true>(a, b, ph, dtc, tc, 1, tc);
-    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-      const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
-      if (c0 + c < W) dst[(size_t)v * W + c0 + c] = res[i];
-    }
+    // the first pass reads F R_s and applies the window, the last pass writes the
+    // responses to HBM (through the chirp products and the convolution for Bluestein
+    // heights)
+    auto src = [&](int t, int e) -> float2 {
+      if (c0 + t >= W) return make_float2(0.f, 0.f);
+      const float fu = fut[t], fv = fvt[e];
+      const float g = lg_window(__fmul_rn(fu, co), fv, so, lg_rinv(fu, fv));
+      const float2 x = base[e * tc + t];
+      return make_float2(x.x * g, x.y * g);
+    };
+    auto out = [&](int t, int e, float2 v) {
+      if (c0 + t < W) dst[(size_t)e * W + c0 + t] = v;
+    };
+    if (!ph.chirp) fft_direct_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+    else fft_bluestein_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
     // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
   }
 }
@@ -555,35 +538,23 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
   const size_t P = (size_t)H * W;
   const size_t pb = (size_t)gr.poff[img];
   float best[RR_MAXPIX];
-  int besto[RR_MAXPIX];
+  unsigned besto = 0;   // the argmax orientation of pixel k in bits 3k..3k+2
 #pragma unroll
-  for (int k = 0; k < RR_MAXPIX; ++k) { best[k] = -1.f; besto[k] = 0; }
+  for (int k = 0; k < RR_MAXPIX; ++k) best[k] = -1.f;
 
   const float2* rows = scratch + NS * NO * pb + (size_t)row * W;
   for (int o = 0; o < NO; ++o) {
-    float2* res;
-    if (!pw.chirp) {
-      // direct transform: the first pass loads the four scales' rows from HBM (zero-window
-      // columns are not read: the column pass may not have written them)
-      auto src = [&](int t, int e) -> float2 {
-        if (zc[o * W + e]) return make_float2(0.f, 0.f);
-        return __ldg(rows + ((size_t)t * NO + o) * P + e);
-      };
-      res = fft_direct_io<true, false>(src, [](int, int, float2) {}, true, a, b, pw,
-                                       fg.dtile[img], NS, L, 1);
-    } else {
-      for (int s = 0; s < NS; ++s) {
-        const float2* src = rows + ((size_t)s * NO + o) * P;
-#pragma unroll 4
-        for (int x = threadIdx.x; x < W; x += blockDim.x) {
-          float2 v = make_float2(0.f, 0.f);
-          if (!zc[o * W + x]) v = __ldg(src + x);
-          a[s * L + x] = v;
-        }
-      }
-      __syncthreads();
-      res = fft_smem<true, false>(a, b, pw, fg.dtile[img], NS, L, 1);
-    }
+    // the first pass loads the four scales' rows from HBM (zero-window columns are not
+    // read: the column pass may not have written them); for a Bluestein width the result
+    // still lacks its chirp product, applied as the pixels are read
+    auto src = [&](int t, int e) -> float2 {
+      if (zc[o * W + e]) return make_float2(0.f, 0.f);
+      return __ldg(rows + ((size_t)t * NO + o) * P + e);
+    };
+    auto nop = [](int, int, float2) {};
+    float2* res = !pw.chirp
+                      ? fft_direct_io<true, false>(src, nop, true, a, b, pw, fg.dtile[img], NS, L, 1)
+                      : fft_bluestein_io<true, false>(src, nop, true, a, b, pw, fg.dtile[img], NS, L, 1);
 #pragma unroll
     for (int k = 0; k < RR_MAXPIX; ++k) {
       int x = threadIdx.x + k * blockDim.x;
@@ -591,6 +562,11 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
       float2 z[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) z[s] = res[s * L + x];
+      if (pw.chirp) {
+        const float2 c = __ldg(pw.chirp + x);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) z[s] = cmulc(z[s], c);
+      }
       float energy, q, an0, sum_an;
       reduce_pixel(z, kp, energy, q, an0, sum_an);
       size_t off = NO * pb + o * P + (size_t)row * W + x;
@@ -598,7 +574,10 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
       q_out[off] = q;
       an0_out[off] = an0;
       if (amp_out) amp_out[off] = sum_an;
-      if (sum_an > best[k]) { best[k] = sum_an; besto[k] = o; }   // lowest o on ties
+      if (sum_an > best[k]) {   // lowest o on ties
+        best[k] = sum_an;
+        besto = (besto & ~(7u << (3 * k))) | ((unsigned)o << (3 * k));
+      }
     }
     __syncthreads();
   }
@@ -606,7 +585,7 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
   for (int k = 0; k < RR_MAXPIX; ++k) {
     int x = threadIdx.x + k * blockDim.x;
     if (x >= W) break;
-    mim_out[((size_t)gr.mrow[img] + row) * mim_pitch + x] = (unsigned char)besto[k];
+    mim_out[((size_t)gr.mrow[img] + row) * mim_pitch + x] = (unsigned char)((besto >> (3 * k)) & 7u);
   }
 }
 
@@ -629,12 +608,14 @@ __global__ void __launch_bounds__(512) lg_rows_split(float2* __restrict__ scratc
   for (int o = 0; o < NO; ++o) {
     float2* rowp = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P +
                    (size_t)row * W;
-    for (int x = threadIdx.x; x < W; x += blockDim.x)
-      a[x] = zc[o * W + x] ? make_float2(0.f, 0.f) : rowp[x];
-    __syncthreads();
-    float2* res = fft_smem<true, false>(a, b, pw, fg.dtile[img], 1, pw.L, 1);
-    for (int x = threadIdx.x; x < W; x += blockDim.x) rowp[x] = res[x];
-    __syncthreads();   // the stores have read res before the next orientation's loads
+    // in place: the first pass reads the row (barriers separate it from the last pass,
+    // which writes the row back)
+    auto src = [&](int, int e) -> float2 {
+      return zc[o * W + e] ? make_float2(0.f, 0.f) : rowp[e];
+    };
+    auto out = [&](int, int e, float2 v) { rowp[e] = v; };
+    if (!pw.chirp) fft_direct_io<true, false>(src, out, false, a, b, pw, fg.dtile[img], 1, pw.L, 1);
+    else fft_bluestein_io<true, false>(src, out, false, a, b, pw, fg.dtile[img], 1, pw.L, 1);
   }
 }
 
