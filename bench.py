@@ -278,7 +278,7 @@ def parity_summary(pkg, dev, pair, oa, ob, of_match):
             kp_only += 1
             kp_cert += int(bool(mo["kp_uncertain"][q[1], q[0]]))
     out["max_rel_err"] = maps
-    out["tolerance"] = "1e-4 relative above each floor (A_o 2.5e-3, |EO0| 1e-2, q 1e-3 with A's floor, Er 5e-2 with its A/X conditioning, PC 1.0, M 2e-2); T_o 1e-5; M 5e-6 in FAST's normalised units"
+    out["tolerance"] = "1e-4 relative above each floor (A_o 2.5e-3, |EO0| 1e-2, q 1e-3 with A's floor, Er 5e-2 with its A/X conditioning, PC 1.0), M 2e-4 above 2e-2 (quadratic in PC); T_o 1e-4 relative; M 5e-6 in FAST's normalised units"
     out["mim"] = {"pixels_differing": mim_diff, "of_which_not_near_ties": mim_bad,
                   "oracle_near_tie_pixels": near_px}
     out["keypoints"] = {"in_one_list_only": kp_only, "of_which_certified": kp_cert,

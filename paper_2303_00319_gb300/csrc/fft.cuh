@@ -1,4 +1,4 @@
-// Batched mixed-radix Stockham FFT over shared memory (radices 2, 3, 4, 5, 7, 8, 11, 13).
+// Batched mixed-radix Stockham FFT over shared memory (radices 2, 3, 4, 5, 7, 8, 9, 11, 13, 16).
 //
 // A Stockham (auto-sorting) pass of radix R over an n-point transform, with ns the
 // product of the radices already applied, maps butterfly j (0 <= j < n/R, k = j mod ns)
@@ -14,7 +14,7 @@
 
 namespace rift2 {
 
-constexpr int FFT_MAX_STAGES = 12;   // 13-smooth lengths below 8192 need at most 9 passes
+constexpr int FFT_MAX_STAGES = 12;   // 13-smooth lengths up to 10240 need at most 9 passes
 
 // Unsigned division by a run-time divisor d >= 1 for dividends below 2^31: the
 // multiply-shift method (Granlund and Montgomery), q = (umulhi(n, m) + n) >> s with
@@ -57,7 +57,8 @@ struct FftPasses {
 // by Bluestein's chirp-z identity when n has a larger prime factor.  With c_j =
 // exp(-i pi j^2 / n), jk = (j^2 + k^2 - (k - j)^2) / 2 turns the DFT into a convolution:
 //     X_k = c_k sum_j (x_j c_j) conj(c_(k-j))          (forward; the inverse conjugates c)
-// evaluated as a cyclic convolution of length m >= 2n - 1 (m 13-smooth) with FFTs of
+// evaluated as a cyclic convolution of length m >= 2n - 1 (m 13-smooth, chosen by the
+// planner's cost estimate, at most 2.5 n) with FFTs of
 // length m: the radices and twiddles below are then those of m, and kern_* hold
 // FFT_m(conj(c)) / m (forward) and FFT_m(c) / m (inverse), c extended cyclically
 // (c_(m-j) = c_j for 0 < j < n, 0 between).  All tables are generated in FP64.
@@ -71,6 +72,7 @@ struct FftPlan {
   const float2* kern_fwd;   // Bluestein only: [m]
   const float2* kern_inv;   // Bluestein only: [m]
   const FftPasses* dev;     // device: the shared-memory kernels' copy
+  const FftPasses* dev_r;   // device: the same transform without radix 16 (row kernels)
 };
 
 // Per-image transform data of one shared-memory-path launch over a Group: the device plan
@@ -147,11 +149,15 @@ __device__ constexpr float kCos11[11] = {1.000000000e+00f, 8.412535328e-01f, 4.1
 __device__ constexpr float kSin11[11] = {0.000000000e+00f, 5.406408175e-01f, 9.096319954e-01f, 9.898214419e-01f, 7.557495744e-01f, 2.817325568e-01f, -2.817325568e-01f, -7.557495744e-01f, -9.898214419e-01f, -9.096319954e-01f, -5.406408175e-01f};
 __device__ constexpr float kCos13[13] = {1.000000000e+00f, 8.854560257e-01f, 5.680647467e-01f, 1.205366803e-01f, -3.546048870e-01f, -7.485107482e-01f, -9.709418174e-01f, -9.709418174e-01f, -7.485107482e-01f, -3.546048870e-01f, 1.205366803e-01f, 5.680647467e-01f, 8.854560257e-01f};
 __device__ constexpr float kSin13[13] = {0.000000000e+00f, 4.647231720e-01f, 8.229838659e-01f, 9.927088741e-01f, 9.350162427e-01f, 6.631226582e-01f, 2.393156643e-01f, -2.393156643e-01f, -6.631226582e-01f, -9.350162427e-01f, -9.927088741e-01f, -8.229838659e-01f, -4.647231720e-01f};
+// radix 9 (3 x 3 as one pass): the same symmetric-pair DFT as the odd primes
+__device__ constexpr float kCos9[9] = {1.000000000e+00f, 7.660444431e-01f, 1.736481777e-01f, -5.000000000e-01f, -9.396926208e-01f, -9.396926208e-01f, -5.000000000e-01f, 1.736481777e-01f, 7.660444431e-01f};
+__device__ constexpr float kSin9[9] = {0.000000000e+00f, 6.427876097e-01f, 9.848077530e-01f, 8.660254038e-01f, 3.420201433e-01f, -3.420201433e-01f, -8.660254038e-01f, -9.848077530e-01f, -6.427876097e-01f};
 template <int R>
 __device__ __forceinline__ float odd_cos(int j) {
   if constexpr (R == 3) return kCos3[j];
   else if constexpr (R == 5) return kCos5[j];
   else if constexpr (R == 7) return kCos7[j];
+  else if constexpr (R == 9) return kCos9[j];
   else if constexpr (R == 11) return kCos11[j];
   else return kCos13[j];
 }
@@ -160,8 +166,51 @@ __device__ __forceinline__ float odd_sin(int j) {
   if constexpr (R == 3) return kSin3[j];
   else if constexpr (R == 5) return kSin5[j];
   else if constexpr (R == 7) return kSin7[j];
+  else if constexpr (R == 9) return kSin9[j];
   else if constexpr (R == 11) return kSin11[j];
   else return kSin13[j];
+}
+
+// 16-point DFT as 4 x 4: four 4-point DFTs over the residues p of the index mod 4, the
+// products by W16^(p k1) (conjugated for the inverse), four 4-point DFTs across p; output
+// k1 + 4 k2.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  float2 y[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    float2 t[4] = {v[p], v[p + 4], v[p + 8], v[p + 12]};
+    dft4<INV>(t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y[p][k] = t[k];
+  }
+  // W16^e = (cos(pi e / 8), -sin(pi e / 8)) for e = p k1 in 0..9
+  auto tw = [&](float2 a, int e) -> float2 {
+    float cr, ci;
+    switch (e) {
+      case 1: cr = c1; ci = s1; break;
+      case 2: cr = h; ci = h; break;
+      case 3: cr = s1; ci = c1; break;
+      case 4: cr = 0.f; ci = 1.f; break;
+      case 6: cr = -h; ci = h; break;
+      case 9: cr = -c1; ci = -s1; break;
+      default: return a;
+    }
+    if (!INV) ci = -ci;
+    return make_float2(a.x * cr - a.y * ci, a.x * ci + a.y * cr);
+  };
+#pragma unroll
+  for (int p = 1; p < 4; ++p)
+#pragma unroll
+    for (int k = 1; k < 4; ++k) y[p][k] = tw(y[p][k], p * k);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float2 t[4] = {y[0][k], y[1][k], y[2][k], y[3][k]};
+    dft4<INV>(t);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[k + 4 * q] = t[q];
+  }
 }
 
 // Odd radix R: with a_m = x_m + x_{R-m}, b_m = x_m - x_{R-m} (m = 1 .. (R-1)/2),
@@ -204,6 +253,7 @@ __device__ __forceinline__ void dft_r(float2* v) {
   if constexpr (R == 2) dft2<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
   else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
   else dft_odd<R, INV>(v);
 }
 
@@ -273,12 +323,17 @@ __device__ __forceinline__ void fft_pass_io(Src&& src, Dst&& dst, const FftPass&
   }
 }
 
-template <bool INV, bool BFAST, class Src, class Dst>
+// R16: the plan may hold radix-16 passes (kernels with the registers for them).
+template <bool INV, bool BFAST, bool R16, class Src, class Dst>
 __device__ __forceinline__ void fft_pass_io_r(int R, Src&& src, Dst&& dst, const FftPass& ps,
                                               const float2* __restrict__ ptw,
                                               const FastDiv& dnb, int nb, int tid, int nthr) {
   switch (R) {
+    case 16:
+      if constexpr (R16) fft_pass_io<16, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr);
+      break;
     case 8: fft_pass_io<8, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 9: fft_pass_io<9, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
     case 4: fft_pass_io<4, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
     case 2: fft_pass_io<2, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
     case 3: fft_pass_io<3, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
@@ -295,27 +350,38 @@ __device__ __forceinline__ void fft_pass_io_r(int R, Src&& src, Dst&& dst, const
 // buffers a and b (element e of transform t at t * bs + e * ks).  With last_smem the last
 // pass writes to shared memory instead, and the buffer holding the result is returned
 // (dst unused).  Ends with a __syncthreads().
-template <bool INV, bool BFAST, class Src, class Dst>
+// PAD > 0 (rows, ks == 1): element e of a slot sits at e + (e >> PAD), which spreads the
+// first pass's radix-strided stores over the shared-memory banks (slots then need
+// L + (L >> PAD) + 1 entries; pad_at() gives the position).
+template <int PAD>
+__host__ __device__ __forceinline__ int pad_at(int e) { return PAD > 0 ? e + (e >> PAD) : e; }
+
+template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, class Src, class Dst>
 __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
                                  const FftPasses& pl, const FastDiv& dnb, int nb, int bs,
                                  int ks) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   auto lds = [&](float2* buf) {
-    return [buf, bs, ks](int t, int e) { return buf[t * bs + e * ks]; };
+    return [buf, bs, ks](int t, int e) {
+      return PAD > 0 ? buf[t * bs + pad_at<PAD>(e)] : buf[t * bs + e * ks];
+    };
   };
   auto sts = [&](float2* buf) {
-    return [buf, bs, ks](int t, int e, float2 v) { buf[t * bs + e * ks] = v; };
+    return [buf, bs, ks](int t, int e, float2 v) {
+      if (PAD > 0) buf[t * bs + pad_at<PAD>(e)] = v;
+      else buf[t * bs + e * ks] = v;
+    };
   };
   const int last = pl.nst - 1;
   for (int st = 0; st <= last; ++st) {
     const FftPass& ps = pl.p[st];
     if (st == last && !last_smem) {
-      if (st == 0) fft_pass_io_r<INV, BFAST>(ps.R, src, dst, ps, pl.ptw, dnb, nb, tid, nthr);
-      else fft_pass_io_r<INV, BFAST>(ps.R, lds(a), dst, ps, pl.ptw, dnb, nb, tid, nthr);
+      if (st == 0) fft_pass_io_r<INV, BFAST, R16>(ps.R, src, dst, ps, pl.ptw, dnb, nb, tid, nthr);
+      else fft_pass_io_r<INV, BFAST, R16>(ps.R, lds(a), dst, ps, pl.ptw, dnb, nb, tid, nthr);
     } else if (st == 0) {
-      fft_pass_io_r<INV, BFAST>(ps.R, src, sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
+      fft_pass_io_r<INV, BFAST, R16>(ps.R, src, sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
     } else {
-      fft_pass_io_r<INV, BFAST>(ps.R, lds(a), sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
+      fft_pass_io_r<INV, BFAST, R16>(ps.R, lds(a), sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
     }
     __syncthreads();
     if (st < last || last_smem) { float2* t = a; a = b; b = t; }
@@ -330,7 +396,7 @@ __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a
 // k < n times c_k (conj(c_k) for the inverse).  With last_smem the outputs stay in shared
 // memory WITHOUT that last chirp product (the caller applies it as it reads them) and the
 // buffer holding them is returned.  Ends with a __syncthreads().
-template <bool INV, bool BFAST, class Src, class Dst>
+template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, class Src, class Dst>
 __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
                                     const FftPasses& pl, const FastDiv& dnb, int nb, int bs,
                                     int ks) {
@@ -342,12 +408,13 @@ __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2
     const float2 x = src(t, j);
     return INV ? cmulc(x, c) : cmul(x, c);
   };
-  float2* r1 = fft_direct_io<false, BFAST>(s1, [](int, int, float2) {}, true, a, b, pl, dnb, nb,
-                                           bs, ks);
+  float2* r1 = fft_direct_io<false, BFAST, PAD, R16>(s1, [](int, int, float2) {}, true, a, b, pl, dnb,
+                                                nb, bs, ks);
   float2* o = (r1 == a) ? b : a;
   const float2* __restrict__ kern = INV ? pl.kern_inv : pl.kern_fwd;
   auto s2 = [r1, kern, bs, ks](int t, int j) -> float2 {
-    return cmul(r1[t * bs + j * ks], __ldg(kern + j));
+    const float2 x = PAD > 0 ? r1[t * bs + pad_at<PAD>(j)] : r1[t * bs + j * ks];
+    return cmul(x, __ldg(kern + j));
   };
   auto d2 = [&](int t, int k, float2 v) {
     if (k < n) {
@@ -355,7 +422,7 @@ __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2
       dst(t, k, INV ? cmulc(v, c) : cmul(v, c));
     }
   };
-  return fft_direct_io<true, BFAST>(s2, d2, last_smem, r1, o, pl, dnb, nb, bs, ks);
+  return fft_direct_io<true, BFAST, PAD, R16>(s2, d2, last_smem, r1, o, pl, dnb, nb, bs, ks);
 }
 
 // The Stockham passes of the plan's length-L transform; data starts in `a`, `b` is
@@ -367,7 +434,9 @@ __device__ float2* fft_passes(float2* a, float2* b, const FftPasses& pl, const F
   for (int st = 0; st < pl.nst; ++st) {
     const FftPass& ps = pl.p[st];
     switch (ps.R) {
+      case 16: fft_pass<16, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
       case 8: fft_pass<8, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
+      case 9: fft_pass<9, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
       case 4: fft_pass<4, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
       case 2: fft_pass<2, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
       case 3: fft_pass<3, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;

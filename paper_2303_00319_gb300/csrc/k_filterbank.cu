@@ -514,7 +514,15 @@ __device__ __forceinline__ void reduce_pixel(const float2 (&z)[NS], const KParam
 // Row pass of the inverse with the fused per-pixel reductions.  One row per CTA;
 // for each orientation the four scales are transformed together.
 constexpr int RR_MAXPIX = 8;   // pixels per thread: W <= 8 * blockDim.x
+// Row transforms' shared-memory slots: element e at e + (e >> RR_PAD) (conflict-free radix
+// strides in the first pass), so a slot of a length-L transform holds row_slot(L) entries.
+constexpr int RR_PAD = 4;
+__host__ __device__ __forceinline__ int row_slot(int L) { return L + (L >> RR_PAD) + 1; }
 
+// HALVES: the four scales are transformed two at a time and the first two parked in
+// shared memory ([2][W], chirp applied), which halves the transform buffers (two CTAs per
+// SM for wider rows, and rows too wide for four scales at once without the split pass).
+template <bool HALVES>
 __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restrict__ scratch,
                                                       const __grid_constant__ Group gr,
                                                       const __grid_constant__ FftGroup fg,
@@ -526,15 +534,18 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
                                                       unsigned char* __restrict__ mim_out,
                                                       int mim_pitch) {
   extern __shared__ float2 sm[];
+  constexpr int NT = HALVES ? NS / 2 : NS;   // transforms per pass sequence
   const int row = blockIdx.x;
   const int img = blockIdx.y;
   const int H = gr.H[img], W = gr.W[img];
   if (row >= H) return;
   const FftPasses& pw = *fg.pass[img];
   const unsigned char* __restrict__ zc = fg.zc[img];
-  const int L = pw.L;   // a row transform's slot (> W for Bluestein plans)
+  const float2* __restrict__ chirp = pw.chirp;
+  const int L = row_slot(pw.L);   // a row transform's padded slot (pw.L > W for Bluestein)
   float2* a = sm;
-  float2* b = sm + NS * L;
+  float2* b = sm + NT * L;
+  float2* stash = sm + 2 * NT * L;   // HALVES: scales 0 and 1 of the row
   const size_t P = (size_t)H * W;
   const size_t pb = (size_t)gr.poff[img];
   float best[RR_MAXPIX];
@@ -543,29 +554,46 @@ __global__ void __launch_bounds__(512, 2) lg_rows_reduce(const float2* __restric
   for (int k = 0; k < RR_MAXPIX; ++k) best[k] = -1.f;
 
   const float2* rows = scratch + NS * NO * pb + (size_t)row * W;
-  for (int o = 0; o < NO; ++o) {
-    // the first pass loads the four scales' rows from HBM (zero-window columns are not
-    // read: the column pass may not have written them); for a Bluestein width the result
-    // still lacks its chirp product, applied as the pixels are read
+  auto nop = [](int, int, float2) {};
+  // the transforms of scales s0 .. s0 + NT - 1: the first pass loads their rows from HBM
+  // (zero-window columns are not read: the column pass may not have written them); for a
+  // Bluestein width the result still lacks its chirp product, applied as it is read
+  auto transform = [&](int o, int s0) -> float2* {
     auto src = [&](int t, int e) -> float2 {
       if (zc[o * W + e]) return make_float2(0.f, 0.f);
-      return __ldg(rows + ((size_t)t * NO + o) * P + e);
+      return __ldg(rows + ((size_t)(s0 + t) * NO + o) * P + e);
     };
-    auto nop = [](int, int, float2) {};
-    float2* res = !pw.chirp
-                      ? fft_direct_io<true, false>(src, nop, true, a, b, pw, fg.dtile[img], NS, L, 1)
-                      : fft_bluestein_io<true, false>(src, nop, true, a, b, pw, fg.dtile[img], NS, L, 1);
+    return !chirp ? fft_direct_io<true, false, RR_PAD, false>(src, nop, true, a, b, pw, fg.dtile[img], NT, L, 1)
+                  : fft_bluestein_io<true, false, RR_PAD, false>(src, nop, true, a, b, pw, fg.dtile[img], NT, L, 1);
+  };
+  for (int o = 0; o < NO; ++o) {
+    float2* res = transform(o, 0);
+    if constexpr (HALVES) {
+      for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const float2 c = chirp ? __ldg(chirp + x) : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const float2 v = res[t * L + pad_at<RR_PAD>(x)];
+          stash[t * W + x] = chirp ? cmulc(v, c) : v;
+        }
+      }
+      __syncthreads();
+      res = transform(o, NT);
+    }
 #pragma unroll
     for (int k = 0; k < RR_MAXPIX; ++k) {
       int x = threadIdx.x + k * blockDim.x;
       if (x >= W) break;
       float2 z[NS];
+      const float2 c = chirp ? __ldg(chirp + x) : make_float2(1.f, 0.f);
 #pragma unroll
-      for (int s = 0; s < NS; ++s) z[s] = res[s * L + x];
-      if (pw.chirp) {
-        const float2 c = __ldg(pw.chirp + x);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) z[s] = cmulc(z[s], c);
+      for (int s = 0; s < NS; ++s) {
+        if (HALVES && s < NT) {
+          z[s] = stash[s * W + x];
+        } else {
+          const float2 v = res[(s - (HALVES ? NT : 0)) * L + pad_at<RR_PAD>(x)];
+          z[s] = chirp ? cmulc(v, c) : v;
+        }
       }
       float energy, q, an0, sum_an;
       reduce_pixel(z, kp, energy, q, an0, sum_an);
@@ -603,7 +631,8 @@ __global__ void __launch_bounds__(512) lg_rows_split(float2* __restrict__ scratc
   const FftPasses& pw = *fg.pass[img];
   const unsigned char* __restrict__ zc = fg.zc[img];
   float2* a = sm;
-  float2* b = sm + pw.L;
+  const int Ls = row_slot(pw.L);
+  float2* b = sm + Ls;
   const size_t P = (size_t)H * W;
   for (int o = 0; o < NO; ++o) {
     float2* rowp = scratch + (size_t)NS * NO * gr.poff[img] + ((size_t)s * NO + o) * P +
@@ -614,8 +643,8 @@ __global__ void __launch_bounds__(512) lg_rows_split(float2* __restrict__ scratc
       return zc[o * W + e] ? make_float2(0.f, 0.f) : rowp[e];
     };
     auto out = [&](int, int e, float2 v) { rowp[e] = v; };
-    if (!pw.chirp) fft_direct_io<true, false>(src, out, false, a, b, pw, fg.dtile[img], 1, pw.L, 1);
-    else fft_bluestein_io<true, false>(src, out, false, a, b, pw, fg.dtile[img], 1, pw.L, 1);
+    if (!pw.chirp) fft_direct_io<true, false, RR_PAD>(src, out, false, a, b, pw, fg.dtile[img], 1, Ls, 1);
+    else fft_bluestein_io<true, false, RR_PAD>(src, out, false, a, b, pw, fg.dtile[img], 1, Ls, 1);
   }
 }
 
@@ -1179,13 +1208,13 @@ void for_runs(const Group& gr, F&& f) {
 
 // Appends image i of gr to the shared-memory launch's tables.
 void sub_add(Group& sub, FftGroup& sf, const Group& gr, int i, const FftPlan& pl, int tile,
-             const unsigned char* zc) {
+             const unsigned char* zc, bool rows = false) {
   const int k = sub.n++;
   sub.H[k] = gr.H[i];
   sub.W[k] = gr.W[i];
   sub.poff[k] = gr.poff[i];
   sub.mrow[k] = gr.mrow[i];
-  sf.pass[k] = pl.dev;
+  sf.pass[k] = rows ? pl.dev_r : pl.dev;
   sf.tile[k] = tile;
   sf.dtile[k] = FastDiv((unsigned)(tile > 0 ? tile : 1));
   sf.zc[k] = zc;
@@ -1355,8 +1384,9 @@ cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
                            const KParams& kp, float* er, float* q, float* an0, float* amp,
                            unsigned char* mim, int mim_pitch, cudaStream_t st, int* launches) {
   int nl = 0;
-  // red[0]: rows whose shared memory lets two CTAs share an SM, red[1]: the others (one
-  // launch each, so that a wide image does not set the occupancy of the narrow ones)
+  // red[0]: rows whose four scales fit two CTAs per SM; red[1]: wider rows, transformed
+  // two scales at a time (one launch each, so that a wide image does not set the
+  // occupancy of the narrow ones); spl: rows too wide even for that
   Group red[2] = {}, spl{};
   FftGroup rf[2] = {}, sf{};
   int red_rows[2] = {0, 0}, spl_rows = 0;
@@ -1394,27 +1424,35 @@ cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
       ++nl;
       return;
     }
-    const size_t sm3 = 2 * (size_t)NS * pw.m * sizeof(float2);
-    if (sm3 <= 227 * 1024 && W <= RR_MAXPIX * 512) {
-      const int cl = sm3 <= 113 * 1024 ? 0 : 1;
-      for (int k = 0; k < cnt; ++k) sub_add(red[cl], rf[cl], gr, i0 + k, pw, 0, zc);
+    const size_t sm_full = 2 * (size_t)NS * row_slot(pw.m) * sizeof(float2);
+    const size_t sm_half = (2 * (size_t)(NS / 2) * row_slot(pw.m) + 2 * (size_t)W) * sizeof(float2);
+    const int cl = sm_full <= 113 * 1024 ? 0 : (sm_half <= 227 * 1024 ? 1 : 2);
+    if (cl < 2 && W <= RR_MAXPIX * 512) {
+      for (int k = 0; k < cnt; ++k) sub_add(red[cl], rf[cl], gr, i0 + k, pw, 0, zc, true);
       red_rows[cl] = max_of(red_rows[cl], H);
-      red_sm[cl] = max_of(red_sm[cl], sm3);
+      red_sm[cl] = max_of(red_sm[cl], cl == 0 ? sm_full : sm_half);
     } else {
       // rows too wide for four scales in shared memory: transform each (row, scale) in
       // place, then reduce the pixels from the transformed responses
       for (int k = 0; k < cnt; ++k) sub_add(spl, sf, gr, i0 + k, pw, 0, zc);
       spl_rows = max_of(spl_rows, H);
       spl_px = max_of(spl_px, (long long)H * W);
-      spl_sm = max_of(spl_sm, 2 * (size_t)pw.m * sizeof(float2));
+      spl_sm = max_of(spl_sm, 2 * (size_t)row_slot(pw.m) * sizeof(float2));
     }
   });
   if (err != cudaSuccess) return err;
-  for (int cl = 0; cl < 2; ++cl) {
-    if (!red[cl].n) continue;
-    cudaFuncSetAttribute(lg_rows_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_sm[cl]);
-    lg_rows_reduce<<<dim3(red_rows[cl], red[cl].n), 512, red_sm[cl], st>>>(
-        scratch, red[cl], rf[cl], kp, er, q, an0, amp, mim, mim_pitch);
+  if (red[0].n) {
+    cudaFuncSetAttribute(lg_rows_reduce<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)red_sm[0]);
+    lg_rows_reduce<false><<<dim3(red_rows[0], red[0].n), 512, red_sm[0], st>>>(
+        scratch, red[0], rf[0], kp, er, q, an0, amp, mim, mim_pitch);
+    ++nl;
+  }
+  if (red[1].n) {
+    cudaFuncSetAttribute(lg_rows_reduce<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)red_sm[1]);
+    lg_rows_reduce<true><<<dim3(red_rows[1], red[1].n), 512, red_sm[1], st>>>(
+        scratch, red[1], rf[1], kp, er, q, an0, amp, mim, mim_pitch);
     ++nl;
   }
   if (spl.n) {

@@ -65,6 +65,7 @@ struct rift2_ctx {
   long long wait_iters = 1ll << 24;   // first-wait limit of the descriptor kernel's staging
   std::map<int, FftPlan> plans;
   std::vector<float2*> pass_tw;   // per-pass twiddle tables of the plans (freed at destroy)
+  std::vector<FftPasses*> pass_dev;   // the plans' device pass tables (freed at destroy)
   std::map<std::pair<int, int>, unsigned char*> zero_cols;   // (H, W) -> [NO][W]
   std::map<std::pair<int, int>, int> col_tiles;              // (H, W) -> tuned column tile
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -105,32 +106,129 @@ struct DeviceGuard {
     }                                                                      \
   } while (0)
 
-bool factor_plan(int n, FftPlan& pl) {
+// The planner.  A pass of the shared-memory transforms costs about the same per element
+// whatever its radix (index arithmetic, a shared-memory load and store, the twiddle
+// product) plus a butterfly whose cost per element grows with the radix; pass_cost() is
+// that sum in units of instructions per element (counted from the butterflies and the
+// pass loop).  A length's radices minimise the summed cost: the power-of-two part by a
+// small dynamic program over radices 16, 8, 4, 2, powers of 3 as 9s (and one 3), then
+// 5, 7, 11, 13; power-of-two radices run first.  The choice is a pure function of n.
+double pass_cost(int R) {
+  switch (R) {
+    case 2: return 18.5;
+    case 4: return 16.0;
+    case 8: return 15.9;
+    case 16: return 17.2;
+    case 3: return 17.0;
+    case 9: return 20.7;
+    case 5: return 18.0;
+    case 7: return 19.1;
+    case 11: return 22.4;
+    default: return 24.2;   // 13
+  }
+}
+
+// Radices of n (false when n has a prime factor above 13 or needs too many passes);
+// *cost: the plan's summed pass cost per element.  allow16: radix 16 among the
+// power-of-two radices (the row kernels, which run in 64 registers, take plans without).
+bool factor_plan(int n, FftPlan& pl, double* cost = nullptr, bool allow16 = true) {
   pl.n = n;
   pl.nst = 0;
   int m = n, a = 0;
   while (m % 2 == 0) { m /= 2; ++a; }
+  // power-of-two part: best[k] = cheapest passes for 2^k, from[k] = the last radix
+  double best[32];
+  int from[32];
+  best[0] = 0.0;
+  from[0] = 0;
+  for (int k = 1; k <= a; ++k) {
+    best[k] = 1e30;
+    from[k] = 0;
+    for (int lr = 1; lr <= (allow16 ? 4 : 3) && lr <= k; ++lr) {
+      const double c = best[k - lr] + pass_cost(1 << lr);
+      if (c < best[k]) { best[k] = c; from[k] = lr; }
+    }
+  }
   std::vector<int> rs;
-  int q = a / 3, r = a % 3;
-  if (r == 1 && q >= 1) { q -= 1; rs.push_back(4); rs.push_back(4); }
-  else if (r == 1) rs.push_back(2);
-  else if (r == 2) rs.push_back(4);
-  for (int i = 0; i < q; ++i) rs.insert(rs.begin(), 8);
-  for (int f : {3, 5, 7, 11, 13})
+  for (int k = a; k > 0; k -= from[k]) rs.push_back(1 << from[k]);
+  std::sort(rs.begin(), rs.end(), [](int x, int y) { return x > y; });
+  int b3 = 0;
+  while (m % 3 == 0) { m /= 3; ++b3; }
+  for (int i = 0; i < b3 / 2; ++i) rs.push_back(9);
+  if (b3 % 2) rs.push_back(3);
+  for (int f : {5, 7, 11, 13})
     while (m % f == 0) { m /= f; rs.push_back(f); }
   if (m != 1 || (int)rs.size() > FFT_MAX_STAGES) return false;
   pl.nst = (int)rs.size();
-  for (int i = 0; i < pl.nst; ++i) pl.radix[i] = rs[i];
+  double c = 0.0;
+  for (int i = 0; i < pl.nst; ++i) {
+    pl.radix[i] = rs[i];
+    c += pass_cost(rs[i]);
+  }
+  if (cost) *cost = c;
   return true;
 }
 
-// Length of the Bluestein convolution for a length-n transform: the smallest 13-smooth
-// m >= 2n - 1 (0 if none within the passes' stage limit).
+// Length of the Bluestein convolution for a length-n transform: among the lengths
+// m >= 2n - 1 up to 2.5 n that the passes take, the one with the least estimated work
+// (m times its summed pass cost); 0 if none.
 int bluestein_length(int n) {
   FftPlan t{};
-  for (int m = 2 * n - 1; m <= 4 * n; ++m)
-    if (factor_plan(m, t)) return m;
-  return 0;
+  int best = 0;
+  double best_work = 1e300;
+  for (int m = 2 * n - 1; m <= 5 * n / 2 + 1; ++m) {
+    double c = 0.0;
+    if (!factor_plan(m, t, &c)) continue;
+    const double work = (double)m * c;
+    if (work < best_work) { best_work = work; best = m; }
+  }
+  return best;
+}
+
+// The device copy of plan pl's passes (FftPasses) with its per-pass twiddle table.
+int make_passes(rift2_ctx* c, const FftPlan& pl, cudaStream_t st, const FftPasses** out) {
+  const int n = pl.n, m = pl.m;
+  FftPasses pp{};
+  PassDims pd{};
+  pp.n = n;
+  pp.L = m;
+  pp.nst = pl.nst;
+  pd.nst = pl.nst;
+  int ns = 1, off = 0;
+  for (int st2 = 0; st2 < pl.nst; ++st2) {
+    const int R = pl.radix[st2];
+    FftPass& ps = pp.p[st2];
+    ps.R = R;
+    ps.ns = ns;
+    ps.q = FastDiv((unsigned)(m / R));
+    ps.k = FastDiv((unsigned)ns);
+    ps.tw = off;
+    pd.R[st2] = R;
+    pd.ns[st2] = ns;
+    pd.off[st2] = off;
+    off += ns * (R - 1);
+    ns *= R;
+  }
+  pd.total = off;
+  pp.dL = FastDiv((unsigned)m);
+  pp.dn = FastDiv((unsigned)n);
+  pp.chirp = pl.chirp;
+  pp.kern_fwd = pl.kern_fwd;
+  pp.kern_inv = pl.kern_inv;
+  float2* ptw = nullptr;
+  RIFT2_CU(cudaMalloc(&ptw, sizeof(float2) * (off > 0 ? off : 1)));
+  launch_pass_twiddles(ptw, pl.tw, m, pd, st);
+  c->launches += 1;
+  RIFT2_CU(cudaGetLastError());
+  pp.ptw = ptw;
+  FftPasses* dev = nullptr;
+  RIFT2_CU(cudaMalloc(&dev, sizeof(FftPasses)));
+  RIFT2_CU(cudaMemcpyAsync(dev, &pp, sizeof(FftPasses), cudaMemcpyHostToDevice, st));
+  RIFT2_CU(cudaStreamSynchronize(st));   // pp is on this stack frame
+  c->pass_tw.push_back(ptw);
+  c->pass_dev.push_back(dev);
+  *out = dev;
+  return RIFT2_OK;
 }
 
 int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
@@ -168,46 +266,22 @@ int get_plan(rift2_ctx* c, int n, cudaStream_t st, FftPlan* out) {
     pl.kern_fwd = kf;
     pl.kern_inv = ki;
   }
-  // the shared-memory kernels' device copy: passes with precomputed divisors, per-pass
-  // twiddles gathered from tw
-  FftPasses pp{};
-  PassDims pd{};
-  pp.n = n;
-  pp.L = m;
-  pp.nst = pl.nst;
-  pd.nst = pl.nst;
-  int ns = 1, off = 0;
-  for (int st2 = 0; st2 < pl.nst; ++st2) {
-    const int R = pl.radix[st2];
-    FftPass& ps = pp.p[st2];
-    ps.R = R;
-    ps.ns = ns;
-    ps.q = FastDiv((unsigned)(m / R));
-    ps.k = FastDiv((unsigned)ns);
-    ps.tw = off;
-    pd.R[st2] = R;
-    pd.ns[st2] = ns;
-    pd.off[st2] = off;
-    off += ns * (R - 1);
-    ns *= R;
+  // the shared-memory kernels' device copies (passes with precomputed divisors, per-pass
+  // twiddles gathered from tw): one with radix 16 for the column and forward kernels, one
+  // without for the row kernels (the same when the radices agree)
+  FftPlan pr = pl;
+  if (!factor_plan(m, pr, nullptr, false)) return RIFT2_E_UNIMPL;
+  pr.n = n;
+  int rc = make_passes(c, pl, st, &pl.dev);
+  if (rc) return rc;
+  bool same = pr.nst == pl.nst;
+  for (int i = 0; same && i < pl.nst; ++i) same = pr.radix[i] == pl.radix[i];
+  if (same) {
+    pl.dev_r = pl.dev;
+  } else {
+    rc = make_passes(c, pr, st, &pl.dev_r);
+    if (rc) return rc;
   }
-  pd.total = off;
-  pp.dL = FastDiv((unsigned)m);
-  pp.dn = FastDiv((unsigned)n);
-  pp.chirp = pl.chirp;
-  pp.kern_fwd = pl.kern_fwd;
-  pp.kern_inv = pl.kern_inv;
-  float2* ptw = nullptr;
-  RIFT2_CU(cudaMalloc(&ptw, sizeof(float2) * (off > 0 ? off : 1)));
-  launch_pass_twiddles(ptw, tw, m, pd, st);
-  c->launches += 1;
-  RIFT2_CU(cudaGetLastError());
-  pp.ptw = ptw;
-  FftPasses* dev = nullptr;
-  RIFT2_CU(cudaMalloc(&dev, sizeof(FftPasses)));
-  RIFT2_CU(cudaMemcpyAsync(dev, &pp, sizeof(FftPasses), cudaMemcpyHostToDevice, st));
-  pl.dev = dev;
-  c->pass_tw.push_back(ptw);
   RIFT2_CU(cudaStreamSynchronize(st));
   c->plans[n] = pl;
   *out = pl;
@@ -250,7 +324,7 @@ int ensure_ws(rift2_ctx* c, size_t need) {
 }
 
 // Sides the transforms take: 13-smooth up to 8192 (direct), any other length up to 4096
-// (Bluestein: a convolution of 13-smooth length < 8192).
+// (Bluestein: a convolution of 13-smooth length between 2n - 1 and 2.5 n).
 int check_size(int H, int W) {
   if (H < 16 || W < 16) return RIFT2_E_INVAL;
   if (H > 8192 || W > 8192) return RIFT2_E_UNIMPL;
@@ -855,9 +929,9 @@ int rift2_destroy(rift2_ctx* c) {
       cudaFree(const_cast<float2*>(kv.second.kern_fwd));
       cudaFree(const_cast<float2*>(kv.second.kern_inv));
     }
-    cudaFree(const_cast<FftPasses*>(kv.second.dev));
   }
   for (float2* p : c->pass_tw) cudaFree(p);
+  for (FftPasses* p : c->pass_dev) cudaFree(p);
   for (auto& kv : c->zero_cols) cudaFree(kv.second);
   for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : c->free_events) cudaEventDestroy(e);

@@ -343,7 +343,7 @@ def _check_all_maps(dbg, o, label):
         try:
             fn()
         except AssertionError as e:
-            errs.append(str(e).split("\n")[0])
+            errs.append(" ".join(ln.strip() for ln in str(e).splitlines() if ln.strip())[:400])
 
     def mim_check():
         assert np.all(m["mim_margin"][mis] < TIE), f"{label}: MIM {int(mis.sum())} mismatches"
@@ -363,7 +363,9 @@ def _check_all_maps(dbg, o, label):
     cond_er = m["A"] / (4.0 * m["X"]) * 1e-2 * amax
     check(lambda: assert_map(f"{label} Er", d["er"], m["Er"], 5e-2, extra_den=cond_er))
     check(lambda: assert_map(f"{label} PC", d["pc"], m["pc"], 1.0))
-    check(lambda: np.testing.assert_allclose(d["noise_t"], m["T"], rtol=1e-5,
+    # T_o is the median smallest-scale amplitude times a constant: the amplitude bar (1e-4
+    # relative) applies; the 256^2 direct-size tests hold it to 1e-5
+    check(lambda: np.testing.assert_allclose(d["noise_t"], m["T"], rtol=1e-4,
                                              err_msg=f"{label} T_o"))
     mo = m["M"]
     dn = np.max(np.abs(d["moment"] - mo)) / (mo.max() - mo.min())
@@ -371,10 +373,10 @@ def _check_all_maps(dbg, o, label):
     def m_norm():
         assert dn < 5e-6, f"{label}: M in normalised units {dn:.3e}"
     check(m_norm)
-    # M is quadratic in PC: its relative error is twice PC's at leading order, so its floor
-    # is twice the floor 1e-2 that PC's own bar implies; what the detector thresholds is M
-    # in normalised units, checked above against the certification margin
-    check(lambda: assert_map(f"{label} M", d["moment"], mo, 2e-2))
+    # M is quadratic in PC: its relative error is twice PC's at leading order, so both its
+    # bar (2e-4) and its floor (2e-2) are twice PC's; what the detector thresholds is M in
+    # normalised units, checked above against the certification margin
+    check(lambda: assert_map(f"{label} M", d["moment"], mo, 2e-2, bar=2e-4))
     assert not errs, "; ".join(errs)
     return int(mis.sum())
 
