@@ -257,42 +257,10 @@ __device__ __forceinline__ void dft_r(float2* v) {
   else dft_odd<R, INV>(v);
 }
 
-// One Stockham pass over nb transforms; element k of transform b at buf[b*bs + k*ks].
-// BFAST: consecutive threads take consecutive transforms (column tiles, ks > 1; dnb is the
-// divisor nb); otherwise consecutive butterflies of one transform (rows, ks == 1).
-template <int R, bool INV, bool BFAST>
-__device__ __forceinline__ void fft_pass(const float2* __restrict__ in, float2* __restrict__ out,
-                                         const FftPass& ps, const float2* __restrict__ ptw,
-                                         const FastDiv& dnb, int nb, int bs, int ks, int tid,
-                                         int nthr) {
-  const int m = (int)ps.q.d;   // butterflies per transform
-  const int ns = ps.ns;
-  const int total = nb * m;
-  const float2* __restrict__ pw = ptw + ps.tw;
-  for (int idx = tid; idx < total; idx += nthr) {
-    int b, j;
-    if (BFAST) { j = (int)dnb.div((unsigned)idx); b = idx - j * nb; }
-    else       { b = (int)ps.q.div((unsigned)idx); j = idx - b * m; }
-    const int k = j - (int)ps.k.div((unsigned)j) * ns;
-    const float2* src = in + b * bs;
-    float2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * ks];
-    if (ns > 1) {
-      const float2* w = pw + k * (R - 1);
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(w, r - 1));
-    }
-    dft_r<R, INV>(v);
-    float2* dst = out + b * bs;
-    const int base = (j - k) * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst[(base + r * ns) * ks] = v[r];
-  }
-}
-
-// The same pass with its input and output as functors: src(t, e) returns element e of
-// transform t, dst(t, e, v) stores it.  The first pass of a transform can read its input
+// One Stockham pass over nb transforms with its input and output as functors: src(t, e)
+// returns element e of transform t, dst(t, e, v) stores it.  BFAST: consecutive threads
+// take consecutive transforms (column tiles; dnb is the divisor nb); otherwise consecutive
+// butterflies of one transform (rows).  The first pass of a transform can read its input
 // from wherever it lives (a window applied on the fly, global memory) and the last pass
 // can write its output there, without a staging round trip through shared memory.
 template <int R, bool INV, bool BFAST, class Src, class Dst>
@@ -423,76 +391,6 @@ __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2
     }
   };
   return fft_direct_io<true, BFAST, PAD, R16>(s2, d2, last_smem, r1, o, pl, dnb, nb, bs, ks);
-}
-
-// The Stockham passes of the plan's length-L transform; data starts in `a`, `b` is
-// scratch.  Returns the buffer holding the result.
-template <bool INV, bool BFAST>
-__device__ float2* fft_passes(float2* a, float2* b, const FftPasses& pl, const FastDiv& dnb,
-                              int nb, int bs, int ks) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int st = 0; st < pl.nst; ++st) {
-    const FftPass& ps = pl.p[st];
-    switch (ps.R) {
-      case 16: fft_pass<16, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 8: fft_pass<8, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 9: fft_pass<9, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 4: fft_pass<4, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 2: fft_pass<2, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 3: fft_pass<3, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 5: fft_pass<5, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 7: fft_pass<7, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 11: fft_pass<11, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      case 13: fft_pass<13, INV, BFAST>(a, b, ps, pl.ptw, dnb, nb, bs, ks, tid, nthr); break;
-      default: break;
-    }
-    __syncthreads();
-    float2* t = a; a = b; b = t;
-  }
-  return a;
-}
-
-// Full transform of nb transforms of length pl.n; element k of transform t at
-// buf[t * bs + k * ks], where each transform owns pl.L slots (pl.L = pl.n for direct
-// plans).  Data starts in `a`, `b` is scratch of the same size; returns the buffer holding
-// the result (the first pl.n elements of each slot).  Ends with a __syncthreads().
-template <bool INV, bool BFAST>
-__device__ float2* fft_smem(float2* a, float2* b, const FftPasses& pl, const FastDiv& dnb,
-                            int nb, int bs, int ks) {
-  if (!pl.chirp) return fft_passes<INV, BFAST>(a, b, pl, dnb, nb, bs, ks);
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int n = pl.n, m = pl.L;
-  // u_j = x_j c_j (conj(c_j) for the inverse) for j < n, zero up to m
-  for (int i = tid; i < nb * m; i += nthr) {
-    const int t = (int)pl.dL.div((unsigned)i), j = i - t * m;
-    float2* p = a + t * bs + j * ks;
-    if (j < n) {
-      const float2 c = __ldg(pl.chirp + j);
-      *p = INV ? cmulc(*p, c) : cmul(*p, c);
-    } else {
-      *p = make_float2(0.f, 0.f);
-    }
-  }
-  __syncthreads();
-  float2* r = fft_passes<false, BFAST>(a, b, pl, dnb, nb, bs, ks);
-  float2* o = (r == a) ? b : a;
-  const float2* kern = INV ? pl.kern_inv : pl.kern_fwd;
-  for (int i = tid; i < nb * m; i += nthr) {
-    const int t = (int)pl.dL.div((unsigned)i), j = i - t * m;
-    float2* p = r + t * bs + j * ks;
-    *p = cmul(*p, __ldg(kern + j));
-  }
-  __syncthreads();
-  r = fft_passes<true, BFAST>(r, o, pl, dnb, nb, bs, ks);
-  // X_k = c_k y_k (conj(c_k) for the inverse), k < n
-  for (int i = tid; i < nb * n; i += nthr) {
-    const int t = (int)pl.dn.div((unsigned)i), k = i - t * n;
-    float2* p = r + t * bs + k * ks;
-    const float2 c = __ldg(pl.chirp + k);
-    *p = INV ? cmulc(*p, c) : cmul(*p, c);
-  }
-  __syncthreads();
-  return r;
 }
 
 }  // namespace rift2

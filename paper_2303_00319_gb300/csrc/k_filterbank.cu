@@ -139,19 +139,19 @@ __global__ void __launch_bounds__(512, 1) fwd_rows(ImgPtrs ip, const float* __re
   __syncthreads();
   seg_means(a, tr, W, 1, L, mean);
   __syncthreads();
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    const int rr = (int)dW.div((unsigned)i), x = i - rr * W;
-    a[rr * L + x].x -= mean[rr].x;
-  }
-  __syncthreads();
-  float2* res = fft_smem<false, false>(a, b, pw, fg.dtile[img], tr, L, 1);
+  // the first pass reads the rows minus their means, the last pass restores bin 0 and
+  // stores the spectrum rows
   float2* dst = spec + gr.poff[img];
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    const int rr = (int)dW.div((unsigned)i), x = i - rr * W, r = r0 + rr;
-    float2 v = res[rr * L + x];
-    if (x == 0) v.x += mean[rr].x * W;
-    if (r < H) dst[(size_t)r * W + x] = v;
-  }
+  auto src_m = [&](int t, int e) -> float2 {
+    const float2 x = a[t * L + e];
+    return make_float2(x.x - mean[t].x, x.y);
+  };
+  auto out = [&](int t, int e, float2 v) {
+    if (e == 0) v.x += mean[t].x * W;
+    if (r0 + t < H) dst[(size_t)(r0 + t) * W + e] = v;
+  };
+  if (!pw.chirp) fft_direct_io<false, false>(src_m, out, false, a, b, pw, fg.dtile[img], tr, L, 1);
+  else fft_bluestein_io<false, false>(src_m, out, false, a, b, pw, fg.dtile[img], tr, L, 1);
 }
 
 // Columns, in place on spec [H][W]: tile of `tc` columns (fg.tile of the image).
@@ -177,22 +177,21 @@ __global__ void __launch_bounds__(512, 1) fwd_cols(float2* __restrict__ spec,
   __syncthreads();
   seg_means(a, tc, H, tc, 1, mean);
   __syncthreads();
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    float2 m = mean[i - (int)dtc.div((unsigned)i) * tc];
-    a[i].x -= m.x;
-    a[i].y -= m.y;
-  }
-  __syncthreads();
-  float2* res = fft_smem<false, true>(a, b, ph, dtc, tc, 1, tc);
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    const int v = (int)dtc.div((unsigned)i), c = i - v * tc;
-    float2 r = res[i];
-    if (v == 0) {
-      r.x += mean[c].x * H;
-      r.y += mean[c].y * H;
+  // the first pass reads the columns minus their means, the last pass restores bin 0 and
+  // writes the columns back
+  auto src_m = [&](int t, int e) -> float2 {
+    const float2 x = a[e * tc + t];
+    return make_float2(x.x - mean[t].x, x.y - mean[t].y);
+  };
+  auto out = [&](int t, int e, float2 v) {
+    if (e == 0) {
+      v.x += mean[t].x * H;
+      v.y += mean[t].y * H;
     }
-    if (c0 + c < W) base[(size_t)v * W + c0 + c] = r;
-  }
+    if (c0 + t < W) base[(size_t)e * W + c0 + t] = v;
+  };
+  if (!ph.chirp) fft_direct_io<false, true>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
+  else fft_bluestein_io<false, true>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
 }
 
 constexpr int REG_NT = 256;   // threads per CTA of the register-tiled row kernels
