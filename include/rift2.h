@@ -71,11 +71,14 @@ enum {
  * The keypoint capacity doubles: cap_kp >= 2 * max_keypoints, and cap_desc / the match
  * capacity double with it.  rift2_detect (the stage entry) ignores the flag. */
 #define RIFT2_FLAG_CORNERS 0x10
-/* Tune per image size (no counterpart in the paper): the first extraction of a size whose
- * column transforms run in shared memory times each candidate column tile (columns per
- * CTA) on that call's own data, synchronising the stream once, and keeps the fastest for
- * the context; every tile computes bit-identical results.  Without the flag the default
- * tile is used.  rift2_tuned_tile reports the choice. */
+/* Tune per image size and per match batch (no counterpart in the paper): the first
+ * extraction of a size whose column transforms run in shared memory times each candidate
+ * column tile (columns per CTA) on that call's own data, and the first tensor-core match
+ * of a batch shape (pairs per launch group, descriptor capacity) times each split of B's
+ * columns over 1 to 4 CTAs per query block; each synchronises the stream once and keeps
+ * the fastest for the context.  Every tile and every split computes bit-identical results
+ * (the matcher's candidates are re-ranked exactly and certified).  Without the flag the
+ * defaults are used.  rift2_tuned_tile and rift2_tuned_match_split report the choices. */
 #define RIFT2_FLAG_AUTOTUNE 0x20
 /* Spatial orientation normalisation of the patch (a variant the paper does not have: §III
  * normalises rotation through the dominant index alone, which leaves the 6x6 cell layout
@@ -286,6 +289,11 @@ int rift2_destroy(rift2_ctx* ctx);
  * 0 if none was tuned (flag off, the size not seen yet, or a register-tiled height), or
  * RIFT2_E_INVAL for a NULL context.  No counterpart in the paper. */
 int rift2_tuned_tile(const rift2_ctx* ctx, int height, int width);
+
+/* The split of B's columns the autotuner chose for tensor-core match launches of n_pairs
+ * pairs in this context (1 to 4 CTAs per block of 128 queries), 0 if none was tuned, or
+ * RIFT2_E_INVAL for a NULL context.  No counterpart in the paper. */
+int rift2_tuned_match_split(const rift2_ctx* ctx, int n_pairs);
 
 /* ------------------------------------------------------------------------------
  * Tracing.  With profiling on, the context brackets every stage of every launch group

@@ -31,7 +31,7 @@ DESC_DIM = CELLS * CELLS * NO
 EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_extract",
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
-           "rift2_describe", "rift2_detect_static", "rift2_tuned_tile",
+           "rift2_describe", "rift2_detect_static", "rift2_tuned_tile", "rift2_tuned_match_split",
            "rift2_required_capacity", "rift2_set_wait_limit", "rift2_evaluate",
            "rift2_workspace_bytes")
 STATIC_MAX_CANDIDATES = 262144
@@ -101,6 +101,7 @@ def lib():
         L.rift2_launch_count.argtypes = [C.c_void_p]
         L.rift2_launch_count.restype = C.c_longlong
         L.rift2_tuned_tile.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.rift2_tuned_match_split.argtypes = [C.c_void_p, C.c_int]
         L.rift2_required_capacity.argtypes = [C.c_void_p, C.POINTER(C.c_int),
                                               C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.rift2_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
@@ -405,6 +406,10 @@ class Context:
     def tuned_tile(self, height: int, width: int) -> int:
         """Column tile the autotuner kept for this size (0: none tuned)."""
         return int(lib().rift2_tuned_tile(self._h, height, width))
+
+    def tuned_match_split(self, n_pairs: int) -> int:
+        """Split of B's columns the autotuner kept for match calls of n_pairs pairs (0: none)."""
+        return int(lib().rift2_tuned_match_split(self._h, int(n_pairs)))
 
     # ---- stage entry points
     def fft2(self, img, stream=None):

@@ -68,6 +68,7 @@ struct rift2_ctx {
   std::vector<FftPasses*> pass_dev;   // the plans' device pass tables (freed at destroy)
   std::map<std::pair<int, int>, unsigned char*> zero_cols;   // (H, W) -> [NO][W]
   std::map<std::pair<int, int>, int> col_tiles;              // (H, W) -> tuned column tile
+  std::map<std::pair<int, int>, int> match_splits;           // (pairs, cap) -> tuned split
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   // tracing
   long long launches = 0;
@@ -990,7 +991,9 @@ int rift2_workspace_bytes(const rift2_ctx* c, int n, const int* heights, const i
   if (n_pairs > 0 && !(c->p.flags & RIFT2_FLAG_PLAIN_MATCH)) {
     const int gp = (c->p.flags & RIFT2_FLAG_NO_GROUPING) ? 1 : (n_pairs < MAXB ? n_pairs : MAXB);
     const int cap = (desc_per_kp(c) * c->kp.kp_cap + 127) / 128 * 128;
-    const size_t t = match_tc_ws_bytes(gp, cap, match_tc_nsplit(gp, cap));
+    // the autotuner's first match of a batch shape runs every split up to 4
+    const int ns = (c->p.flags & RIFT2_FLAG_AUTOTUNE) ? 4 : match_tc_nsplit(gp, cap);
+    const size_t t = match_tc_ws_bytes(gp, cap, ns);
     if (t > need) need = t;
   }
   *bytes = need;
@@ -1015,6 +1018,14 @@ int rift2_tuned_tile(const rift2_ctx* c, int height, int width) {
   if (!c) return RIFT2_E_INVAL;
   auto it = c->col_tiles.find(std::make_pair(height, width));
   return it == c->col_tiles.end() ? 0 : it->second;
+}
+
+int rift2_tuned_match_split(const rift2_ctx* c, int n_pairs) {
+  if (!c || n_pairs < 1) return RIFT2_E_INVAL;
+  const int g = n_pairs < MAXB ? n_pairs : MAXB;
+  const int cap = (desc_per_kp(c) * c->kp.kp_cap + 127) / 128 * 128;
+  auto it = c->match_splits.find(std::make_pair(g, cap));
+  return it == c->match_splits.end() ? 0 : it->second;
 }
 
 int rift2_sync(rift2_ctx* c, void* stream) {
@@ -1109,8 +1120,11 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
       RIFT2_CU(launch_match_simt(mp, g, desc_per_kp(c) * c->kp.kp_cap, st));
     } else {
       const int cap = (desc_per_kp(c) * c->kp.kp_cap + 127) / 128 * 128;
-      const int nsplit = match_tc_nsplit(g, cap);
-      int rc = ensure_ws(c, match_tc_ws_bytes(g, cap, nsplit));
+      const auto key = std::make_pair(g, cap);
+      auto it = c->match_splits.find(key);
+      const bool tune = (c->p.flags & RIFT2_FLAG_AUTOTUNE) && it == c->match_splits.end();
+      const int nsplit = it != c->match_splits.end() ? it->second : match_tc_nsplit(g, cap);
+      int rc = ensure_ws(c, match_tc_ws_bytes(g, cap, tune ? 4 : nsplit));
       if (rc) return rc;
       void *abf, *bbf;
       match_tc_operands(c->ws, g, cap, &abf, &bbf);
@@ -1119,6 +1133,32 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
       if (rc) return rc;
       rc = make_operand_map(c, &tb, bbf, g, cap, match_tc_box_rows(1));
       if (rc) return rc;
+      if (tune) {
+        // every split computes the same matches: time each on this call's descriptors
+        // (a warm-up, then two timed launches each) and keep the fastest; the last run
+        // leaves the call's results in place
+        cudaEvent_t ev[5];
+        for (int k = 0; k < 5; ++k) RIFT2_CU(cudaEventCreate(&ev[k]));
+        RIFT2_CU(launch_match_tc(mp, g, cap, c->ws, &ta, &tb, 1, c->status, st));
+        c->launches += K_MATCH_TC * 9;
+        RIFT2_CU(cudaEventRecord(ev[0], st));
+        for (int k = 1; k <= 4; ++k) {
+          for (int r = 0; r < 2; ++r)
+            RIFT2_CU(launch_match_tc(mp, g, cap, c->ws, &ta, &tb, k, c->status, st));
+          RIFT2_CU(cudaEventRecord(ev[k], st));
+        }
+        RIFT2_CU(cudaEventSynchronize(ev[4]));
+        int best = 1;
+        float best_ms = 1e30f;
+        for (int k = 1; k <= 4; ++k) {
+          float ms = 0.f;
+          RIFT2_CU(cudaEventElapsedTime(&ms, ev[k - 1], ev[k]));
+          if (ms < best_ms) { best_ms = ms; best = k; }
+        }
+        for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+        c->match_splits[key] = best;
+        continue;
+      }
       StageScope sc(c, RIFT2_STAGE_MATCH, st, K_MATCH_TC);
       RIFT2_CU(launch_match_tc(mp, g, cap, c->ws, &ta, &tb, nsplit, c->status, st));
     }

@@ -613,6 +613,24 @@ def test_autotuned_column_tile_gives_identical_features(pkg, dev):
     assert tuned.tuned_tile(1024, 1024) == 0   # never seen
 
 
+def test_autotuned_match_split_bit_identical(pkg, dev, small):
+    """The matcher's split of B's columns, timed over 1..4 on the first call of a batch
+    shape: every split gives the same matches (exact re-rank and certification), and the
+    kept split reproduces them on the next call."""
+    fa, fb = small["fa"], small["fb"]
+    ref = pkg.Context(pkg.default_params(max_keypoints=500), device=0)
+    tuned = pkg.Context(pkg.default_params(max_keypoints=500, flags=pkg.FLAG_AUTOTUNE), device=0)
+    mr = ref.match([fa], [fb])
+    m1 = tuned.match([fa], [fb])   # tunes: the last timed run's results
+    m2 = tuned.match([fa], [fb])   # the kept split
+    ref.sync(); tuned.sync()
+    assert 1 <= tuned.tuned_match_split(1) <= 4 and ref.tuned_match_split(1) == 0
+    r, a, b = mr[0].host(), m1[0].host(), m2[0].host()
+    assert len(r["q_desc"]) > 100
+    for k in ("q_desc", "nn_desc", "d1", "d2", "near_tie"):
+        assert np.array_equal(r[k], a[k]) and np.array_equal(r[k], b[k]), k
+
+
 # ------------------------------------------------------ RIFT ring baseline (§II-C)
 def test_rift_ring_and_template_descriptors_bit_exact(pkg, dev, small):
     o = small["oa"]
