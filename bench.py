@@ -900,6 +900,33 @@ def run_serving_1024(args, device: int):
             "rates": runs}
 
 
+def run_probe(spec: str):
+    """Per-stage device times of extracting four H x W images of the generator with one
+    context (the first call creates the plans and tables; three profiled calls follow):
+    the case the ncu summaries of the shared-memory transforms are taken on."""
+    import torch
+
+    import paper_2303_00319_gb300 as pkg
+    import synth
+    from paper_2303_00319_gb300 import _build
+    _build.build()
+    h, w = (int(v) for v in spec.split(","))
+    dev = torch.device("cuda:0")
+    imgs = [torch.from_numpy(synth.make_pair(h, w, 100 + i, angle_deg=None).a).to(dev)
+            for i in range(4)]
+    ctx = pkg.Context(pkg.default_params(max_keypoints=4000), device=0)
+    feats = [ctx.alloc_features() for _ in imgs]
+    ctx.extract(imgs, feats)
+    ctx.sync()
+    ctx.set_profiling(True)
+    for _ in range(3):
+        ctx.extract(imgs, feats)
+    ctx.sync()
+    st = {k: round(v[0] / 3, 4) for k, v in ctx.profile_read().items()}
+    ctx.close()
+    print(json.dumps({"probe": f"{h}x{w}", "images": 4, "stage_ms_per_call": st}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -925,7 +952,12 @@ def main():
                     help="offered pairs/s of the 1024^2 serving run")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the uneven-batch and 4096^2 summaries of the default line")
+    ap.add_argument("--probe", default=None, metavar="H,W",
+                    help="only print the per-stage times of extracting four H x W images")
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args.probe)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -170,9 +170,22 @@ bool factor_plan(int n, FftPlan& pl, double* cost = nullptr, bool allow16 = true
   return true;
 }
 
+// Occupancy factor of the row kernels for a row of width n transformed at length m: their
+// shared memory holds two padded slots (m + m/16 + 1 entries, as the row kernels lay them
+// out) for each of the four scales, or for two scales plus a parked copy of the other two
+// (2 n entries); two CTAs share an SM below 113 KB, one below 227 KB, else the row pass
+// splits into a transform pass and a pixel pass.  The factors weigh the estimated work.
+double row_occupancy_factor(int n, int m) {
+  const double slot = (double)(m + (m >> 4) + 1) * sizeof(float2);
+  const double full = 8.0 * slot, halves = 4.0 * slot + 2.0 * n * sizeof(float2);
+  if (full <= 113.0 * 1024 || halves <= 113.0 * 1024) return 1.0;
+  if (halves <= 227.0 * 1024) return 1.35;
+  return 2.0;
+}
+
 // Length of the Bluestein convolution for a length-n transform: among the lengths
 // m >= 2n - 1 up to 2.5 n that the passes take, the one with the least estimated work
-// (m times its summed pass cost); 0 if none.
+// (m times its summed pass cost, times the row kernels' occupancy factor); 0 if none.
 int bluestein_length(int n) {
   FftPlan t{};
   int best = 0;
@@ -180,7 +193,7 @@ int bluestein_length(int n) {
   for (int m = 2 * n - 1; m <= 5 * n / 2 + 1; ++m) {
     double c = 0.0;
     if (!factor_plan(m, t, &c)) continue;
-    const double work = (double)m * c;
+    const double work = (double)m * c * row_occupancy_factor(n, m);
     if (work < best_work) { best_work = work; best = m; }
   }
   return best;
