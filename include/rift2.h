@@ -324,6 +324,30 @@ int rift2_profile_read(rift2_ctx* ctx, int n, double* ms, long long* count);
 /* Kernels enqueued by this context since it was created. */
 long long rift2_launch_count(const rift2_ctx* ctx);
 
+/* Host-only planning queries (no device, no context): what the library decides before it
+ * launches anything, so that a caller (or a test) can inspect it.  No counterpart in the
+ * paper.
+ *
+ * rift2_fft_plan: the transform the shared-memory kernels run for a side of length n: the
+ * pass length (*length = n for 13-smooth n, else the Bluestein convolution length chosen
+ * by the planner, 2n - 1 <= *length <= 2.5 n + 1) and its radices in pass order (radices
+ * [max_radices] host array; rows != 0: the row kernels' plan, which has no radix 16).
+ * Returns the number of passes, RIFT2_E_UNIMPL when n cannot be planned (n > 4096 with a
+ * prime factor above 13, n > 8192), RIFT2_E_INVAL for n < 2, NULL pointers or too small
+ * a radices array. */
+int rift2_fft_plan(int n, int rows, int* length, int* radices, int max_radices);
+
+/* rift2_plan_groups: the launch groups rift2_extract forms for n_images images of the
+ * given sizes under params (flags NO_GROUPING / SIZE_GROUPS, the descriptor mode and the
+ * keypoint budget set the workspace) and an HBM budget (0: rift2_create's default,
+ * 16 GiB): order[n_images]
+ * receives the images in launch order, sizes[n_images] the size of each group in turn;
+ * *n_groups their number.  Host arrays.  Errors: RIFT2_E_INVAL (params as rift2_create
+ * validates them, NULL arrays, n_images < 0). */
+int rift2_plan_groups(const rift2_params* params, size_t hbm_budget_bytes, int n_images,
+                      const int* heights, const int* widths, int* order, int* sizes,
+                      int* n_groups);
+
 /* Device workspace the context needs for rift2_extract of n_images images of the given
  * sizes (host arrays; grouped as rift2_extract groups them, no debug maps) followed by
  * rift2_match of n_pairs pairs: the largest launch group's layout or the matcher's (the

@@ -32,6 +32,7 @@ EXPORTS = ("rift2_default_params", "rift2_status_str", "rift2_create", "rift2_ex
            "rift2_match", "rift2_sync", "rift2_destroy", "rift2_set_profiling",
            "rift2_profile_read", "rift2_launch_count", "rift2_fft2", "rift2_detect",
            "rift2_describe", "rift2_detect_static", "rift2_tuned_tile", "rift2_tuned_match_split",
+           "rift2_fft_plan", "rift2_plan_groups",
            "rift2_required_capacity", "rift2_set_wait_limit", "rift2_evaluate",
            "rift2_workspace_bytes")
 STATIC_MAX_CANDIDATES = 262144
@@ -102,6 +103,10 @@ def lib():
         L.rift2_launch_count.restype = C.c_longlong
         L.rift2_tuned_tile.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.rift2_tuned_match_split.argtypes = [C.c_void_p, C.c_int]
+        L.rift2_fft_plan.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]
+        L.rift2_plan_groups.argtypes = [C.c_void_p, C.c_size_t, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.rift2_required_capacity.argtypes = [C.c_void_p, C.POINTER(C.c_int),
                                               C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.rift2_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
@@ -140,6 +145,30 @@ def default_params(**overrides) -> Params:
     for k, v in overrides.items():
         setattr(p, k, v)
     return p
+
+
+def fft_plan(n: int, rows: bool = False) -> tuple[int, list[int]]:
+    """The transform the shared-memory kernels run for a side of length n (host only,
+    rift2_fft_plan): (pass length, radices in pass order)."""
+    length = C.c_int()
+    rad = (C.c_int * 16)()
+    k = lib().rift2_fft_plan(int(n), int(bool(rows)), C.byref(length), rad, 16)
+    if k < 0:
+        raise Rift2Error(k, "rift2_fft_plan")
+    return int(length.value), [int(rad[i]) for i in range(k)]
+
+
+def plan_groups(sizes, params: Params | None = None, hbm_budget: int = 0):
+    """The launch groups rift2_extract forms for images of `sizes` [(H, W), ...] (host
+    only, rift2_plan_groups): (launch order of the images, sizes of the groups)."""
+    n = len(sizes)
+    hs = (C.c_int * max(n, 1))(*[int(h) for h, _ in sizes])
+    ws = (C.c_int * max(n, 1))(*[int(w) for _, w in sizes])
+    order, gs, ng = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))(), C.c_int()
+    p = params if params is not None else default_params()
+    _check(lib().rift2_plan_groups(C.byref(p), int(hbm_budget), n, hs, ws, order, gs,
+                                   C.byref(ng)), "rift2_plan_groups")
+    return [int(order[i]) for i in range(n)], [int(gs[i]) for i in range(ng.value)]
 
 
 def _ptr(t):

@@ -887,9 +887,11 @@ const char* rift2_status_str(int s) {
   }
 }
 
-int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes, rift2_ctx** out) {
-  if (!out) return RIFT2_E_INVAL;
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+// The parameters rift2_create accepts (defaults where params is NULL) into *p.
+int validate_params(const rift2_params* params, rift2_params* out) {
   rift2_params p;
   rift2_default_params(&p);
   if (params) p = *params;
@@ -903,6 +905,55 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
        (p.flags & (RIFT2_FLAG_RIFT_RING | RIFT2_FLAG_RIFT_TEMPLATE))) ||
       !(p.second_ratio >= 0) || !(p.eps > 0))
     return RIFT2_E_INVAL;
+  *out = p;
+  return RIFT2_OK;
+}
+constexpr size_t kDefaultBudget = (size_t)16 << 30;
+}  // namespace
+
+extern "C" {
+
+int rift2_fft_plan(int n, int rows, int* length, int* radices, int max_radices) {
+  if (n < 2 || !length || !radices || max_radices < 1) return RIFT2_E_INVAL;
+  FftPlan pl{};
+  int m = n;
+  if (!factor_plan(n, pl, nullptr, rows == 0)) {
+    if (n > 4096) return RIFT2_E_UNIMPL;
+    m = bluestein_length(n);
+    if (!m || !factor_plan(m, pl, nullptr, rows == 0)) return RIFT2_E_UNIMPL;
+  } else if (n > 8192) {
+    return RIFT2_E_UNIMPL;
+  }
+  if (pl.nst > max_radices) return RIFT2_E_INVAL;
+  *length = m;
+  for (int i = 0; i < pl.nst; ++i) radices[i] = pl.radix[i];
+  return pl.nst;
+}
+
+int rift2_plan_groups(const rift2_params* params, size_t hbm_budget_bytes, int n,
+                      const int* heights, const int* widths, int* order, int* sizes,
+                      int* n_groups) {
+  if (n < 0 || !n_groups || (n > 0 && (!heights || !widths || !order || !sizes)))
+    return RIFT2_E_INVAL;
+  rift2_ctx c;   // host state only: parameters, derived constants, budget
+  const int rc = validate_params(params, &c.p);
+  if (rc) return rc;
+  derive_kparams(c.p, c.kp);
+  c.budget = hbm_budget_bytes ? hbm_budget_bytes : kDefaultBudget;
+  std::vector<int> ord, sz;
+  plan_groups(&c, n, heights, widths, nullptr, ord, sz);
+  for (int i = 0; i < n; ++i) order[i] = ord[i];
+  for (size_t g = 0; g < sz.size(); ++g) sizes[g] = sz[g];
+  *n_groups = (int)sz.size();
+  return RIFT2_OK;
+}
+
+int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes, rift2_ctx** out) {
+  if (!out) return RIFT2_E_INVAL;
+  *out = nullptr;
+  rift2_params p;
+  const int vrc = validate_params(params, &p);
+  if (vrc) return vrc;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -913,7 +964,7 @@ int rift2_create(const rift2_params* params, int device, size_t hbm_budget_bytes
   c->device = device;
   c->p = p;
   derive_kparams(p, c->kp);
-  c->budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)16 << 30);
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : kDefaultBudget;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult qr;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
