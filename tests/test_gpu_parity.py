@@ -64,7 +64,9 @@ def small(pkg, dev):
                                  # Bluestein lengths (a prime factor above 13): primes, 17,
                                  # the largest side, and wide smooth rows beyond the register path
                                  (257, 263), (17, 34), (1021, 97), (4093, 24), (40, 4091),
-                                 (64, 6144)])
+                                 (64, 6144),
+                                 # radix-9 and radix-16 passes (1296 = 16 9 9, 162 = 2 9 9)
+                                 (1296, 96), (288, 162)])
 def test_fft2_matches_numpy(pkg, dev, h, w):
     ctx = pkg.Context(pkg.default_params(), device=0)
     x = np.random.default_rng(h * 7 + w).random((2, h, w)).astype(np.float32)
@@ -405,9 +407,13 @@ def test_end_to_end_1024(pkg, dev):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("h,w", [(384, 640), (1408, 256),
-                                 # Bluestein sides: both prime; and rows too wide for the fused
-                                 # row pass (split path): 6144 = 2^11 3, prime 2053
-                                 (257, 263), (150, 6144), (160, 2053)])
+                                 # Bluestein sides: both prime; and rows too wide for four
+                                 # scales at once: 6144 = 2^11 3 (split pass), prime 2053
+                                 # (two-halves pass)
+                                 (257, 263), (150, 6144), (160, 2053),
+                                 # a Bluestein width whose length the row kernels' occupancy
+                                 # decides (1289 -> 2704), radix-9 heights
+                                 (162, 1289), (1296, 200)])
 def test_mixed_radix_maps_and_descriptors(pkg, dev, h, w):
     """Sizes whose transforms run the shared-memory kernels (lg_cols_inverse, lg_rows_reduce;
     384 = 2^7 3, 640 = 2^7 5, 1408 = 2^7 11), Bluestein's chirp-z form for sides with a
