@@ -320,9 +320,19 @@ __device__ __forceinline__ void fft_pass_io_r(int R, Src&& src, Dst&& dst, const
 // (dst unused).  Ends with a __syncthreads().
 // PAD > 0 (rows, ks == 1): element e of a slot sits at e + (e >> PAD), which spreads the
 // first pass's radix-strided stores over the shared-memory banks (slots then need
-// L + (L >> PAD) + 1 entries; pad_at() gives the position).
+// L + (L >> PAD) + 1 entries; pad_at() gives the position).  PAD < 0 (column tiles): the
+// flattened index q = t * bs + e * ks sits at q + (q >> -PAD) (a buffer of q entries then
+// needs q + (q >> -PAD) + 1).
 template <int PAD>
 __host__ __device__ __forceinline__ int pad_at(int e) { return PAD > 0 ? e + (e >> PAD) : e; }
+template <int PAD>
+__host__ __device__ __forceinline__ int slot_at(int t, int e, int bs, int ks) {
+  if constexpr (PAD > 0) return t * bs + e + (e >> PAD);
+  else if constexpr (PAD < 0) {
+    const int q = t * bs + e * ks;
+    return q + (q >> (-PAD));
+  } else return t * bs + e * ks;
+}
 
 template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, class Src, class Dst>
 __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
@@ -330,15 +340,10 @@ __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a
                                  int ks) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   auto lds = [&](float2* buf) {
-    return [buf, bs, ks](int t, int e) {
-      return PAD > 0 ? buf[t * bs + pad_at<PAD>(e)] : buf[t * bs + e * ks];
-    };
+    return [buf, bs, ks](int t, int e) { return buf[slot_at<PAD>(t, e, bs, ks)]; };
   };
   auto sts = [&](float2* buf) {
-    return [buf, bs, ks](int t, int e, float2 v) {
-      if (PAD > 0) buf[t * bs + pad_at<PAD>(e)] = v;
-      else buf[t * bs + e * ks] = v;
-    };
+    return [buf, bs, ks](int t, int e, float2 v) { buf[slot_at<PAD>(t, e, bs, ks)] = v; };
   };
   const int last = pl.nst - 1;
   for (int st = 0; st <= last; ++st) {
@@ -381,7 +386,7 @@ __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2
   float2* o = (r1 == a) ? b : a;
   const float2* __restrict__ kern = INV ? pl.kern_inv : pl.kern_fwd;
   auto s2 = [r1, kern, bs, ks](int t, int j) -> float2 {
-    const float2 x = PAD > 0 ? r1[t * bs + pad_at<PAD>(j)] : r1[t * bs + j * ks];
+    const float2 x = r1[slot_at<PAD>(t, j, bs, ks)];
     return cmul(x, __ldg(kern + j));
   };
   auto d2 = [&](int t, int k, float2 v) {

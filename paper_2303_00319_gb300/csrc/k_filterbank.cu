@@ -14,6 +14,13 @@
 
 namespace rift2 {
 
+// Column tiles' Stockham buffers: in tiles of at most CC_NARROW columns the flattened index
+// q (element e of column t at e tc + t) sits at q + (q >> CC_PAD), so that the
+// radix-strided stores spread over the shared-memory banks (wider tiles spread them
+// already and run faster unpadded); a buffer for q entries holds col_buf(q) either way.
+constexpr int CC_PAD = 4, CC_NARROW = 3;
+__host__ __device__ __forceinline__ int col_buf(int q) { return q + (q >> CC_PAD) + 1; }
+
 // ------------------------------------------------------------------ twiddle tables
 // tw[e] = exp(-2 pi i e / n), computed in double precision (the only FP64 step).
 __global__ void twiddle_gen(float2* tw, int n) {
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(512, 1) fwd_cols(float2* __restrict__ spec,
   if (c0 >= W) return;
   const int nel = H * tc;
   float2* a = sm;
-  float2* b = sm + ph.L * tc;   // [ph.L][tc] each: a column transform's slot is ph.L long
+  float2* b = sm + col_buf(ph.L * tc);   // [ph.L][tc] each (padded): a column's slot is ph.L long
   float2* base = spec + gr.poff[img];
   const FastDiv& dtc = fg.dtile[img];
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
@@ -190,8 +197,13 @@ __global__ void __launch_bounds__(512, 1) fwd_cols(float2* __restrict__ spec,
     }
     if (c0 + t < W) base[(size_t)e * W + c0 + t] = v;
   };
-  if (!ph.chirp) fft_direct_io<false, true>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
-  else fft_bluestein_io<false, true>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
+  if (tc <= CC_NARROW) {
+    if (!ph.chirp) fft_direct_io<false, true, -CC_PAD>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
+    else fft_bluestein_io<false, true, -CC_PAD>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
+  } else {
+    if (!ph.chirp) fft_direct_io<false, true>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
+    else fft_bluestein_io<false, true>(src_m, out, false, a, b, ph, dtc, tc, 1, tc);
+  }
 }
 
 constexpr int REG_NT = 256;   // threads per CTA of the register-tiled row kernels
@@ -404,8 +416,8 @@ void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaSt
 }
 
 // Column pass of the inverse for the six orientations of scale blockIdx.y.
-// smem: base (F * R_s), a, b each [H][tc].  A tile whose columns all have a zero angular
-// window for an orientation (fg.zc) writes nothing for it.
+// smem: base (F * R_s) [H][tc], a, b [L][tc] each (padded, col_buf).  A tile whose
+// columns all have a zero angular window for an orientation (fg.zc) writes nothing for it.
 __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restrict__ spec,
                                                        float2* __restrict__ scratch,
                                                        const __grid_constant__ Group gr,
@@ -420,7 +432,7 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
   if (c0 >= W) return;
   const size_t P = (size_t)H * W;
   const int nel = H * tc;
-  const int nl = ph.L * tc;   // a transform slot is ph.L long (> H for Bluestein plans)
+  const int nl = col_buf(ph.L * tc);   // transform slots ph.L long (> H for Bluestein plans), padded
   float2* base = sm;
   float2* a = sm + nel;
   float2* b = sm + nel + nl;
@@ -466,8 +478,13 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
     auto out = [&](int t, int e, float2 v) {
       if (c0 + t < W) dst[(size_t)e * W + c0 + t] = v;
     };
-    if (!ph.chirp) fft_direct_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
-    else fft_bluestein_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+    if (tc <= CC_NARROW) {
+      if (!ph.chirp) fft_direct_io<true, true, -CC_PAD>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+      else fft_bluestein_io<true, true, -CC_PAD>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+    } else {
+      if (!ph.chirp) fft_direct_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+      else fft_bluestein_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+    }
     // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
   }
 }
@@ -1297,7 +1314,7 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
       const int tc = cols_tile(ph.m);
       for (int k = 0; k < cnt; ++k) sub_add(sub, sf, gr, i0 + k, ph, tc, nullptr);
       grid_x = max_of(grid_x, (W + tc - 1) / tc);
-      smc = max_of(smc, 2 * (size_t)tc * ph.m * sizeof(float2));
+      smc = max_of(smc, 2 * (size_t)col_buf(tc * ph.m) * sizeof(float2));
     });
     if (sub.n) {
       cudaFuncSetAttribute(fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
@@ -1312,7 +1329,8 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
 // Shared memory of the generic column pass for a tile of tc columns: F R_s (H rows), the
 // two transform buffers (slot length L each) and the per-row frequencies.
 static size_t cols_inverse_smem(int H, int L, int tc) {
-  return ((size_t)H + 2 * (size_t)L) * tc * sizeof(float2) + (size_t)H * sizeof(float);
+  return ((size_t)H * tc + 2 * (size_t)col_buf(L * tc)) * sizeof(float2) +
+         (size_t)H * sizeof(float);
 }
 static int cols_inverse_tile(int H, int L) {
   int tc = cols_tile(L);
