@@ -11,7 +11,9 @@ gamma speckle; at most 5000 keypoints per image).  Prints one JSON line on rank 
 keypoints) and --workload 3 the 4096^2 scene (<= 20000 keypoints); the default line also
 carries an open-loop serving sweep (Poisson arrivals at 50..400 pairs/s).  Besides the
 headline (one context, one stream) the line reports the same step as one replayed CUDA
-graph (graph_form) and split between two contexts on two streams (two_lane_form).
+graph (graph_form), on one context with two lanes (RIFT2_FLAG_TWO_LANES: each call's second
+half of images and pairs on the library's second stream; two_lane_form), and the plain
+one-pair-per-call forms.
 
 Multi-GPU: independent replicas (the pairs shard with no exchange step); launched with
 torch.distributed.run, one rank per GPU, timing = max over ranks.
@@ -433,10 +435,11 @@ def run_ours(args):
     B = args.pairs if args.workload == 1 else wl["pairs"]
     rot = ROTATE if args.workload == 1 else 1
     max_kp = wl["max_kp"]
-    # the column-tile autotuner only acts on sizes whose columns run in shared memory
-    # (the uneven batch); it times them once, during the warm-up steps
-    ctx = pkg.Context(pkg.default_params(max_keypoints=max_kp, flags=pkg.FLAG_AUTOTUNE), device=local,
-                      hbm_budget=96 << 30)
+    # the autotuner times the shared-memory column tiles (the uneven batch) and the
+    # matcher's split once, during the warm-up steps.  One lane: the timed steps read the
+    # per-stage device times, and a profiling context runs every call on the caller's stream
+    ctx = pkg.Context(pkg.default_params(max_keypoints=max_kp, flags=pkg.FLAG_AUTOTUNE),
+                      device=local, hbm_budget=96 << 30)
 
     # inputs: `rot` batches of B pairs, distinct per rank; pinned host copies for e2e
     host = []
@@ -604,31 +607,25 @@ def run_ours(args):
                  "form": "one CUDA graph per batch (extract + match of every pair), replayed"}
         del g
 
-    # two-lane form: the batch split between two contexts on two streams, forked from and
-    # joined back to the timing stream every step, so that one lane's under-filled stages
-    # (top-K sort, median selection, re-rank) overlap the other lane's full-GPU kernels
+    # two-lane form: one context with RIFT2_FLAG_TWO_LANES, called exactly as the headline
+    # calls its context; the library forks each call's second half of images (pairs) onto
+    # its second stream and joins it back, so that one lane's under-filled stages (top-K
+    # sort, median selection, re-rank) overlap the other lane's full-GPU kernels
     lanes = None
     if not args.no_lanes and B >= 2:
-        half = B // 2
-        ctx2 = pkg.Context(pkg.default_params(max_keypoints=max_kp, flags=pkg.FLAG_AUTOTUNE),
+        lctx = pkg.Context(pkg.default_params(max_keypoints=max_kp,
+                                              flags=pkg.FLAG_AUTOTUNE | pkg.FLAG_TWO_LANES),
                            device=local, hbm_budget=96 << 30)
-        s_a, s_b = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
         def step_lanes(imgs):
-            fork = torch.cuda.Event()
-            fork.record(stream)
-            s_a.wait_event(fork)
-            s_b.wait_event(fork)
-            ctx.extract([imgs[i] for i in range(2 * half)], feats[:2 * half], stream=s_a)
-            ctx.match(feats[0:2 * half:2], feats[1:2 * half:2], matches[:half], stream=s_a)
-            ctx2.extract([imgs[i] for i in range(2 * half, 2 * B)], feats[2 * half:], stream=s_b)
-            ctx2.match(feats[2 * half::2], feats[2 * half + 1::2], matches[half:], stream=s_b)
-            stream.wait_stream(s_a)
-            stream.wait_stream(s_b)
+            lctx.extract([imgs[i] for i in range(2 * B)], feats, stream=stream)
+            lctx.match(feats[0::2], feats[1::2], matches, stream=stream)
 
         for i in range(args.warmup):
             step_lanes(devb[i % rot])
+        lctx.sync()
         barrier()
+        l0 = lctx.launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(args.steps):
@@ -639,8 +636,9 @@ def run_ours(args):
         barrier()
         lanes = {"value": whole_job_rate(world, B, args.steps, max_over_ranks(lms, dev)),
                  "unit": "pairs/s", "ms_per_step": lms / args.steps,
-                 "form": f"two contexts on two streams, {half} + {B - half} pairs per step"}
-        ctx2.close()
+                 "launches_per_step": (lctx.launch_count() - l0) / args.steps,
+                 "form": f"one context with two lanes, {B // 2} + {B - B // 2} pairs per call"}
+        lctx.close()
 
     # plain forms: one pair per call, no launch grouping; with the CUDA-core matcher and
     # with the tensor-core one (the latter isolates the gain from batching)

@@ -94,6 +94,14 @@ enum {
  * to RIFT2_MAX_BATCH images of any sizes share one launch per stage; each image's results
  * are bit-identical either way. */
 #define RIFT2_FLAG_SIZE_GROUPS 0x80
+/* Two lanes (no counterpart in the paper): rift2_extract and rift2_match run the second
+ * half of a call's images / pairs on a second internal stream and context (forked from
+ * and joined back to the caller's stream with events), so that one half's under-filled
+ * stages (top-K sort, median selection, re-rank) overlap the other half's kernels.  Each
+ * lane keeps its own workspace within the HBM budget, so the context may hold up to twice
+ * the budget; results are bit-identical to one lane.  Calls with one image or one pair,
+ * and calls with profiling on, run on one lane. */
+#define RIFT2_FLAG_TWO_LANES 0x100
 
 /*
  * Pipeline parameters.  Defaults (rift2_default_params) follow Table 1 (5000 keypoints,
@@ -351,7 +359,8 @@ int rift2_plan_groups(const rift2_params* params, size_t hbm_budget_bytes, int n
 /* Device workspace the context needs for rift2_extract of n_images images of the given
  * sizes (host arrays; grouped as rift2_extract groups them, no debug maps) followed by
  * rift2_match of n_pairs pairs: the largest launch group's layout or the matcher's (the
- * workspace is one buffer reused by every group and by the matcher).  For admission
+ * workspace is one buffer reused by every group and by the matcher; with
+ * RIFT2_FLAG_TWO_LANES the sum of both lanes' workspaces for their halves).  For admission
  * control by a serving loop; no counterpart in the paper.  *bytes is written.
  * Errors: RIFT2_E_INVAL. */
 int rift2_workspace_bytes(const rift2_ctx* ctx, int n_images, const int* heights,

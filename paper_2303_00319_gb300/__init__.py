@@ -24,6 +24,7 @@ FLAG_CORNERS = 0x10        # RIFT's corner keypoints on the minimum moment, afte
 FLAG_AUTOTUNE = 0x20       # time the column tiles of a new image size once, keep the fastest
 FLAG_SPATIAL_NORM = 0x40   # variant: patch grid rotated into the dominant index's frame
 FLAG_SIZE_GROUPS = 0x80    # launch groups of one image size only (mixed sizes share launches without it)
+FLAG_TWO_LANES = 0x100     # halves of a call on two internal streams (overlaps under-filled stages)
 NS, NO, PATCH, CELLS = 4, 6, 96, 6
 DESC_DIM = CELLS * CELLS * NO
 

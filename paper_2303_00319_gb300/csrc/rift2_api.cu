@@ -78,6 +78,11 @@ struct rift2_ctx {
   std::vector<cudaEvent_t> free_events;
   double acc_ms[RIFT2_N_STAGES] = {};
   long long acc_n[RIFT2_N_STAGES] = {};
+  // RIFT2_FLAG_TWO_LANES: the second lane's context and stream, and the events that fork
+  // it from and join it back to the caller's stream (made on first use)
+  rift2_ctx* lane = nullptr;
+  cudaStream_t lane_st = nullptr;
+  cudaEvent_t lane_fork = nullptr, lane_join = nullptr;
 };
 
 namespace {
@@ -847,6 +852,40 @@ void plan_groups(const rift2_ctx* c, int n, const int* H, const int* W, const in
   }
 }
 
+// One lane's share of rift2_extract / rift2_match (defined after the C ABI entry points).
+int extract_impl(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* out,
+                 cudaStream_t st);
+int match_impl(rift2_ctx* c, int n, const rift2_features* a, const rift2_features* b,
+               rift2_matches* out, cudaStream_t st);
+
+// RIFT2_FLAG_TWO_LANES applies to a call of n images or pairs (not while profiling, whose
+// stage events are recorded on one stream).
+bool two_lanes(const rift2_ctx* c, int n) {
+  return (c->p.flags & RIFT2_FLAG_TWO_LANES) && !c->prof && n >= 2;
+}
+
+// The second lane: a context with the same parameters (without the flag) and budget, its
+// own non-blocking stream and the fork / join events; made on first use.
+int lane_of(rift2_ctx* c, rift2_ctx** out) {
+  if (!c->lane) {
+    rift2_params p2 = c->p;
+    p2.flags &= ~RIFT2_FLAG_TWO_LANES;
+    rift2_ctx* ln = nullptr;
+    int rc = rift2_create(&p2, c->device, c->budget, &ln);
+    if (rc) return rc;
+    ln->wait_iters = c->wait_iters;
+    if (cudaStreamCreateWithFlags(&c->lane_st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->lane_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->lane_join, cudaEventDisableTiming) != cudaSuccess) {
+      rift2_destroy(ln);
+      return RIFT2_E_CUDA;
+    }
+    c->lane = ln;
+  }
+  *out = c->lane;
+  return RIFT2_OK;
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -987,6 +1026,12 @@ int rift2_destroy(rift2_ctx* c) {
   if (!c) return RIFT2_E_INVAL;
   DeviceGuard dg(c->device);
   cudaDeviceSynchronize();
+  if (c->lane) {
+    rift2_destroy(c->lane);
+    cudaStreamDestroy(c->lane_st);
+    cudaEventDestroy(c->lane_fork);
+    cudaEventDestroy(c->lane_join);
+  }
   for (auto& kv : c->plans) {
     cudaFree(const_cast<float2*>(kv.second.tw));
     if (kv.second.chirp) {
@@ -1033,11 +1078,16 @@ int rift2_profile_read(rift2_ctx* c, int n, double* ms, long long* count) {
   return RIFT2_OK;
 }
 
-long long rift2_launch_count(const rift2_ctx* c) { return c ? c->launches : -1; }
+long long rift2_launch_count(const rift2_ctx* c) {
+  return c ? c->launches + (c->lane ? c->lane->launches : 0) : -1;
+}
 
-int rift2_workspace_bytes(const rift2_ctx* c, int n, const int* heights, const int* widths,
-                          int n_pairs, size_t* bytes) {
-  if (!c || n < 0 || n_pairs < 0 || !bytes || (n > 0 && (!heights || !widths))) return RIFT2_E_INVAL;
+}  // extern "C"
+
+namespace {
+// Workspace of one lane for n images and n_pairs pairs (the larger of its largest launch
+// group's layout and the matcher's).
+size_t lane_need(const rift2_ctx* c, int n, const int* heights, const int* widths, int n_pairs) {
   size_t need = 0;
   std::vector<int> order, sizes;
   plan_groups(c, n, heights, widths, nullptr, order, sizes);   // the groups rift2_extract forms
@@ -1060,13 +1110,31 @@ int rift2_workspace_bytes(const rift2_ctx* c, int n, const int* heights, const i
     const size_t t = match_tc_ws_bytes(gp, cap, ns);
     if (t > need) need = t;
   }
-  *bytes = need;
+  return need;
+}
+}  // namespace
+
+extern "C" {
+
+int rift2_workspace_bytes(const rift2_ctx* c, int n, const int* heights, const int* widths,
+                          int n_pairs, size_t* bytes) {
+  if (!c || n < 0 || n_pairs < 0 || !bytes || (n > 0 && (!heights || !widths))) return RIFT2_E_INVAL;
+  if (c->p.flags & RIFT2_FLAG_TWO_LANES) {
+    // both lanes' workspaces: the first half of the images and pairs on this context, the
+    // rest on the second lane (a call of one image or pair stays on the first)
+    const int h = n >= 2 ? n / 2 : n, hp = n_pairs >= 2 ? n_pairs / 2 : n_pairs;
+    *bytes = lane_need(c, h, heights, widths, hp) +
+             lane_need(c, n - h, heights + h, widths + h, n_pairs - hp);
+    return RIFT2_OK;
+  }
+  *bytes = lane_need(c, n, heights, widths, n_pairs);
   return RIFT2_OK;
 }
 
 int rift2_set_wait_limit(rift2_ctx* c, long long iters) {
   if (!c || iters < 0) return RIFT2_E_INVAL;
   c->wait_iters = iters;
+  if (c->lane) c->lane->wait_iters = iters;
   return RIFT2_OK;
 }
 
@@ -1096,12 +1164,17 @@ int rift2_sync(rift2_ctx* c, void* stream) {
   if (!c) return RIFT2_E_INVAL;
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int h = 0;
+  // the second lane's work was joined back to the caller's stream, so its status word is
+  // read in order too
+  int h = 0, h2 = 0;
   if (cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      (c->lane && cudaMemcpyAsync(&h2, c->lane->status, sizeof(int), cudaMemcpyDeviceToHost,
+                                  st) != cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return RIFT2_E_CUDA;
-  if (h) {
+  if (h || h2) {
     cudaMemsetAsync(c->status, 0, sizeof(int), st);
+    if (c->lane) cudaMemsetAsync(c->lane->status, 0, sizeof(int), st);
     cudaStreamSynchronize(st);
     return RIFT2_E_TIMEOUT;
   }
@@ -1119,6 +1192,31 @@ int rift2_extract(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* 
   }
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (two_lanes(c, n)) {
+    rift2_ctx* ln = nullptr;
+    int rc = lane_of(c, &ln);
+    if (rc) return rc;
+    const int h = n / 2;
+    RIFT2_CU(cudaEventRecord(c->lane_fork, st));
+    RIFT2_CU(cudaStreamWaitEvent(c->lane_st, c->lane_fork, 0));
+    rc = extract_impl(c, h, imgs, out, st);
+    if (rc) return rc;
+    rc = extract_impl(ln, n - h, imgs + h, out + h, c->lane_st);
+    if (rc) return rc;
+    RIFT2_CU(cudaEventRecord(c->lane_join, c->lane_st));
+    RIFT2_CU(cudaStreamWaitEvent(st, c->lane_join, 0));
+    return RIFT2_OK;
+  }
+  return extract_impl(c, n, imgs, out, st);
+}
+
+}  // extern "C"
+
+namespace {
+// The extraction of n images on one lane (context c, stream st): launch groups as
+// plan_groups forms them.
+int extract_impl(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* out,
+                 cudaStream_t st) {
   std::vector<int> hh(n), ww(n), dbg(n), order, sizes;
   for (int i = 0; i < n; ++i) {
     hh[i] = imgs[i].height;
@@ -1140,6 +1238,9 @@ int rift2_extract(rift2_ctx* c, int n, const rift2_image* imgs, rift2_features* 
   }
   return RIFT2_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_features* b,
                 rift2_matches* out, void* stream) {
@@ -1156,6 +1257,30 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
   }
   DeviceGuard dg(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (two_lanes(c, n)) {
+    rift2_ctx* ln = nullptr;
+    int rc = lane_of(c, &ln);
+    if (rc) return rc;
+    const int h = n / 2;
+    RIFT2_CU(cudaEventRecord(c->lane_fork, st));
+    RIFT2_CU(cudaStreamWaitEvent(c->lane_st, c->lane_fork, 0));
+    rc = match_impl(c, h, a, b, out, st);
+    if (rc) return rc;
+    rc = match_impl(ln, n - h, a + h, b + h, out + h, c->lane_st);
+    if (rc) return rc;
+    RIFT2_CU(cudaEventRecord(c->lane_join, c->lane_st));
+    RIFT2_CU(cudaStreamWaitEvent(st, c->lane_join, 0));
+    return RIFT2_OK;
+  }
+  return match_impl(c, n, a, b, out, st);
+}
+
+}  // extern "C"
+
+namespace {
+// The matching of n pairs on one lane (context c, stream st).
+int match_impl(rift2_ctx* c, int n, const rift2_features* a, const rift2_features* b,
+               rift2_matches* out, cudaStream_t st) {
   const int step = (c->p.flags & RIFT2_FLAG_NO_GROUPING) ? 1 : MAXB;
   for (int i0 = 0; i0 < n; i0 += step) {
     int g = n - i0 < step ? n - i0 : step;
@@ -1228,7 +1353,11 @@ int rift2_match(rift2_ctx* c, int n, const rift2_features* a, const rift2_featur
     }
   }
   return RIFT2_OK;
+  return RIFT2_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int rift2_evaluate(rift2_ctx* c, int n, const rift2_features* a, const rift2_features* b,
                    const rift2_matches* m, const double* affine, double tol, double rmse_cap,
