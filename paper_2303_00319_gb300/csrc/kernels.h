@@ -49,8 +49,12 @@ cudaError_t launch_lg_rows(float2* scratch, const Group& gr, const FbImage* fi,
                            unsigned char* mim, int mim_pitch, cudaStream_t st, int* launches);
 
 // k_pc.cu — exact median of |EO_0,o| (radix select), noise thresholds, PC, moments.
+// Global histogram words per (image, orientation): 32768 round-0 buckets, 65536 round-1
+// buckets for each middle rank, then the counts of 512 chunks of each of the three
+// histograms.  Zero before launch_noise_threshold.
+constexpr int MEDIAN_HIST_WORDS = 32768 + 2 * 65536 + 3 * 512;
 struct MedianWs {
-  unsigned* hist;    // [nimg][NO][2][4096]
+  unsigned* hist;    // [nimg][NO][MEDIAN_HIST_WORDS]
   unsigned* state;   // [nimg][NO][2][2]  (prefix, rank)
   float* noise_t;    // [nimg][NO]
 };

@@ -355,7 +355,7 @@ int check_size(int H, int W) {
 
 // ------------------------------------------------------------------ tracing
 // Kernels enqueued by each launcher (kept next to the launch sequences they count).
-constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_NOISE = 6, K_MOMENT = 1,
+constexpr int K_FFT_FWD = 2, K_LG_COLS = 1, K_NOISE = 4, K_MOMENT = 1,
               K_DESCRIBE = 3, K_MATCH = 1, K_MATCH_TC = 4, K_INIT = 1,
               K_MERGE = 1;
 
@@ -527,7 +527,7 @@ Layout extract_layout(const Group& gr, int max_kp, int kp_cap, bool corners, int
   // rows of the stacked MIMs, at least one TMA box high (the tensor map covers them all)
   L.mim_rows = rows > 160 ? rows : 160;
   L.mim = take((size_t)L.mim_rows * L.mim_pitch);
-  L.mhist = take((size_t)g * NO * 2 * 4096 * 4);
+  L.mhist = take((size_t)g * NO * MEDIAN_HIST_WORDS * 4);
   L.mstate = take((size_t)g * NO * 4 * 4);
   L.noise = take((size_t)g * NO * 4);
   L.minmax = take((size_t)g * 2 * 4);
@@ -725,7 +725,7 @@ int extract_group(rift2_ctx* c, int g, const rift2_image* imgs, rift2_features* 
     c->launches += K_INIT;
     launch_init_detect(minmax_c, ccount_c, g, st);
   }
-  RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * 2 * 4096 * 4, st));
+  RIFT2_CU(cudaMemsetAsync(at<char>(ws, L.mhist), 0, (size_t)g * NO * MEDIAN_HIST_WORDS * 4, st));
   float2* spec = at<float2>(ws, L.spec);
   int nl = 0;
   {

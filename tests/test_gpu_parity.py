@@ -96,10 +96,10 @@ def test_noise_threshold(small):
 
 def test_noise_threshold_concentrated_amplitudes(pkg, dev):
     """A grating's filter responses have one amplitude everywhere (|EO| = |G(k)| / 2 for a
-    one-sided filter), so every |EO_0,o| falls in one 12-bit bucket of the median's
-    selection and overflows its compaction: the last two digits are then selected on the
-    whole slice.  T_o against the oracle (absolute tolerance: orientations whose window
-    misses the grating have amplitudes at FP32 round-off)."""
+    one-sided filter), so nearly every |EO_0,o| falls in one bucket of both rounds of the
+    median's selection (the second round's counting then aggregates equal buckets per
+    warp).  T_o against the oracle (absolute tolerance: orientations whose window misses
+    the grating have amplitudes at FP32 round-off)."""
     h, w = 256, 320
     y, x = np.mgrid[0:h, 0:w]
     img = (0.5 + 0.4 * np.cos(2 * np.pi * (96 * x / w + 13 * y / h))).astype(np.float32)
