@@ -92,6 +92,12 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e) 
   return INV ? make_float2(w.x, -w.y) : w;
 }
 
+template <bool INV>
+__device__ __forceinline__ float2 twiddle_s(const float2* tw, int e) {
+  float2 w = tw[e];
+  return INV ? make_float2(w.x, -w.y) : w;
+}
+
 // Multiply by -i (forward) or +i (inverse).
 template <bool INV>
 __device__ __forceinline__ float2 rot_mi(float2 a) {
@@ -263,10 +269,15 @@ __device__ __forceinline__ void dft_r(float2* v) {
 // butterflies of one transform (rows).  The first pass of a transform can read its input
 // from wherever it lives (a window applied on the fly, global memory) and the last pass
 // can write its output there, without a staging round trip through shared memory.
-template <int R, bool INV, bool BFAST, class Src, class Dst>
-__device__ __forceinline__ void fft_pass_io(Src&& src, Dst&& dst, const FftPass& ps,
-                                            const float2* __restrict__ ptw, const FastDiv& dnb,
+// TWS: ptw points to shared memory (a copy of the plan's twiddles the kernel made).
+// The pass parameters are copied to registers first: the loop's shared-memory stores could
+// alias the generic references as far as the compiler knows, and would force reloads.
+template <int R, bool INV, bool BFAST, bool TWS = false, class Src, class Dst>
+__device__ __forceinline__ void fft_pass_io(Src&& src, Dst&& dst, const FftPass& ps_,
+                                            const float2* __restrict__ ptw, const FastDiv& dnb_,
                                             int nb, int tid, int nthr) {
+  const FftPass ps = ps_;
+  const FastDiv dnb = dnb_;
   const int m = (int)ps.q.d;
   const int ns = ps.ns;
   const int total = nb * m;
@@ -282,7 +293,7 @@ __device__ __forceinline__ void fft_pass_io(Src&& src, Dst&& dst, const FftPass&
     if (ns > 1) {
       const float2* w = pw + k * (R - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<INV>(w, r - 1));
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], TWS ? twiddle_s<INV>(w, r - 1) : twiddle<INV>(w, r - 1));
     }
     dft_r<R, INV>(v);
     const int base = (j - k) * R + k;
@@ -292,23 +303,23 @@ __device__ __forceinline__ void fft_pass_io(Src&& src, Dst&& dst, const FftPass&
 }
 
 // R16: the plan may hold radix-16 passes (kernels with the registers for them).
-template <bool INV, bool BFAST, bool R16, class Src, class Dst>
+template <bool INV, bool BFAST, bool R16, bool TWS = false, class Src, class Dst>
 __device__ __forceinline__ void fft_pass_io_r(int R, Src&& src, Dst&& dst, const FftPass& ps,
                                               const float2* __restrict__ ptw,
                                               const FastDiv& dnb, int nb, int tid, int nthr) {
   switch (R) {
     case 16:
-      if constexpr (R16) fft_pass_io<16, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr);
+      if constexpr (R16) fft_pass_io<16, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr);
       break;
-    case 8: fft_pass_io<8, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 9: fft_pass_io<9, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 4: fft_pass_io<4, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 2: fft_pass_io<2, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 3: fft_pass_io<3, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 5: fft_pass_io<5, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 7: fft_pass_io<7, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 11: fft_pass_io<11, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
-    case 13: fft_pass_io<13, INV, BFAST>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 8: fft_pass_io<8, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 9: fft_pass_io<9, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 4: fft_pass_io<4, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 2: fft_pass_io<2, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 3: fft_pass_io<3, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 5: fft_pass_io<5, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 7: fft_pass_io<7, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 11: fft_pass_io<11, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
+    case 13: fft_pass_io<13, INV, BFAST, TWS>(src, dst, ps, ptw, dnb, nb, tid, nthr); break;
     default: break;
   }
 }
@@ -334,11 +345,15 @@ __host__ __device__ __forceinline__ int slot_at(int t, int e, int bs, int ks) {
   } else return t * bs + e * ks;
 }
 
-template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, class Src, class Dst>
+// TWS: the passes read their twiddles from tws, the kernel's shared-memory copy of
+// pl.ptw (L - 1 entries), instead of global memory.
+template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, bool TWS = false, class Src,
+          class Dst>
 __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
                                  const FftPasses& pl, const FastDiv& dnb, int nb, int bs,
-                                 int ks) {
+                                 int ks, const float2* tws = nullptr) {
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const float2* ptw = TWS ? tws : pl.ptw;
   auto lds = [&](float2* buf) {
     return [buf, bs, ks](int t, int e) { return buf[slot_at<PAD>(t, e, bs, ks)]; };
   };
@@ -349,12 +364,12 @@ __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a
   for (int st = 0; st <= last; ++st) {
     const FftPass& ps = pl.p[st];
     if (st == last && !last_smem) {
-      if (st == 0) fft_pass_io_r<INV, BFAST, R16>(ps.R, src, dst, ps, pl.ptw, dnb, nb, tid, nthr);
-      else fft_pass_io_r<INV, BFAST, R16>(ps.R, lds(a), dst, ps, pl.ptw, dnb, nb, tid, nthr);
+      if (st == 0) fft_pass_io_r<INV, BFAST, R16, TWS>(ps.R, src, dst, ps, ptw, dnb, nb, tid, nthr);
+      else fft_pass_io_r<INV, BFAST, R16, TWS>(ps.R, lds(a), dst, ps, ptw, dnb, nb, tid, nthr);
     } else if (st == 0) {
-      fft_pass_io_r<INV, BFAST, R16>(ps.R, src, sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
+      fft_pass_io_r<INV, BFAST, R16, TWS>(ps.R, src, sts(b), ps, ptw, dnb, nb, tid, nthr);
     } else {
-      fft_pass_io_r<INV, BFAST, R16>(ps.R, lds(a), sts(b), ps, pl.ptw, dnb, nb, tid, nthr);
+      fft_pass_io_r<INV, BFAST, R16, TWS>(ps.R, lds(a), sts(b), ps, ptw, dnb, nb, tid, nthr);
     }
     __syncthreads();
     if (st < last || last_smem) { float2* t = a; a = b; b = t; }
@@ -369,10 +384,11 @@ __device__ float2* fft_direct_io(Src&& src, Dst&& dst, bool last_smem, float2* a
 // k < n times c_k (conj(c_k) for the inverse).  With last_smem the outputs stay in shared
 // memory WITHOUT that last chirp product (the caller applies it as it reads them) and the
 // buffer holding them is returned.  Ends with a __syncthreads().
-template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, class Src, class Dst>
+template <bool INV, bool BFAST, int PAD = 0, bool R16 = true, bool TWS = false, class Src,
+          class Dst>
 __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2* a, float2* b,
                                     const FftPasses& pl, const FastDiv& dnb, int nb, int bs,
-                                    int ks) {
+                                    int ks, const float2* tws = nullptr) {
   const int n = pl.n;
   const float2* __restrict__ chirp = pl.chirp;
   auto s1 = [&](int t, int j) -> float2 {
@@ -381,8 +397,8 @@ __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2
     const float2 x = src(t, j);
     return INV ? cmulc(x, c) : cmul(x, c);
   };
-  float2* r1 = fft_direct_io<false, BFAST, PAD, R16>(s1, [](int, int, float2) {}, true, a, b, pl, dnb,
-                                                nb, bs, ks);
+  float2* r1 = fft_direct_io<false, BFAST, PAD, R16, TWS>(s1, [](int, int, float2) {}, true, a, b,
+                                                     pl, dnb, nb, bs, ks, tws);
   float2* o = (r1 == a) ? b : a;
   const float2* __restrict__ kern = INV ? pl.kern_inv : pl.kern_fwd;
   auto s2 = [r1, kern, bs, ks](int t, int j) -> float2 {
@@ -395,7 +411,8 @@ __device__ float2* fft_bluestein_io(Src&& src, Dst&& dst, bool last_smem, float2
       dst(t, k, INV ? cmulc(v, c) : cmul(v, c));
     }
   };
-  return fft_direct_io<true, BFAST, PAD, R16>(s2, d2, last_smem, r1, o, pl, dnb, nb, bs, ks);
+  return fft_direct_io<true, BFAST, PAD, R16, TWS>(s2, d2, last_smem, r1, o, pl, dnb, nb, bs, ks,
+                                                  tws);
 }
 
 }  // namespace rift2

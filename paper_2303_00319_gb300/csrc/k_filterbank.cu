@@ -416,8 +416,10 @@ void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaSt
 }
 
 // Column pass of the inverse for the six orientations of scale blockIdx.y.
-// smem: base (F * R_s) [H][tc], a, b [L][tc] each (padded, col_buf).  A tile whose
-// columns all have a zero angular window for an orientation (fg.zc) writes nothing for it.
+// smem: base (F * R_s) [H][tc], a, b [L][tc] each (padded, col_buf), the plan's pass
+// twiddles [L - 1] (read by every butterfly of every pass: from shared memory instead of
+// global memory), fftfreq(v, H) [H].  A tile whose columns all have a zero angular window
+// for an orientation (fg.zc) writes nothing for it.
 __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restrict__ spec,
                                                        float2* __restrict__ scratch,
                                                        const __grid_constant__ Group gr,
@@ -436,8 +438,10 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
   float2* base = sm;
   float2* a = sm + nel;
   float2* b = sm + nel + nl;
-  float* fvt = reinterpret_cast<float*>(sm + nel + 2 * nl);   // fftfreq(v, H) per row
+  float2* tws = sm + nel + 2 * nl;
+  float* fvt = reinterpret_cast<float*>(tws + ph.L);   // fftfreq(v, H) per row
   __shared__ float fut[16];                               // fftfreq(u, W) per column
+  for (int i = threadIdx.x; i < ph.L - 1; i += blockDim.x) tws[i] = __ldg(ph.ptw + i);
   const float2* F = spec + gr.poff[img];
   const float log_fs = kp.log_fs[s];
   const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
@@ -479,11 +483,15 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
       if (c0 + t < W) dst[(size_t)e * W + c0 + t] = v;
     };
     if (tc <= CC_NARROW) {
-      if (!ph.chirp) fft_direct_io<true, true, -CC_PAD>(src, out, false, a, b, ph, dtc, tc, 1, tc);
-      else fft_bluestein_io<true, true, -CC_PAD>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+      if (!ph.chirp)
+        fft_direct_io<true, true, -CC_PAD, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
+      else
+        fft_bluestein_io<true, true, -CC_PAD, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
     } else {
-      if (!ph.chirp) fft_direct_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
-      else fft_bluestein_io<true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc);
+      if (!ph.chirp)
+        fft_direct_io<true, true, 0, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
+      else
+        fft_bluestein_io<true, true, 0, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
     }
     // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
   }
@@ -1329,7 +1337,7 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
 // Shared memory of the generic column pass for a tile of tc columns: F R_s (H rows), the
 // two transform buffers (slot length L each) and the per-row frequencies.
 static size_t cols_inverse_smem(int H, int L, int tc) {
-  return ((size_t)H * tc + 2 * (size_t)col_buf(L * tc)) * sizeof(float2) +
+  return ((size_t)H * tc + 2 * (size_t)col_buf(L * tc) + L) * sizeof(float2) +
          (size_t)H * sizeof(float);
 }
 static int cols_inverse_tile(int H, int L) {
