@@ -416,15 +416,16 @@ void launch_zero_cols(int H, int W, const KParams& kp, unsigned char* zc, cudaSt
 }
 
 // Column pass of the inverse for the six orientations of scale blockIdx.y.
-// smem: base (F * R_s) [H][tc], a, b [L][tc] each (padded, col_buf), the plan's pass
-// twiddles [L - 1] (read by every butterfly of every pass: from shared memory instead of
-// global memory), fftfreq(v, H) [H].  A tile whose columns all have a zero angular window
-// for an orientation (fg.zc) writes nothing for it.
+// smem: base (F * R_s) [H][tc], a, b [L][tc] each (padded, col_buf), with tw_smem the
+// plan's pass twiddles [L - 1] (read by every butterfly of every pass: from shared memory
+// instead of global memory, where the launch's tiles leave room for them), fftfreq(v, H)
+// [H].  A tile whose columns all have a zero angular window for an orientation (fg.zc)
+// writes nothing for it.
 __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restrict__ spec,
                                                        float2* __restrict__ scratch,
                                                        const __grid_constant__ Group gr,
                                                        const __grid_constant__ FftGroup fg,
-                                                       KParams kp) {
+                                                       KParams kp, int tw_smem) {
   extern __shared__ float2 sm[];
   const int s = blockIdx.y;
   const int img = blockIdx.z;
@@ -439,9 +440,11 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
   float2* a = sm + nel;
   float2* b = sm + nel + nl;
   float2* tws = sm + nel + 2 * nl;
-  float* fvt = reinterpret_cast<float*>(tws + ph.L);   // fftfreq(v, H) per row
+  float* fvt = reinterpret_cast<float*>(tws + (tw_smem ? ph.L : 0));   // fftfreq(v, H) per row
   __shared__ float fut[16];                               // fftfreq(u, W) per column
-  for (int i = threadIdx.x; i < ph.L - 1; i += blockDim.x) tws[i] = __ldg(ph.ptw + i);
+  if (tw_smem)
+    for (int i = threadIdx.x; i < ph.L - 1; i += blockDim.x) tws[i] = __ldg(ph.ptw + i);
+  const float2* twp = tw_smem ? tws : ph.ptw;
   const float2* F = spec + gr.poff[img];
   const float log_fs = kp.log_fs[s];
   const float inv_hw = 1.f / ((float)H * (float)W);   // the inverse DFT's normalisation
@@ -484,14 +487,14 @@ __global__ void __launch_bounds__(512, 1) lg_cols_inverse(const float2* __restri
     };
     if (tc <= CC_NARROW) {
       if (!ph.chirp)
-        fft_direct_io<true, true, -CC_PAD, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
+        fft_direct_io<true, true, -CC_PAD, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, twp);
       else
-        fft_bluestein_io<true, true, -CC_PAD, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
+        fft_bluestein_io<true, true, -CC_PAD, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, twp);
     } else {
       if (!ph.chirp)
-        fft_direct_io<true, true, 0, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
+        fft_direct_io<true, true, 0, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, twp);
       else
-        fft_bluestein_io<true, true, 0, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, tws);
+        fft_bluestein_io<true, true, 0, true, true>(src, out, false, a, b, ph, dtc, tc, 1, tc, twp);
     }
     // the next orientation overwrites a/b only after everyone has stored (loop-top sync)
   }
@@ -1336,13 +1339,19 @@ cudaError_t launch_fft2_forward(const ImgPtrs* ip, const float* dense, float2* s
 
 // Shared memory of the generic column pass for a tile of tc columns: F R_s (H rows), the
 // two transform buffers (slot length L each) and the per-row frequencies.
-static size_t cols_inverse_smem(int H, int L, int tc) {
-  return ((size_t)H * tc + 2 * (size_t)col_buf(L * tc) + L) * sizeof(float2) +
+// Shared memory of a column tile, with (tw) or without the twiddle copy.
+static constexpr size_t kColSmemMax = 227 * 1024;
+static size_t cols_inverse_smem(int H, int L, int tc, bool tw) {
+  return ((size_t)H * tc + 2 * (size_t)col_buf(L * tc) + (tw ? L : 0)) * sizeof(float2) +
          (size_t)H * sizeof(float);
 }
+// The twiddle copy is made where a one-column tile leaves room for it (all but the
+// tallest Bluestein heights, whose convolution slots fill the shared memory).
+static bool cols_inverse_tw(int H, int L) { return cols_inverse_smem(H, L, 1, true) <= kColSmemMax; }
 static int cols_inverse_tile(int H, int L) {
+  const bool tw = cols_inverse_tw(H, L);
   int tc = cols_tile(L);
-  while (tc > 1 && cols_inverse_smem(H, L, tc) > 227 * 1024) tc /= 2;
+  while (tc > 1 && cols_inverse_smem(H, L, tc, tw) > kColSmemMax) tc /= 2;
   return tc;
 }
 
@@ -1365,6 +1374,10 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, const Group& gr,
   FftGroup sf{};
   int grid_x = 0;
   size_t smx = 0;
+  bool tw_all = true;
+  struct TileDims { int H, L, tc; };
+  TileDims tiles[MAXB];
+  int ntiles = 0;
   cudaError_t err = cudaSuccess;
   for_runs(gr, [&](int i0, int cnt) {
     const int H = gr.H[i0], W = gr.W[i0];
@@ -1393,12 +1406,18 @@ cudaError_t launch_lg_cols(const float2* spec, float2* scratch, const Group& gr,
     if (tuned >= 1 && tuned <= tc) tc = tuned;   // a tuned (smaller) tile; same result
     for (int k = 0; k < cnt; ++k) sub_add(sub, sf, gr, i0 + k, ph, tc, fi[i0].zc);
     grid_x = max_of(grid_x, (W + tc - 1) / tc);
-    smx = max_of(smx, cols_inverse_smem(H, ph.m, tc));
+    tw_all = tw_all && cols_inverse_tw(H, ph.m);
+    tiles[ntiles++] = {H, ph.m, tc};
   });
   if (err != cudaSuccess) return err;
   if (sub.n) {
+    // one launch: the twiddle copy only when every image's tile has room for it (each
+    // tile was sized with the copy where its height allows; without it every tile fits)
+    for (int i = 0; i < ntiles; ++i)
+      smx = max_of(smx, cols_inverse_smem(tiles[i].H, tiles[i].L, tiles[i].tc, tw_all));
     cudaFuncSetAttribute(lg_cols_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
-    lg_cols_inverse<<<dim3(grid_x, NS, sub.n), 512, smx, st>>>(spec, scratch, sub, sf, kp);
+    lg_cols_inverse<<<dim3(grid_x, NS, sub.n), 512, smx, st>>>(spec, scratch, sub, sf, kp,
+                                                                tw_all ? 1 : 0);
     ++nl;
   }
   if (launches) *launches = nl;
