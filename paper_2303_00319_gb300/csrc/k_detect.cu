@@ -381,27 +381,54 @@ __global__ void __launch_bounds__(1024) topk_sort(const __grid_constant__ Group 
       __syncthreads();
       // warp-aggregated: most keys share the leading digits, so lanes with equal digits
       // add their count with one atomic
+      // while the prefix lies in the keys' upper words (the score bits), the digits and
+      // the prefix test use 32-bit shifts of that word
+      const bool hi32 = pbits < 32;
+      const unsigned prefix32 = (unsigned)prefix;
       for (unsigned b0 = threadIdx.x & ~31u; b0 < n; b0 += blockDim.x) {
         const unsigned i = b0 + lane;
         unsigned dig = 256u;   // not counted
         if (i < n) {
           const unsigned long long k = cand[i];
-          if (pbits == 0 || (k >> (64 - pbits)) == prefix) dig = (unsigned)(k >> (56 - pbits)) & 0xFFu;
+          if (hi32) {
+            const unsigned h = (unsigned)(k >> 32);
+            if (pbits == 0 || (h >> (32 - pbits)) == prefix32) dig = (h >> (24 - pbits)) & 0xFFu;
+          } else if ((k >> (64 - pbits)) == prefix) {
+            dig = (unsigned)(k >> (56 - pbits)) & 0xFFu;
+          }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, dig);
         if (dig < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], (unsigned)__popc(peers));
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        unsigned cum = 0;
-        int d = 0;
-        for (; d < 255; ++d) {
-          if (rank < cum + hist[d]) break;
-          cum += hist[d];
+      // the digit holding rank: the first bin whose inclusive count exceeds it (bin 255 if
+      // none), found by warp 0 with eight bins per lane and a shuffle scan
+      if (threadIdx.x < 32) {
+        unsigned c[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { c[j] = hist[lane * 8 + j]; sum += c[j]; }
+        unsigned incl = sum;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const unsigned a = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (lane >= (unsigned)dd) incl += a;
         }
-        s_sel[0] = d;
-        s_sel[1] = cum;
-        s_sel[2] = hist[d];
+        const unsigned over = __ballot_sync(0xffffffffu, rank < incl);
+        const unsigned owner = over ? (unsigned)(__ffs(over) - 1) : 31u;
+        if (lane == owner) {
+          unsigned cum = incl - sum;
+          int j = 0;
+#pragma unroll
+          for (int u = 0; u < 7; ++u) {
+            if (j == u && rank >= cum + c[u]) { cum += c[u]; j = u + 1; }
+          }
+          unsigned hd = c[0];
+#pragma unroll
+          for (int u = 1; u < 8; ++u) hd = (j == u) ? c[u] : hd;
+          s_sel[0] = lane * 8 + j;
+          s_sel[1] = cum;
+          s_sel[2] = hd;
+        }
       }
       __syncthreads();
       unsigned d = s_sel[0], cum = s_sel[1], hd = s_sel[2];
